@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark: element Gram matrices per second on one GB300 (and N GPUs, weak scaling).
+
+Workload ("seq_q5_8x8x8"): the full exact sequence in FP64 -- H1, H(curl), H(div) and L2
+Gram matrices of 512 jittered trilinear hexahedra of an 8^3 unit-cube mesh (O(p^7)
+sum-factorization path) and of the same 512 elements as sheared parallelepipeds (O(p^6)
+affine path), test order q = 5, Gauss 7^3 points, per-element coefficient k_e in
+[0.5, 2].  One step = the 8 calls (4 spaces x 2 maps) = 4096 element matrices, 4.56 GB
+written.  Inputs are resident in HBM when a step starts; L2 is flushed (a 512 MiB
+write) before every step, outside the timed events.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (conventional
+quadrature, the paper's Algorithms 1/4/6/8) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SPACES = ["H1", "HCURL", "HDIV", "L2"]
+WORKLOAD = "seq_q5_8x8x8"
+Q, L = 5, 7
+METRIC = "element Gram matrices/s (H1+H(curl)+H(div)+L2, q=5, trilinear O(p^7) + affine O(p^6), FP64)"
+UNIT = "element matrices/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default=None, help="profiling case: run only this space's call (H1, HCURL, HDIV, L2)")
+    ap.add_argument("--map", default="general", choices=["general", "affine"], help="map of the --only case")
+    ap.add_argument("--elems", type=int, default=0, help="elements of the --only case (default: all 512)")
+    ap.add_argument("--fp32", action="store_true", help="FP32 form for the --only case")
+    return ap.parse_args()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def workload_config():
+    return {"workload": WORKLOAD + ": H1/H(curl)/H(div)/L2 Gram, q=5, L=7, 512 jittered trilinear "
+                                   "+ 512 affine hexahedra per GPU, k_e~U[0.5,2]",
+            "elements_per_step": 4096, "q": Q, "L": L,
+            "l2": "flushed before every step (512 MiB write, outside the timed events)"}
+
+
+# ---------------------------------------------------------------------------- oracle arm
+
+def oracle_sample(n_per_call: int, offset: int = 0):
+    """Time the oracle on n_per_call elements of every (space, map) of the workload."""
+    import numpy as np
+    import oracle
+    from paper_1711_00984_gb300 import meshgen
+    w = meshgen.workload(WORKLOAD)
+    ne = w["verts"].shape[0]
+    idx = (np.arange(n_per_call) * 37 + offset) % ne
+    t0 = time.perf_counter()
+    count = 0
+    for verts in (w["verts"], w["verts_affine"]):
+        for s in SPACES:
+            c = meshgen.coeff_pairs(s, w["k"], ne)
+            oracle.gram(s, Q, L, verts[idx], c[idx], nthreads=host_cores())
+            count += len(idx)
+    return count, time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = host_cores()
+    n = max(1, cores)                           # one element per core per (space, map) call
+    for i in range(args.warmup):
+        oracle_sample(n, offset=i)
+    tot_count, tot_t = 0, 0.0
+    for i in range(args.steps):
+        c, t = oracle_sample(n, offset=args.warmup + i)
+        tot_count += c
+        tot_t += t
+    v = tot_count / tot_t
+    sample = f"{n} elements x 8 (space, map) calls per step, seeded spread of the 512-element workload"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded meshgen)", "config": workload_config(),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.index = index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        import statistics
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1711_00984_gb300 as dpg
+    from paper_1711_00984_gb300 import build as dbuild
+    from paper_1711_00984_gb300 import meshgen
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        dbuild.build()
+    if world > 1:
+        dist.barrier()
+    dpg.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+
+    w = meshgen.workload(WORKLOAD)
+    ne = w["verts"].shape[0]
+    for s in SPACES:
+        dpg.dpg_tables_init_L(Q, L, s)
+    maps = [("general", torch.from_numpy(w["verts"]).to(dev), False),
+            ("affine", torch.from_numpy(w["verts_affine"]).to(dev), True)]
+    coeffs = {s: torch.from_numpy(meshgen.coeff_pairs(s, w["k"], ne)).to(dev) for s in SPACES}
+    outs = {(m, s): torch.empty((ne,) + dpg.matrix_shape(s, Q), dtype=torch.float64, device=dev)
+            for m, _, _ in maps for s in SPACES}
+    out_bytes = sum(o.numel() * 8 for o in outs.values())
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def call(mname, v, aff, s):
+        code = dpg.dpg_integrate(dpg.space_id(s, affine=aff), 0, Q, ne, v.data_ptr(), coeffs[s].data_ptr(),
+                                 outs[(mname, s)].data_ptr(), sh)
+        if code:
+            raise dpg.DpgError(code, "dpg_integrate")
+
+    dom_ev = []
+
+    def step(record_dom=False):
+        for mname, v, aff in maps:
+            for s in SPACES:
+                if record_dom and mname == "general" and s == "HCURL":
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    call(mname, v, aff, s)
+                    b.record(stream)
+                    dom_ev.append((a, b))
+                else:
+                    call(mname, v, aff, s)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    code, bad = dpg.dpg_sync_status(sh)
+    if code:
+        raise RuntimeError(f"device status {dpg.STATUS.get(code)} at element {bad}")
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            ev[i][0].record(stream)
+            step(record_dom=True)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    dom_ms = float(np.mean([a.elapsed_time(b) for a, b in dom_ev]))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    code, bad = dpg.dpg_sync_status(sh)
+    if code:
+        raise RuntimeError(f"device status {dpg.STATUS.get(code)} at element {bad}")
+
+    elems_per_step = ne * len(SPACES) * len(maps)
+    ms_per_step = total_ms / args.steps
+    value = world * elems_per_step / (ms_per_step * 1e-3)
+
+    # ---- e2e through the host-buffer entry point (H2D + integrate + D2H per call)
+    e2e = None
+    if not args.no_e2e:
+        hv = {m: v.cpu().pin_memory() for m, v, _ in maps}
+        hc = {s: c.cpu().pin_memory() for s, c in coeffs.items()}
+        ho = {k: torch.empty(o.shape, dtype=o.dtype).pin_memory() for k, o in outs.items()}
+
+        def hstep():
+            for mname, _, aff in maps:
+                for s in SPACES:
+                    code = dpg.dpg_integrate_host(dpg.space_id(s, affine=aff), 0, Q, ne, hv[mname].data_ptr(),
+                                                  hc[s].data_ptr(), ho[(mname, s)].data_ptr(), sh)
+                    if code:
+                        raise dpg.DpgError(code, "dpg_integrate_host")
+        hstep()
+        ke = max(1, min(args.steps, 3))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            hstep()
+        te = (time.perf_counter() - t0) / ke
+        if world > 1:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        in_bytes = sum(v.numel() * 8 for v in hv.values()) * len(SPACES) + sum(c.numel() * 8 for c in hc.values()) * 2
+        e2e = {"value": world * elems_per_step / te, "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
+               "d2h_bytes_per_step": int(out_bytes), "ms_per_step": 1e3 * te}
+
+    # ---- roofline of the dominant kernel (H(curl) general: geometry + contraction launch pair)
+    fpe = dpg.dpg_flops_per_element(dpg.space_id("HCURL"), 0, Q)
+    peak64 = dpg.dpg_measure_fma_peak(64, sh)
+    achieved = fpe * ne / (dom_ms * 1e-3)
+    roof = {"bound": "alu", "kernel": "sf_general_kernel<double> (H(curl), with its geom_kernel launch)",
+            "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak64, "traffic": None,
+            "peak_source": "FP64 FMA rate measured in this run by dpg_measure_fma_peak (MEASURED_PEAKS has no FP64 entry)",
+            "flops_per_launch": fpe * ne, "launch_ms": dom_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n = 4 * max(2, host_cores())             # about 10-30 s of oracle work
+        cnt, t = oracle_sample(n)
+        cpu = {"value": cnt / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": f"{n} elements per (space, map) call x 8 calls = {cnt} element matrices, FP64"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded meshgen: jittered 8^3 mesh + sheared parallelepipeds)",
+                "config": workload_config(), "output_gbs": world * out_bytes / (ms_per_step * 1e-3) / 1e9,
+                "gpu_launches": 12 * args.steps, "clocks": clk.summary(), "roofline": roof,
+                "cpu_baseline": cpu, "e2e": e2e,
+                "per_step_ms": {"min": min(step_ms), "max": max(step_ms)}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_case(args):
+    """One (space, map, form) call of the workload on a subset of elements, for profilers."""
+    import torch
+    import paper_1711_00984_gb300 as dpg
+    from paper_1711_00984_gb300 import build as dbuild
+    from paper_1711_00984_gb300 import meshgen
+    dbuild.build()
+    dpg.load()
+    torch.cuda.set_device(0)
+    w = meshgen.workload(WORKLOAD)
+    ne = args.elems or w["verts"].shape[0]
+    aff = args.map == "affine"
+    s = args.only
+    dpg.dpg_tables_init_L(Q, L, s)
+    v = torch.from_numpy(w["verts_affine" if aff else "verts"][:ne]).cuda()
+    c = torch.from_numpy(meshgen.coeff_pairs(s, w["k"], w["verts"].shape[0])[:ne]).cuda()
+    out = torch.empty((ne,) + dpg.matrix_shape(s, Q), dtype=torch.float32 if args.fp32 else torch.float64, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        dpg.integrate(s, Q, v, c, affine=aff, fp32=args.fp32, out=out)
+    code, bad = dpg.sync_status()
+    assert code == 0, (code, bad)
+    print(json.dumps({"profile_case": {"space": s, "map": args.map, "elems": ne, "fp32": args.fp32,
+                                       "calls": args.warmup + args.steps}}))
+
+
+def main():
+    args = parse()
+    if args.only:
+        run_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

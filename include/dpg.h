@@ -1,0 +1,160 @@
+/*
+ * dpg.h -- C ABI of the GB300 element-matrix library for
+ * Mora & Demkowicz, "Fast integration of DPG matrices based on tensorization"
+ * (arXiv 1711.00984).
+ *
+ * The library integrates, for a batch of hexahedral elements, the element Gram matrices
+ * of the 3D exact sequence H1 -> H(curl) -> H(div) -> L2 (Eq. 2.1) with integrated
+ * Legendre / Legendre tensor-product shape functions (Eqs. 2.33, 2.51-2.57, 2.69-2.74,
+ * Sec. 2.8.2), by sum factorization (Eqs. 2.20-2.25 and their H1 / H(div) / H(curl)
+ * forms, Eqs. 2.38-2.44, 2.61-2.63, 2.78-2.84), and one mixed stiffness matrix B
+ * (pattern of Eqs. 3.15-3.16).  Elements with a constant Jacobian use the O(p^6)
+ * variant of Sec. 2.8.1 (Algorithm 10, generalised to a full constant Jacobian).
+ *
+ * Conventions shared by every entry point:
+ *   - Element map: trilinear from 8 vertices; vertex v = v1 + 2 v2 + 4 v3 is the image of
+ *     the master-cube corner (v1, v2, v3), master cube (0,1)^3 (Sec. 2.2).
+ *   - Quadrature: L-point Gauss-Legendre rule on (0,1) per direction (Eq. 2.23).
+ *   - Degrees of freedom: the index maps of the paper, i1 fastest (H1: after Eq. 2.33;
+ *     L2: after Eq. 2.17; H(div): Eq. 2.53; H(curl): Eq. 2.71).
+ *   - Output: one dense matrix per element, row-major, both triangles, element-major.
+ *   - Memory: every pointer argument is DEVICE memory owned by the caller, except in
+ *     dpg_integrate_host.  The library owns only its tables and a small status word per
+ *     device; they live until dpg_tables_free or process exit.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *     work is stream-ordered; no entry point synchronises the host except
+ *     dpg_sync_status and dpg_integrate_host.
+ *   - Errors: every entry point returns a dpg_status.  Argument and set-up errors are
+ *     detected on the host before anything is launched.  Errors found on the device
+ *     (a non-positive Jacobian determinant, a non-affine element on the affine path) are
+ *     recorded in the device status word: the offending element's matrix is filled with
+ *     NaN, the call still returns DPG_OK, and dpg_sync_status reports the error and the
+ *     first offending element.  Nothing traps the device.
+ *   - Threading: table set-up (dpg_tables_init*, dpg_tables_free) must not race with
+ *     itself or with integration calls; integration calls on different streams may run
+ *     concurrently.
+ */
+#ifndef DPG_H
+#define DPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- spaces (low byte of `space`) ---- */
+#define DPG_H1             1   /* (u,v) + (grad u, grad v), Eq. 2.28 / 2.31              */
+#define DPG_HCURL          2   /* (E,F) + (curl E, curl F), Eq. 2.65 / 2.68              */
+#define DPG_HDIV           3   /* (V,W) + (div V, div W),   Eq. 2.46 / 2.49              */
+#define DPG_L2             4   /* (p,q),                    Eq. 2.14 / 2.16              */
+#define DPG_B_L2VEC_HCURL  5   /* B_IK = (u_K, psi_I) + (u_K, curl psi_I), vector-L2
+                                  trial u of order p, H(curl) test psi of order q
+                                  (real, unit-coefficient analogue of Eqs. 3.15-3.16)   */
+/* ---- flags ORed into `space` ---- */
+#define DPG_FP32        0x100  /* FP32 contraction stages and FP32 output; geometry FP64 */
+#define DPG_MAP_AFFINE  0x200  /* elements are parallelepipeds: O(p^6) path, Sec. 2.8.1 */
+#define DPG_B_SPLIT     0x400  /* B only: write [2][rows][cols] = (mass part, curl part) */
+
+/* ---- status codes ---- */
+typedef enum {
+    DPG_OK = 0,
+    DPG_ERR_ARG = 1,         /* bad argument (NULL pointer, bad space/flags, p > q ...) */
+    DPG_ERR_NOT_INIT = 2,    /* no tables for (space, q): call dpg_tables_init first    */
+    DPG_ERR_RANGE = 3,       /* q or L outside the supported range                      */
+    DPG_ERR_CUDA = 4,        /* a CUDA runtime call failed                              */
+    DPG_ERR_DEGENERATE = 5,  /* device: |J| <= 0 or not finite at a quadrature point    */
+    DPG_ERR_NOT_AFFINE = 6,  /* device: element is not a parallelepiped (affine path)   */
+    DPG_ERR_NOMEM = 7        /* device or host allocation failed                        */
+} dpg_status;
+
+#define DPG_MAX_Q 12           /* supported test orders: 1 <= q <= DPG_MAX_Q           */
+#define DPG_MAX_L 14           /* supported points per direction: 1 <= L <= DPG_MAX_L  */
+
+/* Build and upload the tables for test order q of `space` (flags ignored) with the
+ * default rule L = q + 2: Gauss nodes and weights on (0,1) (Eq. 2.23), the 1D families
+ * chi_i = L_i, chi'_i, nu_i = P_i at the nodes (Eqs. 2.91-2.101, 2.54), products of pairs
+ * of them (the 1D factors of Eqs. 2.23-2.25), the exact 1D integrals F^{rs} (Eq. 2.90),
+ * and the term programs of each space.  Synchronous (host work and cudaMemcpy); call it
+ * before capturing integration calls in a CUDA graph.  Re-initialising (space, q) with a
+ * different L makes that L the active rule for (space, q).
+ * Errors: DPG_ERR_ARG (unknown space), DPG_ERR_RANGE (q), DPG_ERR_CUDA, DPG_ERR_NOMEM. */
+int dpg_tables_init(int q, int space);
+
+/* Same with an explicit number of Gauss points L per direction (1 <= L <= DPG_MAX_L). */
+int dpg_tables_init_L(int q, int L, int space);
+
+/* Release every table and program on every device.  Not stream-ordered: the caller must
+ * make sure no integration call is in flight. */
+int dpg_tables_free(void);
+
+/* Number of rows of the element matrix: dim of the test space at order q
+ * ((q+1)^3, 3q(q+1)^2, 3(q+1)q^2, q^3 for H1, H(curl), H(div), L2; H(curl) for B).
+ * Returns -1 for a bad space or q. */
+int64_t dpg_matrix_rows(int space, int q);
+
+/* Number of columns: equal to rows for Gram matrices; 3 p^3 for DPG_B_L2VEC_HCURL.
+ * Returns -1 for bad arguments. */
+int64_t dpg_matrix_cols(int space, int p_trial, int q);
+
+/* Integrate the element matrices of n_elem elements (the paper's per-element routine
+ * PROC(mid, G) of Algorithms 2-11, batched; problem statement Eq. 2.13).
+ *   space    : DPG_H1 .. DPG_B_L2VEC_HCURL, ORed with DPG_FP32 / DPG_MAP_AFFINE /
+ *              DPG_B_SPLIT (B only).
+ *   p_trial  : trial order for DPG_B_L2VEC_HCURL (1 <= p_trial <= q_test); ignored
+ *              (pass 0) for Gram matrices.
+ *   q_test   : test order; tables for (space, q_test) must be initialised.
+ *   n_elem   : number of elements (0 is allowed and does nothing).
+ *   vertices : device, double[n_elem][8][3].
+ *   coeffs   : device, double[n_elem][2] = (mass weight c0, derivative weight c1), or
+ *              NULL for (1, 1).  G = c0 (mass term) + c1 (derivative term); L2 uses c0.
+ *              Ignored for B.
+ *   out      : device, double (FP64 form) or float (DPG_FP32) array of
+ *              n_elem * parts * rows * cols values, parts = 2 with DPG_B_SPLIT else 1.
+ *   stream   : cudaStream_t.
+ * The call allocates a stream-ordered workspace for the per-point metric fields from a
+ * library memory pool and frees it in stream order.
+ * Errors: DPG_ERR_ARG, DPG_ERR_NOT_INIT, DPG_ERR_RANGE, DPG_ERR_CUDA, DPG_ERR_NOMEM;
+ * device-detected errors through dpg_sync_status. */
+int dpg_integrate(int space, int p_trial, int q_test, int64_t n_elem,
+                  const double *vertices, const double *coeffs, void *out, void *stream);
+
+/* Same as dpg_integrate, but vertices, coeffs and out are HOST buffers (page-locked for
+ * full copy speed).  Copies the inputs to the device, integrates, copies the result
+ * back, and synchronises `stream` before returning; device buffers are taken from the
+ * library memory pool.  Device-detected errors are returned directly (the call reads
+ * the status word). */
+int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem,
+                       const double *vertices, const double *coeffs, void *out, void *stream);
+
+/* Synchronise `stream`, read and clear the device status word of the current device.
+ * Returns DPG_OK or the first device-detected error; *first_bad_elem (if not NULL)
+ * receives the smallest offending element index of that error, or -1. */
+int dpg_sync_status(void *stream, int64_t *first_bad_elem);
+
+/* Static English description of a status code. */
+const char *dpg_strerror(int code);
+
+/* Diagnostic text of the last CUDA runtime failure seen by the library (the failing call
+ * and the CUDA error name), or "" if none.  Not thread-safe; for error messages only. */
+const char *dpg_last_cuda_error(void);
+
+/* Algorithmic floating-point operations of one element (multiply and add counted
+ * separately) of the sum-factorization path (stages of Eqs. 2.23-2.25 per block of
+ * terms, symmetric tiles counted once), or of the affine path (non-zero products of the
+ * Kronecker sums of Sec. 2.8.1) with DPG_MAP_AFFINE.  Tables must be initialised.
+ * Returns -1 on error.  Used to report the ALU roofline. */
+double dpg_flops_per_element(int space, int p_trial, int q_test);
+
+/* Not part of the paper's method: measure the device's peak fused multiply-add rate in
+ * FP64 (precision = 64) or FP32 (precision = 32) with a register-resident FMA loop on
+ * `stream`; writes the flop rate (2 flops per FMA) in flop/s to *flops.  Synchronous.
+ * Used only to give the ALU roofline a measured denominator. */
+int dpg_measure_fma_peak(int precision, void *stream, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPG_H */

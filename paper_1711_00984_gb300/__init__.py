@@ -1,0 +1,193 @@
+"""GB300 element-matrix library for arXiv 1711.00984 (sum-factorized DPG Gram matrices).
+
+A thin ctypes binding of the C ABI in ``include/dpg.h``: the functions below carry the
+same names and only marshal arguments (tensor pointers, the current CUDA stream).  Every
+step of the integration runs in the CUDA kernels of ``csrc/``; there is no CPU path, and
+calling anything without the built library raises.
+
+Submodules: ``meshgen`` (seeded synthetic meshes, no method arithmetic), ``build``
+(nvcc build of ``_build/libdpg.so``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdpg.so")
+
+# spaces and flags (include/dpg.h)
+DPG_H1, DPG_HCURL, DPG_HDIV, DPG_L2, DPG_B_L2VEC_HCURL = 1, 2, 3, 4, 5
+DPG_FP32, DPG_MAP_AFFINE, DPG_B_SPLIT = 0x100, 0x200, 0x400
+SPACE_IDS = {"H1": DPG_H1, "HCURL": DPG_HCURL, "HDIV": DPG_HDIV, "L2": DPG_L2, "B": DPG_B_L2VEC_HCURL}
+STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANGE", 4: "DPG_ERR_CUDA",
+          5: "DPG_ERR_DEGENERATE", 6: "DPG_ERR_NOT_AFFINE", 7: "DPG_ERR_NOMEM"}
+
+EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
+           "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_host", "dpg_sync_status",
+           "dpg_strerror", "dpg_last_cuda_error", "dpg_flops_per_element", "dpg_measure_fma_peak"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+class DpgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        detail = dpg_strerror(code) if _lib else ""
+        if code in (4, 7) and _lib:
+            detail += "; " + dpg_last_cuda_error()
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({detail})")
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libdpg.so (built by ``build.py``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} (run paper_1711_00984_gb300.build)")
+        lib = ctypes.CDLL(p)
+        i64, vp, dp = ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        lib.dpg_tables_init.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.dpg_tables_init_L.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.dpg_tables_free.argtypes = []
+        lib.dpg_matrix_rows.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.dpg_matrix_rows.restype = i64
+        lib.dpg_matrix_cols.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.dpg_matrix_cols.restype = i64
+        lib.dpg_integrate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
+        lib.dpg_integrate_host.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
+        lib.dpg_sync_status.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.dpg_strerror.argtypes = [ctypes.c_int]
+        lib.dpg_strerror.restype = ctypes.c_char_p
+        lib.dpg_last_cuda_error.argtypes = []
+        lib.dpg_last_cuda_error.restype = ctypes.c_char_p
+        lib.dpg_flops_per_element.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.dpg_flops_per_element.restype = ctypes.c_double
+        lib.dpg_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp]
+        for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate",
+                     "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak"]:
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _L():
+    return _lib if _lib is not None else load()
+
+
+def _check(code: int, where: str) -> int:
+    if code != 0:
+        raise DpgError(code, where)
+    return code
+
+
+def space_id(space, fp32: bool = False, affine: bool = False, split: bool = False) -> int:
+    s = SPACE_IDS[space] if isinstance(space, str) else int(space)
+    return s | (DPG_FP32 if fp32 else 0) | (DPG_MAP_AFFINE if affine else 0) | (DPG_B_SPLIT if split else 0)
+
+
+# ---- the C ABI, name for name ---------------------------------------------------------
+
+def dpg_tables_init(q: int, space) -> int:
+    return _check(_L().dpg_tables_init(q, space_id(space)), "dpg_tables_init")
+
+
+def dpg_tables_init_L(q: int, L: int, space) -> int:
+    return _check(_L().dpg_tables_init_L(q, L, space_id(space)), "dpg_tables_init_L")
+
+
+def dpg_tables_free() -> int:
+    return _check(_L().dpg_tables_free(), "dpg_tables_free")
+
+
+def dpg_matrix_rows(space, q: int) -> int:
+    return int(_L().dpg_matrix_rows(space_id(space), q))
+
+
+def dpg_matrix_cols(space, p_trial: int, q: int) -> int:
+    return int(_L().dpg_matrix_cols(space_id(space), p_trial, q))
+
+
+def dpg_integrate(space: int, p_trial: int, q_test: int, n_elem: int, vertices: int, coeffs: int,
+                  out: int, stream: int) -> int:
+    """Raw call with integer device pointers and a raw cudaStream_t handle."""
+    return _L().dpg_integrate(space, p_trial, q_test, n_elem, vertices or None, coeffs or None, out, stream or None)
+
+
+def dpg_integrate_host(space: int, p_trial: int, q_test: int, n_elem: int, vertices: int, coeffs: int,
+                       out: int, stream: int) -> int:
+    return _L().dpg_integrate_host(space, p_trial, q_test, n_elem, vertices or None, coeffs or None, out, stream or None)
+
+
+def dpg_sync_status(stream: int = 0) -> tuple[int, int]:
+    bad = ctypes.c_int64(-1)
+    code = _L().dpg_sync_status(stream or None, ctypes.byref(bad))
+    return int(code), int(bad.value)
+
+
+def dpg_strerror(code: int) -> str:
+    return _L().dpg_strerror(code).decode()
+
+
+def dpg_last_cuda_error() -> str:
+    return _L().dpg_last_cuda_error().decode()
+
+
+def dpg_flops_per_element(space, p_trial: int, q_test: int) -> float:
+    return float(_L().dpg_flops_per_element(space if isinstance(space, int) else space_id(space), p_trial, q_test))
+
+
+def dpg_measure_fma_peak(precision: int, stream: int = 0) -> float:
+    out = ctypes.c_double(0.0)
+    _check(_L().dpg_measure_fma_peak(precision, stream or None, ctypes.byref(out)), "dpg_measure_fma_peak")
+    return out.value
+
+
+# ---- torch marshalling -----------------------------------------------------------------
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def matrix_shape(space, q: int, p: int = 0, split: bool = False) -> tuple[int, ...]:
+    r = dpg_matrix_rows(space, q)
+    c = dpg_matrix_cols(space, p, q)
+    return (2, r, c) if split else (r, c)
+
+
+def integrate(space, q: int, verts, coeffs=None, *, p: int = 0, fp32: bool = False, affine: bool = False,
+              split: bool = False, out=None, stream=None):
+    """Integrate element matrices of device tensors ``verts[n, 8, 3]`` (float64, CUDA).
+
+    Returns ``out[n, rows, cols]`` (``[n, 2, rows, cols]`` with ``split``) in float64, or
+    float32 with ``fp32``.  Tables for (space, q) must have been initialised.
+    """
+    import torch
+    if not verts.is_cuda or verts.dtype != torch.float64 or not verts.is_contiguous():
+        raise ValueError("verts must be a contiguous float64 CUDA tensor [n, 8, 3]")
+    n = verts.shape[0]
+    if coeffs is not None and (not coeffs.is_cuda or coeffs.dtype != torch.float64 or not coeffs.is_contiguous()):
+        raise ValueError("coeffs must be a contiguous float64 CUDA tensor [n, 2]")
+    shape = (n,) + matrix_shape(space, q, p, split)
+    dt = torch.float32 if fp32 else torch.float64
+    if out is None:
+        out = torch.empty(shape, dtype=dt, device=verts.device)
+    elif out.dtype != dt or tuple(out.shape) != shape or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous {dt} tensor of shape {shape}")
+    sid = space_id(space, fp32, affine, split)
+    code = dpg_integrate(sid, p, q, n, verts.data_ptr(), coeffs.data_ptr() if coeffs is not None else 0,
+                         out.data_ptr(), _stream_handle(stream))
+    _check(code, "dpg_integrate")
+    return out
+
+
+def sync_status(stream=None) -> tuple[int, int]:
+    """(status code, first offending element or -1) after synchronising the stream."""
+    return dpg_sync_status(_stream_handle(stream))

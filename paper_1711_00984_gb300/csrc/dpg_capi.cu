@@ -1,0 +1,448 @@
+// dpg_capi.cu -- the C ABI (include/dpg.h): argument checks, table registry, workspace,
+// launches.  No per-element host work.
+#include "../../include/dpg.h"
+
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "dpg_kernels.h"
+#include "dpg_setup.h"
+
+using namespace dpg;
+
+namespace {
+
+constexpr size_t kWorkspaceLimit = size_t(512) << 20;   // metric fields per launch chunk
+int g_max_dyn_smem = 0;                                  // per launch, set at device set-up
+
+struct TableEntry {
+    HostTables host;
+    double *zeta = nullptr, *w = nullptr, *pp64 = nullptr, *F64 = nullptr;
+    float *pp32 = nullptr, *F32 = nullptr;
+};
+
+struct ProgEntry {
+    Program prog;
+    BlockDesc *d_blocks = nullptr;
+    Unit *d_units = nullptr;
+    size_t smem_aff = 0;            // values of the affine kernel's shared memory
+};
+
+using ProgKey = std::tuple<int, int, int, int, int>;   // space, q, L, p, split
+
+struct DeviceState {
+    DevStatus *status = nullptr;
+    cudaMemPool_t pool = nullptr;
+    std::map<std::pair<int, int>, std::unique_ptr<TableEntry>> tables;   // (q, L)
+    std::map<ProgKey, std::unique_ptr<ProgEntry>> progs;
+    std::map<std::pair<int, int>, int> active_L;                         // (space, q) -> L
+};
+
+std::mutex g_mu;
+std::map<int, std::unique_ptr<DeviceState>> g_dev;
+
+char g_last_error[512] = "";
+
+int cuda_fail(cudaError_t e, const char *what, int line) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s (line %d): %s: %s", what, line,
+                  cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? DPG_ERR_NOMEM : DPG_ERR_CUDA;
+}
+
+#define CK(x)                                                               \
+    do {                                                                    \
+        cudaError_t e_ = (x);                                               \
+        if (e_ != cudaSuccess) { return cuda_fail(e_, #x, __LINE__); }      \
+    } while (0)
+
+template <typename T>
+int upload(const T *src, size_t n, T **dst) {
+    CK(cudaMalloc(dst, n * sizeof(T)));
+    CK(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return DPG_OK;
+}
+
+void reset_host_status(DevStatus &s) {
+    std::memset(&s, 0, sizeof(s));
+    for (int i = 0; i < 8; ++i) s.first_bad[i] = ULLONG_MAX;
+}
+
+int device_state(DeviceState **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    auto it = g_dev.find(dev);
+    if (it != g_dev.end()) { *out = it->second.get(); return DPG_OK; }
+    auto st = std::make_unique<DeviceState>();
+    CK(cudaMalloc(&st->status, sizeof(DevStatus)));
+    DevStatus h;
+    reset_host_status(h);
+    CK(cudaMemcpy(st->status, &h, sizeof(h), cudaMemcpyHostToDevice));
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    CK(cudaMemPoolCreate(&st->pool, &props));
+    uint64_t thr = UINT64_MAX;
+    CK(cudaMemPoolSetAttribute(st->pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CK(init_kernel_attributes(optin));
+    g_max_dyn_smem = max_dynamic_smem(optin);
+    *out = st.get();
+    g_dev[dev] = std::move(st);
+    return DPG_OK;
+}
+
+int get_tables(DeviceState *ds, int q, int L, TableEntry **out) {
+    auto key = std::make_pair(q, L);
+    auto it = ds->tables.find(key);
+    if (it != ds->tables.end()) { *out = it->second.get(); return DPG_OK; }
+    auto te = std::make_unique<TableEntry>();
+    te->host = make_tables(q, L);
+    const HostTables &h = te->host;
+    std::vector<float> pp32(h.pp.begin(), h.pp.end()), F32(h.F.begin(), h.F.end());
+    int r;
+    if ((r = upload(h.zeta.data(), h.zeta.size(), &te->zeta))) return r;
+    if ((r = upload(h.w.data(), h.w.size(), &te->w))) return r;
+    if ((r = upload(h.pp.data(), h.pp.size(), &te->pp64))) return r;
+    if ((r = upload(pp32.data(), pp32.size(), &te->pp32))) return r;
+    if ((r = upload(h.F.data(), h.F.size(), &te->F64))) return r;
+    if ((r = upload(F32.data(), F32.size(), &te->F32))) return r;
+    *out = te.get();
+    ds->tables[key] = std::move(te);
+    return DPG_OK;
+}
+
+int get_program(DeviceState *ds, int space, int q, int L, int p, int split, const HostTables &tab, ProgEntry **out) {
+    ProgKey key{ space, q, L, p, split };
+    auto it = ds->progs.find(key);
+    if (it != ds->progs.end()) { *out = it->second.get(); return DPG_OK; }
+    auto pe = std::make_unique<ProgEntry>();
+    pe->prog = make_program(space, q, L, p, split != 0, tab);
+    const Program &pr = pe->prog;
+    if (pr.smem_values * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
+    int r;
+    if ((r = upload(pr.blocks, (size_t)pr.nblock, &pe->d_blocks))) return r;
+    if ((r = upload(pr.units.data(), pr.units.size(), &pe->d_units))) return r;
+    size_t m = 0;
+    for (int k = 0; k < pr.nblock; ++k) {
+        const BlockDesc &b = pr.blocks[k];
+        m = std::max(m, (size_t)b.ng * b.nr[1] * b.nc[1] * pr.nj);
+    }
+    pe->smem_aff = m;
+    *out = pe.get();
+    ds->progs[key] = std::move(pe);
+    return DPG_OK;
+}
+
+void free_device_state(DeviceState &ds) {
+    for (auto &kv : ds.tables) {
+        TableEntry &t = *kv.second;
+        cudaFree(t.zeta); cudaFree(t.w); cudaFree(t.pp64); cudaFree(t.pp32); cudaFree(t.F64); cudaFree(t.F32);
+    }
+    for (auto &kv : ds.progs) { cudaFree(kv.second->d_blocks); cudaFree(kv.second->d_units); }
+    ds.tables.clear(); ds.progs.clear(); ds.active_L.clear();
+}
+
+bool valid_space(int space) {
+    const int base = space & 0xff;
+    const int flags = space & ~0xff;
+    if (base < S_H1 || base > S_B) return false;
+    if (flags & ~(DPG_FP32 | DPG_MAP_AFFINE | DPG_B_SPLIT)) return false;
+    if ((flags & DPG_B_SPLIT) && base != S_B) return false;
+    return true;
+}
+
+// Resolve the program of a call; fills *pe and *te.
+int resolve(int space, int p_trial, int q, ProgEntry **pe, TableEntry **te, DeviceState **dso) {
+    if (!valid_space(space)) return DPG_ERR_ARG;
+    if (q < 1 || q > DPG_MAX_Q) return DPG_ERR_RANGE;
+    const int base = space & 0xff;
+    int p = 0, split = 0;
+    if (base == S_B) {
+        if (p_trial < 1 || p_trial > q) return DPG_ERR_ARG;
+        p = p_trial;
+        split = (space & DPG_B_SPLIT) ? 1 : 0;
+    }
+    DeviceState *ds = nullptr;
+    int r = device_state(&ds);
+    if (r) return r;
+    auto it = ds->active_L.find(std::make_pair(base, q));
+    if (it == ds->active_L.end()) return DPG_ERR_NOT_INIT;
+    const int L = it->second;
+    auto tt = ds->tables.find(std::make_pair(q, L));
+    if (tt == ds->tables.end()) return DPG_ERR_NOT_INIT;
+    auto pt = ds->progs.find(ProgKey{ base, q, L, p, split });
+    if (pt == ds->progs.end()) return DPG_ERR_NOT_INIT;
+    *pe = pt->second.get();
+    *te = tt->second.get();
+    *dso = ds;
+    return DPG_OK;
+}
+
+template <typename T>
+int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
+                const double *coeffs, T *out, cudaStream_t s) {
+    const Program &pr = pe->prog;
+    const int L = pr.L, L3 = L * L * L;
+    const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
+    const size_t per_elem = (size_t)pr.nfields * L3 * sizeof(T);
+    int64_t chunk = (int64_t)(kWorkspaceLimit / per_elem);
+    if (chunk < 1) chunk = 1;
+    const int64_t max_ctas = INT_MAX / (int64_t)pr.units.size();
+    if (chunk > max_ctas) chunk = max_ctas;
+    if (chunk > n_elem) chunk = n_elem;
+    void *ws = nullptr;
+    CK(cudaMallocFromPoolAsync(&ws, (size_t)chunk * per_elem, ds->pool, s));
+    int rc = DPG_OK;
+    for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK; e0 += chunk) {
+        const int64_t ne = std::min(chunk, n_elem - e0);
+        GeomParams g;
+        g.space = pr.space; g.L = L; g.nfields = pr.nfields;
+        g.n_elem = ne; g.elem_base = e0;
+        g.verts = verts + 24 * e0;
+        g.coeffs = coeffs ? coeffs + 2 * e0 : nullptr;
+        g.zeta = te->zeta; g.w = te->w;
+        g.fields = ws; g.status = ds->status;
+        cudaError_t le = launch_geom<T>(g, s);
+        if (le != cudaSuccess) { rc = cuda_fail(le, "geom_kernel launch", __LINE__); break; }
+        SfParams<T> sp;
+        sp.blocks = pe->d_blocks; sp.units = pe->d_units; sp.nunits = (int)pr.units.size();
+        sp.L = L; sp.nfields = pr.nfields;
+        if constexpr (sizeof(T) == 8) sp.pp = te->pp64; else sp.pp = te->pp32;
+        sp.fields = reinterpret_cast<const T *>(ws);
+        sp.out = out + e0 * mat;
+        sp.mat_stride = mat; sp.ld = pr.cols; sp.n_elem = ne;
+        le = launch_general<T>(sp, pr.smem_values * sizeof(T), s);
+        if (le != cudaSuccess) { rc = cuda_fail(le, "sf_general_kernel launch", __LINE__); break; }
+    }
+    cudaError_t fe = cudaFreeAsync(ws, s);
+    if (fe != cudaSuccess && rc == DPG_OK) rc = cuda_fail(fe, "cudaFreeAsync", __LINE__);
+    return rc;
+}
+
+template <typename T>
+int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
+               const double *coeffs, T *out, cudaStream_t s) {
+    const Program &pr = pe->prog;
+    const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
+    const int64_t per_launch = INT_MAX / (int64_t)pr.units.size();
+    for (int64_t e0 = 0; e0 < n_elem; e0 += per_launch) {
+        const int64_t ne = std::min(per_launch, n_elem - e0);
+        AffParams<T> ap;
+        ap.blocks = pe->d_blocks; ap.units = pe->d_units; ap.nunits = (int)pr.units.size();
+        ap.space = pr.space;
+        if constexpr (sizeof(T) == 8) ap.F = te->F64; else ap.F = te->F32;
+        ap.verts = verts + 24 * e0;
+        ap.coeffs = coeffs ? coeffs + 2 * e0 : nullptr;
+        ap.out = out + e0 * mat;
+        ap.mat_stride = mat; ap.ld = pr.cols; ap.n_elem = ne; ap.elem_base = e0;
+        ap.status = ds->status;
+        cudaError_t le = launch_affine<T>(ap, pe->smem_aff * sizeof(T), s);
+        if (le != cudaSuccess) return cuda_fail(le, "sf_affine_kernel launch", __LINE__);
+    }
+    return DPG_OK;
+}
+
+int integrate_locked(int space, int p_trial, int q_test, int64_t n_elem, const double *vertices,
+                     const double *coeffs, void *out, cudaStream_t s) {
+    ProgEntry *pe; TableEntry *te; DeviceState *ds;
+    int r = resolve(space, p_trial, q_test, &pe, &te, &ds);
+    if (r) return r;
+    if (n_elem < 0) return DPG_ERR_ARG;
+    if (n_elem == 0) return DPG_OK;
+    if (!vertices || !out) return DPG_ERR_ARG;
+    const bool fp32 = (space & DPG_FP32) != 0, affine = (space & DPG_MAP_AFFINE) != 0;
+    const bool use_coeffs = (space & 0xff) != S_B ? true : false;
+    const double *c = use_coeffs ? coeffs : nullptr;
+    if (affine) {
+        return fp32 ? run_affine<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
+                    : run_affine<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s);
+    }
+    return fp32 ? run_general<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
+                : run_general<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s);
+}
+
+int read_status(DeviceState *ds, int64_t *first_bad) {
+    DevStatus h;
+    CK(cudaMemcpy(&h, ds->status, sizeof(h), cudaMemcpyDeviceToHost));
+    DevStatus z;
+    reset_host_status(z);
+    CK(cudaMemcpy(ds->status, &z, sizeof(z), cudaMemcpyHostToDevice));
+    if (first_bad) *first_bad = -1;
+    if (h.code != 0) {
+        if (first_bad && h.code > 0 && h.code < 8 && h.first_bad[h.code] != ULLONG_MAX)
+            *first_bad = (int64_t)h.first_bad[h.code];
+        return h.code;
+    }
+    return DPG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dpg_tables_init_L(int q, int L, int space) {
+    const int base = space & 0xff;
+    if (base < S_H1 || base > S_B) return DPG_ERR_ARG;
+    if (q < 1 || q > DPG_MAX_Q || L < 1 || L > DPG_MAX_L) return DPG_ERR_RANGE;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *ds = nullptr;
+    int r = device_state(&ds);
+    if (r) return r;
+    TableEntry *te = nullptr;
+    if ((r = get_tables(ds, q, L, &te))) return r;
+    ProgEntry *pe = nullptr;
+    if (base == S_B) {
+        for (int p = 1; p <= q; ++p)
+            for (int split = 0; split < 2; ++split)
+                if ((r = get_program(ds, base, q, L, p, split, te->host, &pe))) return r;
+    } else {
+        if ((r = get_program(ds, base, q, L, 0, 0, te->host, &pe))) return r;
+    }
+    ds->active_L[std::make_pair(base, q)] = L;
+    return DPG_OK;
+}
+
+int dpg_tables_init(int q, int space) { return dpg_tables_init_L(q, q + 2 > DPG_MAX_L ? DPG_MAX_L : q + 2, space); }
+
+int dpg_tables_free(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_dev) {
+        cudaSetDevice(kv.first);
+        free_device_state(*kv.second);
+    }
+    cudaSetDevice(cur);
+    return DPG_OK;
+}
+
+int64_t dpg_matrix_rows(int space, int q) { return rows_of(space & 0xff, q); }
+
+int64_t dpg_matrix_cols(int space, int p_trial, int q) {
+    const int base = space & 0xff;
+    if (rows_of(base, q) < 0) return -1;
+    return cols_of(base, p_trial, q);
+}
+
+int dpg_integrate(int space, int p_trial, int q_test, int64_t n_elem, const double *vertices,
+                  const double *coeffs, void *out, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return integrate_locked(space, p_trial, q_test, n_elem, vertices, coeffs, out, (cudaStream_t)stream);
+}
+
+int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem, const double *vertices,
+                       const double *coeffs, void *out, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    ProgEntry *pe; TableEntry *te; DeviceState *ds;
+    int r = resolve(space, p_trial, q_test, &pe, &te, &ds);
+    if (r) return r;
+    if (n_elem < 0) return DPG_ERR_ARG;
+    if (n_elem == 0) return DPG_OK;
+    if (!vertices || !out) return DPG_ERR_ARG;
+    const Program &pr = pe->prog;
+    const size_t esz = (space & DPG_FP32) ? sizeof(float) : sizeof(double);
+    const size_t out_bytes = (size_t)n_elem * pr.parts * pr.rows * pr.cols * esz;
+    const size_t v_bytes = (size_t)n_elem * 24 * sizeof(double);
+    const size_t c_bytes = coeffs ? (size_t)n_elem * 2 * sizeof(double) : 0;
+    void *dv = nullptr, *dc = nullptr, *dout = nullptr;
+    CK(cudaMallocFromPoolAsync(&dv, v_bytes, ds->pool, s));
+    if (c_bytes) CK(cudaMallocFromPoolAsync(&dc, c_bytes, ds->pool, s));
+    CK(cudaMallocFromPoolAsync(&dout, out_bytes, ds->pool, s));
+    CK(cudaMemcpyAsync(dv, vertices, v_bytes, cudaMemcpyHostToDevice, s));
+    if (c_bytes) CK(cudaMemcpyAsync(dc, coeffs, c_bytes, cudaMemcpyHostToDevice, s));
+    r = integrate_locked(space, p_trial, q_test, n_elem, (const double *)dv, (const double *)dc, dout, s);
+    if (r == DPG_OK) {
+        CK(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s));
+    }
+    cudaFreeAsync(dv, s);
+    if (dc) cudaFreeAsync(dc, s);
+    cudaFreeAsync(dout, s);
+    CK(cudaStreamSynchronize(s));
+    if (r) return r;
+    return read_status(ds, nullptr);
+}
+
+int dpg_sync_status(void *stream, int64_t *first_bad_elem) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (first_bad_elem) *first_bad_elem = -1;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    DeviceState *ds = nullptr;
+    int r = device_state(&ds);
+    if (r) return r;
+    return read_status(ds, first_bad_elem);
+}
+
+const char *dpg_last_cuda_error(void) { return g_last_error; }
+
+const char *dpg_strerror(int code) {
+    switch (code) {
+    case DPG_OK: return "ok";
+    case DPG_ERR_ARG: return "invalid argument";
+    case DPG_ERR_NOT_INIT: return "tables not initialised for this (space, q)";
+    case DPG_ERR_RANGE: return "order or quadrature size out of range";
+    case DPG_ERR_CUDA: return "CUDA runtime error";
+    case DPG_ERR_DEGENERATE: return "non-positive or non-finite Jacobian determinant";
+    case DPG_ERR_NOT_AFFINE: return "element is not a parallelepiped";
+    case DPG_ERR_NOMEM: return "out of memory";
+    }
+    return "unknown status";
+}
+
+double dpg_flops_per_element(int space, int p_trial, int q_test) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    ProgEntry *pe; TableEntry *te; DeviceState *ds;
+    if (resolve(space, p_trial, q_test, &pe, &te, &ds) != DPG_OK) return -1.0;
+    return (space & DPG_MAP_AFFINE) ? pe->prog.flops_affine : pe->prog.flops;
+}
+
+int dpg_measure_fma_peak(int precision, void *stream, double *flops) {
+    if (!flops || (precision != 32 && precision != 64)) return DPG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8;
+    void *buf = nullptr;
+    CK(cudaMalloc(&buf, 256 * sizeof(double)));
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    auto run = [&](int iters, float *ms) -> int {
+        CK(cudaEventRecord(a, s));
+        cudaError_t e = precision == 64 ? launch_fma_peak<double>((double *)buf, blocks, iters, s)
+                                        : launch_fma_peak<float>((float *)buf, blocks, iters, s);
+        if (e != cudaSuccess) return DPG_ERR_CUDA;
+        CK(cudaEventRecord(b, s));
+        CK(cudaEventSynchronize(b));
+        CK(cudaEventElapsedTime(ms, a, b));
+        return DPG_OK;
+    };
+    float ms = 0.f;
+    int iters = 16;
+    int r = run(iters, &ms);                           // warm-up and calibration
+    while (r == DPG_OK && ms < 20.f && iters < (1 << 24)) { iters *= 4; r = run(iters, &ms); }
+    double best = 0.0;
+    for (int rep = 0; rep < 5 && r == DPG_OK; ++rep) {
+        r = run(iters, &ms);
+        const double f = 2.0 * 8 * 16 * (double)iters * 256.0 * blocks / (ms * 1e-3);
+        if (f > best) best = f;
+    }
+    cudaEventDestroy(a); cudaEventDestroy(b); cudaFree(buf);
+    if (r) return r;
+    *flops = best;
+    return DPG_OK;
+}
+
+}  // extern "C"

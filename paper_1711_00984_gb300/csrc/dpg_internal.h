@@ -1,0 +1,107 @@
+// dpg_internal.h -- data structures shared by the host set-up and the CUDA kernels of the
+// library (not part of the public ABI).
+//
+// Vocabulary (Mora & Demkowicz, arXiv 1711.00984):
+//   kind   : a 1D factor family.  W = chi_i = L_i (integrated Legendre, Eqs. 2.97-2.101),
+//            D = chi'_i, Y = nu_i = P_i = chi'_{i+1} (Legendre, Eqs. 2.91-2.93, 2.54).
+//   term   : one product  sign * field(xi) * prod_d f^{kr_d}_{i_d}(xi_d) f^{kc_d}_{j_d}(xi_d)
+//            of an inner product written on the master element, e.g. one D_ab entry of
+//            Eq. 2.36, one C_ab entry of Eq. 2.60, one (alpha, beta) curl sub-term of
+//            Eq. 2.77 with its sign (-1)^(alpha+beta) (Eq. 2.84).
+//   block  : the (row component a, column component b) sub-matrix of a vector space
+//            (Eqs. 2.53, 2.71); scalar spaces have one block.
+//   stages : A contracts one direction (Eq. 2.23 contracts xi_3), B a second (Eq. 2.24),
+//            C the last (Eq. 2.25); which direction each stage takes is a per-block choice
+//            (BlockDesc::dir).  Terms with equal stage-C and stage-B kind pairs are summed
+//            after stage A ("h groups"), terms with equal stage-C pairs after stage B
+//            ("g groups"): the sum of Eq. 2.44 / 2.84 regrouped.
+#pragma once
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define DPG_HD __host__ __device__
+#else
+#define DPG_HD
+#endif
+
+namespace dpg {
+
+enum Kind : int { KW = 0, KD = 1, KY = 2 };
+constexpr int NKIND = 3;
+constexpr int NPAIR = NKIND * NKIND;          // pair type = 3 * kr + kc
+constexpr int MAXQ = 12;
+constexpr int NQ1 = MAXQ + 1;                 // max 1D functions per direction
+constexpr int MAXL = 14;
+constexpr int MAXT = 12;                      // terms per block (H1 has 10)
+constexpr int MAXH = 10;                      // (dir1, dir2)-pair groups per block
+constexpr int MAXG = 4;                       // dir1-pair groups per block
+constexpr int MAXP2 = 9;                      // distinct dir2 pairs per block
+constexpr int MAXBLK = 18;                    // B split: 9 blocks x 2 parts
+constexpr int NJMAX = 8;                      // j3 values per work unit
+
+enum SpaceId : int { S_H1 = 1, S_HCURL = 2, S_HDIV = 3, S_L2 = 4, S_B = 5 };
+
+struct TermDesc {
+    int field;        // index of the per-point metric field
+    int sign;         // +1 / -1
+    int kr[3], kc[3]; // row / column kinds per direction
+    int h;            // (dir1, dir2) group
+};
+
+struct BlockDesc {
+    int nr[3], nc[3];        // 1D function counts per direction (rows, columns)
+    int row_off, col_off;    // position of the block in the element matrix
+    int base;                // element-local offset (in values) of the matrix it writes
+    int sym;                 // 0: plain; 1: diagonal block of a symmetric matrix (tiles with
+                             // jA >= iA computed, the others mirrored); 2: off-diagonal
+                             // block of a symmetric matrix (every tile mirrored)
+    int dir[3];              // directions contracted by stage C (dir[0], last), stage B
+                             // (dir[1]) and stage A (dir[2], first); chosen per block to
+                             // minimise the multiply-adds (the paper uses 1, 2, 3)
+    int nterm, nh, ng, np2;
+    TermDesc term[MAXT];
+    int h_g[MAXH];           // g group of each h group
+    int h_p2[MAXH];          // dir2 pair slot of each h group
+    int p2_pair[MAXP2];      // pair type of each dir2 slot
+    int g_pair[MAXG];        // pair type of each g group (dir1)
+    int h_pair2[MAXH];       // pair type of each h group's dir2 pair
+    int h_pair1[MAXH];       // pair type of each h group's dir1 pair
+};
+
+struct Unit {
+    int16_t block, i3, j3b, nj;   // i3 / j3: indices along the stage-A direction dir[2]
+};
+
+// Device-resident tables of one (q, L).
+struct DevTables {
+    int q, L;
+    const double *zeta, *w;          // Gauss rule, [L]
+    const double *pp64;              // [NPAIR][NQ1][NQ1][L]  f_kr(i,l) f_kc(j,l)
+    const float *pp32;
+    const double *F;                 // [NPAIR][NQ1][NQ1]     int_0^1 f_kr,i f_kc,j
+};
+
+// Metric fields per space (per quadrature point, weights and coefficients folded in):
+//   H1   : 0: c0 |J| w,  1..6: c1 D_ab |J| w          (ab = 11,22,33,12,13,23)
+//   L2   : 0: c0 w / |J|
+//   HDIV : 0..5: c0 C_ab w / |J|,  6: c1 w / |J|
+//   HCURL: 0..5: c0 D_ab |J| w,  6..11: c1 C_ab w / |J|
+//   B    : 0..8: (J^-1)_ac w (index 3a + c),  9..17: J_cd w / |J| (index 9 + 3c + d)
+// with D = J^-1 J^-T (Eq. 2.32) and C = J^T J (Eq. 2.50).
+DPG_HD inline int sym_index(int a, int b) {
+    if (a == b) return a;
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+inline int nfields_of(int space) {
+    switch (space) {
+    case S_H1: return 7;
+    case S_L2: return 1;
+    case S_HDIV: return 7;
+    case S_HCURL: return 12;
+    case S_B: return 18;
+    }
+    return 0;
+}
+
+}  // namespace dpg

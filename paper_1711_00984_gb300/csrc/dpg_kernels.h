@@ -1,0 +1,62 @@
+// dpg_kernels.h -- kernel parameter blocks and launchers (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dpg_internal.h"
+
+namespace dpg {
+
+// Device status word: the first error code recorded (0 = none) and, per code, the
+// smallest offending element index.
+struct DevStatus {
+    int code;
+    int pad;
+    unsigned long long first_bad[8];
+};
+
+struct GeomParams {
+    int space, L, nfields;
+    int64_t n_elem;            // elements of this chunk
+    int64_t elem_base;         // index of the chunk's first element in the call
+    const double *verts;       // chunk start, [n_elem][8][3]
+    const double *coeffs;      // chunk start, [n_elem][2] or NULL
+    const double *zeta, *w;    // Gauss rule
+    void *fields;              // [n_elem][nfields][L^3] of the stage type
+    DevStatus *status;
+};
+
+template <typename T>
+struct SfParams {
+    const BlockDesc *blocks;
+    const Unit *units;
+    int nunits;
+    int L, nfields;
+    const T *pp;               // pair products [NPAIR][NQ1][NQ1][L]
+    const T *fields;           // [n_elem][nfields][L^3]
+    T *out;                    // chunk start
+    int64_t mat_stride;        // values per element (parts * rows * cols)
+    int64_t ld;                // columns
+    int64_t n_elem;
+};
+
+template <typename T>
+struct AffParams {
+    const BlockDesc *blocks;
+    const Unit *units;
+    int nunits;
+    int space;
+    const T *F;                // exact 1D integrals [NPAIR][NQ1][NQ1]
+    const double *verts, *coeffs;
+    T *out;
+    int64_t mat_stride, ld, n_elem, elem_base;
+    DevStatus *status;
+};
+
+template <typename TF> cudaError_t launch_geom(const GeomParams &p, cudaStream_t s);
+template <typename T> cudaError_t launch_general(const SfParams<T> &p, size_t smem, cudaStream_t s);
+template <typename T> cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s);
+template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
+cudaError_t init_kernel_attributes(int optin_smem);
+int max_dynamic_smem(int optin_smem);
+
+}  // namespace dpg

@@ -1,0 +1,392 @@
+// dpg_setup.cu -- host set-up: Gauss rule, 1D tables, exact 1D integrals, and the term
+// programs (blocks, terms, groups, work units) of every space.
+//
+// Everything here runs once per (space, q, L) in dpg_tables_init; nothing here runs per
+// element.
+#include "dpg_setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+namespace dpg {
+
+// ---------------------------------------------------------------------------------------
+// Gauss-Legendre rule on (0,1): Newton's method on the classical Legendre polynomial
+// P_L(t) on [-1,1] (three-term recurrence (n+1) P_{n+1} = (2n+1) t P_n - n P_{n-1}),
+// P_L'(t) = L (t P_L - P_{L-1}) / (t^2 - 1), initial guesses from Tricomi's asymptotic
+// form; then t -> (1 - t)/2 (ascending nodes), weights w = 1 / ((1 - t^2) P_L'(t)^2).
+// The rule integrates degree <= 2L-1 exactly (Eq. 2.23).
+// ---------------------------------------------------------------------------------------
+void gauss_rule(int L, double *z, double *w) {
+    const double pi = 3.14159265358979323846;
+    for (int k = 1; k <= L; ++k) {
+        double t = (1.0 - (L - 1.0) / (8.0 * L * L * L)) * std::cos(pi * (4.0 * k - 1.0) / (4.0 * L + 2.0));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int n = 1; n < L; ++n) {
+                double p2 = ((2.0 * n + 1.0) * t * p1 - n * p0) / (n + 1.0);
+                p0 = p1; p1 = p2;
+            }
+            if (L == 1) { p0 = 1.0; }
+            dp = L * (t * p1 - p0) / (t * t - 1.0);
+            double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int n = 1; n < L; ++n) {
+            double p2 = ((2.0 * n + 1.0) * t * p1 - n * p0) / (n + 1.0);
+            p0 = p1; p1 = p2;
+        }
+        if (L == 1) p0 = 1.0;
+        dp = L * (t * p1 - p0) / (t * t - 1.0);
+        z[k - 1] = 0.5 * (1.0 - t);
+        w[k - 1] = 1.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+// Values of the three 1D kinds at x for indices 0..n-1:
+//   Y_i = P_i(x) (Eqs. 2.91-2.93, written with t = 2x - 1), W_i = L_i (Eqs. 2.99-2.101),
+//   D_i = L_i' (Eq. 2.98: D_0 = -1, D_i = P_{i-1}).
+static void families(int n, double x, double *W, double *Dv, double *Y) {
+    double P[NQ1 + 2];
+    double t = 2.0 * x - 1.0;
+    int np = n + 1;
+    P[0] = 1.0;
+    if (np > 1) P[1] = t;
+    for (int i = 1; i + 1 < np; ++i) P[i + 1] = ((2.0 * i + 1.0) * t * P[i] - i * P[i - 1]) / (i + 1.0);
+    for (int i = 0; i < n; ++i) {
+        Y[i] = P[i];
+        if (i == 0) { W[0] = 1.0 - x; Dv[0] = -1.0; }
+        else if (i == 1) { W[1] = x; Dv[1] = 1.0; }
+        else { W[i] = (P[i] - P[i - 2]) / (2.0 * (2.0 * i - 1.0)); Dv[i] = P[i - 1]; }
+    }
+}
+
+HostTables make_tables(int q, int L) {
+    HostTables t;
+    t.q = q; t.L = L;
+    t.zeta.assign(L, 0.0); t.w.assign(L, 0.0);
+    gauss_rule(L, t.zeta.data(), t.w.data());
+    // 1D values at the nodes: X[kind][i][l]
+    std::vector<double> X((size_t)NKIND * NQ1 * L, 0.0);
+    for (int l = 0; l < L; ++l) {
+        double W[NQ1], Dv[NQ1], Y[NQ1];
+        families(q + 1, t.zeta[l], W, Dv, Y);
+        for (int i = 0; i <= q; ++i) {
+            X[((size_t)KW * NQ1 + i) * L + l] = W[i];
+            X[((size_t)KD * NQ1 + i) * L + l] = Dv[i];
+            X[((size_t)KY * NQ1 + i) * L + l] = Y[i];
+        }
+    }
+    // pair products: pp[pair][i][j][l] = X[kr][i][l] X[kc][j][l]
+    t.pp.assign((size_t)NPAIR * NQ1 * NQ1 * L, 0.0);
+    for (int kr = 0; kr < NKIND; ++kr)
+    for (int kc = 0; kc < NKIND; ++kc)
+    for (int i = 0; i <= q; ++i)
+    for (int j = 0; j <= q; ++j)
+    for (int l = 0; l < L; ++l)
+        t.pp[(((size_t)(3 * kr + kc) * NQ1 + i) * NQ1 + j) * L + l] =
+            X[((size_t)kr * NQ1 + i) * L + l] * X[((size_t)kc * NQ1 + j) * L + l];
+    // exact 1D integrals F (Eq. 2.90) with a rule of q+2 points (exact to degree 2q+3)
+    int LF = q + 2;
+    std::vector<double> zf(LF), wf(LF);
+    gauss_rule(LF, zf.data(), wf.data());
+    t.F.assign((size_t)NPAIR * NQ1 * NQ1, 0.0);
+    for (int l = 0; l < LF; ++l) {
+        double V[NKIND][NQ1];
+        families(q + 1, zf[l], V[KW], V[KD], V[KY]);
+        for (int kr = 0; kr < NKIND; ++kr)
+        for (int kc = 0; kc < NKIND; ++kc)
+        for (int i = 0; i <= q; ++i)
+        for (int j = 0; j <= q; ++j)
+            t.F[((size_t)(3 * kr + kc) * NQ1 + i) * NQ1 + j] += wf[l] * V[kr][i] * V[kc][j];
+    }
+    // integrals of products of polynomials of degree <= 2q whose exact value is 0 come
+    // out of the rule at rounding level; store them as exact zeros (orthogonality,
+    // Eqs. 2.95-2.96 and Sec. 2.8.2): the affine path relies on exact zeros.
+    for (size_t k = 0; k < t.F.size(); ++k)
+        if (std::fabs(t.F[k]) < 1e-13) t.F[k] = 0.0;
+    return t;
+}
+
+// ---------------------------------------------------------------------------------------
+// Term programs
+// ---------------------------------------------------------------------------------------
+struct CompLayout { int n[3]; int kind[3]; int offset; };
+
+// Component layouts (Eqs. 2.17, 2.33, 2.52-2.53, 2.70-2.71).
+static int layout(int space, int q, int p, CompLayout c[3]) {
+    if (space == S_H1) { c[0] = { { q + 1, q + 1, q + 1 }, { KW, KW, KW }, 0 }; return 1; }
+    if (space == S_L2) { c[0] = { { q, q, q }, { KY, KY, KY }, 0 }; return 1; }
+    if (space == -S_B) {           // vector-L2 trial of order p
+        for (int k = 0; k < 3; ++k) c[k] = { { p, p, p }, { KY, KY, KY }, k * p * p * p };
+        return 3;
+    }
+    int off = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int d = 0; d < 3; ++d) {
+            bool same = d == a;
+            if (space == S_HDIV) { c[a].n[d] = same ? q + 1 : q; c[a].kind[d] = same ? KW : KY; }
+            else { c[a].n[d] = same ? q : q + 1; c[a].kind[d] = same ? KY : KW; }
+        }
+        c[a].offset = off;
+        off += c[a].n[0] * c[a].n[1] * c[a].n[2];
+    }
+    return 3;
+}
+
+static int dim_of(int space, int q, int p) {
+    CompLayout c[3];
+    int nc = layout(space, q, p, c);
+    int n = 0;
+    for (int k = 0; k < nc; ++k) n += c[k].n[0] * c[k].n[1] * c[k].n[2];
+    return n;
+}
+
+int64_t rows_of(int space, int q) {
+    if (q < 1 || q > MAXQ) return -1;
+    if (space == S_B) return dim_of(S_HCURL, q, 0);
+    if (space < S_H1 || space > S_L2) return -1;
+    return dim_of(space, q, 0);
+}
+
+int64_t cols_of(int space, int p, int q) {
+    if (space == S_B) {
+        if (p < 1 || p > q || q > MAXQ) return -1;
+        return 3LL * p * p * p;
+    }
+    return rows_of(space, q);
+}
+
+struct TermSpec { int field, sign; int kr[3], kc[3]; };
+
+// curl^(f e_a) = grad f x e_a (Eq. 2.67 applied to Eq. 2.74): component a+1 is
+// +d_{a+2} f, component a+2 is -d_{a+1} f; the derivative replaces chi by chi' (kind D)
+// in that direction (Eqs. 2.73, 2.75).
+static void curl_parts(int a, const int base[3], int comp[2], int sign[2], int kinds[2][3]) {
+    int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    comp[0] = a1; sign[0] = +1; comp[1] = a2; sign[1] = -1;
+    for (int d = 0; d < 3; ++d) {
+        kinds[0][d] = (d == a2) ? KD : base[d];
+        kinds[1][d] = (d == a1) ? KD : base[d];
+    }
+}
+
+static void finish_block(BlockDesc &b, const std::vector<TermSpec> &ts, const int dir[3]) {
+    b.nterm = (int)ts.size();
+    for (int k = 0; k < 3; ++k) b.dir[k] = dir[k];
+    std::map<std::pair<int, int>, int> hmap;
+    std::map<int, int> gmap, p2map;
+    b.nh = b.ng = b.np2 = 0;
+    const int dC = dir[0], dB = dir[1];
+    for (int t = 0; t < b.nterm; ++t) {
+        const TermSpec &s = ts[t];
+        TermDesc &d = b.term[t];
+        d.field = s.field; d.sign = s.sign;
+        for (int k = 0; k < 3; ++k) { d.kr[k] = s.kr[k]; d.kc[k] = s.kc[k]; }
+        int p1 = 3 * s.kr[dC] + s.kc[dC], p2 = 3 * s.kr[dB] + s.kc[dB];
+        auto key = std::make_pair(p1, p2);
+        if (!hmap.count(key)) {
+            int h = b.nh++;
+            hmap[key] = h;
+            if (!gmap.count(p1)) { int g = b.ng++; gmap[p1] = g; b.g_pair[g] = p1; }
+            if (!p2map.count(p2)) { int s2 = b.np2++; p2map[p2] = s2; b.p2_pair[s2] = p2; }
+            b.h_g[h] = gmap[p1];
+            b.h_p2[h] = p2map[p2];
+            b.h_pair1[h] = p1;
+            b.h_pair2[h] = p2;
+        }
+        d.h = hmap[key];
+    }
+}
+
+// Multiply-adds of one block of the general path: per tile (iA, jA) stage A costs
+// nterm L^3, stage B nh L^2 nB nB', stage C ng L (outputs of the tile); a diagonal
+// block of a symmetric matrix computes tiles jA >= iA, and its iA == jA tiles count
+// the upper triangle only.
+static double block_fmas(const BlockDesc &b, int L) {
+    const int dC = b.dir[0], dB = b.dir[1], dA = b.dir[2];
+    const double mr = (double)b.nr[dC] * b.nr[dB], mc = (double)b.nc[dC] * b.nc[dB];
+    double f = 0.0;
+    for (int i3 = 0; i3 < b.nr[dA]; ++i3)
+        for (int j3 = (b.sym == 1 ? i3 : 0); j3 < b.nc[dA]; ++j3) {
+            f += (double)b.nterm * L * L * L;
+            f += (double)b.nh * L * L * b.nr[dB] * b.nc[dB];
+            f += (double)b.ng * L * ((b.sym == 1 && j3 == i3) ? 0.5 * mr * (mr + 1.0) : mr * mc);
+        }
+    return f;
+}
+
+static size_t smem_values(const BlockDesc &b, int L, int nj) {
+    auto r4 = [](size_t v) { return (v + 3) & ~size_t(3); };
+    const int dC = b.dir[0], dB = b.dir[1];
+    size_t P1 = r4((size_t)b.ng * b.nr[dC] * b.nc[dC] * L);
+    size_t P2 = r4((size_t)b.np2 * b.nr[dB] * b.nc[dB] * L);
+    size_t P3 = r4((size_t)b.nterm * nj * L);
+    size_t A = r4((size_t)b.nh * L * L * nj);
+    size_t B = r4((size_t)b.ng * L * b.nr[dB] * b.nc[dB] * nj);
+    return P1 + P2 + P3 + A + B;
+}
+
+Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab) {
+    Program pr;
+    std::memset(pr.blocks, 0, sizeof(pr.blocks));
+    pr.space = space; pr.q = q; pr.L = L; pr.p = p; pr.split = split;
+    pr.rows = (int)rows_of(space, q);
+    pr.cols = (int)cols_of(space, p, q);
+    pr.parts = (space == S_B && split) ? 2 : 1;
+    pr.nfields = nfields_of(space);
+    pr.nblock = 0;
+
+    CompLayout R[3], C[3];
+    int nR = layout(space == S_B ? S_HCURL : space, q, 0, R);
+    int nC = space == S_B ? layout(-S_B, q, p, C) : layout(space, q, 0, C);
+
+    for (int a = 0; a < nR; ++a)
+    for (int b = 0; b < nC; ++b) {
+        bool symmetric = space != S_B;
+        if (symmetric && b < a) continue;             // lower blocks come from mirroring
+        for (int part = 0; part < pr.parts; ++part) {
+            std::vector<TermSpec> ts;
+            auto add = [&](int field, int sign, const int kr[3], const int kc[3]) {
+                TermSpec s; s.field = field; s.sign = sign;
+                for (int d = 0; d < 3; ++d) { s.kr[d] = kr[d]; s.kc[d] = kc[d]; }
+                ts.push_back(s);
+            };
+            const int *ka = R[a].kind, *kb = C[b].kind;
+            switch (space) {
+            case S_L2:                                 // Eq. 2.19: nu nu nu |J|^-1
+                add(0, 1, ka, kb);
+                break;
+            case S_H1: {                               // Eqs. 2.41-2.44 and 2.38-2.40
+                add(0, 1, ka, kb);
+                for (int aa = 0; aa < 3; ++aa)
+                for (int bb = 0; bb < 3; ++bb) {
+                    int kr[3], kc[3];
+                    for (int d = 0; d < 3; ++d) { kr[d] = d == aa ? KD : KW; kc[d] = d == bb ? KD : KW; }
+                    add(1 + sym_index(aa, bb), 1, kr, kc);
+                }
+                break;
+            }
+            case S_HDIV: {                             // Eqs. 2.60-2.63 and the div term 2.59
+                add(sym_index(a, b), 1, ka, kb);
+                int kr[3], kc[3];
+                for (int d = 0; d < 3; ++d) { kr[d] = d == a ? KD : ka[d]; kc[d] = d == b ? KD : kb[d]; }
+                add(6, 1, kr, kc);
+                break;
+            }
+            case S_HCURL: {                            // Eqs. 2.76-2.84
+                add(sym_index(a, b), 1, ka, kb);
+                int ca[2], sa[2], kra[2][3], cb[2], sb[2], krb[2][3];
+                curl_parts(a, ka, ca, sa, kra);
+                curl_parts(b, kb, cb, sb, krb);
+                for (int al = 0; al < 2; ++al)
+                for (int be = 0; be < 2; ++be)
+                    add(6 + sym_index(ca[al], cb[be]), sa[al] * sb[be], kra[al], krb[be]);
+                break;
+            }
+            case S_B: {                                // u^.J^-T psi^ + u^.J curl^psi^ / |J|
+                if (part == 0 || !split) add(3 * a + b, 1, ka, kb);
+                if (part == 1 || !split) {
+                    int cc[2], sc[2], kr[2][3];
+                    curl_parts(a, ka, cc, sc, kr);
+                    for (int al = 0; al < 2; ++al) add(9 + 3 * b + cc[al], sc[al], kr[al], kb);
+                }
+                break;
+            }
+            }
+            BlockDesc &bd = pr.blocks[pr.nblock++];
+            for (int d = 0; d < 3; ++d) { bd.nr[d] = R[a].n[d]; bd.nc[d] = C[b].n[d]; }
+            bd.row_off = R[a].offset;
+            bd.col_off = C[b].offset;
+            bd.base = part * pr.rows * pr.cols;
+            bd.sym = symmetric ? (a == b ? 1 : 2) : 0;
+            // stage order: the permutation of directions with the fewest multiply-adds
+            // (ties keep the paper's order: stage A over xi_3, B over xi_2, C over xi_1)
+            static const int perms[6][3] = { { 0, 1, 2 }, { 1, 0, 2 }, { 0, 2, 1 },
+                                             { 2, 0, 1 }, { 1, 2, 0 }, { 2, 1, 0 } };
+            double best = 0.0; int bi = 0;
+            for (int k = 0; k < 6; ++k) {
+                finish_block(bd, ts, perms[k]);
+                const double f = block_fmas(bd, L);
+                if (k == 0 || f < best * (1.0 - 1e-12)) { best = f; bi = k; }
+            }
+            finish_block(bd, ts, perms[bi]);
+        }
+    }
+
+    // stage-A chunk: the largest nj whose FP64 shared memory fits the budget
+    const size_t budget = 160 * 1024;
+    int maxnA = 1;
+    for (int k = 0; k < pr.nblock; ++k) maxnA = std::max(maxnA, pr.blocks[k].nc[pr.blocks[k].dir[2]]);
+    int nj = std::min(NJMAX, maxnA);
+    for (; nj > 1; --nj) {
+        size_t m = 0;
+        for (int k = 0; k < pr.nblock; ++k) m = std::max(m, smem_values(pr.blocks[k], L, nj));
+        if (m * sizeof(double) <= budget) break;
+    }
+    pr.nj = nj;
+    size_t m = 0;
+    for (int k = 0; k < pr.nblock; ++k) m = std::max(m, smem_values(pr.blocks[k], L, nj));
+    pr.smem_values = m;
+
+    // work units (element-local): one per (block, iA, chunk of jA); algorithmic flops
+    pr.units.clear();
+    double fmas = 0.0;
+    for (int k = 0; k < pr.nblock; ++k) {
+        const BlockDesc &b = pr.blocks[k];
+        const int dA = b.dir[2];
+        for (int i3 = 0; i3 < b.nr[dA]; ++i3) {
+            int jlo = b.sym == 1 ? i3 : 0;
+            for (int j = jlo; j < b.nc[dA]; j += nj) {
+                Unit u;
+                u.block = (int16_t)k; u.i3 = (int16_t)i3; u.j3b = (int16_t)j;
+                u.nj = (int16_t)std::min(nj, b.nc[dA] - j);
+                pr.units.push_back(u);
+            }
+        }
+        fmas += block_fmas(b, L);
+    }
+    pr.flops = 2.0 * fmas;
+
+    // affine path: non-zero products of the Kronecker sums (Sec. 2.8.1)
+    double aff = 0.0;
+    auto Fv = [&](int pair, int i, int j) { return tab.F[((size_t)pair * NQ1 + i) * NQ1 + j]; };
+    for (int k = 0; k < pr.nblock; ++k) {
+        const BlockDesc &b = pr.blocks[k];
+        const int dC = b.dir[0], dB = b.dir[1], dA = b.dir[2];
+        for (int i3 = 0; i3 < b.nr[dA]; ++i3)
+        for (int j3 = (b.sym == 1 ? i3 : 0); j3 < b.nc[dA]; ++j3) {
+            // Q_g(iB, jB) = sum_{t in g} c_t F_B,t F_A,t
+            std::vector<char> qnz((size_t)b.ng * b.nr[dB] * b.nc[dB], 0);
+            for (int t = 0; t < b.nterm; ++t) {
+                const TermDesc &d = b.term[t];
+                double f3 = Fv(3 * d.kr[dA] + d.kc[dA], i3, j3);
+                if (f3 == 0.0) continue;
+                int g = b.h_g[d.h];
+                for (int i2 = 0; i2 < b.nr[dB]; ++i2)
+                for (int j2 = 0; j2 < b.nc[dB]; ++j2)
+                    if (Fv(3 * d.kr[dB] + d.kc[dB], i2, j2) != 0.0) {
+                        aff += 2.0;
+                        qnz[((size_t)g * b.nr[dB] + i2) * b.nc[dB] + j2] = 1;
+                    }
+            }
+            for (int g = 0; g < b.ng; ++g)
+            for (int i1 = 0; i1 < b.nr[dC]; ++i1)
+            for (int j1 = 0; j1 < b.nc[dC]; ++j1) {
+                if (Fv(b.g_pair[g], i1, j1) == 0.0) continue;
+                for (int i2 = 0; i2 < b.nr[dB]; ++i2)
+                for (int j2 = 0; j2 < b.nc[dB]; ++j2)
+                    if (qnz[((size_t)g * b.nr[dB] + i2) * b.nc[dB] + j2]) aff += 2.0;
+            }
+        }
+    }
+    pr.flops_affine = aff;
+    return pr;
+}
+
+}  // namespace dpg

@@ -1,0 +1,37 @@
+// dpg_setup.h -- host-side tables and term programs (internal).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "dpg_internal.h"
+
+namespace dpg {
+
+struct HostTables {
+    int q = 0, L = 0;
+    std::vector<double> zeta, w;   // Gauss rule on (0,1), [L]
+    std::vector<double> pp;        // [NPAIR][NQ1][NQ1][L]
+    std::vector<double> F;         // [NPAIR][NQ1][NQ1]
+};
+
+struct Program {
+    int space = 0, q = 0, L = 0, p = 0;
+    bool split = false;
+    int rows = 0, cols = 0, parts = 1, nfields = 0;
+    int nblock = 0;
+    BlockDesc blocks[MAXBLK];
+    std::vector<Unit> units;
+    int nj = 1;
+    size_t smem_values = 0;        // shared-memory values of the general kernel
+    double flops = 0.0;            // algorithmic flops per element, general path
+    double flops_affine = 0.0;     // algorithmic flops per element, affine path
+};
+
+void gauss_rule(int L, double *z, double *w);
+HostTables make_tables(int q, int L);
+Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab);
+int64_t rows_of(int space, int q);
+int64_t cols_of(int space, int p, int q);
+
+}  // namespace dpg
