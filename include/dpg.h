@@ -66,7 +66,9 @@ typedef enum {
     DPG_ERR_CUDA = 4,        /* a CUDA runtime call failed                              */
     DPG_ERR_DEGENERATE = 5,  /* device: |J| <= 0 or not finite at a quadrature point    */
     DPG_ERR_NOT_AFFINE = 6,  /* device: element is not a parallelepiped (affine path)   */
-    DPG_ERR_NOMEM = 7        /* device or host allocation failed                        */
+    DPG_ERR_NOMEM = 7,       /* device or host allocation failed                        */
+    DPG_ERR_SCRATCH = 8      /* dpg_integrate_noalloc: the call needs more metric-field
+                                scratch than DPG_NOALLOC_SCRATCH_BYTES                  */
 } dpg_status;
 
 #define DPG_MAX_Q 12           /* supported test orders: 1 <= q <= DPG_MAX_Q           */
@@ -119,6 +121,32 @@ int64_t dpg_matrix_cols(int space, int p_trial, int q);
  * device-detected errors through dpg_sync_status. */
 int dpg_integrate(int space, int p_trial, int q_test, int64_t n_elem,
                   const double *vertices, const double *coeffs, void *out, void *stream);
+
+/* Allocation-free variant of dpg_integrate for the general (trilinear-map) path.  The
+ * paper has no counterpart: this is a service for callers that must not allocate device
+ * memory while they integrate -- a solver whose device memory is carved up once at start
+ * and may not grow, code that runs inside another framework's allocator or memory
+ * budget, or a call issued where an allocation would stall the stream or the device.
+ * dpg_integrate takes its metric-field workspace from a memory pool; this entry point
+ * instead uses one file-scope device array of DPG_NOALLOC_SCRATCH_BYTES (32 MiB), which
+ * every GPU that loads the library reserves until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   Arguments, layouts and results are those of dpg_integrate; DPG_MAP_AFFINE is
+ *   rejected (DPG_ERR_ARG): the affine path needs no scratch, use dpg_integrate.
+ *   Limit: n_elem * nfields * L^3 * (8 or 4 bytes) must fit the array (nfields = 7, 12,
+ *   7, 1, 18 for H1, H(curl), H(div), L2, B; 4 bytes with DPG_FP32), else the call
+ *   returns DPG_ERR_SCRATCH before launching anything.  Example: H(curl), q = 5, L = 7,
+ *   FP64 fits 1019 elements per call.
+ *   Set-up: the first call on a device (with that device current) looks up the array's
+ *   device address (cudaGetSymbolAddress) and caches it; make that first call before
+ *   any stream capture.  Tables must be initialised with dpg_tables_init beforehand.
+ *   Sharing: all calls use the same array and it keeps the last call's contents (every
+ *   value a call reads is written by that call first, so nothing needs clearing); calls
+ *   that overlap on the GPU, e.g. on two streams, race on it and must be serialised by
+ *   the caller. */
+#define DPG_NOALLOC_SCRATCH_BYTES (32u << 20)
+int dpg_integrate_noalloc(int space, int p_trial, int q_test, int64_t n_elem,
+                          const double *vertices, const double *coeffs, void *out, void *stream);
 
 /* Same as dpg_integrate, but vertices, coeffs and out are HOST buffers (page-locked for
  * full copy speed).  Copies the inputs to the device, integrates, copies the result

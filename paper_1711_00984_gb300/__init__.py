@@ -22,10 +22,10 @@ DPG_H1, DPG_HCURL, DPG_HDIV, DPG_L2, DPG_B_L2VEC_HCURL = 1, 2, 3, 4, 5
 DPG_FP32, DPG_MAP_AFFINE, DPG_B_SPLIT = 0x100, 0x200, 0x400
 SPACE_IDS = {"H1": DPG_H1, "HCURL": DPG_HCURL, "HDIV": DPG_HDIV, "L2": DPG_L2, "B": DPG_B_L2VEC_HCURL}
 STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANGE", 4: "DPG_ERR_CUDA",
-          5: "DPG_ERR_DEGENERATE", 6: "DPG_ERR_NOT_AFFINE", 7: "DPG_ERR_NOMEM"}
+          5: "DPG_ERR_DEGENERATE", 6: "DPG_ERR_NOT_AFFINE", 7: "DPG_ERR_NOMEM", 8: "DPG_ERR_SCRATCH"}
 
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
-           "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_host", "dpg_sync_status",
+           "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_host", "dpg_sync_status",
            "dpg_strerror", "dpg_last_cuda_error", "dpg_flops_per_element", "dpg_measure_fma_peak"]
 
 _lib = None
@@ -61,6 +61,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_matrix_cols.restype = i64
         lib.dpg_integrate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
         lib.dpg_integrate_host.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
+        lib.dpg_integrate_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
         lib.dpg_sync_status.argtypes = [vp, ctypes.POINTER(i64)]
         lib.dpg_strerror.argtypes = [ctypes.c_int]
         lib.dpg_strerror.restype = ctypes.c_char_p
@@ -69,7 +70,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_flops_per_element.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.dpg_flops_per_element.restype = ctypes.c_double
         lib.dpg_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp]
-        for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate",
+        for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc",
                      "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak"]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -117,6 +118,13 @@ def dpg_integrate(space: int, p_trial: int, q_test: int, n_elem: int, vertices: 
                   out: int, stream: int) -> int:
     """Raw call with integer device pointers and a raw cudaStream_t handle."""
     return _L().dpg_integrate(space, p_trial, q_test, n_elem, vertices or None, coeffs or None, out, stream or None)
+
+
+def dpg_integrate_noalloc(space: int, p_trial: int, q_test: int, n_elem: int, vertices: int, coeffs: int,
+                          out: int, stream: int) -> int:
+    """Raw call of the allocation-free variant (fixed device scratch, no allocation)."""
+    return _L().dpg_integrate_noalloc(space, p_trial, q_test, n_elem, vertices or None, coeffs or None, out,
+                                      stream or None)
 
 
 def dpg_integrate_host(space: int, p_trial: int, q_test: int, n_elem: int, vertices: int, coeffs: int,

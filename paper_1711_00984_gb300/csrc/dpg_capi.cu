@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "dpg_kernels.h"
+#include "dpg_registry.h"
 #include "dpg_setup.h"
 
 using namespace dpg;
@@ -289,6 +290,39 @@ int read_status(DeviceState *ds, int64_t *first_bad) {
 
 }  // namespace
 
+int dpg::lookup_program_view(int space, int p_trial, int q, ProgramView *view) {
+    if (!valid_space(space)) return DPG_ERR_ARG;
+    if (q < 1 || q > DPG_MAX_Q) return DPG_ERR_RANGE;
+    const int base = space & 0xff;
+    int p = 0, split = 0;
+    if (base == S_B) {
+        if (p_trial < 1 || p_trial > q) return DPG_ERR_ARG;
+        p = p_trial;
+        split = (space & DPG_B_SPLIT) ? 1 : 0;
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto di = g_dev.find(dev);
+    if (di == g_dev.end()) return DPG_ERR_NOT_INIT;
+    DeviceState *ds = di->second.get();
+    auto it = ds->active_L.find(std::make_pair(base, q));
+    if (it == ds->active_L.end()) return DPG_ERR_NOT_INIT;
+    const int L = it->second;
+    auto tt = ds->tables.find(std::make_pair(q, L));
+    auto pt = ds->progs.find(ProgKey{ base, q, L, p, split });
+    if (tt == ds->tables.end() || pt == ds->progs.end()) return DPG_ERR_NOT_INIT;
+    view->prog = &pt->second->prog;
+    view->d_blocks = pt->second->d_blocks;
+    view->d_units = pt->second->d_units;
+    view->zeta = tt->second->zeta;
+    view->w = tt->second->w;
+    view->pp64 = tt->second->pp64;
+    view->pp32 = tt->second->pp32;
+    view->status = ds->status;
+    return DPG_OK;
+}
+
 extern "C" {
 
 int dpg_tables_init_L(int q, int L, int space) {
@@ -396,6 +430,7 @@ const char *dpg_strerror(int code) {
     case DPG_ERR_DEGENERATE: return "non-positive or non-finite Jacobian determinant";
     case DPG_ERR_NOT_AFFINE: return "element is not a parallelepiped";
     case DPG_ERR_NOMEM: return "out of memory";
+    case DPG_ERR_SCRATCH: return "request larger than the fixed scratch of dpg_integrate_noalloc";
     }
     return "unknown status";
 }
