@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-form sub-measurement")
+    ap.add_argument("--workload", default=None, choices=sorted(SECONDARY), help="secondary workload record")
     ap.add_argument("--only", default=None, help="profiling case: run only this space's call (H1, HCURL, HDIV, L2)")
     ap.add_argument("--map", default="general", choices=["general", "affine"], help="map of the --only case")
     ap.add_argument("--elems", type=int, default=0, help="elements of the --only case (default: all 512)")
@@ -278,12 +280,49 @@ def run_gpu(args):
     # ---- roofline of the dominant kernel (H(curl) general: geometry + contraction launch pair)
     fpe = dpg.dpg_flops_per_element(dpg.space_id("HCURL"), 0, Q)
     peak64 = dpg.dpg_measure_fma_peak(64, sh)
+    peak32 = dpg.dpg_measure_fma_peak(32, sh)
+    peak_dmma = dpg.dpg_measure_fma_peak(65, sh)
     achieved = fpe * ne / (dom_ms * 1e-3)
     roof = {"bound": "alu", "kernel": "sf_general_kernel<double> (H(curl), with its geom_kernel launch)",
             "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak64, "traffic": None,
             "peak_source": "FP64 FMA rate measured in this run by dpg_measure_fma_peak (MEASURED_PEAKS has no FP64 entry)",
-            "flops_per_launch": fpe * ne, "launch_ms": dom_ms}
+            "flops_per_launch": fpe * ne, "launch_ms": dom_ms,
+            "measured_alu_peaks_tflops": {"fp64_dfma": peak64 / 1e12, "fp32_ffma": peak32 / 1e12,
+                                          "fp64_mma_m8n8k4": peak_dmma / 1e12}}
+
+    # ---- the FP32 form on the same workload: time, speed-up, error against the FP64 result
+    fp32 = None
+    if not args.no_fp32:
+        outs32 = {k: torch.empty(o.shape, dtype=torch.float32, device=dev) for k, o in outs.items()}
+
+        def step32():
+            for mname, v, aff in maps:
+                for s_ in SPACES:
+                    code = dpg.dpg_integrate(dpg.space_id(s_, fp32=True, affine=aff), 0, Q, ne, v.data_ptr(),
+                                             coeffs[s_].data_ptr(), outs32[(mname, s_)].data_ptr(), sh)
+                    if code:
+                        raise dpg.DpgError(code, "dpg_integrate")
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step32()
+        ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            ev32[i][0].record(stream)
+            step32()
+            ev32[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms32 = float(np.mean([a.elapsed_time(b) for a, b in ev32]))
+        errs = {}
+        for k in outs:
+            ref = outs[k]
+            d = (outs32[k].double() - ref).flatten(1).norm(dim=1) / ref.flatten(1).norm(dim=1)
+            errs[f"{k[1]}_{k[0]}"] = float(d.max())
+        fp32 = {"ms_per_step": ms32, "value": world * elems_per_step / (ms32 * 1e-3), "unit": UNIT,
+                "speedup_vs_fp64": ms_per_step / ms32, "max_rel_frobenius_err_vs_fp64": max(errs.values()),
+                "target_err": 1e-5, "err_per_call": errs}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -298,11 +337,92 @@ def run_gpu(args):
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded meshgen: jittered 8^3 mesh + sheared parallelepipeds)",
                 "config": workload_config(), "output_gbs": world * out_bytes / (ms_per_step * 1e-3) / 1e9,
                 "gpu_launches": 12 * args.steps, "clocks": clk.summary(), "roofline": roof,
-                "cpu_baseline": cpu, "e2e": e2e,
+                "cpu_baseline": cpu, "e2e": e2e, "fp32_form": fp32,
                 "per_step_ms": {"min": min(step_ms), "max": max(step_ms)}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+SECONDARY = {
+    # name: (meshgen workload, q, L, [(space, p_trial, affine)])
+    "hcurl_q6_p4_16x16x16": ("hcurl_q6_p4_16x16x16", 6, 8, [("HCURL", 0, False), ("B", 4, False)]),
+    "q9_8x8x4": ("q9_8x8x4", 9, 11, [("H1", 0, False), ("HDIV", 0, False), ("H1", 0, True), ("HDIV", 0, True)]),
+}
+
+
+def run_secondary(args):
+    """Per-call FP64 and FP32 timings, rooflines and FP32 error of a secondary workload."""
+    import numpy as np
+    import torch
+    import paper_1711_00984_gb300 as dpg
+    from paper_1711_00984_gb300 import build as dbuild
+    from paper_1711_00984_gb300 import meshgen
+    dbuild.build()
+    dpg.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    wname, q, L, calls = SECONDARY[args.workload]
+    w = meshgen.workload(wname)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    peak64 = dpg.dpg_measure_fma_peak(64, sh)
+    peak32 = dpg.dpg_measure_fma_peak(32, sh)
+    hbm = 6771.1e9
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] * 1e9
+    except Exception:
+        pass
+    rec = {"workload": wname, "q": q, "L": L, "calls": []}
+    for space, p, aff in calls:
+        dpg.dpg_tables_init_L(q, L, space)
+        v = torch.from_numpy(w["verts_affine" if aff else "verts"]).to(dev)
+        ne = v.shape[0]
+        res = {"space": space, "p_trial": p, "map": "affine" if aff else "general", "elements": ne}
+        outs = {}
+        for fp32 in (False, True):
+            sid = dpg.space_id(space, fp32=fp32, affine=aff)
+            shape = (ne,) + dpg.matrix_shape(space, q, p)
+            out = torch.empty(shape, dtype=torch.float32 if fp32 else torch.float64, device=dev)
+
+            def call():
+                code = dpg.dpg_integrate(sid, p, q, ne, v.data_ptr(), 0, out.data_ptr(), sh)
+                if code:
+                    raise dpg.DpgError(code, "dpg_integrate")
+            for _ in range(args.warmup):
+                call()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for i in range(args.steps):
+                flush.fill_(i & 0xff)
+                ev[i][0].record(stream)
+                call()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            code, bad = dpg.dpg_sync_status(sh)
+            assert code == 0, (code, bad)
+            ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+            flops = dpg.dpg_flops_per_element(sid, p, q) * ne
+            nbytes = out.numel() * out.element_size()
+            t_alu = flops / (peak32 if fp32 else peak64)
+            t_mem = nbytes / hbm
+            key = "fp32" if fp32 else "fp64"
+            res[key] = {"ms": ms, "element_matrices_per_s": ne / (ms * 1e-3), "output_gbs": nbytes / (ms * 1e-3) / 1e9,
+                        "tflops": flops / (ms * 1e-3) / 1e12, "bound": "alu" if t_alu > t_mem else "hbm",
+                        "roofline_frac": max(t_alu, t_mem) / (ms * 1e-3)}
+            outs[key] = out
+        errs = []
+        for e0 in range(0, ne, 64):
+            a = outs["fp32"][e0:e0 + 64].double()
+            b = outs["fp64"][e0:e0 + 64]
+            errs.append(((a - b).flatten(1).norm(dim=1) / b.flatten(1).norm(dim=1)).max().item())
+        res["fp32_max_rel_frobenius_err_vs_fp64"] = max(errs)
+        res["fp32_speedup"] = res["fp64"]["ms"] / res["fp32"]["ms"]
+        rec["calls"].append(res)
+        del outs
+        torch.cuda.empty_cache()
+    rec["measured_alu_peaks_tflops"] = {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12}
+    print(json.dumps(rec), flush=True)
 
 
 def run_case(args):
@@ -334,6 +454,8 @@ def main():
     args = parse()
     if args.only:
         run_case(args)
+    elif args.workload:
+        run_secondary(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

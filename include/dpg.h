@@ -176,9 +176,10 @@ const char *dpg_last_cuda_error(void);
 double dpg_flops_per_element(int space, int p_trial, int q_test);
 
 /* Not part of the paper's method: measure the device's peak fused multiply-add rate in
- * FP64 (precision = 64) or FP32 (precision = 32) with a register-resident FMA loop on
- * `stream`; writes the flop rate (2 flops per FMA) in flop/s to *flops.  Synchronous.
- * Used only to give the ALU roofline a measured denominator. */
+ * FP64 (precision = 64) or FP32 (precision = 32) with a register-resident FMA loop, or
+ * the FP64 tensor-core rate (precision = 65, mma.sync m8n8k4 FP64), on `stream`; writes
+ * the flop rate (2 flops per multiply-add) in flop/s to *flops.  Synchronous.  Used only
+ * to give the ALU roofline a measured denominator. */
 int dpg_measure_fma_peak(int precision, void *stream, double *flops);
 
 #ifdef __cplusplus

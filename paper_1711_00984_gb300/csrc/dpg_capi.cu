@@ -23,6 +23,7 @@ namespace {
 
 constexpr size_t kWorkspaceLimit = size_t(512) << 20;   // metric fields per launch chunk
 int g_max_dyn_smem = 0;                                  // per launch, set at device set-up
+int g_num_sms = 152;                                     // set at device set-up
 
 struct TableEntry {
     HostTables host;
@@ -31,9 +32,17 @@ struct TableEntry {
 };
 
 struct ProgEntry {
-    Program prog;
+    Program prog;                   // general path: per-block contraction order
     BlockDesc *d_blocks = nullptr;
     Unit *d_units = nullptr;
+    Program prog_aff;               // affine path: the paper's direction order
+    BlockDesc *d_blocks_aff = nullptr;
+    Unit *d_units_aff = nullptr;
+    Program prog32;                 // FP32 general path: stage A on xi_3
+    BlockDesc *d_blocks32 = nullptr;
+    Unit *d_units32 = nullptr;
+    int max_nc1_32 = 0;             // largest stage-C column extent of prog32
+    int *d_block_units32 = nullptr; // [nblock + 1] unit ranges of prog32
     size_t smem_aff = 0;            // values of the affine kernel's shared memory
 };
 
@@ -98,6 +107,7 @@ int device_state(DeviceState **out) {
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CK(init_kernel_attributes(optin));
     g_max_dyn_smem = max_dynamic_smem(optin);
+    CK(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     *out = st.get();
     g_dev[dev] = std::move(st);
     return DPG_OK;
@@ -129,17 +139,33 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
     if (it != ds->progs.end()) { *out = it->second.get(); return DPG_OK; }
     auto pe = std::make_unique<ProgEntry>();
     pe->prog = make_program(space, q, L, p, split != 0, tab);
+    pe->prog_aff = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL);
+    pe->prog32 = make_program(space, q, L, p, split != 0, tab, ORDER_A3);
     const Program &pr = pe->prog;
     if (pr.smem_values * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     int r;
     if ((r = upload(pr.blocks, (size_t)pr.nblock, &pe->d_blocks))) return r;
     if ((r = upload(pr.units.data(), pr.units.size(), &pe->d_units))) return r;
+    const Program &pa = pe->prog_aff;
+    if ((r = upload(pa.blocks, (size_t)pa.nblock, &pe->d_blocks_aff))) return r;
+    if ((r = upload(pa.units.data(), pa.units.size(), &pe->d_units_aff))) return r;
     size_t m = 0;
-    for (int k = 0; k < pr.nblock; ++k) {
-        const BlockDesc &b = pr.blocks[k];
-        m = std::max(m, (size_t)b.ng * b.nr[1] * b.nc[1] * pr.nj);
+    for (int k = 0; k < pa.nblock; ++k) {
+        const BlockDesc &b = pa.blocks[k];
+        m = std::max(m, affine_smem_values(b.ng, b.nr[0], b.nr[1], b.nc[0], b.nc[1], pa.nj));
     }
+    if (m * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     pe->smem_aff = m;
+    const Program &p3 = pe->prog32;
+    if (p3.smem_bytes > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
+    if ((r = upload(p3.blocks, (size_t)p3.nblock, &pe->d_blocks32))) return r;
+    if ((r = upload(p3.units.data(), p3.units.size(), &pe->d_units32))) return r;
+    for (int k = 0; k < p3.nblock; ++k)
+        pe->max_nc1_32 = std::max(pe->max_nc1_32, p3.blocks[k].nc[p3.blocks[k].dir[0]]);
+    std::vector<int> ubeg(p3.nblock + 1, 0);
+    for (const Unit &u : p3.units) ubeg[u.block + 1]++;
+    for (int k = 0; k < p3.nblock; ++k) ubeg[k + 1] += ubeg[k];
+    if ((r = upload(ubeg.data(), ubeg.size(), &pe->d_block_units32))) return r;
     *out = pe.get();
     ds->progs[key] = std::move(pe);
     return DPG_OK;
@@ -150,7 +176,11 @@ void free_device_state(DeviceState &ds) {
         TableEntry &t = *kv.second;
         cudaFree(t.zeta); cudaFree(t.w); cudaFree(t.pp64); cudaFree(t.pp32); cudaFree(t.F64); cudaFree(t.F32);
     }
-    for (auto &kv : ds.progs) { cudaFree(kv.second->d_blocks); cudaFree(kv.second->d_units); }
+    for (auto &kv : ds.progs) {
+        cudaFree(kv.second->d_blocks); cudaFree(kv.second->d_units);
+        cudaFree(kv.second->d_blocks_aff); cudaFree(kv.second->d_units_aff);
+        cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
+    }
     ds.tables.clear(); ds.progs.clear(); ds.active_L.clear();
 }
 
@@ -193,7 +223,8 @@ int resolve(int space, int p_trial, int q, ProgEntry **pe, TableEntry **te, Devi
 template <typename T>
 int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
                 const double *coeffs, T *out, cudaStream_t s) {
-    const Program &pr = pe->prog;
+    constexpr bool f32 = sizeof(T) == 4;
+    const Program &pr = f32 ? pe->prog32 : pe->prog;
     const int L = pr.L, L3 = L * L * L;
     const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
     const size_t per_elem = (size_t)pr.nfields * L3 * sizeof(T);
@@ -216,15 +247,32 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
         g.fields = ws; g.status = ds->status;
         cudaError_t le = launch_geom<T>(g, s);
         if (le != cudaSuccess) { rc = cuda_fail(le, "geom_kernel launch", __LINE__); break; }
-        SfParams<T> sp;
-        sp.blocks = pe->d_blocks; sp.units = pe->d_units; sp.nunits = (int)pr.units.size();
-        sp.L = L; sp.nfields = pr.nfields;
-        if constexpr (sizeof(T) == 8) sp.pp = te->pp64; else sp.pp = te->pp32;
-        sp.fields = reinterpret_cast<const T *>(ws);
-        sp.out = out + e0 * mat;
-        sp.mat_stride = mat; sp.ld = pr.cols; sp.n_elem = ne;
-        le = launch_general<T>(sp, pr.smem_values * sizeof(T), s);
-        if (le != cudaSuccess) { rc = cuda_fail(le, "sf_general_kernel launch", __LINE__); break; }
+        if constexpr (f32) {
+            SfParams32 sp;
+            sp.blocks = pe->d_blocks32; sp.units = pe->d_units32; sp.block_unit_begin = pe->d_block_units32;
+            sp.nblock = pr.nblock; sp.nj_max = pr.nj;
+            // about four waves of two CTAs per SM, each CTA a chunk of elements of one block
+            const int64_t target = (int64_t)g_num_sms * 2 * 4;
+            int64_t epc = (ne * pr.nblock + target - 1) / target;
+            sp.elems_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(epc, 1 << 20));
+            sp.L = L; sp.nfields = pr.nfields;
+            sp.pp = te->pp32;
+            sp.fields = reinterpret_cast<const float *>(ws);
+            sp.out = reinterpret_cast<float *>(out + e0 * mat);
+            sp.mat_stride = mat; sp.ld = pr.cols; sp.n_elem = ne;
+            le = launch_general_f32(sp, pr.smem_bytes, pe->max_nc1_32, s);
+        } else {
+            SfParams<T> sp;
+            sp.blocks = pe->d_blocks; sp.units = pe->d_units;
+            sp.nunits = (int)pr.units.size();
+            sp.L = L; sp.nfields = pr.nfields;
+            sp.pp = te->pp64;
+            sp.fields = reinterpret_cast<const T *>(ws);
+            sp.out = out + e0 * mat;
+            sp.mat_stride = mat; sp.ld = pr.cols; sp.n_elem = ne;
+            le = launch_general<T>(sp, pr.smem_values * sizeof(T), s);
+        }
+        if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
     }
     cudaError_t fe = cudaFreeAsync(ws, s);
     if (fe != cudaSuccess && rc == DPG_OK) rc = cuda_fail(fe, "cudaFreeAsync", __LINE__);
@@ -234,24 +282,31 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
 template <typename T>
 int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
                const double *coeffs, T *out, cudaStream_t s) {
-    const Program &pr = pe->prog;
+    const Program &pr = pe->prog_aff;
     const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
     const int64_t per_launch = INT_MAX / (int64_t)pr.units.size();
-    for (int64_t e0 = 0; e0 < n_elem; e0 += per_launch) {
+    void *consts = nullptr;
+    CK(cudaMallocFromPoolAsync(&consts, (size_t)n_elem * AFF_CONST_STRIDE * sizeof(double), ds->pool, s));
+    AffConstParams cp;
+    cp.space = pr.space; cp.n_elem = n_elem; cp.elem_base = 0;
+    cp.verts = verts; cp.coeffs = coeffs; cp.consts = (double *)consts; cp.status = ds->status;
+    int rc = DPG_OK;
+    cudaError_t le = launch_affine_const(cp, s);
+    if (le != cudaSuccess) rc = cuda_fail(le, "affine_const_kernel launch", __LINE__);
+    for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK; e0 += per_launch) {
         const int64_t ne = std::min(per_launch, n_elem - e0);
         AffParams<T> ap;
-        ap.blocks = pe->d_blocks; ap.units = pe->d_units; ap.nunits = (int)pr.units.size();
-        ap.space = pr.space;
+        ap.blocks = pe->d_blocks_aff; ap.units = pe->d_units_aff; ap.nunits = (int)pr.units.size();
         if constexpr (sizeof(T) == 8) ap.F = te->F64; else ap.F = te->F32;
-        ap.verts = verts + 24 * e0;
-        ap.coeffs = coeffs ? coeffs + 2 * e0 : nullptr;
+        ap.consts = (const double *)consts + AFF_CONST_STRIDE * e0;
         ap.out = out + e0 * mat;
-        ap.mat_stride = mat; ap.ld = pr.cols; ap.n_elem = ne; ap.elem_base = e0;
-        ap.status = ds->status;
-        cudaError_t le = launch_affine<T>(ap, pe->smem_aff * sizeof(T), s);
-        if (le != cudaSuccess) return cuda_fail(le, "sf_affine_kernel launch", __LINE__);
+        ap.mat_stride = mat; ap.ld = pr.cols; ap.n_elem = ne;
+        le = launch_affine<T>(ap, pe->smem_aff * sizeof(T), s);
+        if (le != cudaSuccess) rc = cuda_fail(le, "sf_affine_kernel launch", __LINE__);
     }
-    return DPG_OK;
+    cudaError_t fe = cudaFreeAsync(consts, s);
+    if (fe != cudaSuccess && rc == DPG_OK) rc = cuda_fail(fe, "cudaFreeAsync", __LINE__);
+    return rc;
 }
 
 int integrate_locked(int space, int p_trial, int q_test, int64_t n_elem, const double *vertices,
@@ -439,11 +494,12 @@ double dpg_flops_per_element(int space, int p_trial, int q_test) {
     std::lock_guard<std::mutex> lk(g_mu);
     ProgEntry *pe; TableEntry *te; DeviceState *ds;
     if (resolve(space, p_trial, q_test, &pe, &te, &ds) != DPG_OK) return -1.0;
-    return (space & DPG_MAP_AFFINE) ? pe->prog.flops_affine : pe->prog.flops;
+    if (space & DPG_MAP_AFFINE) return pe->prog_aff.flops_affine;
+    return (space & DPG_FP32) ? pe->prog32.flops : pe->prog.flops;
 }
 
 int dpg_measure_fma_peak(int precision, void *stream, double *flops) {
-    if (!flops || (precision != 32 && precision != 64)) return DPG_ERR_ARG;
+    if (!flops || (precision != 32 && precision != 64 && precision != 65)) return DPG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
@@ -457,6 +513,7 @@ int dpg_measure_fma_peak(int precision, void *stream, double *flops) {
     auto run = [&](int iters, float *ms) -> int {
         CK(cudaEventRecord(a, s));
         cudaError_t e = precision == 64 ? launch_fma_peak<double>((double *)buf, blocks, iters, s)
+                      : precision == 65 ? launch_dmma_peak((double *)buf, blocks, iters, s)
                                         : launch_fma_peak<float>((float *)buf, blocks, iters, s);
         if (e != cudaSuccess) return DPG_ERR_CUDA;
         CK(cudaEventRecord(b, s));
@@ -471,7 +528,9 @@ int dpg_measure_fma_peak(int precision, void *stream, double *flops) {
     double best = 0.0;
     for (int rep = 0; rep < 5 && r == DPG_OK; ++rep) {
         r = run(iters, &ms);
-        const double f = 2.0 * 8 * 16 * (double)iters * 256.0 * blocks / (ms * 1e-3);
+        // flops per thread and iteration: 8 chains x 16 FMAs x 2, or 8 mma x 512 / 32 lanes
+        const double per = precision == 65 ? 128.0 : 256.0;
+        const double f = per * (double)iters * 256.0 * blocks / (ms * 1e-3);
         if (f > best) best = f;
     }
     cudaEventDestroy(a); cudaEventDestroy(b); cudaFree(buf);

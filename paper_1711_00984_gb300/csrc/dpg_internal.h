@@ -72,6 +72,34 @@ struct Unit {
     int16_t block, i3, j3b, nj;   // i3 / j3: indices along the stage-A direction dir[2]
 };
 
+// Shared-memory layout (in floats, every region a multiple of 4) of the FP32 general
+// kernel for one block and a chunk of nj stage-A partners.  The stage-A direction is
+// xi_3 (dir[2] == 2), so a tile row is one contiguous run of the output.
+struct F32Layout {
+    int nr1, nr2, nc1, nc2;          // stage-C / stage-B extents (rows, columns)
+    int nc1p, n22, n22p, nx, nx4;    // padded j1 range, (i2,j2) pairs, (j2,jj) pairs
+    int nrow, ncol, ldt;             // output tile [nrow][ldt], ncol used columns
+    int oP1, oP2, oP3, oA, oB, oT, total;
+};
+DPG_HD inline int r4i(int v) { return (v + 3) & ~3; }
+DPG_HD inline F32Layout f32_layout(const BlockDesc &b, int L, int nj) {
+    F32Layout f;
+    const int dC = b.dir[0], dB = b.dir[1];
+    f.nr1 = b.nr[dC]; f.nr2 = b.nr[dB]; f.nc1 = b.nc[dC]; f.nc2 = b.nc[dB];
+    f.nc1p = r4i(f.nc1);
+    f.n22 = f.nr2 * f.nc2; f.n22p = r4i(f.n22);
+    f.nx = f.nc2 * nj; f.nx4 = r4i(f.nx);
+    f.nrow = f.nr1 * f.nr2; f.ncol = f.nc1 * f.nc2 * nj; f.ldt = f.ncol | 1;
+    f.oP1 = 0;                                                   // [ng][nr1][L][nc1p]
+    f.oP2 = f.oP1 + b.ng * f.nr1 * L * f.nc1p;                   // [np2][L][n22p]
+    f.oP3 = f.oP2 + b.np2 * L * f.n22p;                          // [nterm][nj][L]
+    f.oA = f.oP3 + r4i(b.nterm * nj * L);                        // [nh][L][L][8]
+    f.oB = f.oA + b.nh * L * L * 8;                              // [ng][L][nr2][nx4]
+    f.oT = f.oB + b.ng * L * f.nr2 * f.nx4;                      // [nrow][ldt]
+    f.total = f.oT + r4i(f.nrow * f.ldt);
+    return f;
+}
+
 // Device-resident tables of one (q, L).
 struct DevTables {
     int q, L;

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(256) geom_kernel(GeomParams p) {
 // general sum factorization
 // --------------------------------------------------------------------------------------
 __device__ __forceinline__ size_t r4(size_t v) { return (v + 3) & ~size_t(3); }
+inline size_t r4_host(size_t v) { return (v + 3) & ~size_t(3); }
 
 __device__ __forceinline__ void load_block(const BlockDesc *src, BlockDesc &dst) {
     const int *s = reinterpret_cast<const int *>(src);
@@ -220,95 +221,383 @@ __global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
     const int psA = dA == 0 ? L2 : (dA == 1 ? L : 1);
 
     // ---- stage A (Eq. 2.23): A_h(l, m, jj) = sum_{t in h} sum_n M_t(l,m,n) P3_t(jj, n),
-    //      l along dC, m along dB, n along dA
+    //      l along dC, m along dB, n along dA; one output per thread (no idle lanes)
     const T *fe = p.fields + (size_t)e * p.nfields * L3;
-    for (int it = tid; it < nh * L2; it += nth) {
-        const int h = it / L2, lm = it - h * L2;
+    for (int it = tid; it < nh * L2 * nj; it += nth) {
+        const int jj = it % nj, r = it / nj;
+        const int lm = r % L2, h = r / L2;
         const int lq = lm / L, mq = lm - lq * L;
-        T acc[NJMAX];
-#pragma unroll
-        for (int jj = 0; jj < NJMAX; ++jj) acc[jj] = T(0);
+        T acc = T(0);
         for (int t = 0; t < nterm; ++t) {
             if (bd.term[t].h != h) continue;
             const T *M = fe + (size_t)bd.term[t].field * L3 + (size_t)lq * psC + (size_t)mq * psB;
-            const T *P3t = P3 + (size_t)t * nj * L;
-            for (int n = 0; n < L; ++n) {
-                const T mv = M[(size_t)n * psA];
-#pragma unroll
-                for (int jj = 0; jj < NJMAX; ++jj)
-                    if (jj < nj) acc[jj] = fma(mv, P3t[jj * L + n], acc[jj]);
-            }
+            const T *P3t = P3 + ((size_t)t * nj + jj) * L;
+            for (int n = 0; n < L; ++n) acc = fma(M[(size_t)n * psA], P3t[n], acc);
         }
-#pragma unroll
-        for (int jj = 0; jj < NJMAX; ++jj)
-            if (jj < nj) A[(size_t)it * nj + jj] = acc[jj];
+        A[it] = acc;
     }
     __syncthreads();
 
     // ---- stage B (Eq. 2.24): B_g(l, i2, j2, jj) = sum_{h in g} sum_m P2_h(i2,j2,m) A_h(l,m,jj)
-    for (int it = tid; it < ng * L * n22; it += nth) {
-        const int ij2 = it % n22, r = it / n22;
-        const int l = r % L, g = r / L;
-        T acc[NJMAX];
-#pragma unroll
-        for (int jj = 0; jj < NJMAX; ++jj) acc[jj] = T(0);
+    for (int it = tid; it < ng * L * n22 * nj; it += nth) {
+        const int jj = it % nj, r = it / nj;
+        const int ij2 = r % n22, r2 = r / n22;
+        const int l = r2 % L, g = r2 / L;
+        T acc = T(0);
         for (int h = 0; h < nh; ++h) {
             if (bd.h_g[h] != g) continue;
             const T *P2h = P2 + ((size_t)bd.h_p2[h] * n22 + ij2) * L;
-            const T *Ah = A + ((size_t)h * L2 + (size_t)l * L) * nj;
-            for (int m = 0; m < L; ++m) {
-                const T pv = P2h[m];
-#pragma unroll
-                for (int jj = 0; jj < NJMAX; ++jj)
-                    if (jj < nj) acc[jj] = fma(pv, Ah[m * nj + jj], acc[jj]);
-            }
+            const T *Ah = A + ((size_t)h * L2 + (size_t)l * L) * nj + jj;
+            for (int m = 0; m < L; ++m) acc = fma(P2h[m], Ah[m * nj], acc);
         }
-#pragma unroll
-        for (int jj = 0; jj < NJMAX; ++jj)
-            if (jj < nj) Bs[(size_t)it * nj + jj] = acc[jj];
+        Bs[it] = acc;
     }
     __syncthreads();
 
     // ---- stage C (Eq. 2.25) and symmetric fill
-    const int nrow = nr1 * nr2, ncol = nc1 * nc2 * nj;
+    const int nrow = nr1 * nr2, ncj = nc1 * nc2;
     T *o = p.out + (size_t)e * p.mat_stride + bd.base;
     const int64_t ld = p.ld;
     // output strides of each direction (index maps Eqs. 2.53 / 2.71, i1 fastest)
-    const int sr[3] = { 1, bd.nr[0], bd.nr[0] * bd.nr[1] };
-    const int sc[3] = { 1, bd.nc[0], bd.nc[0] * bd.nc[1] };
-    const int64_t R0 = bd.row_off + (int64_t)i3 * sr[dA];
-    const int64_t C0 = bd.col_off + (int64_t)j3b * sc[dA];
+    auto stride = [](int d, int n0, int n1) { return d == 0 ? 1 : (d == 1 ? n0 : n0 * n1); };
+    const int srC = stride(dC, bd.nr[0], bd.nr[1]), srB = stride(dB, bd.nr[0], bd.nr[1]);
+    const int scC = stride(dC, bd.nc[0], bd.nc[1]), scB = stride(dB, bd.nc[0], bd.nc[1]);
+    const int scA = stride(dA, bd.nc[0], bd.nc[1]);
+    const int64_t R0 = bd.row_off + (int64_t)i3 * stride(dA, bd.nr[0], bd.nr[1]);
+    const int64_t C0 = bd.col_off + (int64_t)j3b * scA;
     const bool mirror_all = bd.sym == 2, mirror_off = bd.sym == 1;
-    for (int it = tid; it < nrow * ncol; it += nth) {
-        const int row = it / ncol, col = it - row * ncol;
-        const int i1 = row % nr1, i2 = row / nr1;
-        const int j1 = col % nc1, c2 = col / nc1;
-        const int j2 = c2 % nc2, jj = c2 / nc2;
-        const int64_t R = R0 + (int64_t)i1 * sr[dC] + (int64_t)i2 * sr[dB];
-        const int64_t C = C0 + (int64_t)j1 * sc[dC] + (int64_t)j2 * sc[dB] + (int64_t)jj * sc[dA];
-        // on a tile of the diagonal (iA == jA) of a symmetric matrix only R <= C is
-        // computed and mirrored, so the result is exactly symmetric
-        const bool diag_tile = mirror_off && j3b + jj == i3;
-        if (diag_tile && R > C) continue;
+    // jj of the diagonal sub-tile (iA == jA of a diagonal block), or -1: only its upper
+    // triangle (R <= C) is computed and mirrored, so the matrix is exactly symmetric
+    const int jd = (mirror_off && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
+    const int njf = nj - (jd >= 0 ? 1 : 0);
+    const int n_full = nrow * ncj * njf;
+    const int n_tri = jd >= 0 ? nrow * (nrow + 1) / 2 : 0;
+    // rank order of a tile position p (increasing R) for the triangle enumeration
+    const bool c_fast = srC < srB;
+    for (int it = tid; it < n_full + n_tri; it += nth) {
+        int i1, i2, j1, j2, jj;
+        if (it < n_full) {
+            const int row = it / (ncj * njf), col = it - row * (ncj * njf);
+            i1 = row % nr1; i2 = row / nr1;
+            const int cj = col % ncj, jx = col / ncj;
+            j1 = cj % nc1; j2 = cj / nc1;
+            jj = (jd >= 0 && jx >= jd) ? jx + 1 : jx;
+        } else {
+            const int t = it - n_full;
+            int pc = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while (pc * (pc + 1) / 2 > t) --pc;
+            while ((pc + 1) * (pc + 2) / 2 <= t) ++pc;
+            const int pr = t - pc * (pc + 1) / 2;
+            if (c_fast) { i1 = pr % nr1; i2 = pr / nr1; j1 = pc % nc1; j2 = pc / nc1; }
+            else        { i2 = pr % nr2; i1 = pr / nr2; j2 = pc % nc2; j1 = pc / nc2; }
+            jj = jd;
+        }
         T acc = T(0);
         for (int g = 0; g < ng; ++g) {
             const T *P1g = P1 + (((size_t)g * nr1 + i1) * nc1 + j1) * L;
             const T *Bg = Bs + (((size_t)g * L * nr2 + i2) * nc2 + j2) * nj + jj;
             for (int l = 0; l < L; ++l) acc = fma(P1g[l], Bg[(size_t)l * n22 * nj], acc);
         }
+        const int64_t R = R0 + (int64_t)i1 * srC + (int64_t)i2 * srB;
+        const int64_t C = C0 + (int64_t)j1 * scC + (int64_t)j2 * scB + (int64_t)jj * scA;
         o[R * ld + C] = acc;
         if (mirror_all || (mirror_off && R != C)) o[C * ld + R] = acc;
+    }
+}
+
+
+// --------------------------------------------------------------------------------------
+// FP32 general sum factorization (stage A fixed on xi_3)
+// --------------------------------------------------------------------------------------
+// Same stages as sf_general_kernel, built for the FP32 pipe (64x the FP64 rate).  A CTA
+// keeps one block resident -- its stage-C and stage-B tables are loaded once -- and
+// walks a chunk of elements and every work unit (i3, j3 chunk) of the block.  Stage B
+// keeps a 4 (i2,j2) x 4 (jj) register tile per thread with the A values broadcast across
+// the warp; stage C keeps all j1 (padded to 4) x 4 (j2,jj) per thread with the P1 values
+// broadcast; the output tile is staged in shared memory and written as contiguous row
+// runs (the tile) and column runs (its mirror).  Integer divisions by CTA-uniform
+// divisors use multiply-high magic numbers.
+
+// floor(x / d) for 0 <= x < 2^20 and 1 <= d < 2^12: m = ceil(2^32 / d), q = umulhi(x, m)
+__device__ __forceinline__ unsigned div_magic(int d) {
+    return d <= 1 ? 0u : (unsigned)((0x100000000ull + (unsigned)d - 1u) / (unsigned)d);
+}
+__device__ __forceinline__ int fdiv(int x, unsigned m) { return m ? (int)__umulhi((unsigned)x, m) : x; }
+
+constexpr int F32_NXMAX = 128;     // (j2, jj) pairs per unit: nc2 * nj <= 13 * 8
+constexpr int F32_NIJMAX = 176;    // (i2, j2) pairs: nr2 * nc2 <= 13 * 13
+
+template <int NC4MAX>
+__global__ void __launch_bounds__(256, 2) sf_general_f32_kernel(SfParams32 p) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    __shared__ BlockDesc bd;
+    __shared__ int xbase[F32_NXMAX];       // tile column of (j1 = 0, x = j2 + nc2 jj)
+    __shared__ int ijtab[F32_NIJMAX];      // (i2, j2) of ij = i2 nc2 + j2, packed i2 | j2 << 16
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int k = blockIdx.x % p.nblock;
+    const int64_t e0 = (int64_t)(blockIdx.x / p.nblock) * p.elems_per_cta;
+    const int64_t e1 = min(e0 + (int64_t)p.elems_per_cta, p.n_elem);
+    if (e0 >= e1) return;
+    load_block(p.blocks + k, bd);
+    __syncthreads();
+
+    const int L = p.L, L2 = L * L, L3 = L2 * L;
+    const F32Layout f = f32_layout(bd, L, p.nj_max);
+    const int dC = bd.dir[0], dB = bd.dir[1];
+    const int nr1 = f.nr1, nr2 = f.nr2, nc1 = f.nc1, nc2 = f.nc2;
+    const int ng = bd.ng, nh = bd.nh, np2 = bd.np2, nterm = bd.nterm;
+    const int nc1p = f.nc1p, n22 = f.n22, n22p = f.n22p, nx4 = f.nx4, ldt = f.ldt;
+    float *P1 = sm + f.oP1, *P2 = sm + f.oP2, *P3 = sm + f.oP3, *A = sm + f.oA, *Bs = sm + f.oB, *tile = sm + f.oT;
+    const unsigned mL = div_magic(L), mL2 = div_magic(L2), mnc1p = div_magic(nc1p), mnc2 = div_magic(nc2),
+                   mnr1 = div_magic(nr1), mnr2 = div_magic(nr2), mn22p = div_magic(n22p);
+    auto stride = [](int d, int n0, int n1) { return d == 0 ? 1 : (d == 1 ? n0 : n0 * n1); };
+    const int srC = stride(dC, bd.nr[0], bd.nr[1]), srB = stride(dB, bd.nr[0], bd.nr[1]);
+    const int scC = stride(dC, bd.nc[0], bd.nc[1]), scB = stride(dB, bd.nc[0], bd.nc[1]);
+    const int scA = bd.nc[0] * bd.nc[1];
+
+    const float *pp = p.pp;
+    auto PP = [&](int pair, int i, int j) -> const float * {
+        return pp + (((size_t)pair * NQ1 + i) * NQ1 + j) * L;
+    };
+    for (int it = tid; it < ng * nr1 * L * nc1p; it += nth) {          // P1[g][i1][l][j1]
+        const int r = fdiv(it, mnc1p), j1 = it - r * nc1p;
+        const int r2 = fdiv(r, mL), l = r - r2 * L;
+        const int g = fdiv(r2, mnr1), i1 = r2 - g * nr1;
+        P1[it] = j1 < nc1 ? PP(bd.g_pair[g], i1, j1)[l] : 0.0f;
+    }
+    for (int it = tid; it < np2 * L * n22p; it += nth) {               // P2[s][m][i2 nc2 + j2]
+        const int r = fdiv(it, mn22p), ij = it - r * n22p;
+        const int s2 = fdiv(r, mL), m = r - s2 * L;
+        const int i2 = fdiv(ij, mnc2), j2 = ij - i2 * nc2;
+        P2[it] = ij < n22 ? PP(bd.p2_pair[s2], i2, j2)[m] : 0.0f;
+    }
+    for (int x = tid; x < nc2 * p.nj_max; x += nth) {
+        const int jj = fdiv(x, mnc2), j2 = x - jj * nc2;
+        xbase[x] = j2 * scB + jj * scA;
+    }
+    for (int ij = tid; ij < n22; ij += nth) {
+        const int i2 = fdiv(ij, mnc2);
+        ijtab[ij] = i2 | ((ij - i2 * nc2) << 16);
+    }
+
+    const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
+    const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
+    const int psC = dC == 0 ? L2 : L, psB = dB == 0 ? L2 : L;
+    const int nq = n22p >> 2, nc4 = nc1p >> 2;
+    const unsigned mnq = div_magic(nq);
+    const int mc = nc1 * nc2;                                           // tile columns per jj
+    for (int64_t e = e0; e < e1; ++e) {
+        const float *fe = p.fields + (size_t)e * p.nfields * L3;
+        float *o = p.out + (size_t)e * p.mat_stride + bd.base;
+        for (int ui = ub; ui < ue; ++ui) {
+            const Unit u = p.units[ui];
+            const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
+            const unsigned mnj = div_magic(nj);
+            __syncthreads();                  // previous unit's tile / tables are consumed
+            for (int it = tid; it < nterm * nj * L; it += nth) {       // P3[t][jj][n]
+                const int r = fdiv(it, mL), n = it - r * L;
+                const int t = fdiv(r, mnj), jj = r - t * nj;
+                const TermDesc &td = bd.term[t];
+                const float v = PP(3 * td.kr[2] + td.kc[2], i3, j3b + jj)[n];
+                P3[it] = td.sign > 0 ? v : -v;
+            }
+            for (int it = tid; it < ng * L * nr2 * nx4; it += nth) Bs[it] = 0.0f;
+            __syncthreads();
+
+            // ---- stage A: A[h][l][m][jj] (jj padded to 8 with zeros); n runs along xi_3
+            for (int it = tid; it < nh * L2 * 8; it += nth) {
+                const int jj = it & 7, r = it >> 3;
+                const int h = fdiv(r, mL2), lm = r - h * L2;
+                float acc = 0.0f;
+                if (jj < nj) {
+                    const int lq = fdiv(lm, mL), mq = lm - lq * L;
+                    for (int t = 0; t < nterm; ++t) {
+                        if (bd.term[t].h != h) continue;
+                        const float *M = fe + (size_t)bd.term[t].field * L3 + lq * psC + mq * psB;
+                        const float *P3t = P3 + (t * nj + jj) * L;
+                        for (int n = 0; n < L; ++n) acc = fmaf(M[n], P3t[n], acc);
+                    }
+                }
+                A[it] = acc;
+            }
+            __syncthreads();
+
+            // ---- stage B: thread = (g, l, group of 4 (i2,j2), half of the 8 jj)
+            for (int it = tid; it < ng * L * nq * 2; it += nth) {
+                const int half = it & 1, r = it >> 1;
+                const int r2 = fdiv(r, mnq), q4 = r - r2 * nq;
+                const int g = fdiv(r2, mL), l = r2 - g * L;
+                if (4 * half >= nj) continue;
+                float acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+                for (int h = 0; h < nh; ++h) {
+                    if (bd.h_g[h] != g) continue;
+                    const float4 *P2h = reinterpret_cast<const float4 *>(P2 + bd.h_p2[h] * L * n22p) + q4;
+                    const float4 *Ah = reinterpret_cast<const float4 *>(A + ((h * L + l) * L) * 8) + half;
+                    for (int m = 0; m < L; ++m) {
+                        const float4 pv = P2h[m * nq];
+                        const float4 av = Ah[2 * m];
+                        const float pa[4] = { pv.x, pv.y, pv.z, pv.w };
+                        const float aa[4] = { av.x, av.y, av.z, av.w };
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], aa[b], acc[a][b]);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int ij = 4 * q4 + a;
+                    if (ij < n22) {
+                        const int pk = ijtab[ij], i2 = pk & 0xffff, j2 = pk >> 16;
+                        float *dst = Bs + ((g * L + l) * nr2 + i2) * nx4 + j2;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            if (4 * half + b < nj) dst[(4 * half + b) * nc2] = acc[a][b];
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ---- stage C: thread = (i1, i2, group of 4 x = j2 + nc2 jj), all j1 in registers
+            const int nx = nc2 * nj, nxg = (nx + 3) >> 2;
+            const unsigned mnxg = div_magic(nxg);
+            for (int it = tid; it < nr1 * nr2 * nxg; it += nth) {
+                const int r = fdiv(it, mnxg), xg = it - r * nxg;
+                const int i1 = fdiv(r, mnr2), i2 = r - i1 * nr2;
+                float acc[4 * NC4MAX][4];
+#pragma unroll
+                for (int a = 0; a < 4 * NC4MAX; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+                for (int g = 0; g < ng; ++g) {
+                    const float4 *P1g = reinterpret_cast<const float4 *>(P1 + ((g * nr1 + i1) * L) * nc1p);
+                    const float4 *Bg = reinterpret_cast<const float4 *>(Bs + (g * L * nr2 + i2) * nx4) + xg;
+                    for (int l = 0; l < L; ++l) {
+                        const float4 bv = Bg[l * nr2 * (nx4 >> 2)];
+                        const float bb[4] = { bv.x, bv.y, bv.z, bv.w };
+#pragma unroll
+                        for (int c4 = 0; c4 < NC4MAX; ++c4) {
+                            if (c4 < nc4) {
+                                const float4 av = P1g[l * nc4 + c4];
+                                const float aa[4] = { av.x, av.y, av.z, av.w };
+#pragma unroll
+                                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                                    for (int b = 0; b < 4; ++b)
+                                        acc[4 * c4 + a][b] = fmaf(aa[a], bb[b], acc[4 * c4 + a][b]);
+                            }
+                        }
+                    }
+                }
+                float *trow = tile + (i1 * srC + i2 * srB) * ldt;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int x = 4 * xg + b;
+                    if (x < nx) {
+                        float *tb = trow + xbase[x];
+#pragma unroll
+                        for (int a = 0; a < 4 * NC4MAX; ++a)
+                            if (a < nc1) tb[a * scC] = acc[a][b];
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ---- stores: tile rows, then the mirror (tile column c = output row C0 + c)
+            const int64_t ld = p.ld;
+            const int nrow = nr1 * nr2;
+            const int64_t R0 = bd.row_off + (int64_t)i3 * nrow;
+            const int64_t C0 = bd.col_off + (int64_t)j3b * mc;
+            const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
+            for (int row = warp; row < nrow; row += nwarp) {
+                float *orow = o + (R0 + row) * ld + C0;
+                const float *trw = tile + row * ldt;
+                for (int jj = 0; jj < nj; ++jj) {
+                    const int cs = jj == jd ? row : 0;                  // diagonal sub-tile: upper part
+                    for (int c = cs + lane; c < mc; c += 32) orow[jj * mc + c] = trw[jj * mc + c];
+                }
+            }
+            if (bd.sym != 0) {
+                for (int jj = 0; jj < nj; ++jj)
+                    for (int cj = warp; cj < mc; cj += nwarp) {
+                        const int c = jj * mc + cj;
+                        const int rend = jj == jd ? cj : nrow;          // strictly upper rows
+                        float *orow = o + (C0 + c) * ld + R0;
+                        for (int row = lane; row < rend; row += 32) orow[row] = tile[row * ldt + c];
+                    }
+            }
+        }
     }
 }
 
 // --------------------------------------------------------------------------------------
 // affine path (Sec. 2.8.1)
 // --------------------------------------------------------------------------------------
+// Store-bound: the tile is produced in column panels of AFF_W columns staged in shared
+// memory, then written as row segments (the tile) and as column segments (its mirror),
+// both contiguous in the row-major output.  The program uses the paper's direction order
+// (stage C over xi_1, B over xi_2, A over xi_3), so a tile row is one contiguous segment.
+constexpr int AFF_W = 32;
+
+// Per-element constants of the affine path, one thread per element: the Jacobian from the
+// edge vectors at vertex 0 (the element must be a parallelepiped), its metric fields with
+// unit weight (the 1D integrals F carry the quadrature) and the status of the element.
+__global__ void __launch_bounds__(128) affine_const_kernel(AffConstParams p) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.n_elem) return;
+    const double *v = p.verts + 24 * e;
+    Jac g;
+    double scale = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        g.J[i][0] = v[3 * 1 + i] - v[i];
+        g.J[i][1] = v[3 * 2 + i] - v[i];
+        g.J[i][2] = v[3 * 4 + i] - v[i];
+        for (int d = 0; d < 3; ++d) scale = fmax(scale, fabs(g.J[i][d]));
+    }
+    int f = 0;
+    for (int c = 0; c < 8; ++c) {
+        const double s1 = c & 1, s2 = (c >> 1) & 1, s3 = (c >> 2) & 1;
+        for (int i = 0; i < 3; ++i) {
+            const double pred = v[i] + g.J[i][0] * s1 + g.J[i][1] * s2 + g.J[i][2] * s3;
+            if (!(fabs(v[3 * c + i] - pred) <= 1e-10 * scale)) f = 6; /*DPG_ERR_NOT_AFFINE*/
+        }
+    }
+    finish_jac(g);
+    if (f == 0 && (!(g.det > 0.0) || !isfinite(g.det))) f = 5; /*DPG_ERR_DEGENERATE*/
+    const double c0 = p.coeffs ? p.coeffs[2 * e] : 1.0;
+    const double c1 = p.coeffs ? p.coeffs[2 * e + 1] : 1.0;
+    double fv[18];
+    const int nf = metric_fields(p.space, g, 1.0, c0, c1, fv);
+    double *dst = p.consts + AFF_CONST_STRIDE * e;
+    for (int k = 0; k < nf; ++k) dst[k] = fv[k];
+    dst[AFF_CONST_STRIDE - 1] = (double)f;
+    if (f) report(p.status, f, p.elem_base + e);
+}
+
+// zero test on the bit pattern (+0 and -0), on the integer pipe: the bits are moved out
+// through inline PTX so that the compiler cannot fold the test back into a floating-point
+// compare, which on this GPU would run on the slow FP64 pipe
+__device__ __forceinline__ bool is_zero(double x) {
+    unsigned lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+    return ((hi << 1) | lo) == 0u;
+}
+__device__ __forceinline__ bool is_zero(float x) {
+    unsigned b;
+    asm("mov.b32 %0, %1;" : "=r"(b) : "f"(x));
+    return (b << 1) == 0u;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockDesc bd;
-    __shared__ double cf[18];
+    __shared__ T cf[18];
     __shared__ int flag;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int64_t cta = blockIdx.x;
@@ -317,44 +606,19 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     if (e >= p.n_elem) return;
     const Unit u = p.units[uidx];
     load_block(p.blocks + u.block, bd);
-    if (tid == 0) {
-        // Jacobian from the edge vectors at vertex 0; the element must be a parallelepiped
-        const double *v = p.verts + 24 * e;
-        Jac g;
-        double scale = 0.0;
-        for (int i = 0; i < 3; ++i) {
-            g.J[i][0] = v[3 * 1 + i] - v[i];
-            g.J[i][1] = v[3 * 2 + i] - v[i];
-            g.J[i][2] = v[3 * 4 + i] - v[i];
-            for (int d = 0; d < 3; ++d) scale = fmax(scale, fabs(g.J[i][d]));
-        }
-        int f = 0;
-        for (int c = 0; c < 8; ++c) {
-            const double s1 = c & 1, s2 = (c >> 1) & 1, s3 = (c >> 2) & 1;
-            for (int i = 0; i < 3; ++i) {
-                const double pred = v[i] + g.J[i][0] * s1 + g.J[i][1] * s2 + g.J[i][2] * s3;
-                if (!(fabs(v[3 * c + i] - pred) <= 1e-10 * scale)) f = 6; /*DPG_ERR_NOT_AFFINE*/
-            }
-        }
-        finish_jac(g);
-        if (f == 0 && (!(g.det > 0.0) || !isfinite(g.det))) f = 5; /*DPG_ERR_DEGENERATE*/
-        const double c0 = p.coeffs ? p.coeffs[2 * e] : 1.0;
-        const double c1 = p.coeffs ? p.coeffs[2 * e + 1] : 1.0;
-        double fv[18];
-        const int nf = metric_fields(p.space, g, 1.0, c0, c1, fv);
-        for (int k = 0; k < nf; ++k) cf[k] = fv[k];
-        flag = f;
-        if (f) report(p.status, f, p.elem_base + e);
-    }
+    if (tid < 18) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
+    if (tid == 18) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
     __syncthreads();
 
-    const int dC = bd.dir[0], dB = bd.dir[1], dA = bd.dir[2];
-    const int nr1 = bd.nr[dC], nr2 = bd.nr[dB], nc1 = bd.nc[dC], nc2 = bd.nc[dB];
+    const int nr1 = bd.nr[0], nr2 = bd.nr[1], nc1 = bd.nc[0], nc2 = bd.nc[1];
     const int i3 = u.i3, j3b = u.j3b, nj = u.nj, ng = bd.ng;
     const int n22 = nr2 * nc2;
     const T *F = p.F;
     auto Fv = [&](int pair, int i, int j) -> T { return F[((size_t)pair * NQ1 + i) * NQ1 + j]; };
+    const int nrow = nr1 * nr2, ncol = nc1 * nc2 * nj;
     T *Q = reinterpret_cast<T *>(smem_raw);                            // [ng][nr2][nc2][nj]
+    T *F1 = Q + r4((size_t)ng * n22 * nj);                              // [ng][nr1][nc1]
+    T *panel = F1 + r4((size_t)ng * nr1 * nc1);                        // [nrow][AFF_W + 1]
     // Q_g(i2, j2, jj) = sum_{t in g} sign_t c_t F2_t(i2, j2) F3_t(i3, j3)
     for (int it = tid; it < ng * n22 * nj; it += nth) {
         const int jj = it % nj, r = it / nj;
@@ -364,44 +628,77 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         for (int t = 0; t < bd.nterm; ++t) {
             const TermDesc &td = bd.term[t];
             if (bd.h_g[td.h] != g) continue;
-            const T f3 = Fv(3 * td.kr[dA] + td.kc[dA], i3, j3b + jj);
-            if (f3 == T(0)) continue;
-            const T f2 = Fv(3 * td.kr[dB] + td.kc[dB], i2, j2);
-            if (f2 == T(0)) continue;
-            const T c = (T)(td.sign > 0 ? cf[td.field] : -cf[td.field]);
+            const T f3 = Fv(3 * td.kr[2] + td.kc[2], i3, j3b + jj);
+            if (is_zero(f3)) continue;
+            const T f2 = Fv(3 * td.kr[1] + td.kc[1], i2, j2);
+            if (is_zero(f2)) continue;
+            const T c = td.sign > 0 ? cf[td.field] : -cf[td.field];
             acc = fma(c * f3, f2, acc);
         }
         Q[it] = acc;
     }
+    for (int it = tid; it < ng * nr1 * nc1; it += nth) {
+        const int j1 = it % nc1, r = it / nc1;
+        const int i1 = r % nr1, g = r / nr1;
+        F1[it] = Fv(bd.g_pair[g], i1, j1);
+    }
     __syncthreads();
 
-    const int nrow = nr1 * nr2, ncol = nc1 * nc2 * nj;
     T *o = p.out + (size_t)e * p.mat_stride + bd.base;
     const int64_t ld = p.ld;
     const bool bad = flag != 0;
-    const int sr[3] = { 1, bd.nr[0], bd.nr[0] * bd.nr[1] };
-    const int sc[3] = { 1, bd.nc[0], bd.nc[0] * bd.nc[1] };
-    const int64_t R0 = bd.row_off + (int64_t)i3 * sr[dA];
-    const int64_t C0 = bd.col_off + (int64_t)j3b * sc[dA];
-    for (int it = tid; it < nrow * ncol; it += nth) {
-        const int row = it / ncol, col = it - row * ncol;
-        const int i1 = row % nr1, i2 = row / nr1;
-        const int j1 = col % nc1, c2 = col / nc1;
-        const int j2 = c2 % nc2, jj = c2 / nc2;
-        const int64_t R = R0 + (int64_t)i1 * sr[dC] + (int64_t)i2 * sr[dB];
-        const int64_t C = C0 + (int64_t)j1 * sc[dC] + (int64_t)j2 * sc[dB] + (int64_t)jj * sc[dA];
-        if (bd.sym == 1 && j3b + jj == i3 && R > C) continue;      // mirrored below
-        T acc = T(0);
-        for (int g = 0; g < ng; ++g) {
-            const T f1 = Fv(bd.g_pair[g], i1, j1);
-            if (f1 == T(0)) continue;
-            const T qv = Q[(((size_t)g * nr2 + i2) * nc2 + j2) * nj + jj];
-            if (qv != T(0)) acc = fma(f1, qv, acc);
+    const int64_t R0 = bd.row_off + (int64_t)i3 * nr1 * nr2;     // row of tile row 0
+    const int64_t C0 = bd.col_off + (int64_t)j3b * nc1 * nc2;    // column of tile column 0
+    const int ncj = nc1 * nc2;
+    const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
+    const bool mir = bd.sym != 0;
+    const int ps = AFF_W + 1;
+    // 2-D layout: lane tx walks columns (contiguous output), ty walks rows
+    const int tx = tid % AFF_W, ty = tid / AFF_W, ny = nth / AFF_W;
+    for (int cb = 0; cb < ncol; cb += AFF_W) {
+        const int wc = min(AFF_W, ncol - cb);
+        const int col = cb + tx;
+        const bool colok = tx < wc;
+        const int cj = colok ? col % ncj : 0, jj = colok ? col / ncj : 0;
+        const int j1 = cj % nc1, j2 = cj / nc1;
+        const T *F1c = F1 + j1;                                       // [g][i1][j1]
+        const T *Qc = Q + (size_t)j2 * nj + jj;                       // [g][i2][j2][jj]
+        int i1 = ty % nr1, i2 = ty / nr1;
+        for (int row = ty; row < nrow; row += ny) {
+            if (colok) {
+                T acc = T(0);
+                if (!(jj == jd && row > cj)) {          // lower triangle of a diagonal tile: mirrored
+                    for (int g = 0; g < ng; ++g) {
+                        const T f1 = F1c[(g * nr1 + i1) * nc1];
+                        if (is_zero(f1)) continue;
+                        const T qv = Qc[(size_t)((g * nr2 + i2) * nc2) * nj];
+                        if (!is_zero(qv)) acc = fma(f1, qv, acc);
+                    }
+                }
+                panel[row * ps + tx] = bad ? qnan<T>() : acc;
+                if (!(jj == jd && row > cj)) o[(R0 + row) * ld + C0 + col] = panel[row * ps + tx];
+            }
+            i1 += ny;                                                 // advance (i1, i2) by ny rows
+            while (i1 >= nr1) { i1 -= nr1; ++i2; }
         }
-        if (bad) acc = qnan<T>();
-        o[R * ld + C] = acc;
-        if (bd.sym == 2 || (bd.sym == 1 && R != C)) o[C * ld + R] = acc;
+        if (mir) {
+            __syncthreads();
+            // the mirror: tile column c is output row C0 + c, a contiguous segment of nrow
+            for (int w = ty; w < wc; w += ny) {
+                const int c = cb + w;
+                const int cjw = c % ncj, jjw = c / ncj;
+                for (int row = tx; row < nrow; row += AFF_W) {
+                    if (jjw == jd && row >= cjw) continue;
+                    o[(C0 + c) * ld + R0 + row] = panel[row * ps + w];
+                }
+            }
+            __syncthreads();
+        }
     }
+}
+
+size_t affine_smem_values(int ng, int nr1, int nr2, int nc1, int nc2, int nj) {
+    return r4_host((size_t)ng * nr2 * nc2 * nj) + r4_host((size_t)ng * nr1 * nc1) + (size_t)nr1 * nr2 * (AFF_W + 1);
 }
 
 // --------------------------------------------------------------------------------------
@@ -422,6 +719,30 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(T *out, int iters, T a, T
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += x[k];
     if (s == T(-12345)) out[threadIdx.x] = s;  // keeps the loop alive, never true
+}
+
+// FP64 tensor-core rate probe: independent chains of mma.sync m8n8k4 (FP64 in, FP64
+// accumulate), 512 flops per warp-level instruction.
+__global__ void __launch_bounds__(256) dmma_peak_kernel(double *out, int iters) {
+    const double a = 1e-3 * (threadIdx.x + 1), b = 1.0 - 1e-4 * threadIdx.x;
+    double c[8][2];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { c[k][0] = 0.0; c[k][1] = 0.0; }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                         : "+d"(c[k][0]), "+d"(c[k][1]) : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += c[k][0] + c[k][1];
+    if (s == -12345.0) out[threadIdx.x] = s;  // keeps the loop alive, never true
+}
+
+cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s) {
+    dmma_peak_kernel<<<blocks, 256, 0, s>>>(out, iters);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------------------
@@ -449,6 +770,21 @@ cudaError_t launch_general(const SfParams<T> &p, size_t smem, cudaStream_t s) {
 template cudaError_t launch_general<double>(const SfParams<double> &, size_t, cudaStream_t);
 template cudaError_t launch_general<float>(const SfParams<float> &, size_t, cudaStream_t);
 
+cudaError_t launch_general_f32(const SfParams32 &p, size_t smem, int max_nc1, cudaStream_t s) {
+    if (p.n_elem == 0) return cudaSuccess;
+    const int64_t chunks = (p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta;
+    const int64_t ctas = chunks * p.nblock;
+    if (max_nc1 <= 12) sf_general_f32_kernel<3><<<(unsigned)ctas, 256, smem, s>>>(p);
+    else sf_general_f32_kernel<4><<<(unsigned)ctas, 256, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s) {
+    if (p.n_elem == 0) return cudaSuccess;
+    affine_const_kernel<<<(unsigned)((p.n_elem + 127) / 128), 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s) {
     const int64_t ctas = (int64_t)p.nunits * p.n_elem;
@@ -472,6 +808,8 @@ cudaError_t init_kernel_attributes(int optin_smem) {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = one((const void *)sf_general_kernel<double>);
     if (e == cudaSuccess) e = one((const void *)sf_general_kernel<float>);
+    if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<3>);
+    if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<4>);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<double>);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<float>);
     return e;

@@ -39,24 +39,51 @@ struct SfParams {
     int64_t n_elem;
 };
 
+// Per-element constants of the affine path: 18 metric fields and the element's status
+// code in the last slot.
+constexpr int AFF_CONST_STRIDE = 20;
+
+struct AffConstParams {
+    int space;
+    int64_t n_elem, elem_base;
+    const double *verts, *coeffs;
+    double *consts;            // [n_elem][AFF_CONST_STRIDE]
+    DevStatus *status;
+};
+
+// FP32 general kernel: one CTA per (block, chunk of elements).
+struct SfParams32 {
+    const BlockDesc *blocks;
+    const Unit *units;
+    const int *block_unit_begin;   // [nblock + 1]: units of block k are [begin[k], begin[k+1])
+    int nblock, nj_max, elems_per_cta;
+    int L, nfields;
+    const float *pp;               // pair products [NPAIR][NQ1][NQ1][L]
+    const float *fields;           // [n_elem][nfields][L^3]
+    float *out;
+    int64_t mat_stride, ld, n_elem;
+};
+
 template <typename T>
 struct AffParams {
     const BlockDesc *blocks;
     const Unit *units;
     int nunits;
-    int space;
     const T *F;                // exact 1D integrals [NPAIR][NQ1][NQ1]
-    const double *verts, *coeffs;
+    const double *consts;      // [n_elem][AFF_CONST_STRIDE] from affine_const_kernel
     T *out;
-    int64_t mat_stride, ld, n_elem, elem_base;
-    DevStatus *status;
+    int64_t mat_stride, ld, n_elem;
 };
 
 template <typename TF> cudaError_t launch_geom(const GeomParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_general(const SfParams<T> &p, size_t smem, cudaStream_t s);
+cudaError_t launch_general_f32(const SfParams32 &p, size_t smem, int max_nc1, cudaStream_t s);
+cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
+cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);
+size_t affine_smem_values(int ng, int nr1, int nr2, int nc1, int nc2, int nj);
 int max_dynamic_smem(int optin_smem);
 
 }  // namespace dpg

@@ -232,7 +232,7 @@ static size_t smem_values(const BlockDesc &b, int L, int nj) {
     return P1 + P2 + P3 + A + B;
 }
 
-Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab) {
+Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order) {
     Program pr;
     std::memset(pr.blocks, 0, sizeof(pr.blocks));
     pr.space = space; pr.q = q; pr.L = L; pr.p = p; pr.split = split;
@@ -306,11 +306,13 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             bd.base = part * pr.rows * pr.cols;
             bd.sym = symmetric ? (a == b ? 1 : 2) : 0;
             // stage order: the permutation of directions with the fewest multiply-adds
-            // (ties keep the paper's order: stage A over xi_3, B over xi_2, C over xi_1)
+            // (ties keep the paper's order: stage A over xi_3, B over xi_2, C over xi_1);
+            // ORDER_A3 keeps stage A on xi_3, ORDER_NATURAL keeps the paper's order
             static const int perms[6][3] = { { 0, 1, 2 }, { 1, 0, 2 }, { 0, 2, 1 },
                                              { 2, 0, 1 }, { 1, 2, 0 }, { 2, 1, 0 } };
+            const int nperm = order == ORDER_NATURAL ? 1 : (order == ORDER_A3 ? 2 : 6);
             double best = 0.0; int bi = 0;
-            for (int k = 0; k < 6; ++k) {
+            for (int k = 0; k < nperm; ++k) {
                 finish_block(bd, ts, perms[k]);
                 const double f = block_fmas(bd, L);
                 if (k == 0 || f < best * (1.0 - 1e-12)) { best = f; bi = k; }
@@ -319,20 +321,29 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
         }
     }
 
-    // stage-A chunk: the largest nj whose FP64 shared memory fits the budget
-    const size_t budget = 160 * 1024;
+    // stage-A chunk: the largest nj whose shared memory fits the budget (FP64 general
+    // kernel model, or the FP32 kernel's layout for ORDER_A3 programs)
+    auto smem_bytes = [&](const BlockDesc &b, int njv) -> size_t {
+        if (order == ORDER_A3) return (size_t)f32_layout(b, L, njv).total * sizeof(float);
+        return smem_values(b, L, njv) * sizeof(double);
+    };
+    const size_t budget = order == ORDER_A3 ? 110 * 1024 : 160 * 1024;
     int maxnA = 1;
     for (int k = 0; k < pr.nblock; ++k) maxnA = std::max(maxnA, pr.blocks[k].nc[pr.blocks[k].dir[2]]);
     int nj = std::min(NJMAX, maxnA);
     for (; nj > 1; --nj) {
         size_t m = 0;
-        for (int k = 0; k < pr.nblock; ++k) m = std::max(m, smem_values(pr.blocks[k], L, nj));
-        if (m * sizeof(double) <= budget) break;
+        for (int k = 0; k < pr.nblock; ++k) m = std::max(m, smem_bytes(pr.blocks[k], nj));
+        if (m <= budget) break;
     }
     pr.nj = nj;
-    size_t m = 0;
-    for (int k = 0; k < pr.nblock; ++k) m = std::max(m, smem_values(pr.blocks[k], L, nj));
+    size_t m = 0, mb = 0;
+    for (int k = 0; k < pr.nblock; ++k) {
+        m = std::max(m, smem_values(pr.blocks[k], L, nj));
+        mb = std::max(mb, smem_bytes(pr.blocks[k], nj));
+    }
     pr.smem_values = m;
+    pr.smem_bytes = mb;
 
     // work units (element-local): one per (block, iA, chunk of jA); algorithmic flops
     pr.units.clear();

@@ -23,14 +23,20 @@ struct Program {
     BlockDesc blocks[MAXBLK];
     std::vector<Unit> units;
     int nj = 1;
-    size_t smem_values = 0;        // shared-memory values of the general kernel
+    size_t smem_values = 0;        // shared-memory values of the FP64-model general kernel
+    size_t smem_bytes = 0;         // shared memory of the kernel this program is built for
     double flops = 0.0;            // algorithmic flops per element, general path
     double flops_affine = 0.0;     // algorithmic flops per element, affine path
 };
 
 void gauss_rule(int L, double *z, double *w);
 HostTables make_tables(int q, int L);
-Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab);
+// Contraction order of the blocks: ORDER_BEST picks the cheapest of the six direction
+// permutations (FP64 general kernel); ORDER_A3 the cheaper of the two with stage A over
+// xi_3 (FP32 general kernel: contiguous tile rows); ORDER_NATURAL the paper's order
+// (stage A over xi_3, B over xi_2, C over xi_1; affine kernel).
+enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2 };
+Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order = ORDER_BEST);
 int64_t rows_of(int space, int q);
 int64_t cols_of(int space, int p, int q);
 
