@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-form sub-measurement")
-    ap.add_argument("--workload", default=None, choices=sorted(SECONDARY), help="secondary workload record")
+    ap.add_argument("--workload", default=None, choices=sorted(SECONDARY) + ["hp_q2to8_16x16x16"],
+                    help="secondary workload record")
     ap.add_argument("--only", default=None, help="profiling case: run only this space's call (H1, HCURL, HDIV, L2)")
     ap.add_argument("--map", default="general", choices=["general", "affine"], help="map of the --only case")
     ap.add_argument("--elems", type=int, default=0, help="elements of the --only case (default: all 512)")
@@ -425,6 +426,89 @@ def run_secondary(args):
     print(json.dumps(rec), flush=True)
 
 
+def run_hp(args):
+    """hp_q2to8_16x16x16: one dpg_integrate_hp call per space (graph-captured, replayed)."""
+    import numpy as np
+    import torch
+    import paper_1711_00984_gb300 as dpg
+    from paper_1711_00984_gb300 import build as dbuild
+    from paper_1711_00984_gb300 import meshgen
+    dbuild.build()
+    dpg.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    w = meshgen.workload("hp_q2to8_16x16x16")
+    v = torch.from_numpy(w["verts"]).to(dev)
+    qn = w["q_elem"].astype(np.int32)
+    qt = torch.from_numpy(qn).to(dev)
+    ne = len(qn)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    peak64 = dpg.dpg_measure_fma_peak(64, sh)
+    peak32 = dpg.dpg_measure_fma_peak(32, sh)
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] * 1e9 if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6771.1e9
+    rec = {"workload": "hp_q2to8_16x16x16", "elements": ne,
+           "q_histogram": {int(q): int((qn == q).sum()) for q in range(2, 9)}, "calls": []}
+    tuned = {}
+    for space in SPACES:
+        for q in range(2, 9):
+            dpg.dpg_tables_init(q, space)
+            tuned[f"{space}_q{q}"] = [dpg.dpg_autotune(q, space, False, sh), dpg.dpg_autotune(q, space, True, sh)]
+        dims = np.array([dpg.dpg_matrix_rows(space, int(q)) for q in qn], dtype=np.int64)
+        sizes = dims * dims
+        off = np.zeros(ne, dtype=np.int64)
+        off[1:] = np.cumsum(sizes)[:-1]
+        offt = torch.from_numpy(off).to(dev)
+        total = int(sizes.sum())
+        flops = sum(int((qn == q).sum()) * dpg.dpg_flops_per_element(dpg.space_id(space), 0, q) for q in range(2, 9))
+        res = {"space": space, "output_values": total}
+        outs = {}
+        for fp32 in (False, True):
+            out = torch.empty(total, dtype=torch.float32 if fp32 else torch.float64, device=dev)
+            sid = dpg.space_id(space, fp32=fp32)
+
+            def call():
+                code = dpg.dpg_integrate_hp(sid, ne, v.data_ptr(), 0, qt.data_ptr(), offt.data_ptr(), out.data_ptr(), sh)
+                if code:
+                    raise dpg.DpgError(code, "dpg_integrate_hp")
+            for _ in range(args.warmup):
+                call()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for i in range(args.steps):
+                flush.fill_(i & 0xff)
+                ev[i][0].record(stream)
+                call()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            code, bad = dpg.dpg_sync_status(sh)
+            assert code == 0, (code, bad)
+            ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+            nbytes = out.numel() * out.element_size()
+            t_alu = flops / (peak32 if fp32 else peak64)
+            t_mem = nbytes / hbm
+            res["fp32" if fp32 else "fp64"] = {
+                "ms": ms, "element_matrices_per_s": ne / (ms * 1e-3), "output_gbs": nbytes / (ms * 1e-3) / 1e9,
+                "tflops": flops / (ms * 1e-3) / 1e12, "bound": "alu" if t_alu > t_mem else "hbm",
+                "roofline_frac": max(t_alu, t_mem) / (ms * 1e-3)}
+            outs[fp32] = out
+        err = 0.0
+        for e0 in range(0, ne, 256):
+            for e in range(e0, min(ne, e0 + 256), 37):
+                a = outs[True][off[e]:off[e] + sizes[e]].double()
+                b = outs[False][off[e]:off[e] + sizes[e]]
+                err = max(err, float((a - b).norm() / b.norm()))
+        res["fp32_max_rel_frobenius_err_vs_fp64_sampled"] = err
+        res["fp32_speedup"] = res["fp64"]["ms"] / res["fp32"]["ms"]
+        rec["calls"].append(res)
+        del outs
+        torch.cuda.empty_cache()
+    rec["flops_note"] = "algorithmic flops of the FP64-order programs, summed over the elements' orders"
+    rec["autotuned_nj_fp64_fp32"] = tuned
+    print(json.dumps(rec), flush=True)
+
+
 def run_case(args):
     """One (space, map, form) call of the workload on a subset of elements, for profilers."""
     import torch
@@ -454,6 +538,8 @@ def main():
     args = parse()
     if args.only:
         run_case(args)
+    elif args.workload == "hp_q2to8_16x16x16":
+        run_hp(args)
     elif args.workload:
         run_secondary(args)
     elif args.impl == "reference":

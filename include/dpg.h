@@ -122,6 +122,38 @@ int64_t dpg_matrix_cols(int space, int p_trial, int q);
 int dpg_integrate(int space, int p_trial, int q_test, int64_t n_elem,
                   const double *vertices, const double *coeffs, void *out, void *stream);
 
+/* hp-mixed batch (elements of different test orders q in one call), general map: the
+ * per-element routine of the paper (Algorithms 5, 7, 9 and their L2 form) for every
+ * element at its own order q_elem[e] with its own rule L(q) (the active rule of
+ * dpg_tables_init for (space, q)).  One device-driven sequence: the elements are sorted by
+ * descending q on the device, the work units of all elements are handed out by one
+ * persistent kernel from an atomic counter, and the whole sequence is captured into a
+ * CUDA graph on the first call with a given argument set and replayed afterwards (the
+ * cache is cleared by dpg_tables_init* and dpg_tables_free).
+ *   space      : DPG_H1, DPG_HCURL, DPG_HDIV or DPG_L2, optionally | DPG_FP32.
+ *   q_elem     : device, int[n_elem], each in [1, DPG_MAX_Q] with tables initialised.
+ *   out_offset : device, int64[n_elem]: element e's rows(q_e) x cols(q_e) matrix starts
+ *                at out + out_offset[e] (counted in values of the output type).
+ *   vertices, coeffs, out : as for dpg_integrate (out is the packed batch).
+ * Elements with an order outside the range or without tables are skipped and reported
+ * through dpg_sync_status (DPG_ERR_RANGE / DPG_ERR_NOT_INIT with the first such element).
+ * Workspace: stream-ordered from the library pool, about n_elem * (max nfields L^3) values.
+ * Errors: DPG_ERR_ARG, DPG_ERR_NOT_INIT (no order of `space` initialised), DPG_ERR_CUDA. */
+int dpg_integrate_hp(int space, int64_t n_elem, const double *vertices, const double *coeffs,
+                     const int *q_elem, const int64_t *out_offset, void *out, void *stream);
+
+/* Autotuner (not in the paper): for the general path of (space, q) with its active rule,
+ * time every stage-A chunk width nj (the number of partner indices j_A one work unit
+ * produces: tile shape and stage schedule of the contraction kernels) on a synthetic batch
+ * of 128 elements on `stream`, and install the fastest for dpg_integrate and
+ * dpg_integrate_hp.  space = DPG_H1 .. DPG_L2, optionally | DPG_FP32 (tunes the FP32
+ * kernel).  If the environment variable DPG_AUTOTUNE_CACHE names a file, a choice stored
+ * there for (space, q, L, precision) is installed without timing, and new choices are
+ * appended as JSON lines.  Synchronous; allocates temporary device buffers; call it at
+ * set-up, not inside stream capture.  *best_nj (if not NULL) receives the chosen width.
+ * Errors: DPG_ERR_ARG, DPG_ERR_NOT_INIT, DPG_ERR_RANGE, DPG_ERR_CUDA. */
+int dpg_autotune(int q, int space, void *stream, int *best_nj);
+
 /* Allocation-free variant of dpg_integrate for the general (trilinear-map) path.  The
  * paper has no counterpart: this is a service for callers that must not allocate device
  * memory while they integrate -- a solver whose device memory is carved up once at start

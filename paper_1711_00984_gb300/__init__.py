@@ -25,8 +25,8 @@ STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANG
           5: "DPG_ERR_DEGENERATE", 6: "DPG_ERR_NOT_AFFINE", 7: "DPG_ERR_NOMEM", 8: "DPG_ERR_SCRATCH"}
 
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
-           "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_host", "dpg_sync_status",
-           "dpg_strerror", "dpg_last_cuda_error", "dpg_flops_per_element", "dpg_measure_fma_peak"]
+           "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",
+           "dpg_strerror", "dpg_last_cuda_error", "dpg_autotune", "dpg_flops_per_element", "dpg_measure_fma_peak"]
 
 _lib = None
 _lock = threading.Lock()
@@ -62,6 +62,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_integrate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
         lib.dpg_integrate_host.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
         lib.dpg_integrate_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
+        lib.dpg_integrate_hp.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, vp]
+        lib.dpg_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
+        lib.dpg_autotune.restype = ctypes.c_int
         lib.dpg_sync_status.argtypes = [vp, ctypes.POINTER(i64)]
         lib.dpg_strerror.argtypes = [ctypes.c_int]
         lib.dpg_strerror.restype = ctypes.c_char_p
@@ -70,7 +73,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_flops_per_element.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.dpg_flops_per_element.restype = ctypes.c_double
         lib.dpg_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp]
-        for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc",
+        for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp",
                      "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak"]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -127,6 +130,45 @@ def dpg_integrate_noalloc(space: int, p_trial: int, q_test: int, n_elem: int, ve
                                       stream or None)
 
 
+def dpg_integrate_hp(space: int, n_elem: int, vertices: int, coeffs: int, q_elem: int, out_offset: int,
+                     out: int, stream: int) -> int:
+    """Raw call of the hp-mixed batch entry point (device pointers)."""
+    return _L().dpg_integrate_hp(space, n_elem, vertices or None, coeffs or None, q_elem or None,
+                                 out_offset or None, out, stream or None)
+
+
+def integrate_hp(space, verts, q_elem, coeffs=None, *, fp32: bool = False, out=None, stream=None):
+    """hp batch of device tensors: verts[n, 8, 3] float64, q_elem[n] int32 (CUDA).
+
+    Returns (out, offsets): the packed 1-D output and the int64 element offsets into it.
+    Tables for every q present must have been initialised.
+    """
+    import torch
+    n = verts.shape[0]
+    qs = q_elem.to(torch.int64)
+    if space in ("H1", DPG_H1):
+        dims = (qs + 1) ** 3
+    elif space in ("L2", DPG_L2):
+        dims = qs ** 3
+    elif space in ("HDIV", DPG_HDIV):
+        dims = 3 * (qs + 1) * qs * qs
+    else:
+        dims = 3 * qs * (qs + 1) ** 2
+    sizes = dims * dims
+    offsets = torch.zeros(n, dtype=torch.int64, device=verts.device)
+    if n > 1:
+        offsets[1:] = torch.cumsum(sizes, 0)[:-1]
+    total = int(sizes.sum().item()) if n else 0
+    dt = torch.float32 if fp32 else torch.float64
+    if out is None:
+        out = torch.empty(total, dtype=dt, device=verts.device)
+    sid = space_id(space, fp32)
+    code = dpg_integrate_hp(sid, n, verts.data_ptr(), coeffs.data_ptr() if coeffs is not None else 0,
+                            q_elem.data_ptr(), offsets.data_ptr(), out.data_ptr(), _stream_handle(stream))
+    _check(code, "dpg_integrate_hp")
+    return out, offsets
+
+
 def dpg_integrate_host(space: int, p_trial: int, q_test: int, n_elem: int, vertices: int, coeffs: int,
                        out: int, stream: int) -> int:
     return _L().dpg_integrate_host(space, p_trial, q_test, n_elem, vertices or None, coeffs or None, out, stream or None)
@@ -140,6 +182,13 @@ def dpg_sync_status(stream: int = 0) -> tuple[int, int]:
 
 def dpg_strerror(code: int) -> str:
     return _L().dpg_strerror(code).decode()
+
+
+def dpg_autotune(q: int, space, fp32: bool = False, stream: int = 0) -> int:
+    """Tune the stage-A chunk of (space, q); returns the chosen width."""
+    nj = ctypes.c_int(0)
+    _check(_L().dpg_autotune(q, space_id(space, fp32), stream or None, ctypes.byref(nj)), "dpg_autotune")
+    return nj.value
 
 
 def dpg_last_cuda_error() -> str:

@@ -28,6 +28,12 @@ template <typename T> __device__ __forceinline__ T qnan();
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 
+// floor(x / d) for 0 <= x < 2^20 and 1 <= d < 2^12: m = ceil(2^32 / d), q = umulhi(x, m)
+__device__ __forceinline__ unsigned div_magic(int d) {
+    return d <= 1 ? 0u : (unsigned)((0x100000000ull + (unsigned)d - 1u) / (unsigned)d);
+}
+__device__ __forceinline__ int fdiv(int x, unsigned m) { return m ? (int)__umulhi((unsigned)x, m) : x; }
+
 // --------------------------------------------------------------------------------------
 // geometry
 // --------------------------------------------------------------------------------------
@@ -163,20 +169,14 @@ __device__ __forceinline__ void load_block(const BlockDesc *src, BlockDesc &dst)
     for (int i = threadIdx.x; i < (int)(sizeof(BlockDesc) / sizeof(int)); i += blockDim.x) d[i] = s[i];
 }
 
+// One work unit (block bd, stage-A index u.i3, partners u.j3b .. +u.nj) of one element:
+// fe = the element's metric fields, o = its output matrix (leading dimension ld).  All
+// threads of the CTA take part; bd must be in shared memory and visible to every thread.
 template <typename T>
-__global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ BlockDesc bd;
+__device__ void sf_unit(const BlockDesc &bd, const Unit u, const T *__restrict__ fe, T *__restrict__ o,
+                        const T *__restrict__ pp, int L, int64_t ld, unsigned char *smem_raw) {
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int64_t cta = blockIdx.x;
-    const int uidx = (int)(cta % p.nunits);
-    const int64_t e = cta / p.nunits;
-    if (e >= p.n_elem) return;
-    const Unit u = p.units[uidx];
-    load_block(p.blocks + u.block, bd);
-    __syncthreads();
-
-    const int L = p.L, L2 = L * L, L3 = L2 * L;
+    const int L2 = L * L;
     const int dC = bd.dir[0], dB = bd.dir[1], dA = bd.dir[2];
     // stage-C extents (nr1, nc1), stage-B extents (nr2, nc2); index (i3, j3) runs along dA
     const int nr1 = bd.nr[dC], nr2 = bd.nr[dB], nc1 = bd.nc[dC], nc2 = bd.nc[dB];
@@ -190,7 +190,6 @@ __global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
     T *A = P3 + r4((size_t)nterm * nj * L);                          // [nh][L][L][nj]
     T *Bs = A + r4((size_t)nh * L2 * nj);                            // [ng][L][nr2][nc2][nj]
 
-    const T *pp = p.pp;
     auto PP = [&](int pair, int i, int j) -> const T * {
         return pp + (((size_t)pair * NQ1 + i) * NQ1 + j) * L;
     };
@@ -222,7 +221,7 @@ __global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
 
     // ---- stage A (Eq. 2.23): A_h(l, m, jj) = sum_{t in h} sum_n M_t(l,m,n) P3_t(jj, n),
     //      l along dC, m along dB, n along dA; one output per thread (no idle lanes)
-    const T *fe = p.fields + (size_t)e * p.nfields * L3;
+    const int L3 = L2 * L;
     for (int it = tid; it < nh * L2 * nj; it += nth) {
         const int jj = it % nj, r = it / nj;
         const int lm = r % L2, h = r / L2;
@@ -256,8 +255,6 @@ __global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
 
     // ---- stage C (Eq. 2.25) and symmetric fill
     const int nrow = nr1 * nr2, ncj = nc1 * nc2;
-    T *o = p.out + (size_t)e * p.mat_stride + bd.base;
-    const int64_t ld = p.ld;
     // output strides of each direction (index maps Eqs. 2.53 / 2.71, i1 fastest)
     auto stride = [](int d, int n0, int n1) { return d == 0 ? 1 : (d == 1 ? n0 : n0 * n1); };
     const int srC = stride(dC, bd.nr[0], bd.nr[1]), srB = stride(dB, bd.nr[0], bd.nr[1]);
@@ -303,6 +300,23 @@ __global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
         o[R * ld + C] = acc;
         if (mirror_all || (mirror_off && R != C)) o[C * ld + R] = acc;
     }
+    (void)L3;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockDesc bd;
+    const int64_t cta = blockIdx.x;
+    const int uidx = (int)(cta % p.nunits);
+    const int64_t e = cta / p.nunits;
+    if (e >= p.n_elem) return;
+    const Unit u = p.units[uidx];
+    load_block(p.blocks + u.block, bd);
+    __syncthreads();
+    const int L3 = p.L * p.L * p.L;
+    sf_unit<T>(bd, u, p.fields + (size_t)e * p.nfields * L3, p.out + (size_t)e * p.mat_stride + bd.base, p.pp,
+               p.L, p.ld, smem_raw);
 }
 
 
@@ -318,11 +332,6 @@ __global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
 // runs (the tile) and column runs (its mirror).  Integer divisions by CTA-uniform
 // divisors use multiply-high magic numbers.
 
-// floor(x / d) for 0 <= x < 2^20 and 1 <= d < 2^12: m = ceil(2^32 / d), q = umulhi(x, m)
-__device__ __forceinline__ unsigned div_magic(int d) {
-    return d <= 1 ? 0u : (unsigned)((0x100000000ull + (unsigned)d - 1u) / (unsigned)d);
-}
-__device__ __forceinline__ int fdiv(int x, unsigned m) { return m ? (int)__umulhi((unsigned)x, m) : x; }
 
 constexpr int F32_NXMAX = 128;     // (j2, jj) pairs per unit: nc2 * nj <= 13 * 8
 constexpr int F32_NIJMAX = 176;    // (i2, j2) pairs: nr2 * nc2 <= 13 * 13
@@ -599,106 +608,348 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     __shared__ BlockDesc bd;
     __shared__ T cf[18];
     __shared__ int flag;
+    __shared__ T st[MAXT * NJMAX];             // s_t = sign_t c_t F3_t(i3, j3) of the current unit
+    __shared__ unsigned char f1n[NQ1 * NQ1], f1g[NQ1 * NQ1 * MAXG];
+    __shared__ int coldec[NQ1 * NQ1 * NJMAX];  // column decode of the current unit's tile
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int64_t cta = blockIdx.x;
-    const int uidx = (int)(cta % p.nunits);
-    const int64_t e = cta / p.nunits;
+    // one CTA per (element, block): the block's tables are built once, then every work
+    // unit (i3, chunk of j3) of the block is produced in turn
+    const int k = blockIdx.x % p.nblock;
+    const int64_t e = blockIdx.x / p.nblock;
     if (e >= p.n_elem) return;
-    const Unit u = p.units[uidx];
-    load_block(p.blocks + u.block, bd);
+    load_block(p.blocks + k, bd);
     if (tid < 18) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
     if (tid == 18) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
     __syncthreads();
 
     const int nr1 = bd.nr[0], nr2 = bd.nr[1], nc1 = bd.nc[0], nc2 = bd.nc[1];
-    const int i3 = u.i3, j3b = u.j3b, nj = u.nj, ng = bd.ng;
+    const int ng = bd.ng, nterm = bd.nterm, njm = p.nj_max;
     const int n22 = nr2 * nc2;
     const T *F = p.F;
     auto Fv = [&](int pair, int i, int j) -> T { return F[((size_t)pair * NQ1 + i) * NQ1 + j]; };
-    const int nrow = nr1 * nr2, ncol = nc1 * nc2 * nj;
     T *Q = reinterpret_cast<T *>(smem_raw);                            // [ng][nr2][nc2][nj]
-    T *F1 = Q + r4((size_t)ng * n22 * nj);                              // [ng][nr1][nc1]
-    T *panel = F1 + r4((size_t)ng * nr1 * nc1);                        // [nrow][AFF_W + 1]
-    // Q_g(i2, j2, jj) = sum_{t in g} sign_t c_t F2_t(i2, j2) F3_t(i3, j3)
-    for (int it = tid; it < ng * n22 * nj; it += nth) {
-        const int jj = it % nj, r = it / nj;
-        const int ij2 = r % n22, g = r / n22;
-        const int i2 = ij2 / nc2, j2 = ij2 % nc2;
-        T acc = T(0);
-        for (int t = 0; t < bd.nterm; ++t) {
-            const TermDesc &td = bd.term[t];
-            if (bd.h_g[td.h] != g) continue;
-            const T f3 = Fv(3 * td.kr[2] + td.kc[2], i3, j3b + jj);
-            if (is_zero(f3)) continue;
-            const T f2 = Fv(3 * td.kr[1] + td.kc[1], i2, j2);
-            if (is_zero(f2)) continue;
-            const T c = td.sign > 0 ? cf[td.field] : -cf[td.field];
-            acc = fma(c * f3, f2, acc);
+    T *F1 = Q + r4((size_t)ng * n22 * njm);                             // [nr1][nc1][MAXG] non-zeros
+    T *panel = F1 + r4((size_t)MAXG * nr1 * nc1);                      // [nrow][AFF_W + 1]
+    T *F2 = panel + (size_t)nr1 * nr2 * (AFF_W + 1);                   // [nterm][nr2][nc2]
+    // stage-C factors: per (i1, j1) the number of non-zero groups and their values (the
+    // loop over them has a data-dependent trip count: no predicated FP64 FMAs)
+    for (int it = tid; it < nr1 * nc1; it += nth) {
+        int cnt = 0;
+        for (int g = 0; g < ng; ++g) {
+            const T v = Fv(bd.g_pair[g], it / nc1, it % nc1);
+            if (!is_zero(v)) { F1[it * MAXG + cnt] = v; f1g[it * MAXG + cnt] = (unsigned char)g; ++cnt; }
         }
-        Q[it] = acc;
+        f1n[it] = (unsigned char)cnt;
     }
-    for (int it = tid; it < ng * nr1 * nc1; it += nth) {
-        const int j1 = it % nc1, r = it / nc1;
-        const int i1 = r % nr1, g = r / nr1;
-        F1[it] = Fv(bd.g_pair[g], i1, j1);
+    for (int it = tid; it < nterm * n22; it += nth) {                   // F2_t(i2, j2)
+        const int t = it / n22, ij = it - t * n22;
+        const TermDesc &td = bd.term[t];
+        F2[it] = Fv(3 * td.kr[1] + td.kc[1], ij / nc2, ij % nc2);
     }
-    __syncthreads();
 
     T *o = p.out + (size_t)e * p.mat_stride + bd.base;
     const int64_t ld = p.ld;
     const bool bad = flag != 0;
-    const int64_t R0 = bd.row_off + (int64_t)i3 * nr1 * nr2;     // row of tile row 0
-    const int64_t C0 = bd.col_off + (int64_t)j3b * nc1 * nc2;    // column of tile column 0
     const int ncj = nc1 * nc2;
-    const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
     const bool mir = bd.sym != 0;
     const int ps = AFF_W + 1;
-    // 2-D layout: lane tx walks columns (contiguous output), ty walks rows
     const int tx = tid % AFF_W, ty = tid / AFF_W, ny = nth / AFF_W;
-    for (int cb = 0; cb < ncol; cb += AFF_W) {
-        const int wc = min(AFF_W, ncol - cb);
-        const int col = cb + tx;
-        const bool colok = tx < wc;
-        const int cj = colok ? col % ncj : 0, jj = colok ? col / ncj : 0;
-        const int j1 = cj % nc1, j2 = cj / nc1;
-        const T *F1c = F1 + j1;                                       // [g][i1][j1]
-        const T *Qc = Q + (size_t)j2 * nj + jj;                       // [g][i2][j2][jj]
-        int i1 = ty % nr1, i2 = ty / nr1;
-        for (int row = ty; row < nrow; row += ny) {
-            if (colok) {
-                T acc = T(0);
-                if (!(jj == jd && row > cj)) {          // lower triangle of a diagonal tile: mirrored
-                    for (int g = 0; g < ng; ++g) {
-                        const T f1 = F1c[(g * nr1 + i1) * nc1];
-                        if (is_zero(f1)) continue;
-                        const T qv = Qc[(size_t)((g * nr2 + i2) * nc2) * nj];
-                        if (!is_zero(qv)) acc = fma(f1, qv, acc);
-                    }
-                }
-                panel[row * ps + tx] = bad ? qnan<T>() : acc;
-                if (!(jj == jd && row > cj)) o[(R0 + row) * ld + C0 + col] = panel[row * ps + tx];
-            }
-            i1 += ny;                                                 // advance (i1, i2) by ny rows
-            while (i1 >= nr1) { i1 -= nr1; ++i2; }
+    const int nrow = nr1 * nr2;
+    const unsigned mncj = div_magic(ncj), mnc1 = div_magic(nc1), mn22 = div_magic(n22);
+    const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
+    for (int ui = ub; ui < ue; ++ui) {
+        const Unit u = p.units[ui];
+        const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
+        const unsigned mnju = div_magic(nj);
+        __syncthreads();                                                // previous unit done
+        for (int it = tid; it < nterm * nj; it += nth) {
+            const int t = fdiv(it, mnju), jj = it - t * nj;
+            const TermDesc &td = bd.term[t];
+            const T f3 = Fv(3 * td.kr[2] + td.kc[2], i3, j3b + jj);
+            st[it] = is_zero(f3) ? T(0) : (td.sign > 0 ? cf[td.field] : -cf[td.field]) * f3;
         }
-        if (mir) {
-            __syncthreads();
-            // the mirror: tile column c is output row C0 + c, a contiguous segment of nrow
-            for (int w = ty; w < wc; w += ny) {
-                const int c = cb + w;
-                const int cjw = c % ncj, jjw = c / ncj;
-                for (int row = tx; row < nrow; row += AFF_W) {
-                    if (jjw == jd && row >= cjw) continue;
-                    o[(C0 + c) * ld + R0 + row] = panel[row * ps + w];
-                }
+        // column decode of the unit's tile: col -> (j1, j2, jj, cj = j1 + nc1 j2)
+        const int ncol = ncj * nj;
+        for (int c = tid; c < ncol; c += nth) {
+            const int jj = fdiv(c, mncj), cj = c - jj * ncj;
+            const int j2 = fdiv(cj, mnc1), j1 = cj - j2 * nc1;
+            coldec[c] = j1 | (j2 << 8) | (jj << 16);
+        }
+        __syncthreads();
+        // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2)
+        for (int it = tid; it < ng * n22 * nj; it += nth) {
+            const int r = fdiv(it, mnju), jj = it - r * nj;
+            const int g = fdiv(r, mn22), ij2 = r - g * n22;
+            T acc = T(0);
+            for (int t = 0; t < nterm; ++t) {
+                if (bd.h_g[bd.term[t].h] != g) continue;
+                const T sv = st[t * nj + jj];
+                if (is_zero(sv)) continue;
+                const T f2 = F2[t * n22 + ij2];
+                if (!is_zero(f2)) acc = fma(sv, f2, acc);
             }
-            __syncthreads();
+            Q[it] = acc;
+        }
+        __syncthreads();
+
+        const int64_t R0 = bd.row_off + (int64_t)i3 * nr1 * nr2;     // row of tile row 0
+        const int64_t C0 = bd.col_off + (int64_t)j3b * ncj;          // column of tile column 0
+        const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
+        T *orow0 = o + R0 * ld + C0;
+        for (int cb = 0; cb < ncol; cb += AFF_W) {
+            const int wc = min(AFF_W, ncol - cb);
+            const int col = cb + tx;
+            const bool colok = tx < wc;
+            const int dec = colok ? coldec[col] : 0;
+            const int j1 = dec & 0xff, j2 = (dec >> 8) & 0xff, jj = dec >> 16;
+            const int cj = j1 + nc1 * j2;
+            const T *Qc = Q + (size_t)j2 * nj + jj;                   // [g][i2][j2][jj]
+            int i1 = ty % nr1, i2 = ty / nr1;
+            T *op = orow0 + (int64_t)ty * ld + col;
+            const int64_t ostep = (int64_t)ny * ld;
+            for (int row = ty; row < nrow; row += ny, op += ostep) {
+                if (colok) {
+                    T acc = T(0);
+                    if (!(jj == jd && row > cj)) {      // lower triangle of a diagonal tile: mirrored
+                        const int ij1 = i1 * nc1 + j1, cnt = f1n[ij1];
+                        for (int kk = 0; kk < cnt; ++kk) {
+                            const int g = f1g[ij1 * MAXG + kk];
+                            const T qv = Qc[(size_t)((g * nr2 + i2) * nc2) * nj];
+                            if (!is_zero(qv)) acc = fma(F1[ij1 * MAXG + kk], qv, acc);
+                        }
+                        if (bad) acc = qnan<T>();
+                        *op = acc;
+                    }
+                    panel[row * ps + tx] = acc;
+                }
+                i1 += ny;                                             // advance (i1, i2) by ny rows
+                while (i1 >= nr1) { i1 -= nr1; ++i2; }
+            }
+            if (mir) {
+                __syncthreads();
+                // the mirror: tile column c is output row C0 + c, a contiguous segment of nrow
+                for (int w = ty; w < wc; w += ny) {
+                    const int c = cb + w;
+                    const int dw = coldec[c];
+                    const int jjw = dw >> 16, cjw = (dw & 0xff) + nc1 * ((dw >> 8) & 0xff);
+                    const int rend = jjw == jd ? cjw : nrow;            // strictly upper rows
+                    T *mrow = o + (C0 + c) * ld + R0;
+                    for (int row = tx; row < rend; row += AFF_W) mrow[row] = panel[row * ps + w];
+                }
+                __syncthreads();
+            }
         }
     }
 }
 
-size_t affine_smem_values(int ng, int nr1, int nr2, int nc1, int nc2, int nj) {
-    return r4_host((size_t)ng * nr2 * nc2 * nj) + r4_host((size_t)ng * nr1 * nc1) + (size_t)nr1 * nr2 * (AFF_W + 1);
+size_t affine_smem_values(int ng, int nterm, int nr1, int nr2, int nc1, int nc2, int nj) {
+    return r4_host((size_t)ng * nr2 * nc2 * nj) + r4_host((size_t)MAXG * nr1 * nc1) + (size_t)nr1 * nr2 * (AFF_W + 1) +
+           (size_t)nterm * nr2 * nc2;
+}
+
+
+// --------------------------------------------------------------------------------------
+// hp batching: elements of mixed order q in one persistent launch
+// --------------------------------------------------------------------------------------
+// Work generation runs on the device (no host synchronisation, capturable in a CUDA
+// graph): a histogram of q, a counting sort of the elements by descending q (the most
+// expensive elements are handed out first), prefix sums of the work units and of the
+// metric-field sizes, a map from work item to element, the geometry of every element
+// with its own rule L(q), then one persistent kernel whose CTAs take work items from an
+// atomic counter.
+__device__ __forceinline__ bool hp_valid(const HpParams &p, int q) {
+    return q >= 1 && q <= MAXQ && p.tab[q].valid;
+}
+
+__global__ void hp_count_kernel(HpParams p) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.n_elem) return;
+    const int q = p.q_elem[e];
+    if (!hp_valid(p, q)) {
+        report(p.status, (q < 1 || q > MAXQ) ? 3 /*DPG_ERR_RANGE*/ : 2 /*DPG_ERR_NOT_INIT*/, e);
+        p.fcnt[e] = 0;
+        return;
+    }
+    atomicAdd(&p.hist[q], 1);
+    const HpProg &g = p.tab[q];
+    p.fcnt[e] = (int64_t)g.nfields * g.L * g.L * g.L;
+}
+
+__global__ void hp_bucket_kernel(HpParams p) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int run = 0;
+    for (int q = MAXQ; q >= 1; --q) { p.bstart[q] = run; run += p.hist[q]; p.bfill[q] = 0; }
+    p.counters[0] = 0;
+    p.counters[2] = run;
+}
+
+__global__ void hp_scatter_kernel(HpParams p) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.n_elem) return;
+    const int q = p.q_elem[e];
+    if (!hp_valid(p, q)) return;
+    const int pos = p.bstart[q] + atomicAdd(&p.bfill[q], 1);
+    p.order[pos] = (int)e;
+    p.ucnt[pos] = p.tab[q].nunits;
+}
+
+// exclusive prefix sum of int64 values, three launches: per-block scan, scan of the block
+// sums (one CTA), add back
+__global__ void __launch_bounds__(1024) scan_block_kernel(const int64_t *in, int64_t *out, int64_t *bsum, int64_t n) {
+    __shared__ int64_t wsum[32];
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    const int64_t v = i < n ? in[i] : 0;
+    int64_t x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = wsum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d) t += y;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    const int64_t incl = x + (w > 0 ? wsum[w - 1] : 0);
+    if (i < n) out[i] = incl - v;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(1024) scan_top_kernel(int64_t *bsum, int64_t nb, int64_t *total) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < nb ? bsum[i] : 0;
+        int64_t x = v;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int64_t t = wsum[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, t, d);
+                if (lane >= d) t += y;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        const int64_t incl = x + (w > 0 ? wsum[w - 1] : 0);
+        if (i < nb) bsum[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(1024) scan_add_kernel(int64_t *out, const int64_t *bsum, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+__global__ void hp_items_kernel(HpParams p) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.counters[2]) return;
+    const int64_t b = p.uoff[k], c = p.ucnt[k];
+    for (int64_t u = 0; u < c; ++u) p.item_k[b + u] = (int)k;
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(256) hp_geom_kernel(HpParams p) {
+    const int64_t e = blockIdx.x;
+    const int q = p.q_elem[e];
+    if (!hp_valid(p, q)) return;
+    const HpProg &g = p.tab[q];
+    const int L = g.L, L2 = L * L, L3 = L2 * L;
+    const double c0 = p.coeffs ? p.coeffs[2 * e] : 1.0;
+    const double c1 = p.coeffs ? p.coeffs[2 * e + 1] : 1.0;
+    TF *dst0 = reinterpret_cast<TF *>(p.fields) + p.foff[e];
+    for (int pt = threadIdx.x; pt < L3; pt += blockDim.x) {
+        const int l = pt / L2, m = (pt / L) % L, n = pt % L;
+        Jac jg;
+        trilinear_jac(p.verts + 24 * e, g.zeta[l], g.zeta[m], g.zeta[n], jg);
+        finish_jac(jg);
+        double f[18];
+        const int nf = metric_fields(p.space, jg, g.w[l] * g.w[m] * g.w[n], c0, c1, f);
+        const bool bad = !(jg.det > 0.0) || !isfinite(jg.det);
+        if (bad) report(p.status, 5 /*DPG_ERR_DEGENERATE*/, e);
+        for (int k = 0; k < nf; ++k) dst0[(int64_t)k * L3 + pt] = bad ? qnan<TF>() : (TF)f[k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) hp_contract_kernel(HpParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockDesc bd;
+    __shared__ long long item_s;
+    const int64_t total = p.counters[1];
+    for (;;) {
+        if (threadIdx.x == 0) item_s = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(p.counters), 1ull);
+        __syncthreads();
+        const int64_t item = item_s;
+        if (item >= total) break;
+        const int k = p.item_k[item];
+        const int e = p.order[k];
+        const HpProg &g = p.tab[p.q_elem[e]];
+        const Unit u = g.units[item - p.uoff[k]];
+        load_block(g.blocks + u.block, bd);
+        __syncthreads();
+        sf_unit<T>(bd, u, reinterpret_cast<const T *>(p.fields) + p.foff[e],
+                   reinterpret_cast<T *>(p.out) + p.out_offset[e] + bd.base,
+                   reinterpret_cast<const T *>(g.pp), g.L, g.cols, smem_raw);
+        __syncthreads();
+    }
+}
+
+int hp_ctas_per_sm(bool fp32, size_t smem) {
+    int n = 0;
+    cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hp_contract_kernel<float>, 256, smem)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hp_contract_kernel<double>, 256, smem);
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+static cudaError_t scan(const int64_t *in, int64_t *out, int64_t *tmp, int64_t n, int64_t *total, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = (n + 1023) / 1024;
+    scan_block_kernel<<<(unsigned)nb, 1024, 0, s>>>(in, out, tmp, n);
+    scan_top_kernel<<<1, 1024, 0, s>>>(tmp, nb, total);
+    scan_add_kernel<<<(unsigned)nb, 1024, 0, s>>>(out, tmp, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hp(const HpParams &p, bool fp32, size_t smem, int persistent_ctas, cudaStream_t s) {
+    if (p.n_elem == 0) return cudaSuccess;
+    const unsigned eb = (unsigned)((p.n_elem + 255) / 256);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p.hist, 0, 16 * sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.ucnt, 0, p.n_elem * sizeof(int64_t), s)) != cudaSuccess) return e;
+    hp_count_kernel<<<eb, 256, 0, s>>>(p);
+    hp_bucket_kernel<<<1, 32, 0, s>>>(p);
+    hp_scatter_kernel<<<eb, 256, 0, s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan(p.ucnt, p.uoff, p.scan_tmp, p.n_elem, p.counters + 1, s)) != cudaSuccess) return e;
+    if ((e = scan(p.fcnt, p.foff, p.scan_tmp, p.n_elem, nullptr, s)) != cudaSuccess) return e;
+    hp_items_kernel<<<eb, 256, 0, s>>>(p);
+    if (fp32) hp_geom_kernel<float><<<(unsigned)p.n_elem, 256, 0, s>>>(p);
+    else hp_geom_kernel<double><<<(unsigned)p.n_elem, 256, 0, s>>>(p);
+    if (fp32) hp_contract_kernel<float><<<persistent_ctas, 256, smem, s>>>(p);
+    else hp_contract_kernel<double><<<persistent_ctas, 256, smem, s>>>(p);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------------------
@@ -787,7 +1038,7 @@ cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s) {
-    const int64_t ctas = (int64_t)p.nunits * p.n_elem;
+    const int64_t ctas = (int64_t)p.nblock * p.n_elem;
     if (ctas == 0) return cudaSuccess;
     sf_affine_kernel<T><<<(unsigned)ctas, 256, smem, s>>>(p);
     return cudaGetLastError();
@@ -808,6 +1059,8 @@ cudaError_t init_kernel_attributes(int optin_smem) {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = one((const void *)sf_general_kernel<double>);
     if (e == cudaSuccess) e = one((const void *)sf_general_kernel<float>);
+    if (e == cudaSuccess) e = one((const void *)hp_contract_kernel<double>);
+    if (e == cudaSuccess) e = one((const void *)hp_contract_kernel<float>);
     if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<3>);
     if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<4>);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<double>);

@@ -68,12 +68,45 @@ template <typename T>
 struct AffParams {
     const BlockDesc *blocks;
     const Unit *units;
-    int nunits;
+    const int *block_unit_begin;   // [nblock + 1]
+    int nblock, nj_max;
     const T *F;                // exact 1D integrals [NPAIR][NQ1][NQ1]
     const double *consts;      // [n_elem][AFF_CONST_STRIDE] from affine_const_kernel
     T *out;
     int64_t mat_stride, ld, n_elem;
 };
+
+// hp batching: per-q programs in device memory, indexed by q (entry 0 unused).
+struct HpProg {
+    const BlockDesc *blocks;
+    const Unit *units;
+    const void *pp;            // pair products of the stage type (double or float)
+    const double *zeta, *w;    // Gauss rule
+    int nunits, L, nfields, cols, valid;
+};
+
+struct HpParams {
+    int space;                 // base space id
+    int64_t n_elem;
+    const double *verts, *coeffs;
+    const int *q_elem;
+    const int64_t *out_offset;
+    void *out;
+    const HpProg *tab;         // [MAXQ + 1]
+    DevStatus *status;
+    // workspace (stream-ordered, per call)
+    int *hist, *bstart, *bfill;      // [16] each
+    int *order;                      // [n_elem]: elements sorted by descending q
+    int64_t *ucnt, *uoff;            // [n_elem]: units of order[k] and their exclusive prefix
+    int64_t *fcnt, *foff;            // [n_elem]: field values of element e and their prefix
+    int *item_k;                     // [max_items]: position k of each work item
+    int64_t *counters;               // [4]: 0 work counter, 1 total items, 2 valid elements
+    int64_t *scan_tmp;               // block sums of the scans
+    void *fields;
+};
+
+cudaError_t launch_hp(const HpParams &p, bool fp32, size_t smem, int persistent_ctas, cudaStream_t s);
+int hp_ctas_per_sm(bool fp32, size_t smem);
 
 template <typename TF> cudaError_t launch_geom(const GeomParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_general(const SfParams<T> &p, size_t smem, cudaStream_t s);
@@ -83,7 +116,7 @@ template <typename T> cudaError_t launch_affine(const AffParams<T> &p, size_t sm
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
 cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);
-size_t affine_smem_values(int ng, int nr1, int nr2, int nc1, int nc2, int nj);
+size_t affine_smem_values(int ng, int nterm, int nr1, int nr2, int nc1, int nc2, int nj);
 int max_dynamic_smem(int optin_smem);
 
 }  // namespace dpg

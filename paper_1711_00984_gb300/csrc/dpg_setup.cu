@@ -232,7 +232,7 @@ static size_t smem_values(const BlockDesc &b, int L, int nj) {
     return P1 + P2 + P3 + A + B;
 }
 
-Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order) {
+Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order, int force_nj) {
     Program pr;
     std::memset(pr.blocks, 0, sizeof(pr.blocks));
     pr.space = space; pr.q = q; pr.L = L; pr.p = p; pr.split = split;
@@ -331,10 +331,14 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     int maxnA = 1;
     for (int k = 0; k < pr.nblock; ++k) maxnA = std::max(maxnA, pr.blocks[k].nc[pr.blocks[k].dir[2]]);
     int nj = std::min(NJMAX, maxnA);
-    for (; nj > 1; --nj) {
-        size_t m = 0;
-        for (int k = 0; k < pr.nblock; ++k) m = std::max(m, smem_bytes(pr.blocks[k], nj));
-        if (m <= budget) break;
+    if (force_nj > 0) {
+        nj = std::min(force_nj, nj);                       // autotuned chunk (caller checks smem)
+    } else {
+        for (; nj > 1; --nj) {
+            size_t m = 0;
+            for (int k = 0; k < pr.nblock; ++k) m = std::max(m, smem_bytes(pr.blocks[k], nj));
+            if (m <= budget) break;
+        }
     }
     pr.nj = nj;
     size_t m = 0, mb = 0;

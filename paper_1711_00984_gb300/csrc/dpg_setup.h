@@ -36,7 +36,10 @@ HostTables make_tables(int q, int L);
 // xi_3 (FP32 general kernel: contiguous tile rows); ORDER_NATURAL the paper's order
 // (stage A over xi_3, B over xi_2, C over xi_1; affine kernel).
 enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2 };
-Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order = ORDER_BEST);
+// force_nj > 0 fixes the stage-A chunk (autotuner); otherwise the largest chunk whose
+// shared memory fits the kernel's budget is taken.
+Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order = ORDER_BEST,
+                     int force_nj = 0);
 int64_t rows_of(int space, int q);
 int64_t cols_of(int space, int p, int q);
 
