@@ -359,7 +359,17 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
                const double *coeffs, T *out, cudaStream_t s) {
     const Program &pr = pe->prog_aff;
     const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
-    const int64_t per_launch = INT_MAX / (int64_t)pr.nblock;
+    // CTAs per (element, block): enough for about six waves of the SMs, at most one per unit
+    int max_units_block = 1;
+    for (int k = 0; k < pr.nblock; ++k) {
+        int c = 0;
+        for (const Unit &u : pr.units) c += u.block == k;
+        max_units_block = std::max(max_units_block, c);
+    }
+    const int64_t target = (int64_t)g_num_sms * 6 * 4;
+    const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_units_block,
+                                              (target + n_elem * pr.nblock - 1) / (n_elem * pr.nblock)));
+    const int64_t per_launch = INT_MAX / ((int64_t)pr.nblock * nsplit);
     void *consts = nullptr;
     CK(cudaMallocFromPoolAsync(&consts, (size_t)n_elem * AFF_CONST_STRIDE * sizeof(double), ds->pool, s));
     AffConstParams cp;
@@ -372,7 +382,7 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         const int64_t ne = std::min(per_launch, n_elem - e0);
         AffParams<T> ap;
         ap.blocks = pe->d_blocks_aff; ap.units = pe->d_units_aff; ap.block_unit_begin = pe->d_block_units_aff;
-        ap.nblock = pr.nblock; ap.nj_max = pr.nj;
+        ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit;
         if constexpr (sizeof(T) == 8) ap.F = te->F64; else ap.F = te->F32;
         ap.consts = (const double *)consts + AFF_CONST_STRIDE * e0;
         ap.out = out + e0 * mat;

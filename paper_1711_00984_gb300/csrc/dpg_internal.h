@@ -100,6 +100,28 @@ DPG_HD inline F32Layout f32_layout(const BlockDesc &b, int L, int nj) {
     return f;
 }
 
+// Shared-memory layout (in values of the output type, every region a multiple of 4) of the
+// affine kernel for one block and a chunk of nj partners: Q and its non-zero list, F2, the
+// non-zero stage-C factors, and the output tile [nrow][ldt].  Index lists are ints stored
+// in value-sized slots.
+struct AffLayout {
+    int ldt, oQ, oF2, oQV, oQI, oF1V, oF1I, oT, total;
+};
+DPG_HD inline AffLayout aff_layout(int ng, int nterm, int nr1, int nr2, int nc1, int nc2, int nj) {
+    AffLayout a;
+    const int n22 = nr2 * nc2, n11 = nr1 * nc1, nrow = nr1 * nr2, ncol = nc1 * nc2 * nj;
+    a.ldt = ncol | 1;
+    a.oQ = 0;
+    a.oF2 = a.oQ + r4i(ng * n22 * nj);
+    a.oQV = a.oF2 + r4i(nterm * n22);
+    a.oQI = a.oQV + r4i(ng * n22 * nj);
+    a.oF1V = a.oQI + r4i(ng * n22 * nj);
+    a.oF1I = a.oF1V + r4i(ng * n11);
+    a.oT = a.oF1I + r4i(ng * n11);
+    a.total = a.oT + r4i(nrow * a.ldt);
+    return a;
+}
+
 // Device-resident tables of one (q, L).
 struct DevTables {
     int q, L;

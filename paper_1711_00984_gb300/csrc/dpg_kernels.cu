@@ -609,142 +609,145 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     __shared__ T cf[18];
     __shared__ int flag;
     __shared__ T st[MAXT * NJMAX];             // s_t = sign_t c_t F3_t(i3, j3) of the current unit
-    __shared__ unsigned char f1n[NQ1 * NQ1], f1g[NQ1 * NQ1 * MAXG];
-    __shared__ int coldec[NQ1 * NQ1 * NJMAX];  // column decode of the current unit's tile
+    __shared__ int f1c[MAXG], qc[MAXG];        // non-zero counts per group
     const int tid = threadIdx.x, nth = blockDim.x;
-    // one CTA per (element, block): the block's tables are built once, then every work
-    // unit (i3, chunk of j3) of the block is produced in turn
-    const int k = blockIdx.x % p.nblock;
-    const int64_t e = blockIdx.x / p.nblock;
+    // CTA = (element, block, share of the block's units): the block's tables are built once
+    const int nsplit = p.nsplit;
+    const int ks = blockIdx.x % (p.nblock * nsplit);
+    const int k = ks / nsplit, split = ks - k * nsplit;
+    const int64_t e = blockIdx.x / (p.nblock * nsplit);
     if (e >= p.n_elem) return;
     load_block(p.blocks + k, bd);
     if (tid < 18) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
     if (tid == 18) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
+    if (tid < MAXG) f1c[tid] = 0;
     __syncthreads();
 
     const int nr1 = bd.nr[0], nr2 = bd.nr[1], nc1 = bd.nc[0], nc2 = bd.nc[1];
     const int ng = bd.ng, nterm = bd.nterm, njm = p.nj_max;
-    const int n22 = nr2 * nc2;
+    const int n11 = nr1 * nc1, n22 = nr2 * nc2, ncj = nc1 * nc2, nrow = nr1 * nr2;
     const T *F = p.F;
     auto Fv = [&](int pair, int i, int j) -> T { return F[((size_t)pair * NQ1 + i) * NQ1 + j]; };
-    T *Q = reinterpret_cast<T *>(smem_raw);                            // [ng][nr2][nc2][nj]
-    T *F1 = Q + r4((size_t)ng * n22 * njm);                             // [nr1][nc1][MAXG] non-zeros
-    T *panel = F1 + r4((size_t)MAXG * nr1 * nc1);                      // [nrow][AFF_W + 1]
-    T *F2 = panel + (size_t)nr1 * nr2 * (AFF_W + 1);                   // [nterm][nr2][nc2]
-    // stage-C factors: per (i1, j1) the number of non-zero groups and their values (the
-    // loop over them has a data-dependent trip count: no predicated FP64 FMAs)
-    for (int it = tid; it < nr1 * nc1; it += nth) {
-        int cnt = 0;
-        for (int g = 0; g < ng; ++g) {
-            const T v = Fv(bd.g_pair[g], it / nc1, it % nc1);
-            if (!is_zero(v)) { F1[it * MAXG + cnt] = v; f1g[it * MAXG + cnt] = (unsigned char)g; ++cnt; }
+    const AffLayout lay = aff_layout(ng, nterm, nr1, nr2, nc1, nc2, njm);
+    T *Q = reinterpret_cast<T *>(smem_raw) + lay.oQ;                   // [ng][nr2][nc2][nj]
+    T *F2 = reinterpret_cast<T *>(smem_raw) + lay.oF2;                 // [nterm][nr2][nc2]
+    T *qv = reinterpret_cast<T *>(smem_raw) + lay.oQV;                 // [ng][n22 nj] non-zero Q
+    T *f1v = reinterpret_cast<T *>(smem_raw) + lay.oF1V;               // [ng][n11] non-zero F1
+    T *tile = reinterpret_cast<T *>(smem_raw) + lay.oT;                // [nrow][ldt]
+    int *qi = reinterpret_cast<int *>(reinterpret_cast<T *>(smem_raw) + lay.oQI);   // packed (i2,j2,jj)
+    int *f1i = reinterpret_cast<int *>(reinterpret_cast<T *>(smem_raw) + lay.oF1I); // packed (i1,j1)
+    const unsigned mnc1 = div_magic(nc1), mnc2 = div_magic(nc2), mn22 = div_magic(n22), mncj = div_magic(ncj);
+
+    // stage-C factors: compact non-zero lists per group
+    for (int it = tid; it < ng * n11; it += nth) {
+        const int g = it / n11, ij = it - g * n11;
+        const int i1 = fdiv(ij, mnc1), j1 = ij - i1 * nc1;
+        const T v = Fv(bd.g_pair[g], i1, j1);
+        if (!is_zero(v)) {
+            const int slot = atomicAdd(&f1c[g], 1);
+            f1v[g * n11 + slot] = v;
+            f1i[g * n11 + slot] = i1 | (j1 << 16);
         }
-        f1n[it] = (unsigned char)cnt;
     }
     for (int it = tid; it < nterm * n22; it += nth) {                   // F2_t(i2, j2)
         const int t = it / n22, ij = it - t * n22;
         const TermDesc &td = bd.term[t];
-        F2[it] = Fv(3 * td.kr[1] + td.kc[1], ij / nc2, ij % nc2);
+        const int i2 = fdiv(ij, mnc2);
+        F2[it] = Fv(3 * td.kr[1] + td.kc[1], i2, ij - i2 * nc2);
     }
 
     T *o = p.out + (size_t)e * p.mat_stride + bd.base;
     const int64_t ld = p.ld;
     const bool bad = flag != 0;
-    const int ncj = nc1 * nc2;
-    const bool mir = bd.sym != 0;
-    const int ps = AFF_W + 1;
-    const int tx = tid % AFF_W, ty = tid / AFF_W, ny = nth / AFF_W;
-    const int nrow = nr1 * nr2;
-    const unsigned mncj = div_magic(ncj), mnc1 = div_magic(nc1), mn22 = div_magic(n22);
+    const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
     const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
-    for (int ui = ub; ui < ue; ++ui) {
+    for (int ui = ub + split; ui < ue; ui += nsplit) {               // this CTA's share of the units
         const Unit u = p.units[ui];
         const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
-        const unsigned mnju = div_magic(nj);
+        const unsigned mnj = div_magic(nj);
+        const int ncol = ncj * nj, ldt = lay.ldt;
         __syncthreads();                                                // previous unit done
         for (int it = tid; it < nterm * nj; it += nth) {
-            const int t = fdiv(it, mnju), jj = it - t * nj;
+            const int t = fdiv(it, mnj), jj = it - t * nj;
             const TermDesc &td = bd.term[t];
             const T f3 = Fv(3 * td.kr[2] + td.kc[2], i3, j3b + jj);
             st[it] = is_zero(f3) ? T(0) : (td.sign > 0 ? cf[td.field] : -cf[td.field]) * f3;
         }
-        // column decode of the unit's tile: col -> (j1, j2, jj, cj = j1 + nc1 j2)
-        const int ncol = ncj * nj;
-        for (int c = tid; c < ncol; c += nth) {
-            const int jj = fdiv(c, mncj), cj = c - jj * ncj;
-            const int j2 = fdiv(cj, mnc1), j1 = cj - j2 * nc1;
-            coldec[c] = j1 | (j2 << 8) | (jj << 16);
-        }
+        if (tid < MAXG) qc[tid] = 0;
+        for (int it = tid; it < nrow * ldt; it += nth) tile[it] = T(0);
         __syncthreads();
-        // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2)
+        // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2), kept as a list of its non-zeros
         for (int it = tid; it < ng * n22 * nj; it += nth) {
-            const int r = fdiv(it, mnju), jj = it - r * nj;
+            const int r = fdiv(it, mnj), jj = it - r * nj;
             const int g = fdiv(r, mn22), ij2 = r - g * n22;
             T acc = T(0);
+            bool any = false;
             for (int t = 0; t < nterm; ++t) {
                 if (bd.h_g[bd.term[t].h] != g) continue;
                 const T sv = st[t * nj + jj];
                 if (is_zero(sv)) continue;
                 const T f2 = F2[t * n22 + ij2];
-                if (!is_zero(f2)) acc = fma(sv, f2, acc);
+                if (!is_zero(f2)) { acc = fma(sv, f2, acc); any = true; }
             }
-            Q[it] = acc;
+            if (any && !is_zero(acc)) {
+                const int slot = atomicAdd(&qc[g], 1);
+                const int i2 = fdiv(ij2, mnc2), j2 = ij2 - i2 * nc2;
+                qv[g * n22 * njm + slot] = acc;
+                qi[g * n22 * njm + slot] = i2 | (j2 << 8) | (jj << 16);
+            }
         }
         __syncthreads();
-
-        const int64_t R0 = bd.row_off + (int64_t)i3 * nr1 * nr2;     // row of tile row 0
-        const int64_t C0 = bd.col_off + (int64_t)j3b * ncj;          // column of tile column 0
-        const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
-        T *orow0 = o + R0 * ld + C0;
-        for (int cb = 0; cb < ncol; cb += AFF_W) {
-            const int wc = min(AFF_W, ncol - cb);
-            const int col = cb + tx;
-            const bool colok = tx < wc;
-            const int dec = colok ? coldec[col] : 0;
-            const int j1 = dec & 0xff, j2 = (dec >> 8) & 0xff, jj = dec >> 16;
-            const int cj = j1 + nc1 * j2;
-            const T *Qc = Q + (size_t)j2 * nj + jj;                   // [g][i2][j2][jj]
-            int i1 = ty % nr1, i2 = ty / nr1;
-            T *op = orow0 + (int64_t)ty * ld + col;
-            const int64_t ostep = (int64_t)ny * ld;
-            for (int row = ty; row < nrow; row += ny, op += ostep) {
-                if (colok) {
-                    T acc = T(0);
-                    if (!(jj == jd && row > cj)) {      // lower triangle of a diagonal tile: mirrored
-                        const int ij1 = i1 * nc1 + j1, cnt = f1n[ij1];
-                        for (int kk = 0; kk < cnt; ++kk) {
-                            const int g = f1g[ij1 * MAXG + kk];
-                            const T qv = Qc[(size_t)((g * nr2 + i2) * nc2) * nj];
-                            if (!is_zero(qv)) acc = fma(F1[ij1 * MAXG + kk], qv, acc);
-                        }
-                        if (bad) acc = qnan<T>();
-                        *op = acc;
-                    }
-                    panel[row * ps + tx] = acc;
-                }
-                i1 += ny;                                             // advance (i1, i2) by ny rows
-                while (i1 >= nr1) { i1 -= nr1; ++i2; }
+        // scatter the non-zero products group by group (one product per entry per group)
+        for (int g = 0; g < ng; ++g) {
+            const int nf = f1c[g], nq = qc[g];
+            for (int it = tid; it < nf * nq; it += nth) {
+                const int a = it / nq, b = it - a * nq;
+                const int fi = f1i[g * n11 + a], qq = qi[g * n22 * njm + b];
+                const int i1 = fi & 0xffff, j1 = fi >> 16;
+                const int i2 = qq & 0xff, j2 = (qq >> 8) & 0xff, jj = qq >> 16;
+                T *dst = tile + (i1 + nr1 * i2) * ldt + j1 + nc1 * (j2 + nc2 * jj);
+                *dst = fma(f1v[g * n11 + a], qv[g * n22 * njm + b], *dst);
             }
-            if (mir) {
-                __syncthreads();
-                // the mirror: tile column c is output row C0 + c, a contiguous segment of nrow
-                for (int w = ty; w < wc; w += ny) {
-                    const int c = cb + w;
-                    const int dw = coldec[c];
-                    const int jjw = dw >> 16, cjw = (dw & 0xff) + nc1 * ((dw >> 8) & 0xff);
-                    const int rend = jjw == jd ? cjw : nrow;            // strictly upper rows
-                    T *mrow = o + (C0 + c) * ld + R0;
-                    for (int row = tx; row < rend; row += AFF_W) mrow[row] = panel[row * ps + w];
+            __syncthreads();
+        }
+        // write-out: tile rows are contiguous runs of the output; on the diagonal sub-tile
+        // (iA == jA of a diagonal block) the lower half is taken from the upper entries
+        const int64_t R0 = bd.row_off + (int64_t)i3 * nrow;
+        const int64_t C0 = bd.col_off + (int64_t)j3b * ncj;
+        const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
+        const T nanv = qnan<T>();
+        for (int row = warp; row < nrow; row += nwarp) {
+            T *orow = o + (R0 + row) * ld + C0;
+            const T *trw = tile + row * ldt;
+            for (int jj = 0; jj < nj; ++jj) {
+                const int cb = jj * ncj;
+                if (jj == jd) {
+                    for (int c = lane; c < ncj; c += 32) {
+                        const T v = c >= row ? trw[cb + c] : tile[c * ldt + cb + row];
+                        orow[cb + c] = bad ? nanv : v;
+                    }
+                } else {
+                    for (int c = lane; c < ncj; c += 32) orow[cb + c] = bad ? nanv : trw[cb + c];
                 }
-                __syncthreads();
             }
         }
+        if (bd.sym != 0) {
+            // the mirror of the off-diagonal sub-tiles: tile column c -> output row C0 + c
+            for (int jj = 0; jj < nj; ++jj) {
+                if (jj == jd) continue;
+                for (int cj = warp; cj < ncj; cj += nwarp) {
+                    const int c = jj * ncj + cj;
+                    T *mrow = o + (C0 + c) * ld + R0;
+                    for (int row = lane; row < nrow; row += 32) mrow[row] = bad ? nanv : tile[row * ldt + c];
+                }
+            }
+        }
+        (void)mncj;
     }
 }
 
 size_t affine_smem_values(int ng, int nterm, int nr1, int nr2, int nc1, int nc2, int nj) {
-    return r4_host((size_t)ng * nr2 * nc2 * nj) + r4_host((size_t)MAXG * nr1 * nc1) + (size_t)nr1 * nr2 * (AFF_W + 1) +
-           (size_t)nterm * nr2 * nc2;
+    return (size_t)aff_layout(ng, nterm, nr1, nr2, nc1, nc2, nj).total;
 }
 
 
@@ -1038,7 +1041,7 @@ cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s) {
-    const int64_t ctas = (int64_t)p.nblock * p.n_elem;
+    const int64_t ctas = (int64_t)p.nblock * p.nsplit * p.n_elem;
     if (ctas == 0) return cudaSuccess;
     sf_affine_kernel<T><<<(unsigned)ctas, 256, smem, s>>>(p);
     return cudaGetLastError();

@@ -70,6 +70,7 @@ struct AffParams {
     const Unit *units;
     const int *block_unit_begin;   // [nblock + 1]
     int nblock, nj_max;
+    int nsplit;                    // CTAs per (element, block): each takes every nsplit-th unit
     const T *F;                // exact 1D integrals [NPAIR][NQ1][NQ1]
     const double *consts;      // [n_elem][AFF_CONST_STRIDE] from affine_const_kernel
     T *out;

@@ -325,9 +325,11 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     // kernel model, or the FP32 kernel's layout for ORDER_A3 programs)
     auto smem_bytes = [&](const BlockDesc &b, int njv) -> size_t {
         if (order == ORDER_A3) return (size_t)f32_layout(b, L, njv).total * sizeof(float);
+        if (order == ORDER_NATURAL)
+            return (size_t)aff_layout(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], njv).total * sizeof(double);
         return smem_values(b, L, njv) * sizeof(double);
     };
-    const size_t budget = order == ORDER_A3 ? 110 * 1024 : 160 * 1024;
+    const size_t budget = order == ORDER_BEST ? 160 * 1024 : 110 * 1024;
     int maxnA = 1;
     for (int k = 0; k < pr.nblock; ++k) maxnA = std::max(maxnA, pr.blocks[k].nc[pr.blocks[k].dir[2]]);
     int nj = std::min(NJMAX, maxnA);
