@@ -181,10 +181,11 @@ int dpg_integrate_noalloc(int space, int p_trial, int q_test, int64_t n_elem,
                           const double *vertices, const double *coeffs, void *out, void *stream);
 
 /* Same as dpg_integrate, but vertices, coeffs and out are HOST buffers (page-locked for
- * full copy speed).  Copies the inputs to the device, integrates, copies the result
- * back, and synchronises `stream` before returning; device buffers are taken from the
- * library memory pool.  Device-detected errors are returned directly (the call reads
- * the status word). */
+ * full copy speed).  Copies the inputs to the device, then streams the batch: chunks of
+ * about 64 MB of output are integrated on `stream` while earlier chunks are copied back
+ * on library-owned copy streams, so compute and device-to-host traffic overlap.  The call
+ * synchronises `stream` before returning; device buffers come from the library memory
+ * pool.  Device-detected errors are returned directly (the call reads the status word). */
 int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem,
                        const double *vertices, const double *coeffs, void *out, void *stream);
 

@@ -72,6 +72,7 @@ struct DeviceState {
     int hp_max_units[6] = {};        // most work units of an initialised q
     int64_t hp_max_fields[6] = {};   // most metric-field values of an initialised q
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t copy_streams[4] = {};   // device-to-host drains of dpg_integrate_host
     std::map<HpKey, cudaGraphExec_t> hp_graphs;
     std::map<std::pair<int, int>, std::unique_ptr<TableEntry>> tables;   // (q, L)
     std::map<ProgKey, std::unique_ptr<ProgEntry>> progs;
@@ -131,6 +132,7 @@ int device_state(DeviceState **out) {
     g_max_dyn_smem = max_dynamic_smem(optin);
     CK(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
+    for (auto &cs : st->copy_streams) CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     *out = st.get();
     g_dev[dev] = std::move(st);
     return DPG_OK;
@@ -631,7 +633,8 @@ int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem, const
     if (!vertices || !out) return DPG_ERR_ARG;
     const Program &pr = pe->prog;
     const size_t esz = (space & DPG_FP32) ? sizeof(float) : sizeof(double);
-    const size_t out_bytes = (size_t)n_elem * pr.parts * pr.rows * pr.cols * esz;
+    const size_t per_out = (size_t)pr.parts * pr.rows * pr.cols * esz;
+    const size_t out_bytes = (size_t)n_elem * per_out;
     const size_t v_bytes = (size_t)n_elem * 24 * sizeof(double);
     const size_t c_bytes = coeffs ? (size_t)n_elem * 2 * sizeof(double) : 0;
     void *dv = nullptr, *dc = nullptr, *dout = nullptr;
@@ -640,14 +643,39 @@ int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem, const
     CK(cudaMallocFromPoolAsync(&dout, out_bytes, ds->pool, s));
     CK(cudaMemcpyAsync(dv, vertices, v_bytes, cudaMemcpyHostToDevice, s));
     if (c_bytes) CK(cudaMemcpyAsync(dc, coeffs, c_bytes, cudaMemcpyHostToDevice, s));
-    r = integrate_locked(space, p_trial, q_test, n_elem, (const double *)dv, (const double *)dc, dout, s);
-    if (r == DPG_OK) {
-        CK(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s));
+    // stream the batch: chunk k is integrated on `s` while earlier chunks drain to the
+    // host on the copy streams (about 64 MB per chunk, at most 64 chunks)
+    const int64_t by_bytes = (int64_t)((out_bytes + (size_t(64) << 20) - 1) / (size_t(64) << 20));
+    const int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>({ n_elem, by_bytes, 64 }));
+    const int64_t per = (n_elem + nchunk - 1) / nchunk;
+    std::vector<cudaEvent_t> evs;
+    for (int64_t e0 = 0, c = 0; e0 < n_elem && r == DPG_OK; e0 += per, ++c) {
+        const int64_t ne = std::min(per, n_elem - e0);
+        r = integrate_locked(space, p_trial, q_test, ne, (const double *)dv + 24 * e0,
+                             dc ? (const double *)dc + 2 * e0 : nullptr, (char *)dout + e0 * per_out, s);
+        if (r) break;
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        evs.push_back(ev);
+        CK(cudaEventRecord(ev, s));
+        cudaStream_t cs = ds->copy_streams[c % 4];
+        CK(cudaStreamWaitEvent(cs, ev, 0));
+        CK(cudaMemcpyAsync((char *)out + e0 * per_out, (char *)dout + e0 * per_out, ne * per_out,
+                           cudaMemcpyDeviceToHost, cs));
+    }
+    // join the copy streams back into `s` before the buffers are released
+    for (auto cs : ds->copy_streams) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        evs.push_back(ev);
+        CK(cudaEventRecord(ev, cs));
+        CK(cudaStreamWaitEvent(s, ev, 0));
     }
     cudaFreeAsync(dv, s);
     if (dc) cudaFreeAsync(dc, s);
     cudaFreeAsync(dout, s);
     CK(cudaStreamSynchronize(s));
+    for (auto ev : evs) cudaEventDestroy(ev);
     if (r) return r;
     return read_status(ds, nullptr);
 }

@@ -203,3 +203,19 @@ def test_non_affine_element_on_affine_path(gpu_lib):
     got, code, bad = run(gpu_lib, "H1", 2, v, affine=True)
     assert code == 6 and bad == 2
     assert np.all(np.isnan(got[2])) and np.all(np.isfinite(np.delete(got, 2, axis=0)))
+
+
+def test_host_buffer_entry_point(gpu_lib):
+    """dpg_integrate_host (pinned host buffers, streamed chunks) equals dpg_integrate."""
+    dpg = gpu_lib
+    w = meshgen.workload("seq_q5_8x8x8")
+    for space in ["HCURL", "L2"]:
+        dpg.dpg_tables_init_L(5, 7, space)
+        v = torch.from_numpy(w["verts"]).pin_memory()
+        c = torch.from_numpy(meshgen.coeff_pairs(space, w["k"], 512)).pin_memory()
+        shape = (512,) + dpg.matrix_shape(space, 5)
+        out = torch.empty(shape, dtype=torch.float64).pin_memory()
+        sh = int(torch.cuda.current_stream().cuda_stream)
+        assert dpg.dpg_integrate_host(dpg.space_id(space), 0, 5, 512, v.data_ptr(), c.data_ptr(), out.data_ptr(), sh) == 0
+        ref = dpg.integrate(space, 5, v.cuda(), c.cuda()).cpu()
+        assert torch.equal(out, ref)
