@@ -204,7 +204,8 @@ const char *dpg_last_cuda_error(void);
 /* Algorithmic floating-point operations of one element (multiply and add counted
  * separately) of the sum-factorization path (stages of Eqs. 2.23-2.25 per block of
  * terms, symmetric tiles counted once), or of the affine path (non-zero products of the
- * Kronecker sums of Sec. 2.8.1) with DPG_MAP_AFFINE.  Tables must be initialised.
+ * Kronecker sums of Sec. 2.8.1) with DPG_MAP_AFFINE.  The count is the same for the FP64
+ * and FP32 forms (cheapest direction order per block).  Tables must be initialised.
  * Returns -1 on error.  Used to report the ALU roofline. */
 double dpg_flops_per_element(int space, int p_trial, int q_test);
 

@@ -40,7 +40,11 @@ struct ProgEntry {
     Program prog_aff;               // affine path: the paper's direction order
     BlockDesc *d_blocks_aff = nullptr;
     Unit *d_units_aff = nullptr;
-    Program prog32;                 // FP32 general path: stage A on xi_3
+    Program prog32;                 // FP32 general path: row-panel program (panel32) or
+                                    // the mirrored-tile program with stage A on xi_3
+    bool panel32 = false;
+    float *d_ctab32 = nullptr;      // panel32: constant operands of every block
+    int *d_ctab_off32 = nullptr;    // panel32: [nblock] offsets into d_ctab32
     BlockDesc *d_blocks32 = nullptr;
     Unit *d_units32 = nullptr;
     int max_nc1_32 = 0;             // largest stage-C column extent of prog32
@@ -158,6 +162,43 @@ int get_tables(DeviceState *ds, int q, int L, TableEntry **out) {
     return DPG_OK;
 }
 
+// Build and upload the FP32 general-path program of pe with stage-A chunk nj (0: largest
+// that fits): the row-panel program where its shared memory fits a CTA, else the
+// mirrored-tile program.  The previous device copies are freed (the caller synchronises).
+int setup_prog32(ProgEntry *pe, int space, int q, int L, int p, bool split, const HostTables &tab, int nj) {
+    Program np = make_program(space, q, L, p, split, tab, ORDER_PANEL, nj);
+    const bool panel = np.smem_bytes <= (size_t)g_max_dyn_smem;
+    if (!panel) np = make_program(space, q, L, p, split, tab, ORDER_A3, nj);
+    if (np.smem_bytes > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
+    BlockDesc *db = nullptr;
+    Unit *du = nullptr;
+    int *dbu = nullptr, *doff = nullptr;
+    float *dct = nullptr;
+    int r;
+    if ((r = upload(np.blocks, (size_t)np.nblock, &db))) return r;
+    if ((r = upload(np.units.data(), np.units.size(), &du))) return r;
+    std::vector<int> ub(np.nblock + 1, 0);
+    for (const Unit &u : np.units) ub[u.block + 1]++;
+    for (int k = 0; k < np.nblock; ++k) ub[k + 1] += ub[k];
+    if ((r = upload(ub.data(), ub.size(), &dbu))) return r;
+    if (panel) {
+        std::vector<float> ct;
+        std::vector<int> off;
+        build_panel_tables(np, tab, ct, off);
+        if ((r = upload(ct.data(), ct.size(), &dct))) return r;
+        if ((r = upload(off.data(), off.size(), &doff))) return r;
+    }
+    cudaFree(pe->d_blocks32); cudaFree(pe->d_units32); cudaFree(pe->d_block_units32);
+    cudaFree(pe->d_ctab32); cudaFree(pe->d_ctab_off32);
+    pe->d_blocks32 = db; pe->d_units32 = du; pe->d_block_units32 = dbu;
+    pe->d_ctab32 = dct; pe->d_ctab_off32 = doff;
+    pe->panel32 = panel;
+    pe->prog32 = np;
+    pe->max_nc1_32 = 0;
+    for (int k = 0; k < np.nblock; ++k) pe->max_nc1_32 = std::max(pe->max_nc1_32, np.blocks[k].nc[np.blocks[k].dir[0]]);
+    return DPG_OK;
+}
+
 int get_program(DeviceState *ds, int space, int q, int L, int p, int split, const HostTables &tab, ProgEntry **out) {
     ProgKey key{ space, q, L, p, split };
     auto it = ds->progs.find(key);
@@ -165,7 +206,6 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
     auto pe = std::make_unique<ProgEntry>();
     pe->prog = make_program(space, q, L, p, split != 0, tab);
     pe->prog_aff = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL);
-    pe->prog32 = make_program(space, q, L, p, split != 0, tab, ORDER_A3);
     const Program &pr = pe->prog;
     if (pr.smem_values * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     int r;
@@ -187,16 +227,7 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
     }
     if (m * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     pe->smem_aff = m;
-    const Program &p3 = pe->prog32;
-    if (p3.smem_bytes > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
-    if ((r = upload(p3.blocks, (size_t)p3.nblock, &pe->d_blocks32))) return r;
-    if ((r = upload(p3.units.data(), p3.units.size(), &pe->d_units32))) return r;
-    for (int k = 0; k < p3.nblock; ++k)
-        pe->max_nc1_32 = std::max(pe->max_nc1_32, p3.blocks[k].nc[p3.blocks[k].dir[0]]);
-    std::vector<int> ubeg(p3.nblock + 1, 0);
-    for (const Unit &u : p3.units) ubeg[u.block + 1]++;
-    for (int k = 0; k < p3.nblock; ++k) ubeg[k + 1] += ubeg[k];
-    if ((r = upload(ubeg.data(), ubeg.size(), &pe->d_block_units32))) return r;
+    if ((r = setup_prog32(pe.get(), space, q, L, p, split != 0, tab, 0))) return r;
     *out = pe.get();
     ds->progs[key] = std::move(pe);
     return DPG_OK;
@@ -247,6 +278,7 @@ void free_device_state(DeviceState &ds) {
         cudaFree(kv.second->d_blocks); cudaFree(kv.second->d_units);
         cudaFree(kv.second->d_blocks_aff); cudaFree(kv.second->d_units_aff); cudaFree(kv.second->d_block_units_aff);
         cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
+        cudaFree(kv.second->d_ctab32); cudaFree(kv.second->d_ctab_off32);
     }
     for (auto &kv : ds.hp_graphs) cudaGraphExecDestroy(kv.second);
     ds.hp_graphs.clear();
@@ -324,6 +356,24 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
         g.fields = ws; g.status = ds->status;
         cudaError_t le = launch_geom<T>(g, s);
         if (le != cudaSuccess) { rc = cuda_fail(le, "geom_kernel launch", __LINE__); break; }
+        if constexpr (f32) if (pe->panel32) {
+            PanelParams pp;
+            pp.blocks = pe->d_blocks32; pp.units = pe->d_units32; pp.block_unit_begin = pe->d_block_units32;
+            pp.ctab = pe->d_ctab32; pp.ctab_off = pe->d_ctab_off32;
+            pp.nblock = pr.nblock; pp.nj_max = pr.nj;
+            // about four waves of two CTAs per SM, each CTA a chunk of elements of one block
+            const int64_t target = (int64_t)g_num_sms * 2 * 4;
+            int64_t epc = (ne * pr.nblock + target - 1) / target;
+            pp.elems_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(epc, 1 << 20));
+            pp.L = L; pp.nfields = pr.nfields;
+            pp.pp = te->pp32;
+            pp.fields = reinterpret_cast<const float *>(ws);
+            pp.out = reinterpret_cast<float *>(out + e0 * mat);
+            pp.mat_stride = mat; pp.ld = pr.cols; pp.n_elem = ne;
+            le = launch_panel_f32(pp, pr.smem_bytes, s);
+            if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
+            continue;
+        }
         if constexpr (f32) {
             SfParams32 sp;
             sp.blocks = pe->d_blocks32; sp.units = pe->d_units32; sp.block_unit_begin = pe->d_block_units32;
@@ -455,31 +505,21 @@ int enqueue_hp(DeviceState *ds, int space, int64_t n, const double *verts, const
 // Replace the general-path program of pe (FP32 kernel's or FP64 kernel's) by one built
 // with stage-A chunk nj.  Synchronises the device (the old descriptors are freed).
 int install_program(ProgEntry *pe, TableEntry *te, int space, int q, int L, bool fp32, int nj) {
-    Program np = make_program(space, q, L, 0, false, te->host, fp32 ? ORDER_A3 : ORDER_BEST, nj);
-    const size_t need = fp32 ? np.smem_bytes : np.smem_values * sizeof(double);
-    if (need > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
+    if (fp32) {
+        CK(cudaDeviceSynchronize());
+        return setup_prog32(pe, space, q, L, 0, false, te->host, nj);
+    }
+    Program np = make_program(space, q, L, 0, false, te->host, ORDER_BEST, nj);
+    if (np.smem_values * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     BlockDesc *db = nullptr;
     Unit *du = nullptr;
-    int *dbu = nullptr;
     int r;
     if ((r = upload(np.blocks, (size_t)np.nblock, &db))) return r;
     if ((r = upload(np.units.data(), np.units.size(), &du))) return r;
     CK(cudaDeviceSynchronize());
-    if (fp32) {
-        std::vector<int> ub(np.nblock + 1, 0);
-        for (const Unit &u : np.units) ub[u.block + 1]++;
-        for (int k = 0; k < np.nblock; ++k) ub[k + 1] += ub[k];
-        if ((r = upload(ub.data(), ub.size(), &dbu))) return r;
-        cudaFree(pe->d_blocks32); cudaFree(pe->d_units32); cudaFree(pe->d_block_units32);
-        pe->d_blocks32 = db; pe->d_units32 = du; pe->d_block_units32 = dbu;
-        pe->prog32 = np;
-        pe->max_nc1_32 = 0;
-        for (int k = 0; k < np.nblock; ++k) pe->max_nc1_32 = std::max(pe->max_nc1_32, np.blocks[k].nc[np.blocks[k].dir[0]]);
-    } else {
-        cudaFree(pe->d_blocks); cudaFree(pe->d_units);
-        pe->d_blocks = db; pe->d_units = du;
-        pe->prog = np;
-    }
+    cudaFree(pe->d_blocks); cudaFree(pe->d_units);
+    pe->d_blocks = db; pe->d_units = du;
+    pe->prog = np;
     return DPG_OK;
 }
 
@@ -797,7 +837,9 @@ double dpg_flops_per_element(int space, int p_trial, int q_test) {
     ProgEntry *pe; TableEntry *te; DeviceState *ds;
     if (resolve(space, p_trial, q_test, &pe, &te, &ds) != DPG_OK) return -1.0;
     if (space & DPG_MAP_AFFINE) return pe->prog_aff.flops_affine;
-    return (space & DPG_FP32) ? pe->prog32.flops : pe->prog.flops;
+    // the same algorithmic count for both forms (the FP32 row-panel kernel also computes
+    // the mirrored blocks; that extra work is not counted)
+    return pe->prog.flops;
 }
 
 int dpg_measure_fma_peak(int precision, void *stream, double *flops) {

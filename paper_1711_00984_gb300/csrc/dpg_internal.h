@@ -122,6 +122,48 @@ DPG_HD inline AffLayout aff_layout(int ng, int nterm, int nr1, int nr2, int nc1,
     return a;
 }
 
+// Shared-memory layout (in floats, every region 16-byte aligned) of the FP32 row-panel
+// kernel for one block in the paper's direction order (stage C over xi_1, B over xi_2, A
+// over xi_3) and a chunk of nj stage-A partners.  Stages B and C are tensor-core
+// products (m16n8k8, TF32 operands split into high and low parts):
+//   stage B: D[(i2,j2)][(jj,l)] = sum_{h in g} sum_m P2_h[(i2,j2)][m] A_h[m][(jj,l)]
+//   stage C: D[(i2,x)][(i1,j1)] = sum_{g,l} Bs[(i2,x)][(g,l)] P1_g[(g,l)][(i1,j1)],
+// with x = j2 + nc2 jj.  The constant operands (P1, P2) are stored pre-split in fragment
+// order; the stage outputs A ([k][n], row stride = 8 or 24 mod 32) and Bs ([m][k], row
+// stride an odd multiple of 4) are plain FP32 and are split as they are loaded, both
+// layouts giving conflict-free fragment loads.
+struct PanelLayout {
+    int lpad, lsh, ksh;            // L rounded up to 8 (8 or 16), its log2, k-steps per group
+    int nr1, nr2, nc1, nc2;
+    int nt1, n1p, ks1;             // P1: n-tiles per i1, rows (i1, j1 padded), k-steps
+    int n22, mtb;                  // P2: rows (i2, j2), m-tiles
+    int nb, sn;                    // stage-A output: columns (jj, l), row stride
+    int nx, mc, mtc2, skc;         // stage-B output: x range, rows (i2, x), m-tiles (even), stride
+    int oP1, oP2, oA, oB, oP3, p3sz, oMo, oSt, stw, total;
+};
+constexpr int PANEL_WARPS = 8;
+DPG_HD inline PanelLayout panel_layout(const BlockDesc &b, int L, int nj) {
+    PanelLayout f;
+    f.lpad = (L + 7) & ~7; f.lsh = f.lpad == 8 ? 3 : 4; f.ksh = f.lpad >> 3;
+    f.nr1 = b.nr[0]; f.nr2 = b.nr[1]; f.nc1 = b.nc[0]; f.nc2 = b.nc[1];
+    f.nt1 = (f.nc1 + 7) >> 3; f.n1p = f.nr1 * f.nt1 * 8;
+    f.ks1 = b.ng * f.ksh;
+    f.n22 = f.nr2 * f.nc2; f.mtb = (f.n22 + 15) >> 4;
+    f.nb = nj * f.lpad; f.sn = (f.nb & 15) ? f.nb : f.nb + 8;
+    f.nx = f.nc2 * nj; f.mc = f.nr2 * f.nx; f.mtc2 = ((f.mc + 31) >> 5) * 2; f.skc = b.ng * f.lpad + 4;
+    f.oP1 = 0;                                                   // [ks][n][tig][4]
+    f.oP2 = f.oP1 + f.ks1 * f.n1p * 16;                          // [slot][mt][ks][lane][8]
+    f.oA = f.oP2 + b.np2 * f.mtb * f.ksh * 256;                  // [h lpad + m][sn]
+    f.oB = f.oA + r4i(b.nh * f.lpad * f.sn);                     // [mtc2 16][skc]
+    f.oP3 = f.oB + f.mtc2 * 16 * f.skc;                          // 2 x [t][n][8]
+    f.p3sz = b.nterm * L * 8;
+    f.oMo = f.oP3 + 2 * f.p3sz;                                  // int [mtc2 16]
+    f.oSt = f.oMo + f.mtc2 * 16;                                 // per warp [32][nc1]
+    f.stw = r4i(32 * f.nc1);
+    f.total = f.oSt + PANEL_WARPS * f.stw;
+    return f;
+}
+
 // Device-resident tables of one (q, L).
 struct DevTables {
     int q, L;

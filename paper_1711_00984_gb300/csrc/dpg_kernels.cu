@@ -545,6 +545,366 @@ __global__ void __launch_bounds__(256, 2) sf_general_f32_kernel(SfParams32 p) {
 }
 
 // --------------------------------------------------------------------------------------
+// FP32 row-panel kernel: stages B and C on the tensor cores (3xTF32)
+// --------------------------------------------------------------------------------------
+// Every (a, b) block is computed (no mirrored tiles), so each output row of the element
+// matrix is written by the CTAs of its row component as long contiguous runs.  A CTA keeps
+// one block resident (its constant operands are loaded once) and walks a chunk of
+// elements and every (i3, j3-chunk) unit of the block.  Per unit:
+//   stage A (FMA pipe)   A_h[(jj,l)][m] = sum_{t in h} sum_n M_t(l,m,n) P3_t(jj,n)     (Eq. 2.23)
+//   stage B (mma)        Bs[(i2,x)][(g,l)] = sum_{h in g} sum_m P2_h[(i2,j2)][m] A_h[(jj,l)][m]  (Eq. 2.24)
+//   stage C (mma)        G[(i1,i2)][(j1,x)] = sum_{g,l} Bs[(i2,x)][(g,l)] P1_g[(i1,j1)][l]      (Eq. 2.25)
+// Products are split as a = a_hi + a_lo with a_hi the TF32 rounding of a; each product is
+// a_lo b_hi + a_hi b_lo + a_hi b_hi (the a_lo b_lo term, 2^-22 relative, dropped) with FP32
+// accumulation.  Stage-C results pass through a per-warp staging buffer and leave as
+// coalesced row runs.  Two barriers per unit: stage A of the next unit overlaps the
+// stage C of warps still finishing the current one.
+
+__device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo) {
+    unsigned h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = h;
+    lo = __float_as_uint(x - __uint_as_float(h));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += a b in 3xTF32 (small terms first)
+__device__ __forceinline__ void mma3_tf32(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
+                                          unsigned bh0, unsigned bh1, unsigned bl0, unsigned bl1) {
+    mma_tf32(d, al, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+    mma_tf32(d, ah, bh0, bh1);
+}
+
+// Per-chunk schedule of the row-panel kernel (depends on the unit's nj only).
+struct PanelSched {
+    int nj, nx, mc, pairs;
+    unsigned mnx, mnc1;
+    int nch, cb, ntaskB;            // stage B: chunks of n-tiles, chunk size, tasks
+    unsigned mnch;
+    int ngrp, per, ntaskC;          // stage C: i1 groups, i1 per group, tasks
+    unsigned mgrp;
+};
+
+__device__ PanelSched panel_sched(const PanelLayout &f, const BlockDesc &bd, int nj) {
+    PanelSched c;
+    c.nj = nj; c.nx = f.nc2 * nj; c.mc = f.nr2 * c.nx; c.pairs = (c.mc + 31) >> 5;
+    c.mnx = div_magic(c.nx); c.mnc1 = div_magic(f.nc1);
+    const int ntb = nj * f.ksh;
+    int nch = (ntb + 7) >> 3;
+    while (bd.ng * f.mtb * nch < 2 * PANEL_WARPS && (ntb + nch) / (nch + 1) >= 2) ++nch;
+    c.nch = nch; c.cb = (ntb + nch - 1) / nch; c.ntaskB = bd.ng * f.mtb * nch; c.mnch = div_magic(nch);
+    // stage C groups: fewest rounds of PANEL_WARPS tasks, then fewest n-tiles per task
+    const int maxper = 8 / f.nt1;
+    int ngrp = (f.nr1 + maxper - 1) / maxper, best = 1 << 30;
+    for (int gc = ngrp; gc <= f.nr1 && gc <= 4 * ngrp; ++gc) {
+        const int per = (f.nr1 + gc - 1) / gc;
+        const int rounds = (c.pairs * gc + PANEL_WARPS - 1) / PANEL_WARPS;
+        const int cost = rounds * (2 * per * f.nt1 + 3);
+        if (cost < best) { best = cost; ngrp = gc; }
+    }
+    c.ngrp = ngrp; c.per = (f.nr1 + ngrp - 1) / ngrp; c.ntaskC = c.pairs * ngrp; c.mgrp = div_magic(ngrp);
+    return c;
+}
+
+// Stage B of one warp task: group g, m-tile mt of (i2, j2), CNT n-tiles of (jj, l) from
+// nt0; results into Bs rows (i2, x = j2 + nc2 jj), columns (g, l).
+template <int CNT>
+__device__ __forceinline__ void panel_stage_b(const float *__restrict__ sm, const PanelLayout &f, const BlockDesc &bd,
+                                              float *__restrict__ Bs, int g, int mt, int nt0, int nx, unsigned mnc2,
+                                              int lane) {
+    const int gid = lane >> 2, tig = lane & 3;
+    const float *As = sm + f.oA;
+    float acc[CNT][4];
+#pragma unroll
+    for (int c = 0; c < CNT; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.0f;
+    const int sn4 = 4 * f.sn;
+    for (int h = 0; h < bd.nh; ++h) {
+        if (bd.h_g[h] != g) continue;
+        const float *ap = sm + f.oP2 + ((bd.h_p2[h] * f.mtb + mt) * f.ksh) * 256 + lane * 8;
+        const float *bp = As + ((h << f.lsh) + tig) * f.sn + nt0 * 8 + gid;
+        for (int ks = 0; ks < f.ksh; ++ks, ap += 256, bp += 8 * f.sn) {
+            const float4 x0 = *reinterpret_cast<const float4 *>(ap);
+            const float4 x1 = *reinterpret_cast<const float4 *>(ap + 4);
+            const unsigned ah[4] = { __float_as_uint(x0.x), __float_as_uint(x0.y), __float_as_uint(x0.z), __float_as_uint(x0.w) };
+            const unsigned al[4] = { __float_as_uint(x1.x), __float_as_uint(x1.y), __float_as_uint(x1.z), __float_as_uint(x1.w) };
+#pragma unroll
+            for (int c = 0; c < CNT; ++c) {
+                unsigned bh0, bl0, bh1, bl1;
+                tf32_split(bp[c * 8], bh0, bl0);
+                tf32_split(bp[c * 8 + sn4], bh1, bl1);
+                mma3_tf32(acc[c], ah, al, bh0, bh1, bl0, bl1);
+            }
+        }
+    }
+    const int lmask = f.lpad - 1, nc2 = f.nc2;
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+        const int rr = mt * 16 + gid + 8 * hf;
+        if (rr < f.n22) {
+            const int i2 = fdiv(rr, mnc2), j2 = rr - i2 * nc2;
+            float *brow = Bs + (i2 * nx + j2) * f.skc + (g << f.lsh);
+#pragma unroll
+            for (int c = 0; c < CNT; ++c) {
+                const int n = (nt0 + c) * 8 + 2 * tig;
+                const int jj = n >> f.lsh, l = n & lmask;
+                *reinterpret_cast<float2 *>(brow + nc2 * jj * f.skc + l) = make_float2(acc[c][2 * hf], acc[c][2 * hf + 1]);
+            }
+        }
+    }
+}
+
+// Stage C of one warp task: m-tiles 2 mp and 2 mp + 1 of (i2, x), CNT n-tiles (NT1 per
+// i1) from i1b; each finished i1 is staged as [m (32)][j1] in the warp's buffer and
+// written as contiguous runs of the output rows (i1, i2), offsets moff[m] + j1.
+template <int CNT, int NT1>
+__device__ __forceinline__ void panel_stage_c(const float *__restrict__ sm, const PanelLayout &f, const PanelSched &sch,
+                                              int mp, int i1b, float *__restrict__ orow0, int64_t ld,
+                                              float *__restrict__ stage, int lane) {
+    const int gid = lane >> 2, tig = lane & 3;
+    const float *Bs = sm + f.oB;
+    const int *moff = reinterpret_cast<const int *>(sm + f.oMo);
+    const int skc = f.skc;
+    float acc[2][CNT][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int c = 0; c < CNT; ++c) acc[mi][c][0] = acc[mi][c][1] = acc[mi][c][2] = acc[mi][c][3] = 0.0f;
+    const float *ap = Bs + (mp * 32 + gid) * skc + tig;
+    const float *bp = sm + f.oP1 + (i1b * NT1 * 8 + gid) * 16 + tig * 4;
+    const int s8 = 8 * skc, s16 = 16 * skc, bstep = f.n1p * 16;
+    for (int ks = 0; ks < f.ks1; ++ks, ap += 8, bp += bstep) {
+        unsigned ah[2][4], al[2][4];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            const float *a = ap + mi * s16;
+            tf32_split(a[0], ah[mi][0], al[mi][0]);
+            tf32_split(a[s8], ah[mi][1], al[mi][1]);
+            tf32_split(a[4], ah[mi][2], al[mi][2]);
+            tf32_split(a[s8 + 4], ah[mi][3], al[mi][3]);
+        }
+#pragma unroll
+        for (int c = 0; c < CNT; ++c) {
+            const float4 bv = *reinterpret_cast<const float4 *>(bp + c * 128);
+            const unsigned bh0 = __float_as_uint(bv.x), bh1 = __float_as_uint(bv.y);
+            const unsigned bl0 = __float_as_uint(bv.z), bl1 = __float_as_uint(bv.w);
+            mma3_tf32(acc[0][c], ah[0], al[0], bh0, bh1, bl0, bl1);
+            mma3_tf32(acc[1][c], ah[1], al[1], bh0, bh1, bl0, bl1);
+        }
+    }
+    // the task's 32 rows (i2, x) map to at most three runs of consecutive x (one per i2):
+    // staged element f = ml nc1 + j1 goes to output offset f + delta(run of f)
+    const int nc1 = f.nc1;
+    const int m0 = mp * 32;
+    const int fend = min(32, sch.mc - m0) * nc1;
+    const int i20 = fdiv(m0, sch.mnx);
+    const int r1 = (i20 + 1) * sch.nx - m0, r2 = r1 + sch.nx;      // first rows of the next runs
+    const int f1 = r1 * nc1, f2 = r2 * nc1;
+    const int d0 = moff[m0];
+    const int d1 = r1 < 32 && m0 + r1 < sch.mc ? moff[m0 + r1] - f1 : 0;
+    const int d2 = r2 < 32 && m0 + r2 < sch.mc ? moff[m0 + r2] - f2 : 0;
+#pragma unroll
+    for (int c = 0; c < CNT; ++c) {
+        const int j1 = (c % NT1) * 8 + 2 * tig;
+        float *sr = stage + gid * nc1 + j1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {                                // rows gid + 8 q
+            if (j1 < nc1) sr[8 * q * nc1] = acc[q >> 1][c][2 * (q & 1)];
+            if (j1 + 1 < nc1) sr[8 * q * nc1 + 1] = acc[q >> 1][c][2 * (q & 1) + 1];
+        }
+        if (c % NT1 == NT1 - 1) {
+            __syncwarp();
+            float *orow = orow0 + (int64_t)(i1b + c / NT1) * ld;
+            if (sch.nx >= 16) {
+                for (int fi = lane; fi < fend; fi += 32) {
+                    const int d = fi < f1 ? d0 : (fi < f2 ? d1 : d2);
+                    orow[fi + d] = stage[fi];
+                }
+            } else {                                               // short runs: row by row
+                for (int fi = lane; fi < fend; fi += 32) {
+                    const int ml = fdiv(fi, sch.mnc1);
+                    orow[moff[m0 + ml] + fi - ml * nc1] = stage[fi];
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(PANEL_WARPS * 32, 2) sf_panel_f32_kernel(PanelParams p) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    __shared__ BlockDesc bd;
+    __shared__ PanelLayout f;
+    __shared__ PanelSched sched[2];      // nj_max and the remainder chunk
+    const int tid = threadIdx.x, nth = PANEL_WARPS * 32;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int k = blockIdx.x % p.nblock;
+    const int64_t e0 = (int64_t)(blockIdx.x / p.nblock) * p.elems_per_cta;
+    const int64_t e1 = min(e0 + (int64_t)p.elems_per_cta, p.n_elem);
+    if (e0 >= e1) return;
+    load_block(p.blocks + k, bd);
+    __syncthreads();
+    if (tid == 0) f = panel_layout(bd, p.L, p.nj_max);
+    __syncthreads();
+    if (tid < 2) {
+        const int nA = bd.nc[2], rem = nA % p.nj_max;
+        sched[tid] = panel_sched(f, bd, tid == 0 ? min(p.nj_max, nA) : (rem ? rem : p.nj_max));
+    }
+
+    const int L = p.L, L2 = L * L, L3 = L2 * L;
+    const int lpad = f.lpad, lsh = f.lsh;
+    const int nr1 = f.nr1, nr2 = f.nr2, nc1 = f.nc1, nc2 = f.nc2, nt1 = f.nt1;
+    const int ng = bd.ng, nh = bd.nh, nterm = bd.nterm;
+    float *As = sm + f.oA, *Bs = sm + f.oB;
+    int *moff = reinterpret_cast<int *>(sm + f.oMo);
+    float *stage = sm + f.oSt + warp * f.stw;
+
+    // constant operands of the block: one contiguous image
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(p.ctab + p.ctab_off[k]);
+        for (int i = tid; i < (f.oA >> 2); i += nth) smem4[i] = src[i];
+    }
+
+    const unsigned mL = div_magic(L), mnc2 = div_magic(nc2), mmtb_c = div_magic(f.mtb);
+    const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
+    const float *pp = p.pp;
+    const int64_t ld = p.ld;
+    // P3[t][n][jj] (jj padded to 8 with zeros) of unit ui into buffer b
+    auto fill_p3 = [&](int ui, int b) {
+        const Unit u = p.units[ui];
+        float *P3 = sm + f.oP3 + b * f.p3sz;
+        for (int it = tid; it < nterm * L * 8; it += nth) {
+            const int jj = it & 7, r = it >> 3;
+            const int t = fdiv(r, mL), n = r - t * L;
+            float v = 0.0f;
+            if (jj < u.nj) {
+                const TermDesc &td = bd.term[t];
+                v = pp[(((size_t)(3 * td.kr[2] + td.kc[2]) * NQ1 + u.i3) * NQ1 + u.j3b + jj) * L + n];
+                if (td.sign < 0) v = -v;
+            }
+            P3[it] = v;
+        }
+    };
+    fill_p3(ub, 0);
+    __syncthreads();
+
+    int buf = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+        const float *fe = p.fields + (size_t)e * p.nfields * L3;
+        float *o = p.out + (size_t)e * p.mat_stride + bd.base;
+        for (int ui = ub; ui < ue; ++ui, buf ^= 1) {
+            const Unit u = p.units[ui];
+            const int nj = u.nj;
+            const PanelSched &sch = sched[nj == sched[0].nj ? 0 : 1];
+            const int nx = sch.nx, mc = sch.mc, pairs = sch.pairs;
+            const float *P3 = sm + f.oP3 + buf * f.p3sz;
+
+            // ---- stage A: item (h, m, l) over [0, lpad)^2 (l fastest), all jj in registers;
+            //      output rows of moff for this unit meanwhile
+            for (int it = tid; it < nh << (2 * lsh); it += nth) {
+                const int l = it & (lpad - 1), m = (it >> lsh) & (lpad - 1), h = it >> (2 * lsh);
+                float acc[NJMAX];
+#pragma unroll
+                for (int jj = 0; jj < NJMAX; ++jj) acc[jj] = 0.0f;
+                if (l < L && m < L) {
+                    for (int t = 0; t < nterm; ++t) {
+                        if (bd.term[t].h != h) continue;
+                        const float *M = fe + (size_t)bd.term[t].field * L3 + l * L2 + m * L;
+                        const float4 *Pt = reinterpret_cast<const float4 *>(P3 + t * L * 8);
+                        for (int n = 0; n < L; ++n) {
+                            const float mv = __ldg(M + n);
+                            const float4 q0 = Pt[2 * n], q1 = Pt[2 * n + 1];
+                            acc[0] = fmaf(mv, q0.x, acc[0]); acc[1] = fmaf(mv, q0.y, acc[1]);
+                            acc[2] = fmaf(mv, q0.z, acc[2]); acc[3] = fmaf(mv, q0.w, acc[3]);
+                            acc[4] = fmaf(mv, q1.x, acc[4]); acc[5] = fmaf(mv, q1.y, acc[5]);
+                            acc[6] = fmaf(mv, q1.z, acc[6]); acc[7] = fmaf(mv, q1.w, acc[7]);
+                        }
+                    }
+                }
+                float *dst = As + ((h << lsh) + m) * f.sn + l;
+#pragma unroll
+                for (int jj = 0; jj < NJMAX; ++jj)
+                    if (jj < nj) dst[jj << lsh] = acc[jj];
+            }
+            {
+                for (int m = tid; m < pairs * 32; m += nth) {
+                    int off = -1;
+                    if (m < mc) {
+                        const int i2 = fdiv(m, sch.mnx), x = m - i2 * nx;
+                        off = nr1 * i2 * (int)ld + nc1 * x;
+                    }
+                    moff[m] = off;
+                }
+            }
+            __syncthreads();
+
+            // ---- stage B: task (g, m-tile, chunk of n-tiles); P3 of the next unit meanwhile
+            {
+                const int un = ui + 1 < ue ? ui + 1 : ub;
+                if (ui + 1 < ue || e + 1 < e1) fill_p3(un, buf ^ 1);
+                const int ntb = nj * f.ksh, nch = sch.nch, cb = sch.cb, ntask = sch.ntaskB;
+                const unsigned mnch = sch.mnch, mmtb = mmtb_c;
+                for (int task = warp; task < ntask; task += PANEL_WARPS) {
+                    const int r = fdiv(task, mnch), ch = task - r * nch;
+                    const int g = fdiv(r, mmtb), mt = r - g * f.mtb;
+                    const int nt0 = ch * cb, cnt = min(cb, ntb - nt0);
+                    switch (cnt) {
+                    case 1: panel_stage_b<1>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    case 2: panel_stage_b<2>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    case 3: panel_stage_b<3>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    case 4: panel_stage_b<4>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    case 5: panel_stage_b<5>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    case 6: panel_stage_b<6>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    case 7: panel_stage_b<7>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    case 8: panel_stage_b<8>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    default: break;
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ---- stage C: task (pair of m-tiles, group of i1)
+            {
+                const int ngrp = sch.ngrp, per = sch.per, ntask = sch.ntaskC;
+                const unsigned mgrp = sch.mgrp;
+                float *orow0 = o + (bd.row_off + (int64_t)u.i3 * nr1 * nr2) * ld + bd.col_off + (int64_t)u.j3b * nc1 * nc2;
+                for (int task = warp; task < ntask; task += PANEL_WARPS) {
+                    const int mp = fdiv(task, mgrp), grp = task - mp * ngrp;
+                    const int i1b = grp * per, cnt = min(per, nr1 - i1b) * nt1;
+                    if (nt1 == 1) {
+                        switch (cnt) {
+                        case 1: panel_stage_c<1, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 2: panel_stage_c<2, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 3: panel_stage_c<3, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 4: panel_stage_c<4, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 5: panel_stage_c<5, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 6: panel_stage_c<6, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 7: panel_stage_c<7, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 8: panel_stage_c<8, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        default: break;
+                        }
+                    } else {
+                        switch (cnt) {
+                        case 2: panel_stage_c<2, 2>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 4: panel_stage_c<4, 2>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 6: panel_stage_c<6, 2>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 8: panel_stage_c<8, 2>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        default: break;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------------
 // affine path (Sec. 2.8.1)
 // --------------------------------------------------------------------------------------
 // Store-bound: the tile is produced in column panels of AFF_W columns staged in shared
@@ -1033,6 +1393,14 @@ cudaError_t launch_general_f32(const SfParams32 &p, size_t smem, int max_nc1, cu
     return cudaGetLastError();
 }
 
+cudaError_t launch_panel_f32(const PanelParams &p, size_t smem, cudaStream_t s) {
+    if (p.n_elem == 0) return cudaSuccess;
+    const int64_t chunks = (p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta;
+    const int64_t ctas = chunks * p.nblock;
+    sf_panel_f32_kernel<<<(unsigned)ctas, PANEL_WARPS * 32, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s) {
     if (p.n_elem == 0) return cudaSuccess;
     affine_const_kernel<<<(unsigned)((p.n_elem + 127) / 128), 128, 0, s>>>(p);
@@ -1066,6 +1434,7 @@ cudaError_t init_kernel_attributes(int optin_smem) {
     if (e == cudaSuccess) e = one((const void *)hp_contract_kernel<float>);
     if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<3>);
     if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<4>);
+    if (e == cudaSuccess) e = one((const void *)sf_panel_f32_kernel);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<double>);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<float>);
     return e;

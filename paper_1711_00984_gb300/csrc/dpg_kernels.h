@@ -64,6 +64,21 @@ struct SfParams32 {
     int64_t mat_stride, ld, n_elem;
 };
 
+// FP32 row-panel kernel: one CTA per (block, chunk of elements).
+struct PanelParams {
+    const BlockDesc *blocks;
+    const Unit *units;
+    const int *block_unit_begin;   // [nblock + 1]
+    const float *ctab;             // constant operands of every block (build_panel_tables)
+    const int *ctab_off;           // [nblock]
+    int nblock, nj_max, elems_per_cta;
+    int L, nfields;
+    const float *pp;               // pair products [NPAIR][NQ1][NQ1][L]
+    const float *fields;           // [n_elem][nfields][L^3]
+    float *out;
+    int64_t mat_stride, ld, n_elem;
+};
+
 template <typename T>
 struct AffParams {
     const BlockDesc *blocks;
@@ -112,6 +127,7 @@ int hp_ctas_per_sm(bool fp32, size_t smem);
 template <typename TF> cudaError_t launch_geom(const GeomParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_general(const SfParams<T> &p, size_t smem, cudaStream_t s);
 cudaError_t launch_general_f32(const SfParams32 &p, size_t smem, int max_nc1, cudaStream_t s);
+cudaError_t launch_panel_f32(const PanelParams &p, size_t smem, cudaStream_t s);
 cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);

@@ -248,7 +248,7 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
 
     for (int a = 0; a < nR; ++a)
     for (int b = 0; b < nC; ++b) {
-        bool symmetric = space != S_B;
+        bool symmetric = space != S_B && order != ORDER_PANEL;
         if (symmetric && b < a) continue;             // lower blocks come from mirroring
         for (int part = 0; part < pr.parts; ++part) {
             std::vector<TermSpec> ts;
@@ -310,7 +310,7 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             // ORDER_A3 keeps stage A on xi_3, ORDER_NATURAL keeps the paper's order
             static const int perms[6][3] = { { 0, 1, 2 }, { 1, 0, 2 }, { 0, 2, 1 },
                                              { 2, 0, 1 }, { 1, 2, 0 }, { 2, 1, 0 } };
-            const int nperm = order == ORDER_NATURAL ? 1 : (order == ORDER_A3 ? 2 : 6);
+            const int nperm = (order == ORDER_NATURAL || order == ORDER_PANEL) ? 1 : (order == ORDER_A3 ? 2 : 6);
             double best = 0.0; int bi = 0;
             for (int k = 0; k < nperm; ++k) {
                 finish_block(bd, ts, perms[k]);
@@ -325,11 +325,13 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     // kernel model, or the FP32 kernel's layout for ORDER_A3 programs)
     auto smem_bytes = [&](const BlockDesc &b, int njv) -> size_t {
         if (order == ORDER_A3) return (size_t)f32_layout(b, L, njv).total * sizeof(float);
+        if (order == ORDER_PANEL) return (size_t)panel_layout(b, L, njv).total * sizeof(float);
         if (order == ORDER_NATURAL)
             return (size_t)aff_layout(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], njv).total * sizeof(double);
         return smem_values(b, L, njv) * sizeof(double);
     };
-    const size_t budget = order == ORDER_BEST ? 160 * 1024 : 110 * 1024;
+    // (ORDER_PANEL: two CTAs per SM)
+    const size_t budget = order == ORDER_BEST ? 160 * 1024 : (order == ORDER_PANEL ? 112 * 1024 : 110 * 1024);
     int maxnA = 1;
     for (int k = 0; k < pr.nblock; ++k) maxnA = std::max(maxnA, pr.blocks[k].nc[pr.blocks[k].dir[2]]);
     int nj = std::min(NJMAX, maxnA);
@@ -404,6 +406,65 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     }
     pr.flops_affine = aff;
     return pr;
+}
+
+// TF32 high / low parts of x: hi keeps 10 mantissa bits (rounded to nearest, ties away
+// from zero), lo = x - hi is exact in FP32.
+static void split_tf32(float x, float &hi, float &lo) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xffffe000u;
+    std::memcpy(&hi, &u, 4);
+    lo = x - hi;
+}
+
+void build_panel_tables(const Program &pr, const HostTables &tab, std::vector<float> &ctab, std::vector<int> &off) {
+    ctab.clear();
+    off.assign(pr.nblock, 0);
+    const int L = pr.L;
+    auto ppv = [&](int pair, int i, int j, int l) -> float {
+        return (float)tab.pp[(((size_t)pair * NQ1 + i) * NQ1 + j) * L + l];
+    };
+    for (int k = 0; k < pr.nblock; ++k) {
+        const BlockDesc &b = pr.blocks[k];
+        const PanelLayout f = panel_layout(b, L, 1);
+        off[k] = (int)ctab.size();
+        std::vector<float> t((size_t)f.oA, 0.0f);
+        // P1 as the B operand of stage C: per k-step ks and row n = (i1, j1 padded to
+        // nt1*8), per lane column tg the values {hi(k0), hi(k0+4), lo(k0), lo(k0+4)},
+        // k0 = 8 ks + tg
+        auto p1 = [&](int kk, int i1, int j1) -> float {
+            const int g = kk / f.lpad, l = kk % f.lpad;
+            return (j1 < f.nc1 && l < L) ? ppv(b.g_pair[g], i1, j1, l) : 0.0f;
+        };
+        for (int ks = 0; ks < f.ks1; ++ks)
+            for (int n = 0; n < f.n1p; ++n) {
+                const int i1 = n / (f.nt1 * 8), j1 = n % (f.nt1 * 8);
+                for (int tg = 0; tg < 4; ++tg) {
+                    float *d = &t[(size_t)f.oP1 + ((size_t)ks * f.n1p + n) * 16 + tg * 4];
+                    split_tf32(p1(ks * 8 + tg, i1, j1), d[0], d[2]);
+                    split_tf32(p1(ks * 8 + tg + 4, i1, j1), d[1], d[3]);
+                }
+            }
+        // P2 as the A operand of stage B: per (slot, m-tile, k-step) and lane (gid, tg) the
+        // values {hi(a0..a3), lo(a0..a3)} of rows gid, gid+8 and columns tg, tg+4
+        auto p2 = [&](int s2, int r, int m) -> float {
+            return (r < f.n22 && m < L) ? ppv(b.p2_pair[s2], r / f.nc2, r % f.nc2, m) : 0.0f;
+        };
+        for (int s2 = 0; s2 < b.np2; ++s2)
+            for (int mt = 0; mt < f.mtb; ++mt)
+                for (int ks = 0; ks < f.ksh; ++ks)
+                    for (int lane = 0; lane < 32; ++lane) {
+                        const int gid = lane >> 2, tg = lane & 3;
+                        const int r0 = mt * 16 + gid, m0 = ks * 8 + tg;
+                        float *d = &t[(size_t)f.oP2 + (((size_t)s2 * f.mtb + mt) * f.ksh + ks) * 256 + lane * 8];
+                        split_tf32(p2(s2, r0, m0), d[0], d[4]);
+                        split_tf32(p2(s2, r0 + 8, m0), d[1], d[5]);
+                        split_tf32(p2(s2, r0, m0 + 4), d[2], d[6]);
+                        split_tf32(p2(s2, r0 + 8, m0 + 4), d[3], d[7]);
+                    }
+        ctab.insert(ctab.end(), t.begin(), t.end());
+    }
 }
 
 }  // namespace dpg

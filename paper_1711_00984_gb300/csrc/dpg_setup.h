@@ -35,11 +35,17 @@ HostTables make_tables(int q, int L);
 // permutations (FP64 general kernel); ORDER_A3 the cheaper of the two with stage A over
 // xi_3 (FP32 general kernel: contiguous tile rows); ORDER_NATURAL the paper's order
 // (stage A over xi_3, B over xi_2, C over xi_1; affine kernel).
-enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2 };
+// ORDER_PANEL: the paper's order and every (a, b) block of a symmetric matrix built (no
+// mirrored tiles): the FP32 row-panel kernel writes every output row itself.
+enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3 };
 // force_nj > 0 fixes the stage-A chunk (autotuner); otherwise the largest chunk whose
 // shared memory fits the kernel's budget is taken.
 Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order = ORDER_BEST,
                      int force_nj = 0);
+// Constant operands of the FP32 row-panel kernel for every block of an ORDER_PANEL
+// program (the shared-memory image [0, oA) of panel_layout), concatenated; off[k] is the
+// first float of block k.
+void build_panel_tables(const Program &pr, const HostTables &tab, std::vector<float> &ctab, std::vector<int> &off);
 int64_t rows_of(int space, int q);
 int64_t cols_of(int space, int p, int q);
 
