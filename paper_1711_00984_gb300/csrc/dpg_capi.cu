@@ -38,6 +38,7 @@ struct ProgEntry {
     BlockDesc *d_blocks = nullptr;
     Unit *d_units = nullptr;
     Program prog_aff;               // affine path: the paper's direction order
+    double flops_aff = 0.0;         // algorithmic flops of the affine path
     BlockDesc *d_blocks_aff = nullptr;
     Unit *d_units_aff = nullptr;
     Program prog32;                 // FP32 general path: row-panel program (panel32) or
@@ -206,6 +207,7 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
     auto pe = std::make_unique<ProgEntry>();
     pe->prog = make_program(space, q, L, p, split != 0, tab);
     pe->prog_aff = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL);
+    pe->flops_aff = pe->prog_aff.flops_affine;
     const Program &pr = pe->prog;
     if (pr.smem_values * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     int r;
@@ -836,7 +838,7 @@ double dpg_flops_per_element(int space, int p_trial, int q_test) {
     std::lock_guard<std::mutex> lk(g_mu);
     ProgEntry *pe; TableEntry *te; DeviceState *ds;
     if (resolve(space, p_trial, q_test, &pe, &te, &ds) != DPG_OK) return -1.0;
-    if (space & DPG_MAP_AFFINE) return pe->prog_aff.flops_affine;
+    if (space & DPG_MAP_AFFINE) return pe->flops_aff;
     // the same algorithmic count for both forms (the FP32 row-panel kernel also computes
     // the mirrored blocks; that extra work is not counted)
     return pe->prog.flops;

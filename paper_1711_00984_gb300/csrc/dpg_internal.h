@@ -139,9 +139,10 @@ struct PanelLayout {
     int n22, mtb;                  // P2: rows (i2, j2), m-tiles
     int nb, sn;                    // stage-A output: columns (jj, l), row stride
     int nx, mc, mtc2, skc;         // stage-B output: x range, rows (i2, x), m-tiles (even), stride
-    int oP1, oP2, oA, oB, oP3, p3sz, oMo, oSt, stw, total;
+    int nrow, ncol, ldt;           // output tile [nrow][ldt] (rows i1 + nr1 i2, columns nc1 x + j1)
+    int oP1, oP2, oA, oB, oP3, p3sz, oMo, oT, total;
 };
-constexpr int PANEL_WARPS = 8;
+constexpr int PANEL_SMEM_2CTA = 112 * 1024;   // dynamic shared memory for two CTAs per SM
 DPG_HD inline PanelLayout panel_layout(const BlockDesc &b, int L, int nj) {
     PanelLayout f;
     f.lpad = (L + 7) & ~7; f.lsh = f.lpad == 8 ? 3 : 4; f.ksh = f.lpad >> 3;
@@ -151,6 +152,7 @@ DPG_HD inline PanelLayout panel_layout(const BlockDesc &b, int L, int nj) {
     f.n22 = f.nr2 * f.nc2; f.mtb = (f.n22 + 15) >> 4;
     f.nb = nj * f.lpad; f.sn = (f.nb & 15) ? f.nb : f.nb + 8;
     f.nx = f.nc2 * nj; f.mc = f.nr2 * f.nx; f.mtc2 = ((f.mc + 31) >> 5) * 2; f.skc = b.ng * f.lpad + 4;
+    f.nrow = f.nr1 * f.nr2; f.ncol = f.nc1 * f.nx; f.ldt = f.ncol | 1;
     f.oP1 = 0;                                                   // [ks][n][tig][4]
     f.oP2 = f.oP1 + f.ks1 * f.n1p * 16;                          // [slot][mt][ks][lane][8]
     f.oA = f.oP2 + b.np2 * f.mtb * f.ksh * 256;                  // [h lpad + m][sn]
@@ -158,9 +160,8 @@ DPG_HD inline PanelLayout panel_layout(const BlockDesc &b, int L, int nj) {
     f.oP3 = f.oB + f.mtc2 * 16 * f.skc;                          // 2 x [t][n][8]
     f.p3sz = b.nterm * L * 8;
     f.oMo = f.oP3 + 2 * f.p3sz;                                  // int [mtc2 16]
-    f.oSt = f.oMo + f.mtc2 * 16;                                 // per warp [32][nc1]
-    f.stw = r4i(32 * f.nc1);
-    f.total = f.oSt + PANEL_WARPS * f.stw;
+    f.oT = f.oMo + f.mtc2 * 16;                                  // [nrow][ldt]
+    f.total = f.oT + r4i(f.nrow * f.ldt);
     return f;
 }
 

@@ -30,7 +30,7 @@ template <> __device__ __forceinline__ float qnan<float>() { return __int_as_flo
 
 // floor(x / d) for 0 <= x < 2^20 and 1 <= d < 2^12: m = ceil(2^32 / d), q = umulhi(x, m)
 __device__ __forceinline__ unsigned div_magic(int d) {
-    return d <= 1 ? 0u : (unsigned)((0x100000000ull + (unsigned)d - 1u) / (unsigned)d);
+    return d <= 1 ? 0u : 0xffffffffu / (unsigned)d + 1u;     // = ceil(2^32 / d)
 }
 __device__ __forceinline__ int fdiv(int x, unsigned m) { return m ? (int)__umulhi((unsigned)x, m) : x; }
 
@@ -560,9 +560,11 @@ __global__ void __launch_bounds__(256, 2) sf_general_f32_kernel(SfParams32 p) {
 // coalesced row runs.  Two barriers per unit: stage A of the next unit overlaps the
 // stage C of warps still finishing the current one.
 
+// x = hi + lo with hi = x rounded to 10 mantissa bits (nearest, ties away from zero; the
+// tensor core reads only those bits of a TF32 operand) and lo = x - hi, exact in FP32.
+// Non-finite x leave a non-finite lo, so NaN still reaches the product.
 __device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo) {
-    unsigned h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const unsigned h = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
     hi = h;
     lo = __float_as_uint(x - __uint_as_float(h));
 }
@@ -585,26 +587,29 @@ __device__ __forceinline__ void mma3_tf32(float (&d)[4], const unsigned (&ah)[4]
 struct PanelSched {
     int nj, nx, mc, pairs;
     unsigned mnx, mnc1;
+    int ncol, nwch;                 // tile columns and 32-column chunks of the write-out
+    unsigned mwch;
     int nch, cb, ntaskB;            // stage B: chunks of n-tiles, chunk size, tasks
     unsigned mnch;
     int ngrp, per, ntaskC;          // stage C: i1 groups, i1 per group, tasks
     unsigned mgrp;
 };
 
-__device__ PanelSched panel_sched(const PanelLayout &f, const BlockDesc &bd, int nj) {
+__device__ PanelSched panel_sched(const PanelLayout &f, const BlockDesc &bd, int nj, int nw) {
     PanelSched c;
     c.nj = nj; c.nx = f.nc2 * nj; c.mc = f.nr2 * c.nx; c.pairs = (c.mc + 31) >> 5;
     c.mnx = div_magic(c.nx); c.mnc1 = div_magic(f.nc1);
+    c.ncol = f.nc1 * c.nx; c.nwch = (c.ncol + 31) >> 5; c.mwch = div_magic(c.nwch);
     const int ntb = nj * f.ksh;
     int nch = (ntb + 7) >> 3;
-    while (bd.ng * f.mtb * nch < 2 * PANEL_WARPS && (ntb + nch) / (nch + 1) >= 2) ++nch;
+    while (bd.ng * f.mtb * nch < 2 * nw && (ntb + nch) / (nch + 1) >= 2) ++nch;
     c.nch = nch; c.cb = (ntb + nch - 1) / nch; c.ntaskB = bd.ng * f.mtb * nch; c.mnch = div_magic(nch);
-    // stage C groups: fewest rounds of PANEL_WARPS tasks, then fewest n-tiles per task
+    // stage C groups: fewest rounds of nw tasks, then fewest n-tiles per task
     const int maxper = 8 / f.nt1;
     int ngrp = (f.nr1 + maxper - 1) / maxper, best = 1 << 30;
     for (int gc = ngrp; gc <= f.nr1 && gc <= 4 * ngrp; ++gc) {
         const int per = (f.nr1 + gc - 1) / gc;
-        const int rounds = (c.pairs * gc + PANEL_WARPS - 1) / PANEL_WARPS;
+        const int rounds = (c.pairs * gc + nw - 1) / nw;
         const int cost = rounds * (2 * per * f.nt1 + 3);
         if (cost < best) { best = cost; ngrp = gc; }
     }
@@ -617,15 +622,15 @@ __device__ PanelSched panel_sched(const PanelLayout &f, const BlockDesc &bd, int
 template <int CNT>
 __device__ __forceinline__ void panel_stage_b(const float *__restrict__ sm, const PanelLayout &f, const BlockDesc &bd,
                                               float *__restrict__ Bs, int g, int mt, int nt0, int nx, unsigned mnc2,
-                                              int lane) {
+                                              int lane, const signed char *hl, int nhl) {
     const int gid = lane >> 2, tig = lane & 3;
     const float *As = sm + f.oA;
     float acc[CNT][4];
 #pragma unroll
     for (int c = 0; c < CNT; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.0f;
     const int sn4 = 4 * f.sn;
-    for (int h = 0; h < bd.nh; ++h) {
-        if (bd.h_g[h] != g) continue;
+    for (int hi = 0; hi < nhl; ++hi) {
+        const int h = hl[hi];
         const float *ap = sm + f.oP2 + ((bd.h_p2[h] * f.mtb + mt) * f.ksh) * 256 + lane * 8;
         const float *bp = As + ((h << f.lsh) + tig) * f.sn + nt0 * 8 + gid;
         for (int ks = 0; ks < f.ksh; ++ks, ap += 256, bp += 8 * f.sn) {
@@ -660,15 +665,13 @@ __device__ __forceinline__ void panel_stage_b(const float *__restrict__ sm, cons
 }
 
 // Stage C of one warp task: m-tiles 2 mp and 2 mp + 1 of (i2, x), CNT n-tiles (NT1 per
-// i1) from i1b; each finished i1 is staged as [m (32)][j1] in the warp's buffer and
-// written as contiguous runs of the output rows (i1, i2), offsets moff[m] + j1.
+// i1) from i1b; results scattered into the output tile at rowoff[m] + i1 ldt + j1.
 template <int CNT, int NT1>
-__device__ __forceinline__ void panel_stage_c(const float *__restrict__ sm, const PanelLayout &f, const PanelSched &sch,
-                                              int mp, int i1b, float *__restrict__ orow0, int64_t ld,
-                                              float *__restrict__ stage, int lane) {
+__device__ __forceinline__ void panel_stage_c(const float *__restrict__ sm, float *__restrict__ tile,
+                                              const PanelLayout &f, int mp, int i1b, int lane) {
     const int gid = lane >> 2, tig = lane & 3;
     const float *Bs = sm + f.oB;
-    const int *moff = reinterpret_cast<const int *>(sm + f.oMo);
+    const int *rowoff = reinterpret_cast<const int *>(sm + f.oMo);
     const int skc = f.skc;
     float acc[2][CNT][4];
 #pragma unroll
@@ -697,52 +700,52 @@ __device__ __forceinline__ void panel_stage_c(const float *__restrict__ sm, cons
             mma3_tf32(acc[1][c], ah[1], al[1], bh0, bh1, bl0, bl1);
         }
     }
-    // the task's 32 rows (i2, x) map to at most three runs of consecutive x (one per i2):
-    // staged element f = ml nc1 + j1 goes to output offset f + delta(run of f)
-    const int nc1 = f.nc1;
-    const int m0 = mp * 32;
-    const int fend = min(32, sch.mc - m0) * nc1;
-    const int i20 = fdiv(m0, sch.mnx);
-    const int r1 = (i20 + 1) * sch.nx - m0, r2 = r1 + sch.nx;      // first rows of the next runs
-    const int f1 = r1 * nc1, f2 = r2 * nc1;
-    const int d0 = moff[m0];
-    const int d1 = r1 < 32 && m0 + r1 < sch.mc ? moff[m0 + r1] - f1 : 0;
-    const int d2 = r2 < 32 && m0 + r2 < sch.mc ? moff[m0 + r2] - f2 : 0;
+    const int nc1 = f.nc1, ldt = f.ldt;
+    int ro[4];                                                   // rows gid + 8 q of the pair
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ro[q] = rowoff[mp * 32 + gid + 8 * q];
 #pragma unroll
     for (int c = 0; c < CNT; ++c) {
         const int j1 = (c % NT1) * 8 + 2 * tig;
-        float *sr = stage + gid * nc1 + j1;
+        const int cofs = (i1b + c / NT1) * ldt + j1;
+        const bool v0 = j1 < nc1, v1 = j1 + 1 < nc1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {                                // rows gid + 8 q
-            if (j1 < nc1) sr[8 * q * nc1] = acc[q >> 1][c][2 * (q & 1)];
-            if (j1 + 1 < nc1) sr[8 * q * nc1 + 1] = acc[q >> 1][c][2 * (q & 1) + 1];
-        }
-        if (c % NT1 == NT1 - 1) {
-            __syncwarp();
-            float *orow = orow0 + (int64_t)(i1b + c / NT1) * ld;
-            if (sch.nx >= 16) {
-                for (int fi = lane; fi < fend; fi += 32) {
-                    const int d = fi < f1 ? d0 : (fi < f2 ? d1 : d2);
-                    orow[fi + d] = stage[fi];
-                }
-            } else {                                               // short runs: row by row
-                for (int fi = lane; fi < fend; fi += 32) {
-                    const int ml = fdiv(fi, sch.mnc1);
-                    orow[moff[m0 + ml] + fi - ml * nc1] = stage[fi];
-                }
+        for (int q = 0; q < 4; ++q) {
+            if (ro[q] >= 0) {
+                float *t = tile + ro[q] + cofs;
+                if (v0) t[0] = acc[q >> 1][c][2 * (q & 1)];
+                if (v1) t[1] = acc[q >> 1][c][2 * (q & 1) + 1];
             }
-            __syncwarp();
         }
     }
 }
 
-__global__ void __launch_bounds__(PANEL_WARPS * 32, 2) sf_panel_f32_kernel(PanelParams p) {
+// Rows of the output tile of unit (i3, j3b) to global memory: one warp per row, each a
+// coalesced run of its output row.
+__device__ __forceinline__ void panel_write_tile(const float *__restrict__ tile, const PanelLayout &f,
+                                                 const BlockDesc &bd, float *__restrict__ o, int64_t ld,
+                                                 int i3, int j3b, int ncol, int warp, int nwarp, int lane) {
+    float *base = o + (bd.row_off + (int64_t)i3 * f.nrow) * ld + bd.col_off + (int64_t)j3b * f.nc1 * f.nc2;
+    for (int row = warp; row < f.nrow; row += nwarp) {
+        float *orow = base + row * ld;
+        const float *trow = tile + row * f.ldt;
+#pragma unroll 4
+        for (int c = lane; c < ncol; c += 32) orow[c] = trow[c];
+    }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) sf_panel_f32_kernel(PanelParams p) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ BlockDesc bd;
     __shared__ PanelLayout f;
     __shared__ PanelSched sched[2];      // nj_max and the remainder chunk
-    const int tid = threadIdx.x, nth = PANEL_WARPS * 32;
+    __shared__ signed char hterm[MAXH][MAXT];
+    __shared__ int hcount[MAXH];
+    __shared__ signed char gh[MAXG][MAXH];       // h groups of each g group
+    __shared__ int ghcount[MAXG];
+    const int tid = threadIdx.x, nth = NW * 32;
     const int lane = tid & 31, warp = tid >> 5;
     const int k = blockIdx.x % p.nblock;
     const int64_t e0 = (int64_t)(blockIdx.x / p.nblock) * p.elems_per_cta;
@@ -750,20 +753,33 @@ __global__ void __launch_bounds__(PANEL_WARPS * 32, 2) sf_panel_f32_kernel(Panel
     if (e0 >= e1) return;
     load_block(p.blocks + k, bd);
     __syncthreads();
-    if (tid == 0) f = panel_layout(bd, p.L, p.nj_max);
+    if (tid == 0) {
+        f = panel_layout(bd, p.L, p.nj_max);
+        for (int h = 0; h < bd.nh; ++h) {
+            int n = 0;
+            for (int t = 0; t < bd.nterm; ++t)
+                if (bd.term[t].h == h) hterm[h][n++] = (signed char)t;
+            hcount[h] = n;
+        }
+        for (int g = 0; g < bd.ng; ++g) {
+            int n = 0;
+            for (int h = 0; h < bd.nh; ++h)
+                if (bd.h_g[h] == g) gh[g][n++] = (signed char)h;
+            ghcount[g] = n;
+        }
+    }
     __syncthreads();
     if (tid < 2) {
         const int nA = bd.nc[2], rem = nA % p.nj_max;
-        sched[tid] = panel_sched(f, bd, tid == 0 ? min(p.nj_max, nA) : (rem ? rem : p.nj_max));
+        sched[tid] = panel_sched(f, bd, tid == 0 ? min(p.nj_max, nA) : (rem ? rem : p.nj_max), NW);
     }
 
     const int L = p.L, L2 = L * L, L3 = L2 * L;
     const int lpad = f.lpad, lsh = f.lsh;
-    const int nr1 = f.nr1, nr2 = f.nr2, nc1 = f.nc1, nc2 = f.nc2, nt1 = f.nt1;
-    const int ng = bd.ng, nh = bd.nh, nterm = bd.nterm;
-    float *As = sm + f.oA, *Bs = sm + f.oB;
-    int *moff = reinterpret_cast<int *>(sm + f.oMo);
-    float *stage = sm + f.oSt + warp * f.stw;
+    const int nr1 = f.nr1, nc1 = f.nc1, nc2 = f.nc2, nt1 = f.nt1;
+    const int nterm = bd.nterm;
+    float *As = sm + f.oA, *Bs = sm + f.oB, *tile = sm + f.oT;
+    int *rowoff = reinterpret_cast<int *>(sm + f.oMo);
 
     // constant operands of the block: one contiguous image
     {
@@ -771,10 +787,11 @@ __global__ void __launch_bounds__(PANEL_WARPS * 32, 2) sf_panel_f32_kernel(Panel
         for (int i = tid; i < (f.oA >> 2); i += nth) smem4[i] = src[i];
     }
 
-    const unsigned mL = div_magic(L), mnc2 = div_magic(nc2), mmtb_c = div_magic(f.mtb);
+    const unsigned mL = div_magic(L), mnc2 = div_magic(nc2), mmtb = div_magic(f.mtb);
     const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
     const float *pp = p.pp;
     const int64_t ld = p.ld;
+
     // P3[t][n][jj] (jj padded to 8 with zeros) of unit ui into buffer b
     auto fill_p3 = [&](int ui, int b) {
         const Unit u = p.units[ui];
@@ -795,28 +812,36 @@ __global__ void __launch_bounds__(PANEL_WARPS * 32, 2) sf_panel_f32_kernel(Panel
     __syncthreads();
 
     int buf = 0;
+    // the previous unit, whose tile is written out during the next unit's stage A
+    float *prev_o = nullptr;
+    int prev_i3 = 0, prev_j3b = 0, prev_s = 0;
     for (int64_t e = e0; e < e1; ++e) {
         const float *fe = p.fields + (size_t)e * p.nfields * L3;
         float *o = p.out + (size_t)e * p.mat_stride + bd.base;
         for (int ui = ub; ui < ue; ++ui, buf ^= 1) {
             const Unit u = p.units[ui];
             const int nj = u.nj;
-            const PanelSched &sch = sched[nj == sched[0].nj ? 0 : 1];
-            const int nx = sch.nx, mc = sch.mc, pairs = sch.pairs;
+            const int si = nj == sched[0].nj ? 0 : 1;
+            const PanelSched &sch = sched[si];
             const float *P3 = sm + f.oP3 + buf * f.p3sz;
 
-            // ---- stage A: item (h, m, l) over [0, lpad)^2 (l fastest), all jj in registers;
-            //      output rows of moff for this unit meanwhile
-            for (int it = tid; it < nh << (2 * lsh); it += nth) {
+            // ---- phase 1: write-out of the previous tile; stage A; tile rows of this unit
+            if (prev_o) {
+                const PanelSched &ps = sched[prev_s];
+                panel_write_tile(tile, f, bd, prev_o, ld, prev_i3, prev_j3b, ps.ncol, warp, NW, lane);
+            }
+            for (int it = tid; it < bd.nh << (2 * lsh); it += nth) {
                 const int l = it & (lpad - 1), m = (it >> lsh) & (lpad - 1), h = it >> (2 * lsh);
                 float acc[NJMAX];
 #pragma unroll
                 for (int jj = 0; jj < NJMAX; ++jj) acc[jj] = 0.0f;
                 if (l < L && m < L) {
-                    for (int t = 0; t < nterm; ++t) {
-                        if (bd.term[t].h != h) continue;
+                    const int nt = hcount[h];
+                    for (int ti = 0; ti < nt; ++ti) {
+                        const int t = hterm[h][ti];
                         const float *M = fe + (size_t)bd.term[t].field * L3 + l * L2 + m * L;
                         const float4 *Pt = reinterpret_cast<const float4 *>(P3 + t * L * 8);
+#pragma unroll 4
                         for (int n = 0; n < L; ++n) {
                             const float mv = __ldg(M + n);
                             const float4 q0 = Pt[2 * n], q1 = Pt[2 * n + 1];
@@ -832,86 +857,89 @@ __global__ void __launch_bounds__(PANEL_WARPS * 32, 2) sf_panel_f32_kernel(Panel
                 for (int jj = 0; jj < NJMAX; ++jj)
                     if (jj < nj) dst[jj << lsh] = acc[jj];
             }
-            {
-                for (int m = tid; m < pairs * 32; m += nth) {
-                    int off = -1;
-                    if (m < mc) {
-                        const int i2 = fdiv(m, sch.mnx), x = m - i2 * nx;
-                        off = nr1 * i2 * (int)ld + nc1 * x;
-                    }
-                    moff[m] = off;
+            for (int m = tid; m < sch.pairs * 32; m += nth) {
+                int off = -1;
+                if (m < sch.mc) {
+                    const int i2 = fdiv(m, sch.mnx), x = m - i2 * sch.nx;
+                    off = nr1 * i2 * f.ldt + nc1 * x;
                 }
+                rowoff[m] = off;
             }
             __syncthreads();
 
-            // ---- stage B: task (g, m-tile, chunk of n-tiles); P3 of the next unit meanwhile
+            // ---- phase 2: stage B; P3 of the next unit
             {
                 const int un = ui + 1 < ue ? ui + 1 : ub;
                 if (ui + 1 < ue || e + 1 < e1) fill_p3(un, buf ^ 1);
                 const int ntb = nj * f.ksh, nch = sch.nch, cb = sch.cb, ntask = sch.ntaskB;
-                const unsigned mnch = sch.mnch, mmtb = mmtb_c;
-                for (int task = warp; task < ntask; task += PANEL_WARPS) {
+                const unsigned mnch = sch.mnch;
+                for (int task = warp; task < ntask; task += NW) {
                     const int r = fdiv(task, mnch), ch = task - r * nch;
                     const int g = fdiv(r, mmtb), mt = r - g * f.mtb;
                     const int nt0 = ch * cb, cnt = min(cb, ntb - nt0);
                     switch (cnt) {
-                    case 1: panel_stage_b<1>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
-                    case 2: panel_stage_b<2>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
-                    case 3: panel_stage_b<3>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
-                    case 4: panel_stage_b<4>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
-                    case 5: panel_stage_b<5>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
-                    case 6: panel_stage_b<6>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
-                    case 7: panel_stage_b<7>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
-                    case 8: panel_stage_b<8>(sm, f, bd, Bs, g, mt, nt0, nx, mnc2, lane); break;
+                    case 1: panel_stage_b<1>(sm, f, bd, Bs, g, mt, nt0, sch.nx, mnc2, lane, gh[g], ghcount[g]); break;
+                    case 2: panel_stage_b<2>(sm, f, bd, Bs, g, mt, nt0, sch.nx, mnc2, lane, gh[g], ghcount[g]); break;
+                    case 3: panel_stage_b<3>(sm, f, bd, Bs, g, mt, nt0, sch.nx, mnc2, lane, gh[g], ghcount[g]); break;
+                    case 4: panel_stage_b<4>(sm, f, bd, Bs, g, mt, nt0, sch.nx, mnc2, lane, gh[g], ghcount[g]); break;
+                    case 5: panel_stage_b<5>(sm, f, bd, Bs, g, mt, nt0, sch.nx, mnc2, lane, gh[g], ghcount[g]); break;
+                    case 6: panel_stage_b<6>(sm, f, bd, Bs, g, mt, nt0, sch.nx, mnc2, lane, gh[g], ghcount[g]); break;
+                    case 7: panel_stage_b<7>(sm, f, bd, Bs, g, mt, nt0, sch.nx, mnc2, lane, gh[g], ghcount[g]); break;
+                    case 8: panel_stage_b<8>(sm, f, bd, Bs, g, mt, nt0, sch.nx, mnc2, lane, gh[g], ghcount[g]); break;
                     default: break;
                     }
                 }
             }
             __syncthreads();
 
-            // ---- stage C: task (pair of m-tiles, group of i1)
+            // ---- phase 3: stage C into the tile
             {
                 const int ngrp = sch.ngrp, per = sch.per, ntask = sch.ntaskC;
                 const unsigned mgrp = sch.mgrp;
-                float *orow0 = o + (bd.row_off + (int64_t)u.i3 * nr1 * nr2) * ld + bd.col_off + (int64_t)u.j3b * nc1 * nc2;
-                for (int task = warp; task < ntask; task += PANEL_WARPS) {
+                for (int task = warp; task < ntask; task += NW) {
                     const int mp = fdiv(task, mgrp), grp = task - mp * ngrp;
                     const int i1b = grp * per, cnt = min(per, nr1 - i1b) * nt1;
                     if (nt1 == 1) {
                         switch (cnt) {
-                        case 1: panel_stage_c<1, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 2: panel_stage_c<2, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 3: panel_stage_c<3, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 4: panel_stage_c<4, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 5: panel_stage_c<5, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 6: panel_stage_c<6, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 7: panel_stage_c<7, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 8: panel_stage_c<8, 1>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 1: panel_stage_c<1, 1>(sm, tile, f, mp, i1b, lane); break;
+                        case 2: panel_stage_c<2, 1>(sm, tile, f, mp, i1b, lane); break;
+                        case 3: panel_stage_c<3, 1>(sm, tile, f, mp, i1b, lane); break;
+                        case 4: panel_stage_c<4, 1>(sm, tile, f, mp, i1b, lane); break;
+                        case 5: panel_stage_c<5, 1>(sm, tile, f, mp, i1b, lane); break;
+                        case 6: panel_stage_c<6, 1>(sm, tile, f, mp, i1b, lane); break;
+                        case 7: panel_stage_c<7, 1>(sm, tile, f, mp, i1b, lane); break;
+                        case 8: panel_stage_c<8, 1>(sm, tile, f, mp, i1b, lane); break;
                         default: break;
                         }
                     } else {
                         switch (cnt) {
-                        case 2: panel_stage_c<2, 2>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 4: panel_stage_c<4, 2>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 6: panel_stage_c<6, 2>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
-                        case 8: panel_stage_c<8, 2>(sm, f, sch, mp, i1b, orow0, ld, stage, lane); break;
+                        case 2: panel_stage_c<2, 2>(sm, tile, f, mp, i1b, lane); break;
+                        case 4: panel_stage_c<4, 2>(sm, tile, f, mp, i1b, lane); break;
+                        case 6: panel_stage_c<6, 2>(sm, tile, f, mp, i1b, lane); break;
+                        case 8: panel_stage_c<8, 2>(sm, tile, f, mp, i1b, lane); break;
                         default: break;
                         }
                     }
                 }
             }
+            __syncthreads();
+            prev_o = o; prev_i3 = u.i3; prev_j3b = u.j3b; prev_s = si;
         }
+    }
+    {
+        const PanelSched &ps = sched[prev_s];
+        panel_write_tile(tile, f, bd, prev_o, ld, prev_i3, prev_j3b, ps.ncol, warp, NW, lane);
     }
 }
 
 // --------------------------------------------------------------------------------------
 // affine path (Sec. 2.8.1)
 // --------------------------------------------------------------------------------------
-// Store-bound: the tile is produced in column panels of AFF_W columns staged in shared
-// memory, then written as row segments (the tile) and as column segments (its mirror),
-// both contiguous in the row-major output.  The program uses the paper's direction order
-// (stage C over xi_1, B over xi_2, A over xi_3), so a tile row is one contiguous segment.
-constexpr int AFF_W = 32;
+// Store-bound: per work unit the tile is zero-filled in shared memory, the non-zero
+// products of the Kronecker sums are scattered into it, and it is written as row runs
+// (the tile) and as column runs (its mirror), both contiguous in the row-major output.
+// The program uses the paper's direction order (stage C over xi_1, B over xi_2, A over
+// xi_3), so a tile row is one contiguous segment.
 
 // Per-element constants of the affine path, one thread per element: the Jacobian from the
 // edge vectors at vertex 0 (the element must be a parallelepiped), its metric fields with
@@ -994,9 +1022,11 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     T *qv = reinterpret_cast<T *>(smem_raw) + lay.oQV;                 // [ng][n22 nj] non-zero Q
     T *f1v = reinterpret_cast<T *>(smem_raw) + lay.oF1V;               // [ng][n11] non-zero F1
     T *tile = reinterpret_cast<T *>(smem_raw) + lay.oT;                // [nrow][ldt]
-    int *qi = reinterpret_cast<int *>(reinterpret_cast<T *>(smem_raw) + lay.oQI);   // packed (i2,j2,jj)
-    int *f1i = reinterpret_cast<int *>(reinterpret_cast<T *>(smem_raw) + lay.oF1I); // packed (i1,j1)
-    const unsigned mnc1 = div_magic(nc1), mnc2 = div_magic(nc2), mn22 = div_magic(n22), mncj = div_magic(ncj);
+    // tile offsets of the non-zeros: a product F1(i1,j1) Q(i2,j2,jj) lands at
+    // (i1 ldt + j1) + (nr1 i2 ldt + nc1 (j2 + nc2 jj))
+    int *qi = reinterpret_cast<int *>(reinterpret_cast<T *>(smem_raw) + lay.oQI);
+    int *f1i = reinterpret_cast<int *>(reinterpret_cast<T *>(smem_raw) + lay.oF1I);
+    const unsigned mnc1 = div_magic(nc1), mnc2 = div_magic(nc2), mn22 = div_magic(n22);
 
     // stage-C factors: compact non-zero lists per group
     for (int it = tid; it < ng * n11; it += nth) {
@@ -1006,7 +1036,7 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         if (!is_zero(v)) {
             const int slot = atomicAdd(&f1c[g], 1);
             f1v[g * n11 + slot] = v;
-            f1i[g * n11 + slot] = i1 | (j1 << 16);
+            f1i[g * n11 + slot] = i1 * lay.ldt + j1;
         }
     }
     for (int it = tid; it < nterm * n22; it += nth) {                   // F2_t(i2, j2)
@@ -1025,7 +1055,7 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         const Unit u = p.units[ui];
         const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
         const unsigned mnj = div_magic(nj);
-        const int ncol = ncj * nj, ldt = lay.ldt;
+        const int ldt = lay.ldt;
         __syncthreads();                                                // previous unit done
         for (int it = tid; it < nterm * nj; it += nth) {
             const int t = fdiv(it, mnj), jj = it - t * nj;
@@ -1053,20 +1083,23 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
                 const int slot = atomicAdd(&qc[g], 1);
                 const int i2 = fdiv(ij2, mnc2), j2 = ij2 - i2 * nc2;
                 qv[g * n22 * njm + slot] = acc;
-                qi[g * n22 * njm + slot] = i2 | (j2 << 8) | (jj << 16);
+                qi[g * n22 * njm + slot] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
             }
         }
         __syncthreads();
-        // scatter the non-zero products group by group (one product per entry per group)
+        // scatter the non-zero products group by group (one product per entry per group):
+        // a warp per stage-C non-zero, its lanes over the Q non-zeros
         for (int g = 0; g < ng; ++g) {
             const int nf = f1c[g], nq = qc[g];
-            for (int it = tid; it < nf * nq; it += nth) {
-                const int a = it / nq, b = it - a * nq;
-                const int fi = f1i[g * n11 + a], qq = qi[g * n22 * njm + b];
-                const int i1 = fi & 0xffff, j1 = fi >> 16;
-                const int i2 = qq & 0xff, j2 = (qq >> 8) & 0xff, jj = qq >> 16;
-                T *dst = tile + (i1 + nr1 * i2) * ldt + j1 + nc1 * (j2 + nc2 * jj);
-                *dst = fma(f1v[g * n11 + a], qv[g * n22 * njm + b], *dst);
+            const T *qvg = qv + g * n22 * njm;
+            const int *qig = qi + g * n22 * njm;
+            for (int a = warp; a < nf; a += nwarp) {
+                const T fv = f1v[g * n11 + a];
+                T *trow = tile + f1i[g * n11 + a];
+                for (int b = lane; b < nq; b += 32) {
+                    T *dst = trow + qig[b];
+                    *dst = fma(fv, qvg[b], *dst);
+                }
             }
             __syncthreads();
         }
@@ -1076,33 +1109,29 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         const int64_t C0 = bd.col_off + (int64_t)j3b * ncj;
         const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
         const T nanv = qnan<T>();
+        const int ncolu = ncj * nj, cb = jd * ncj;
         for (int row = warp; row < nrow; row += nwarp) {
             T *orow = o + (R0 + row) * ld + C0;
             const T *trw = tile + row * ldt;
-            for (int jj = 0; jj < nj; ++jj) {
-                const int cb = jj * ncj;
-                if (jj == jd) {
-                    for (int c = lane; c < ncj; c += 32) {
-                        const T v = c >= row ? trw[cb + c] : tile[c * ldt + cb + row];
-                        orow[cb + c] = bad ? nanv : v;
-                    }
-                } else {
-                    for (int c = lane; c < ncj; c += 32) orow[cb + c] = bad ? nanv : trw[cb + c];
-                }
+            for (int c = lane; c < ncolu; c += 32) {
+                T v = trw[c];
+                const unsigned cc = (unsigned)(c - cb);
+                if (jd >= 0 && cc < (unsigned)row) v = tile[cc * ldt + cb + row];
+                orow[c] = bad ? nanv : v;
             }
         }
         if (bd.sym != 0) {
-            // the mirror of the off-diagonal sub-tiles: tile column c -> output row C0 + c
-            for (int jj = 0; jj < nj; ++jj) {
-                if (jj == jd) continue;
-                for (int cj = warp; cj < ncj; cj += nwarp) {
-                    const int c = jj * ncj + cj;
-                    T *mrow = o + (C0 + c) * ld + R0;
-                    for (int row = lane; row < nrow; row += 32) mrow[row] = bad ? nanv : tile[row * ldt + c];
-                }
+            // the mirror of the off-diagonal sub-tiles: tile column c -> output row C0 + c,
+            // a run of nrow values at column R0; (column, row) pairs flattened over the CTA
+            const int nmc = jd >= 0 ? ncolu - ncj : ncolu;
+            const unsigned mnrow = div_magic(nrow);
+            T *mbase = o + C0 * ld + R0;
+            for (int it = tid; it < nmc * nrow; it += nth) {
+                const int mcix = fdiv(it, mnrow), row = it - mcix * nrow;
+                const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                mbase[(int64_t)c * ld + row] = bad ? nanv : tile[row * ldt + c];
             }
         }
-        (void)mncj;
     }
 }
 
@@ -1397,7 +1426,9 @@ cudaError_t launch_panel_f32(const PanelParams &p, size_t smem, cudaStream_t s) 
     if (p.n_elem == 0) return cudaSuccess;
     const int64_t chunks = (p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta;
     const int64_t ctas = chunks * p.nblock;
-    sf_panel_f32_kernel<<<(unsigned)ctas, PANEL_WARPS * 32, smem, s>>>(p);
+    // two CTAs of 8 warps per SM where the shared memory allows, else one of 16 warps
+    if (smem <= PANEL_SMEM_2CTA) sf_panel_f32_kernel<8><<<(unsigned)ctas, 256, smem, s>>>(p);
+    else sf_panel_f32_kernel<16><<<(unsigned)ctas, 512, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -1434,7 +1465,8 @@ cudaError_t init_kernel_attributes(int optin_smem) {
     if (e == cudaSuccess) e = one((const void *)hp_contract_kernel<float>);
     if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<3>);
     if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<4>);
-    if (e == cudaSuccess) e = one((const void *)sf_panel_f32_kernel);
+    if (e == cudaSuccess) e = one((const void *)sf_panel_f32_kernel<8>);
+    if (e == cudaSuccess) e = one((const void *)sf_panel_f32_kernel<16>);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<double>);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<float>);
     return e;

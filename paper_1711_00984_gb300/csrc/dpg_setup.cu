@@ -330,8 +330,9 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             return (size_t)aff_layout(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], njv).total * sizeof(double);
         return smem_values(b, L, njv) * sizeof(double);
     };
-    // (ORDER_PANEL: two CTAs per SM)
-    const size_t budget = order == ORDER_BEST ? 160 * 1024 : (order == ORDER_PANEL ? 112 * 1024 : 110 * 1024);
+    // (ORDER_PANEL: the largest chunk that fits one CTA per SM; the launch takes two
+    // 8-warp CTAs per SM where the chunk fits PANEL_SMEM_2CTA, else one of 16 warps)
+    const size_t budget = order == ORDER_BEST ? 160 * 1024 : (order == ORDER_PANEL ? (size_t)200 * 1024 : 110 * 1024);
     int maxnA = 1;
     for (int k = 0; k < pr.nblock; ++k) maxnA = std::max(maxnA, pr.blocks[k].nc[pr.blocks[k].dir[2]]);
     int nj = std::min(NJMAX, maxnA);
