@@ -33,14 +33,22 @@ struct TableEntry {
     float *pp32 = nullptr, *F32 = nullptr;
 };
 
+struct AffProg {
+    Program prog;
+    BlockDesc *d_blocks = nullptr;
+    Unit *d_units = nullptr;
+    int *d_block_units = nullptr;   // [nblock + 1] unit ranges
+    size_t smem_values = 0;         // values of the kernel's shared memory
+};
+
 struct ProgEntry {
     Program prog;                   // general path: per-block contraction order
     BlockDesc *d_blocks = nullptr;
     Unit *d_units = nullptr;
-    Program prog_aff;               // affine path: the paper's direction order
+    // affine path, the paper's direction order: [0] FP64 kernel (a chunk for three CTAs per
+    // SM), [1] FP32 kernel (the larger chunk that fits two)
+    AffProg aff[2];
     double flops_aff = 0.0;         // algorithmic flops of the affine path
-    BlockDesc *d_blocks_aff = nullptr;
-    Unit *d_units_aff = nullptr;
     Program prog32;                 // FP32 general path: row-panel program (panel32) or
                                     // the mirrored-tile program with stage A on xi_3
     bool panel32 = false;
@@ -50,8 +58,6 @@ struct ProgEntry {
     Unit *d_units32 = nullptr;
     int max_nc1_32 = 0;             // largest stage-C column extent of prog32
     int *d_block_units32 = nullptr; // [nblock + 1] unit ranges of prog32
-    size_t smem_aff = 0;            // values of the affine kernel's shared memory
-    int *d_block_units_aff = nullptr; // [nblock + 1] unit ranges of prog_aff
 };
 
 using ProgKey = std::tuple<int, int, int, int, int>;   // space, q, L, p, split
@@ -206,29 +212,30 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
     if (it != ds->progs.end()) { *out = it->second.get(); return DPG_OK; }
     auto pe = std::make_unique<ProgEntry>();
     pe->prog = make_program(space, q, L, p, split != 0, tab);
-    pe->prog_aff = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL);
-    pe->flops_aff = pe->prog_aff.flops_affine;
     const Program &pr = pe->prog;
     if (pr.smem_values * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     int r;
     if ((r = upload(pr.blocks, (size_t)pr.nblock, &pe->d_blocks))) return r;
     if ((r = upload(pr.units.data(), pr.units.size(), &pe->d_units))) return r;
-    const Program &pa = pe->prog_aff;
-    if ((r = upload(pa.blocks, (size_t)pa.nblock, &pe->d_blocks_aff))) return r;
-    if ((r = upload(pa.units.data(), pa.units.size(), &pe->d_units_aff))) return r;
-    size_t m = 0;
-    for (int k = 0; k < pa.nblock; ++k) {
-        const BlockDesc &b = pa.blocks[k];
-        m = std::max(m, affine_smem_values(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], pa.nj));
-    }
-    {
+    for (int prec = 0; prec < 2; ++prec) {
+        AffProg &ap = pe->aff[prec];
+        ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL, 0, prec == 0 ? 72 * 1024 : 0);
+        const Program &pa = ap.prog;
+        if ((r = upload(pa.blocks, (size_t)pa.nblock, &ap.d_blocks))) return r;
+        if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
+        size_t m = 0;
+        for (int k = 0; k < pa.nblock; ++k) {
+            const BlockDesc &b = pa.blocks[k];
+            m = std::max(m, affine_smem_values(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], pa.nj));
+        }
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
         for (int k = 0; k < pa.nblock; ++k) ub[k + 1] += ub[k];
-        if ((r = upload(ub.data(), ub.size(), &pe->d_block_units_aff))) return r;
+        if ((r = upload(ub.data(), ub.size(), &ap.d_block_units))) return r;
+        if (m * (prec ? sizeof(float) : sizeof(double)) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
+        ap.smem_values = m;
     }
-    if (m * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
-    pe->smem_aff = m;
+    pe->flops_aff = pe->aff[0].prog.flops_affine;
     if ((r = setup_prog32(pe.get(), space, q, L, p, split != 0, tab, 0))) return r;
     *out = pe.get();
     ds->progs[key] = std::move(pe);
@@ -278,7 +285,7 @@ void free_device_state(DeviceState &ds) {
     }
     for (auto &kv : ds.progs) {
         cudaFree(kv.second->d_blocks); cudaFree(kv.second->d_units);
-        cudaFree(kv.second->d_blocks_aff); cudaFree(kv.second->d_units_aff); cudaFree(kv.second->d_block_units_aff);
+        for (AffProg &ap : kv.second->aff) { cudaFree(ap.d_blocks); cudaFree(ap.d_units); cudaFree(ap.d_block_units); }
         cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
         cudaFree(kv.second->d_ctab32); cudaFree(kv.second->d_ctab_off32);
     }
@@ -411,7 +418,8 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
 template <typename T>
 int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
                const double *coeffs, T *out, cudaStream_t s) {
-    const Program &pr = pe->prog_aff;
+    const AffProg &aprog = pe->aff[sizeof(T) == 4 ? 1 : 0];
+    const Program &pr = aprog.prog;
     const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
     // CTAs per (element, block): enough for about six waves of the SMs, at most one per unit
     int max_units_block = 1;
@@ -435,13 +443,13 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
     for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK; e0 += per_launch) {
         const int64_t ne = std::min(per_launch, n_elem - e0);
         AffParams<T> ap;
-        ap.blocks = pe->d_blocks_aff; ap.units = pe->d_units_aff; ap.block_unit_begin = pe->d_block_units_aff;
+        ap.blocks = aprog.d_blocks; ap.units = aprog.d_units; ap.block_unit_begin = aprog.d_block_units;
         ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit;
         if constexpr (sizeof(T) == 8) ap.F = te->F64; else ap.F = te->F32;
         ap.consts = (const double *)consts + AFF_CONST_STRIDE * e0;
         ap.out = out + e0 * mat;
         ap.mat_stride = mat; ap.ld = pr.cols; ap.n_elem = ne;
-        le = launch_affine<T>(ap, pe->smem_aff * sizeof(T), s);
+        le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
         if (le != cudaSuccess) rc = cuda_fail(le, "sf_affine_kernel launch", __LINE__);
     }
     cudaError_t fe = cudaFreeAsync(consts, s);

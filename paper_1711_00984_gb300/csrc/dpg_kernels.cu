@@ -1124,12 +1124,20 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             // the mirror of the off-diagonal sub-tiles: tile column c -> output row C0 + c,
             // a run of nrow values at column R0; (column, row) pairs flattened over the CTA
             const int nmc = jd >= 0 ? ncolu - ncj : ncolu;
-            const unsigned mnrow = div_magic(nrow);
             T *mbase = o + C0 * ld + R0;
-            for (int it = tid; it < nmc * nrow; it += nth) {
-                const int mcix = fdiv(it, mnrow), row = it - mcix * nrow;
-                const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
-                mbase[(int64_t)c * ld + row] = bad ? nanv : tile[row * ldt + c];
+            if (nrow >= 64) {                                   // long runs: a warp per column
+                for (int mcix = warp; mcix < nmc; mcix += nwarp) {
+                    const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                    T *mrow = mbase + (int64_t)c * ld;
+                    for (int row = lane; row < nrow; row += 32) mrow[row] = bad ? nanv : tile[row * ldt + c];
+                }
+            } else {                                            // short runs: full warps
+                const unsigned mnrow = div_magic(nrow);
+                for (int it = tid; it < nmc * nrow; it += nth) {
+                    const int mcix = fdiv(it, mnrow), row = it - mcix * nrow;
+                    const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                    mbase[(int64_t)c * ld + row] = bad ? nanv : tile[row * ldt + c];
+                }
             }
         }
     }

@@ -232,7 +232,8 @@ static size_t smem_values(const BlockDesc &b, int L, int nj) {
     return P1 + P2 + P3 + A + B;
 }
 
-Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order, int force_nj) {
+Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order, int force_nj,
+                     size_t smem_budget) {
     Program pr;
     std::memset(pr.blocks, 0, sizeof(pr.blocks));
     pr.space = space; pr.q = q; pr.L = L; pr.p = p; pr.split = split;
@@ -332,7 +333,8 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     };
     // (ORDER_PANEL: the largest chunk that fits one CTA per SM; the launch takes two
     // 8-warp CTAs per SM where the chunk fits PANEL_SMEM_2CTA, else one of 16 warps)
-    const size_t budget = order == ORDER_BEST ? 160 * 1024 : (order == ORDER_PANEL ? (size_t)200 * 1024 : 110 * 1024);
+    const size_t budget = smem_budget ? smem_budget
+                                      : (order == ORDER_BEST ? 160 * 1024 : (order == ORDER_PANEL ? (size_t)200 * 1024 : 110 * 1024));
     int maxnA = 1;
     for (int k = 0; k < pr.nblock; ++k) maxnA = std::max(maxnA, pr.blocks[k].nc[pr.blocks[k].dir[2]]);
     int nj = std::min(NJMAX, maxnA);

@@ -39,9 +39,10 @@ HostTables make_tables(int q, int L);
 // mirrored tiles): the FP32 row-panel kernel writes every output row itself.
 enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3 };
 // force_nj > 0 fixes the stage-A chunk (autotuner); otherwise the largest chunk whose
-// shared memory fits the kernel's budget is taken.
+// shared memory fits the kernel's budget (smem_budget bytes, or the order's default when
+// 0) is taken.
 Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order = ORDER_BEST,
-                     int force_nj = 0);
+                     int force_nj = 0, size_t smem_budget = 0);
 // Constant operands of the FP32 row-panel kernel for every block of an ORDER_PANEL
 // program (the shared-memory image [0, oA) of panel_layout), concatenated; off[k] is the
 // first float of block k.
