@@ -28,6 +28,25 @@ SPACES = ["H1", "HCURL", "HDIV", "L2"]
 WORKLOAD = "seq_q5_8x8x8"
 Q, L = 5, 7
 METRIC = "element Gram matrices/s (H1+H(curl)+H(div)+L2, q=5, trilinear O(p^7) + affine O(p^6), FP64)"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant launch, the
+# H(curl) general contraction of this workload, from one ncu capture of this script
+# (command and figures in profiles/launches_seq_q5_8x8x8_fp64.md).  It is reported only
+# while the source of that kernel (the text between the two markers below in
+# dpg_kernels.cu) is the one the counters were taken on.
+TRAFFIC = {"bytes": 127710976 + 1240180224,
+           "kernel_sha256": "057a2fd106afd81cbdb9f51e9eea11cbd1d21527df77b94ab5490c2d35376ab1",
+           "markers": ("// general sum factorization", "// FP32 general sum factorization")}
+
+
+def dominant_traffic():
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_1711_00984_gb300", "csrc", "dpg_kernels.cu")).read()
+        a, b = src.index(TRAFFIC["markers"][0]), src.index(TRAFFIC["markers"][1])
+    except (OSError, ValueError):
+        return None
+    return TRAFFIC["bytes"] if hashlib.sha256(src[a:b].encode()).hexdigest() == TRAFFIC["kernel_sha256"] else None
 UNIT = "element matrices/s"
 
 
@@ -286,7 +305,8 @@ def run_gpu(args):
     achieved = fpe * ne / (dom_ms * 1e-3)
     roof = {"bound": "alu", "kernel": "sf_general_kernel<double> (H(curl), with its geom_kernel launch)",
             "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak64, "traffic": None,
+            "frac": achieved / peak64, "traffic": dominant_traffic(),
+            "traffic_unit": "bytes per launch (the contraction launch; its geom_kernel launch not included)",
             "peak_source": "FP64 FMA rate measured in this run by dpg_measure_fma_peak (MEASURED_PEAKS has no FP64 entry)",
             "flops_per_launch": fpe * ne, "launch_ms": dom_ms,
             "measured_alu_peaks_tflops": {"fp64_dfma": peak64 / 1e12, "fp32_ffma": peak32 / 1e12,
