@@ -53,7 +53,13 @@ extern "C" {
                                   trial u of order p, H(curl) test psi of order q
                                   (real, unit-coefficient analogue of Eqs. 3.15-3.16)   */
 /* ---- flags ORed into `space` ---- */
-#define DPG_FP32        0x100  /* FP32 contraction stages and FP32 output; geometry FP64 */
+/* DPG_FP32: geometry and metric fields computed in FP64, then rounded to FP32; the
+ * contraction stages run in FP32 (stage A on the FMA pipe; stages B and C of the general
+ * path as tensor-core TF32 products of high/low operand splits, three products per pair,
+ * FP32 accumulation); FP32 output.  Target: relative Frobenius error <= 1e-5 per element
+ * matrix against the FP64 form.  General-path FP32 Gram matrices are computed block by
+ * block without mirroring, so they are symmetric to rounding, not bit for bit. */
+#define DPG_FP32        0x100  /* FP32 form (above) */
 #define DPG_MAP_AFFINE  0x200  /* elements are parallelepipeds: O(p^6) path, Sec. 2.8.1 */
 #define DPG_B_SPLIT     0x400  /* B only: write [2][rows][cols] = (mass part, curl part) */
 
