@@ -13,6 +13,10 @@ Functions and the passages they follow:
                             their master-element grad / curl / div (Eqs. 2.30, 2.67, 2.48).
 * ``gram(space, ...)``   -- Gram matrices (Eqs. 2.13, 2.16, 2.31, 2.49, 2.68).
 * ``mixed_b(...)``       -- mixed stiffness B (pattern of Eqs. 3.15-3.16).
+* ``acoustic_cross(...)`` -- cross terms of the acoustics adjoint graph norm, Eq. 3.18
+                            (the coefficient of i*omega).
+* ``acoustic_b(...)``    -- ultraweak acoustics stiffness, Eqs. 3.14-3.16, as (part without
+                            i*omega, coefficient of i*omega).
 """
 from __future__ import annotations
 
@@ -68,6 +72,11 @@ def _load():
             lib.oracle_mixed_b.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                            dp, dp, ctypes.c_int, ctypes.c_int]
             lib.oracle_mixed_b.restype = ctypes.c_int64
+            lib.oracle_acoustic_cross.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int]
+            lib.oracle_acoustic_cross.restype = ctypes.c_int64
+            lib.oracle_acoustic_b.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                              dp, dp, ctypes.c_int]
+            lib.oracle_acoustic_b.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -157,4 +166,30 @@ def mixed_b(q: int, p: int, L: int, verts: np.ndarray, split: bool = False,
     r = _load().oracle_mixed_b(q, p, L, ne, _ptr(v), _ptr(out), 1 if split else 0, nthreads)
     if r < 0:
         raise ValueError("oracle_mixed_b: bad arguments")
+    return out, int(r) - 1
+
+
+def acoustic_cross(q: int, L: int, verts: np.ndarray, nthreads: int = 0) -> tuple[np.ndarray, int]:
+    """Cross block ``[n_elem, dim H(div), dim H1]`` of the acoustics adjoint graph norm
+    (Eq. 3.18, coefficient of i*omega): -(div v_I, q_J) + (v_I, grad q_J)."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    ne = v.shape[0]
+    out = np.empty((ne, dim("HDIV", q), dim("H1", q)))
+    r = _load().oracle_acoustic_cross(q, L, ne, _ptr(v), _ptr(out), nthreads)
+    if r < 0:
+        raise ValueError("oracle_acoustic_cross: bad arguments")
+    return out, int(r) - 1
+
+
+def acoustic_b(q: int, p: int, L: int, verts: np.ndarray, nthreads: int = 0) -> tuple[np.ndarray, int]:
+    """Ultraweak acoustics stiffness ``[n_elem, 2, dim H1 + dim H(div), 4 p^3]`` (Eq. 3.16):
+    part 0 = -(p, div v) - (u, grad q), part 1 = coefficient of i*omega: (p, q) + (u, v).
+    Rows: H1 test functions then H(div) ones; columns: scalar L2 trial then (L2)^3."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    ne = v.shape[0]
+    rows = dim("H1", q) + dim("HDIV", q)
+    out = np.empty((ne, 2, rows, 4 * p ** 3))
+    r = _load().oracle_acoustic_b(q, p, L, ne, _ptr(v), _ptr(out), nthreads)
+    if r < 0:
+        raise ValueError("oracle_acoustic_b: bad arguments")
     return out, int(r) - 1

@@ -479,3 +479,157 @@ int64_t oracle_mixed_b(int q, int p, int L, int64_t n_elem, const double *verts,
     }
     return first_bad;
 }
+
+/* ------------------------------------------------------------------------------------
+ * Ultraweak acoustics (Sec. 3.3), real arithmetic: the i*omega factors are kept apart
+ * ---------------------------------------------------------------------------------- */
+
+/* Cross terms of the adjoint graph norm (Eq. 3.18): the coefficient of i*omega in
+ * -i w (div dv, q) + i w (dv, grad q), i.e.
+ *   X_{IJ} = ( -(div v_I) q_J + v_I . grad q_J )_K
+ * with v_I the H(div) test functions of order q (rows) and q_J the H1 test functions of
+ * order q (columns), both mapped to the physical element (Eqs. 2.3, 2.5) and integrated
+ * there.  out: [n_elem][dim H(div)][dim H1]. */
+int64_t oracle_acoustic_cross(int q, int L, int64_t n_elem, const double *verts, double *out, int nthreads) {
+    if (q < 1 || L < 1) return -1;
+    int64_t nv = space_dim(OR_HDIV, q, 0), nh = space_dim(OR_H1, q, 0);
+    double zeta[64], wq[64];
+    if (oracle_gauss(L, zeta, wq) != 0) return -1;
+    int64_t first_bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    #pragma omp parallel
+    {
+        double *vv = (double *)malloc(sizeof(double) * 3 * nv), *vd = (double *)malloc(sizeof(double) * 9 * nv);
+        double *hv = (double *)malloc(sizeof(double) * 3 * nh), *hd = (double *)malloc(sizeof(double) * 9 * nh);
+        double *V = (double *)malloc(sizeof(double) * 3 * nv), *dV = (double *)malloc(sizeof(double) * 3 * nv);
+        double *u = (double *)malloc(sizeof(double) * 3 * nh), *gu = (double *)malloc(sizeof(double) * 3 * nh);
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t e = 0; e < n_elem; ++e) {
+            const double *ve = verts + 24 * e;
+            double *X = out + e * nv * nh;
+            memset(X, 0, sizeof(double) * nv * nh);
+            int bad = 0;
+            for (int l = 0; l < L && !bad; ++l)
+            for (int m = 0; m < L && !bad; ++m)
+            for (int k = 0; k < L && !bad; ++k) {
+                double xi[3] = { zeta[l], zeta[m], zeta[k] };
+                double w = wq[l] * wq[m] * wq[k];
+                double J[3][3], Ji[3][3];
+                double det = trilinear_jacobian(ve, xi, J);
+                if (!(det > 0.0) || !isfinite(det)) { bad = 1; break; }
+                inverse3(J, det, Ji);
+                shape3(OR_HDIV, q, 0, xi, vv, vd);
+                map_to_physical(OR_HDIV, nv, vv, vd, J, det, Ji, V, dV);
+                shape3(OR_H1, q, 0, xi, hv, hd);
+                map_to_physical(OR_H1, nh, hv, hd, J, det, Ji, u, gu);
+                double s = w * det;
+                for (int64_t I = 0; I < nv; ++I) {
+                    const double *a = V + 3 * I;
+                    const double dv = dV[3 * I];
+                    double *row = X + I * nh;
+                    for (int64_t Jd = 0; Jd < nh; ++Jd) {
+                        const double *g = gu + 3 * Jd;
+                        row[Jd] += s * (-dv * u[3 * Jd] + (a[0] * g[0] + a[1] * g[1] + a[2] * g[2]));
+                    }
+                }
+            }
+            if (bad) {
+                for (int64_t i = 0; i < nv * nh; ++i) X[i] = NAN;
+                #pragma omp critical
+                { if (first_bad == 0 || e + 1 < first_bad) first_bad = e + 1; }
+            }
+        }
+        free(vv); free(vd); free(hv); free(hd); free(V); free(dV); free(u); free(gu);
+    }
+    return first_bad;
+}
+
+/* Stiffness of the ultraweak acoustics formulation (Eqs. 3.14-3.16):
+ *   b((p,u),(q,v)) = (i w u, v) - (p, div v) + (i w p, q) - (u, grad q)
+ * with test (q, v) in H1 x H(div) of order q and trial (p, u) in L2 x (L2)^3 of order p
+ * (the scalar P_k1 P_k2 P_k3 and each vector component mapped by T, Eq. 2.6).
+ * Rows: the H1 test functions, then the H(div) ones; columns: the scalar L2 trial
+ * functions, then the three vector components.  out: [n_elem][2][rows][cols]:
+ *   part 0 (terms without i w): -(p_K, div v_I) and -(u_K, grad q_I);
+ *   part 1 (coefficient of i w): (p_K, q_I) and (u_K, v_I). */
+int64_t oracle_acoustic_b(int q, int p, int L, int64_t n_elem, const double *verts, double *out, int nthreads) {
+    if (q < 1 || p < 1 || p > q || L < 1) return -1;
+    int64_t nh = space_dim(OR_H1, q, 0), nv = space_dim(OR_HDIV, q, 0);
+    int64_t np = space_dim(OR_L2, p, 0), nu = space_dim(-OR_B, q, p);
+    int64_t rows = nh + nv, cols = np + nu;
+    double zeta[64], wq[64];
+    if (oracle_gauss(L, zeta, wq) != 0) return -1;
+    int64_t first_bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    #pragma omp parallel
+    {
+        double *hv = (double *)malloc(sizeof(double) * 3 * nh), *hd = (double *)malloc(sizeof(double) * 9 * nh);
+        double *vv = (double *)malloc(sizeof(double) * 3 * nv), *vd = (double *)malloc(sizeof(double) * 9 * nv);
+        double *pv = (double *)malloc(sizeof(double) * 3 * np), *pd = (double *)malloc(sizeof(double) * 9 * np);
+        double *uv = (double *)malloc(sizeof(double) * 3 * nu), *ud = (double *)malloc(sizeof(double) * 9 * nu);
+        double *qf = (double *)malloc(sizeof(double) * 3 * nh), *gq = (double *)malloc(sizeof(double) * 3 * nh);
+        double *V = (double *)malloc(sizeof(double) * 3 * nv), *dV = (double *)malloc(sizeof(double) * 3 * nv);
+        double *pf = (double *)malloc(sizeof(double) * 3 * np), *pdum = (double *)malloc(sizeof(double) * 3 * np);
+        double *uf = (double *)malloc(sizeof(double) * 3 * nu), *udum = (double *)malloc(sizeof(double) * 3 * nu);
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t e = 0; e < n_elem; ++e) {
+            const double *ve = verts + 24 * e;
+            double *B0 = out + e * 2 * rows * cols, *B1 = B0 + rows * cols;
+            memset(B0, 0, sizeof(double) * 2 * rows * cols);
+            int bad = 0;
+            for (int l = 0; l < L && !bad; ++l)
+            for (int m = 0; m < L && !bad; ++m)
+            for (int k = 0; k < L && !bad; ++k) {
+                double xi[3] = { zeta[l], zeta[m], zeta[k] };
+                double w = wq[l] * wq[m] * wq[k];
+                double J[3][3], Ji[3][3];
+                double det = trilinear_jacobian(ve, xi, J);
+                if (!(det > 0.0) || !isfinite(det)) { bad = 1; break; }
+                inverse3(J, det, Ji);
+                shape3(OR_H1, q, 0, xi, hv, hd);
+                map_to_physical(OR_H1, nh, hv, hd, J, det, Ji, qf, gq);
+                shape3(OR_HDIV, q, 0, xi, vv, vd);
+                map_to_physical(OR_HDIV, nv, vv, vd, J, det, Ji, V, dV);
+                shape3(OR_L2, p, 0, xi, pv, pd);
+                map_to_physical(OR_L2, np, pv, pd, J, det, Ji, pf, pdum);
+                shape3(-OR_B, q, p, xi, uv, ud);
+                map_to_physical(-OR_B, nu, uv, ud, J, det, Ji, uf, udum);
+                double s = w * det;
+                for (int64_t I = 0; I < nh; ++I) {                    /* H1 test rows */
+                    const double qi = qf[3 * I], *g = gq + 3 * I;
+                    double *r0 = B0 + I * cols, *r1 = B1 + I * cols;
+                    for (int64_t K = 0; K < np; ++K) r1[K] += s * pf[3 * K] * qi;
+                    for (int64_t K = 0; K < nu; ++K) {
+                        const double *c = uf + 3 * K;
+                        r0[np + K] -= s * (c[0] * g[0] + c[1] * g[1] + c[2] * g[2]);
+                    }
+                }
+                for (int64_t I = 0; I < nv; ++I) {                    /* H(div) test rows */
+                    const double *a = V + 3 * I, dv = dV[3 * I];
+                    double *r0 = B0 + (nh + I) * cols, *r1 = B1 + (nh + I) * cols;
+                    for (int64_t K = 0; K < np; ++K) r0[K] -= s * pf[3 * K] * dv;
+                    for (int64_t K = 0; K < nu; ++K) {
+                        const double *c = uf + 3 * K;
+                        r1[np + K] += s * (c[0] * a[0] + c[1] * a[1] + c[2] * a[2]);
+                    }
+                }
+            }
+            if (bad) {
+                for (int64_t i = 0; i < 2 * rows * cols; ++i) B0[i] = NAN;
+                #pragma omp critical
+                { if (first_bad == 0 || e + 1 < first_bad) first_bad = e + 1; }
+            }
+        }
+        free(hv); free(hd); free(vv); free(vd); free(pv); free(pd); free(uv); free(ud);
+        free(qf); free(gq); free(V); free(dV); free(pf); free(pdum); free(uf); free(udum);
+    }
+    return first_bad;
+}

@@ -243,3 +243,54 @@ def affine_mixed_b(q: int, p: int, J, split: bool = False):
     if split:
         return M, K
     return [[M[i][j] + K[i][j] for j in range(len(cols))] for i in range(len(rows))]
+
+
+# ---------------------------------------------------------------- ultraweak acoustics
+
+def _dkind(kinds, d):
+    """Kinds of d/dxi_d of a tensor function (chi -> chi' in direction d)."""
+    return tuple("D" if e == d else kinds[e] for e in range(3))
+
+
+def acoustic_cross(q: int):
+    """Exact cross block of the acoustics adjoint graph norm (Eq. 3.18, coefficient of
+    i*omega) on the master cube: X[I_v][I_q] = int -(div^ v^) q^ + v^ . grad^ q^.  The
+    Piola maps cancel in both products, so this is the value on every element."""
+    rows = dofs("HDIV", q)
+    cols = dofs("H1", q)
+    X = [[Fraction(0)] * len(cols) for _ in rows]
+    for I, a, ir, ka in rows:
+        for Jd, _, jc, kq in cols:
+            X[I][Jd] = -_prod(_dkind(ka, a), ir, kq, jc) + _prod(ka, ir, _dkind(kq, a), jc)
+    return X
+
+
+def affine_acoustic_b(q: int, p: int, J):
+    """Exact ultraweak acoustics stiffness (Eq. 3.16) on an affine element with Jacobian J:
+    (B0, B1) with B0 = -(p, div v) - (u, grad q) and B1 = (p, q) + (u, v) (coefficient of
+    i*omega).  Rows: H1 test functions then H(div); columns: scalar L2 trial (order p)
+    then the three L2 components."""
+    J = [[Fraction(x) for x in row] for row in J]
+    det = det3(J)
+    Ji = inv3(J)
+    h1, hdiv = dofs("H1", q), dofs("HDIV", q)
+    pl = dofs("L2", p)
+    ul = dofs("TRIAL_L2VEC", q, p)
+    nh, npp = len(h1), len(pl)
+    rows, cols = nh + len(hdiv), npp + len(ul)
+    B0 = [[Fraction(0)] * cols for _ in range(rows)]
+    B1 = [[Fraction(0)] * cols for _ in range(rows)]
+    for I, _, ir, kq in h1:
+        for K, _, kk, kp in pl:
+            B1[I][K] = _prod(kq, ir, kp, kk)                          # (p, q): p^ q^
+        for K, cc, kk, ku in ul:
+            s = Fraction(0)
+            for d in range(3):                                        # u^ . J^-T grad^ q^
+                s += Ji[d][cc] * _prod(_dkind(kq, d), ir, ku, kk)
+            B0[I][npp + K] = -s
+    for I, a, ir, kv in hdiv:
+        for K, _, kk, kp in pl:
+            B0[nh + I][K] = -_prod(_dkind(kv, a), ir, kp, kk) / det  # p^ div^ v^ / |J|
+        for K, cc, kk, ku in ul:
+            B1[nh + I][npp + K] = J[cc][a] * _prod(kv, ir, ku, kk) / det   # u^ . J v^ / |J|
+    return B0, B1

@@ -436,3 +436,71 @@ def test_degenerate_element_flagged():
     G, bad = oracle.gram("H1", 2, 4, bad_v)
     assert bad == 3
     assert np.all(np.isnan(G[3])) and np.all(np.isfinite(G[[0, 1, 2, 4]]))
+
+
+# ------------------------------------------------------------------ ultraweak acoustics
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_acoustic_cross_exact_and_geometry_free(q):
+    """Eq. 3.18: -(div v, q) + (v, grad q) computed in physical variables equals the
+    master-cube value on every element (the H(div) and H1 Piola maps cancel), pinned
+    against exact rational 1D integrals; trilinear elements included."""
+    ex = _frac_matrix_to_float(exact.acoustic_cross(q))
+    ident = meshgen.reference_cube()
+    tri = meshgen.jittered_grid(2, seed=7, jitter=0.3)[:3]
+    X, bad = oracle.acoustic_cross(q, q + 2, np.concatenate([ident, tri]))
+    assert bad == -1
+    for e in range(X.shape[0]):
+        assert _rel_fro(X[e], ex) < 1e-13
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_acoustic_cross_boundary_form(q):
+    """div(q v) = q div v + v . grad q: with (div v_I, q_J) = sum_N Dd[N, I] (w_N, q_J) on
+    the master cube (div^ H(div) lies in L2 through the pinned Dd; the Piola maps cancel),
+    X + 2 Dd^T M = (div v, q) + (v, grad q) = <v.n, q> on the boundary, which vanishes for
+    every H(div) function with v.n = 0 there (chi_i, i >= 2, in its own direction) and not
+    for the others; M[N, J] = int w^_N q^_J exactly."""
+    v = meshgen.jittered_grid(2, seed=8, jitter=0.3)[:2]
+    X, _ = oracle.acoustic_cross(q, q + 2, v)
+    Dd = discrete_div(q)
+    lw, hq = exact.dofs("L2", q), exact.dofs("H1", q)
+    M = np.array([[float(exact._prod(kn, nn, kj, jj)) for _, _, jj, kj in hq] for _, _, nn, kn in lw])
+    bnd = X + 2.0 * (Dd.T @ M)[None]
+    scale = np.abs(bnd).max()
+    for I, a, ir, _ in exact.dofs("HDIV", q):
+        row = np.abs(bnd[:, I, :]).max()
+        if ir[a] >= 2:
+            assert row < 1e-13 * scale
+        else:
+            assert row > 1e-3 * scale
+
+
+@pytest.mark.parametrize("q,p", [(1, 1), (2, 1), (3, 2)])
+def test_affine_acoustic_b_equals_exact_rational(q, p):
+    """Eq. 3.16 on a parallelepiped with a full Jacobian: both parts (without i*omega and
+    the coefficient of i*omega) equal their exact rational values."""
+    Jf = np.array([[float(x) for x in r] for r in _J_RAT])
+    verts = meshgen.affine_from_matrix(Jf, origin=(0.25, -0.5, 0.125))
+    B, bad = oracle.acoustic_b(q, p, q + 1, verts)
+    assert bad == -1
+    B0, B1 = exact.affine_acoustic_b(q, p, _J_RAT)
+    assert _rel_fro(B[0, 0], _frac_matrix_to_float(B0)) < 1e-14
+    assert _rel_fro(B[0, 1], _frac_matrix_to_float(B1)) < 1e-14
+
+
+def test_acoustic_b_grad_block_matches_mixed_b_on_trilinear_maps():
+    """-(u, grad q_I) = -sum_K Gd[K, I] (u, psi_K) for every map (grad^ H1 lies in H(curl)
+    through Gd): the (H1, (L2)^3) block of part 0 equals -Gd^T times the mass part of the
+    (separately pinned) mixed stiffness; the (H1, L2) block of part 1 is geometry-free."""
+    q, p = 3, 2
+    v = meshgen.jittered_grid(2, seed=9, jitter=0.3)[:3]
+    B, _ = oracle.acoustic_b(q, p, q + 2, v)
+    M, _ = oracle.mixed_b(q, p, q + 2, v, split=True)
+    Gd = discrete_grad(q)
+    nh, npp = oracle.dim("H1", q), p ** 3
+    ex_qp = _frac_matrix_to_float(exact.affine_acoustic_b(q, p, [[1, 0, 0], [0, 1, 0], [0, 0, 1]])[1])[:nh, :npp]
+    for e in range(v.shape[0]):
+        assert _rel_fro(B[e, 0, :nh, npp:], -Gd.T @ M[e, 0]) < 1e-13
+        assert _rel_fro(B[e, 1, :nh, :npp], ex_qp) < 1e-13
+        assert np.abs(B[e, 0, :nh, :npp]).max() == 0.0 and np.abs(B[e, 1, nh:, :npp]).max() == 0.0
