@@ -52,6 +52,21 @@ extern "C" {
 #define DPG_B_L2VEC_HCURL  5   /* B_IK = (u_K, psi_I) + (u_K, curl psi_I), vector-L2
                                   trial u of order p, H(curl) test psi of order q
                                   (real, unit-coefficient analogue of Eqs. 3.15-3.16)   */
+/* Ultraweak acoustics (Sec. 3.3), real arithmetic with the i*omega factors kept apart.
+ * The Gram matrix of the adjoint graph norm (Eq. 3.17) of the test space H1 x H(div) is
+ *   [[ G_H1(c0 = omega^2 + alpha, c1 = 1),  -i omega X^T                           ],
+ *    [ i omega X,                            G_HDIV(c0 = omega^2 + alpha, c1 = 1)  ]]
+ * with the two diagonal blocks from DPG_H1 / DPG_HDIV with coefficients and X below. */
+#define DPG_ACOUSTIC_CROSS 6   /* X_IJ = -(div v_I, q_J) + (v_I, grad q_J) (Eq. 3.18, the
+                                  coefficient of i omega): rows the H(div) test functions,
+                                  columns the H1 test functions, both of order q      */
+#define DPG_ACOUSTIC_B     7   /* stiffness of Eq. 3.16, test (q, v) in H1 x H(div) of order
+                                  q (rows: H1 then H(div)), trial (p, u) in L2 x (L2)^3 of
+                                  order p_trial (columns: scalar then three components);
+                                  output [2][rows][cols]: part 0 = -(p, div v) - (u, grad q),
+                                  part 1 = (p, q) + (u, v), the coefficient of i omega;
+                                  the blocks a part does not contain are written as
+                                  zeros (also for an element reported degenerate) */
 /* ---- flags ORed into `space` ---- */
 /* DPG_FP32: geometry and metric fields computed in FP64, then rounded to FP32; the
  * contraction stages run in FP32 (stage A on the FMA pipe; stages B and C of the general
@@ -98,28 +113,30 @@ int dpg_tables_init_L(int q, int L, int space);
 int dpg_tables_free(void);
 
 /* Number of rows of the element matrix: dim of the test space at order q
- * ((q+1)^3, 3q(q+1)^2, 3(q+1)q^2, q^3 for H1, H(curl), H(div), L2; H(curl) for B).
+ * ((q+1)^3, 3q(q+1)^2, 3(q+1)q^2, q^3 for H1, H(curl), H(div), L2; H(curl) for B;
+ * H(div) for DPG_ACOUSTIC_CROSS; H1 + H(div) for DPG_ACOUSTIC_B).
  * Returns -1 for a bad space or q. */
 int64_t dpg_matrix_rows(int space, int q);
 
-/* Number of columns: equal to rows for Gram matrices; 3 p^3 for DPG_B_L2VEC_HCURL.
- * Returns -1 for bad arguments. */
+/* Number of columns: equal to rows for Gram matrices; 3 p^3 for DPG_B_L2VEC_HCURL;
+ * (q+1)^3 for DPG_ACOUSTIC_CROSS; 4 p^3 for DPG_ACOUSTIC_B.  Returns -1 for bad arguments. */
 int64_t dpg_matrix_cols(int space, int p_trial, int q);
 
 /* Integrate the element matrices of n_elem elements (the paper's per-element routine
  * PROC(mid, G) of Algorithms 2-11, batched; problem statement Eq. 2.13).
  *   space    : DPG_H1 .. DPG_B_L2VEC_HCURL, ORed with DPG_FP32 / DPG_MAP_AFFINE /
  *              DPG_B_SPLIT (B only).
- *   p_trial  : trial order for DPG_B_L2VEC_HCURL (1 <= p_trial <= q_test); ignored
- *              (pass 0) for Gram matrices.
+ *   p_trial  : trial order for DPG_B_L2VEC_HCURL and DPG_ACOUSTIC_B
+ *              (1 <= p_trial <= q_test); ignored (pass 0) otherwise.
  *   q_test   : test order; tables for (space, q_test) must be initialised.
  *   n_elem   : number of elements (0 is allowed and does nothing).
  *   vertices : device, double[n_elem][8][3].
  *   coeffs   : device, double[n_elem][2] = (mass weight c0, derivative weight c1), or
  *              NULL for (1, 1).  G = c0 (mass term) + c1 (derivative term); L2 uses c0.
- *              Ignored for B.
+ *              Ignored for the non-Gram spaces (B, acoustics cross block and stiffness).
  *   out      : device, double (FP64 form) or float (DPG_FP32) array of
- *              n_elem * parts * rows * cols values, parts = 2 with DPG_B_SPLIT else 1.
+ *              n_elem * parts * rows * cols values, parts = 2 with DPG_B_SPLIT and for
+ *              DPG_ACOUSTIC_B, else 1.
  *   stream   : cudaStream_t.
  * The call allocates a stream-ordered workspace for the per-point metric fields from a
  * library memory pool and frees it in stream order.

@@ -19,8 +19,10 @@ LIB_PATH = os.path.join(HERE, "_build", "libdpg.so")
 
 # spaces and flags (include/dpg.h)
 DPG_H1, DPG_HCURL, DPG_HDIV, DPG_L2, DPG_B_L2VEC_HCURL = 1, 2, 3, 4, 5
+DPG_ACOUSTIC_CROSS, DPG_ACOUSTIC_B = 6, 7
 DPG_FP32, DPG_MAP_AFFINE, DPG_B_SPLIT = 0x100, 0x200, 0x400
-SPACE_IDS = {"H1": DPG_H1, "HCURL": DPG_HCURL, "HDIV": DPG_HDIV, "L2": DPG_L2, "B": DPG_B_L2VEC_HCURL}
+SPACE_IDS = {"H1": DPG_H1, "HCURL": DPG_HCURL, "HDIV": DPG_HDIV, "L2": DPG_L2, "B": DPG_B_L2VEC_HCURL,
+             "ACOUSTIC_CROSS": DPG_ACOUSTIC_CROSS, "ACOUSTIC_B": DPG_ACOUSTIC_B}
 STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANGE", 4: "DPG_ERR_CUDA",
           5: "DPG_ERR_DEGENERATE", 6: "DPG_ERR_NOT_AFFINE", 7: "DPG_ERR_NOMEM", 8: "DPG_ERR_SCRATCH"}
 
@@ -214,9 +216,12 @@ def _stream_handle(stream=None) -> int:
 
 
 def matrix_shape(space, q: int, p: int = 0, split: bool = False) -> tuple[int, ...]:
+    """Per-element output shape: (rows, cols), or (2, rows, cols) for split B and for the
+    acoustics stiffness (part 0 and the coefficient of i*omega)."""
     r = dpg_matrix_rows(space, q)
     c = dpg_matrix_cols(space, p, q)
-    return (2, r, c) if split else (r, c)
+    two = split or (space_id(space) & 0xff) == DPG_ACOUSTIC_B
+    return (2, r, c) if two else (r, c)
 
 
 def integrate(space, q: int, verts, coeffs=None, *, p: int = 0, fp32: bool = False, affine: bool = False,

@@ -305,7 +305,7 @@ void free_device_state(DeviceState &ds) {
 bool valid_space(int space) {
     const int base = space & 0xff;
     const int flags = space & ~0xff;
-    if (base < S_H1 || base > S_B) return false;
+    if (base < S_H1 || base > S_AB) return false;
     if (flags & ~(DPG_FP32 | DPG_MAP_AFFINE | DPG_B_SPLIT)) return false;
     if ((flags & DPG_B_SPLIT) && base != S_B) return false;
     return true;
@@ -317,7 +317,7 @@ int resolve(int space, int p_trial, int q, ProgEntry **pe, TableEntry **te, Devi
     if (q < 1 || q > DPG_MAX_Q) return DPG_ERR_RANGE;
     const int base = space & 0xff;
     int p = 0, split = 0;
-    if (base == S_B) {
+    if (base == S_B || base == S_AB) {
         if (p_trial < 1 || p_trial > q) return DPG_ERR_ARG;
         p = p_trial;
         split = (space & DPG_B_SPLIT) ? 1 : 0;
@@ -466,7 +466,7 @@ int integrate_locked(int space, int p_trial, int q_test, int64_t n_elem, const d
     if (n_elem == 0) return DPG_OK;
     if (!vertices || !out) return DPG_ERR_ARG;
     const bool fp32 = (space & DPG_FP32) != 0, affine = (space & DPG_MAP_AFFINE) != 0;
-    const bool use_coeffs = (space & 0xff) != S_B ? true : false;
+    const bool use_coeffs = (space & 0xff) <= S_L2;            // Gram matrices only
     const double *c = use_coeffs ? coeffs : nullptr;
     if (affine) {
         return fp32 ? run_affine<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
@@ -555,7 +555,7 @@ int dpg::lookup_program_view(int space, int p_trial, int q, ProgramView *view) {
     if (q < 1 || q > DPG_MAX_Q) return DPG_ERR_RANGE;
     const int base = space & 0xff;
     int p = 0, split = 0;
-    if (base == S_B) {
+    if (base == S_B || base == S_AB) {
         if (p_trial < 1 || p_trial > q) return DPG_ERR_ARG;
         p = p_trial;
         split = (space & DPG_B_SPLIT) ? 1 : 0;
@@ -587,7 +587,7 @@ extern "C" {
 
 int dpg_tables_init_L(int q, int L, int space) {
     const int base = space & 0xff;
-    if (base < S_H1 || base > S_B) return DPG_ERR_ARG;
+    if (base < S_H1 || base > S_AB) return DPG_ERR_ARG;
     if (q < 1 || q > DPG_MAX_Q || L < 1 || L > DPG_MAX_L) return DPG_ERR_RANGE;
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceState *ds = nullptr;
@@ -596,15 +596,15 @@ int dpg_tables_init_L(int q, int L, int space) {
     TableEntry *te = nullptr;
     if ((r = get_tables(ds, q, L, &te))) return r;
     ProgEntry *pe = nullptr;
-    if (base == S_B) {
+    if (base == S_B || base == S_AB) {
         for (int p = 1; p <= q; ++p)
-            for (int split = 0; split < 2; ++split)
+            for (int split = 0; split < (base == S_B ? 2 : 1); ++split)
                 if ((r = get_program(ds, base, q, L, p, split, te->host, &pe))) return r;
     } else {
         if ((r = get_program(ds, base, q, L, 0, 0, te->host, &pe))) return r;
     }
     ds->active_L[std::make_pair(base, q)] = L;
-    if (base != S_B && (r = update_hp_table(ds, base, q, pe, te))) return r;
+    if (base <= S_L2 && (r = update_hp_table(ds, base, q, pe, te))) return r;
     return DPG_OK;
 }
 

@@ -36,10 +36,11 @@ constexpr int MAXT = 12;                      // terms per block (H1 has 10)
 constexpr int MAXH = 10;                      // (dir1, dir2)-pair groups per block
 constexpr int MAXG = 4;                       // dir1-pair groups per block
 constexpr int MAXP2 = 9;                      // distinct dir2 pairs per block
-constexpr int MAXBLK = 18;                    // B split: 9 blocks x 2 parts
+constexpr int MAXBLK = 32;                    // acoustics B: 16 blocks x 2 parts
 constexpr int NJMAX = 8;                      // j3 values per work unit
 
-enum SpaceId : int { S_H1 = 1, S_HCURL = 2, S_HDIV = 3, S_L2 = 4, S_B = 5 };
+enum SpaceId : int { S_H1 = 1, S_HCURL = 2, S_HDIV = 3, S_L2 = 4, S_B = 5, S_AX = 6, S_AB = 7 };
+constexpr int MAXFIELDS = 20;                 // metric fields per point (acoustics B)
 
 struct TermDesc {
     int field;        // index of the per-point metric field
@@ -180,6 +181,9 @@ struct DevTables {
 //   HDIV : 0..5: c0 C_ab w / |J|,  6: c1 w / |J|
 //   HCURL: 0..5: c0 D_ab |J| w,  6..11: c1 C_ab w / |J|
 //   B    : 0..8: (J^-1)_ac w (index 3a + c),  9..17: J_cd w / |J| (index 9 + 3c + d)
+//   AX   : 0: w   (acoustics cross block: the Piola maps cancel, Eq. 3.18)
+//   AB   : 0: w,  1..9: (J^-1)_dc w (index 1 + 3d + c),  10: w / |J|,
+//          11..19: J_ca w / |J| (index 11 + 3c + a)   (acoustics stiffness, Eq. 3.16)
 // with D = J^-1 J^-T (Eq. 2.32) and C = J^T J (Eq. 2.50).
 DPG_HD inline int sym_index(int a, int b) {
     if (a == b) return a;
@@ -193,6 +197,8 @@ inline int nfields_of(int space) {
     case S_HDIV: return 7;
     case S_HCURL: return 12;
     case S_B: return 18;
+    case S_AX: return 1;
+    case S_AB: return 20;
     }
     return 0;
 }

@@ -131,6 +131,21 @@ __device__ __forceinline__ int metric_fields(int space, const Jac &g, double wt,
             }
         return 18;
     }
+    case S_AX:                                   // Eq. 3.18: the Piola maps cancel
+        f[0] = wt;
+        return 1;
+    case S_AB: {                                 // Eq. 3.16
+        f[0] = wt;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                f[1 + 3 * d + c] = g.Ji[d][c] * wt;
+                f[11 + 3 * d + c] = g.J[d][c] * wt * idet;
+            }
+        f[10] = wt * idet;
+        return 20;
+    }
     }
     return 0;
 }
@@ -149,7 +164,7 @@ __global__ void __launch_bounds__(256) geom_kernel(GeomParams p) {
     finish_jac(g);
     const double c0 = p.coeffs ? p.coeffs[2 * e] : 1.0;
     const double c1 = p.coeffs ? p.coeffs[2 * e + 1] : 1.0;
-    double f[18];
+    double f[MAXFIELDS];
     const int nf = metric_fields(p.space, g, wt, c0, c1, f);
     TF *dst = reinterpret_cast<TF *>(p.fields) + (e * p.nfields) * L3 + pt;
     const bool bad = !(g.det > 0.0) || !isfinite(g.det);
@@ -968,7 +983,7 @@ __global__ void __launch_bounds__(128) affine_const_kernel(AffConstParams p) {
     if (f == 0 && (!(g.det > 0.0) || !isfinite(g.det))) f = 5; /*DPG_ERR_DEGENERATE*/
     const double c0 = p.coeffs ? p.coeffs[2 * e] : 1.0;
     const double c1 = p.coeffs ? p.coeffs[2 * e + 1] : 1.0;
-    double fv[18];
+    double fv[MAXFIELDS];
     const int nf = metric_fields(p.space, g, 1.0, c0, c1, fv);
     double *dst = p.consts + AFF_CONST_STRIDE * e;
     for (int k = 0; k < nf; ++k) dst[k] = fv[k];
@@ -994,10 +1009,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockDesc bd;
-    __shared__ T cf[18];
+    __shared__ T cf[MAXFIELDS];
     __shared__ int flag;
     __shared__ T st[MAXT * NJMAX];             // s_t = sign_t c_t F3_t(i3, j3) of the current unit
     __shared__ int f1c[MAXG], qc[MAXG];        // non-zero counts per group
+    __shared__ signed char gt[MAXG][MAXT];     // terms of each group
+    __shared__ int gtn[MAXG];
     const int tid = threadIdx.x, nth = blockDim.x;
     // CTA = (element, block, share of the block's units): the block's tables are built once
     const int nsplit = p.nsplit;
@@ -1006,10 +1023,18 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     const int64_t e = blockIdx.x / (p.nblock * nsplit);
     if (e >= p.n_elem) return;
     load_block(p.blocks + k, bd);
-    if (tid < 18) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
-    if (tid == 18) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
+    if (tid < MAXFIELDS) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
+    if (tid == MAXFIELDS) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
     if (tid < MAXG) f1c[tid] = 0;
     __syncthreads();
+    if (tid == 0) {
+        for (int g = 0; g < bd.ng; ++g) {
+            int n = 0;
+            for (int t = 0; t < bd.nterm; ++t)
+                if (bd.h_g[bd.term[t].h] == g) gt[g][n++] = (signed char)t;
+            gtn[g] = n;
+        }
+    }
 
     const int nr1 = bd.nr[0], nr2 = bd.nr[1], nc1 = bd.nc[0], nc2 = bd.nc[1];
     const int ng = bd.ng, nterm = bd.nterm, njm = p.nj_max;
@@ -1029,8 +1054,9 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     const unsigned mnc1 = div_magic(nc1), mnc2 = div_magic(nc2), mn22 = div_magic(n22);
 
     // stage-C factors: compact non-zero lists per group
+    const unsigned mn11 = div_magic(n11), mn22t = div_magic(n22);
     for (int it = tid; it < ng * n11; it += nth) {
-        const int g = it / n11, ij = it - g * n11;
+        const int g = fdiv(it, mn11), ij = it - g * n11;
         const int i1 = fdiv(ij, mnc1), j1 = ij - i1 * nc1;
         const T v = Fv(bd.g_pair[g], i1, j1);
         if (!is_zero(v)) {
@@ -1040,7 +1066,7 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         }
     }
     for (int it = tid; it < nterm * n22; it += nth) {                   // F2_t(i2, j2)
-        const int t = it / n22, ij = it - t * n22;
+        const int t = fdiv(it, mn22t), ij = it - t * n22;
         const TermDesc &td = bd.term[t];
         const int i2 = fdiv(ij, mnc2);
         F2[it] = Fv(3 * td.kr[1] + td.kc[1], i2, ij - i2 * nc2);
@@ -1064,7 +1090,12 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             st[it] = is_zero(f3) ? T(0) : (td.sign > 0 ? cf[td.field] : -cf[td.field]) * f3;
         }
         if (tid < MAXG) qc[tid] = 0;
-        for (int it = tid; it < nrow * ldt; it += nth) tile[it] = T(0);
+        {
+            float4 *t4 = reinterpret_cast<float4 *>(tile);            // tile is 16-byte aligned
+            const int n4 = (int)((nrow * ldt * sizeof(T)) / 16);
+            for (int it = tid; it < n4; it += nth) t4[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int it = n4 * (16 / (int)sizeof(T)) + tid; it < nrow * ldt; it += nth) tile[it] = T(0);
+        }
         __syncthreads();
         // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2), kept as a list of its non-zeros
         for (int it = tid; it < ng * n22 * nj; it += nth) {
@@ -1072,8 +1103,9 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             const int g = fdiv(r, mn22), ij2 = r - g * n22;
             T acc = T(0);
             bool any = false;
-            for (int t = 0; t < nterm; ++t) {
-                if (bd.h_g[bd.term[t].h] != g) continue;
+            const int ngt = gtn[g];
+            for (int k2 = 0; k2 < ngt; ++k2) {
+                const int t = gt[g][k2];
                 const T sv = st[t * nj + jj];
                 if (is_zero(sv)) continue;
                 const T f2 = F2[t * n22 + ij2];
@@ -1284,7 +1316,7 @@ __global__ void __launch_bounds__(256) hp_geom_kernel(HpParams p) {
         Jac jg;
         trilinear_jac(p.verts + 24 * e, g.zeta[l], g.zeta[m], g.zeta[n], jg);
         finish_jac(jg);
-        double f[18];
+        double f[MAXFIELDS];
         const int nf = metric_fields(p.space, jg, g.w[l] * g.w[m] * g.w[n], c0, c1, f);
         const bool bad = !(jg.det > 0.0) || !isfinite(jg.det);
         if (bad) report(p.status, 5 /*DPG_ERR_DEGENERATE*/, e);

@@ -39,9 +39,9 @@ struct SfParams {
     int64_t n_elem;
 };
 
-// Per-element constants of the affine path: 18 metric fields and the element's status
-// code in the last slot.
-constexpr int AFF_CONST_STRIDE = 20;
+// Per-element constants of the affine path: up to MAXFIELDS metric fields and the
+// element's status code in the last slot.
+constexpr int AFF_CONST_STRIDE = 24;
 
 struct AffConstParams {
     int space;

@@ -79,7 +79,7 @@ extern "C" int dpg_integrate_noalloc(int space, int p_trial, int q_test, int64_t
     if ((int64_t)v.prog->units.size() * n_elem > INT_MAX) return DPG_ERR_SCRATCH;
     void *ws = nullptr;
     if ((r = scratch_address(&ws))) return r;
-    const double *c = (space & 0xff) == DPG_B_L2VEC_HCURL ? nullptr : coeffs;
+    const double *c = (space & 0xff) > DPG_L2 ? nullptr : coeffs;          // Gram matrices only
     cudaStream_t s = (cudaStream_t)stream;
     return fp32 ? run<float>(v, n_elem, vertices, c, (float *)out, ws, s)
                 : run<double>(v, n_elem, vertices, c, (double *)out, ws, s);

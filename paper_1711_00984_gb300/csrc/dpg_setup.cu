@@ -119,12 +119,22 @@ HostTables make_tables(int q, int L) {
 struct CompLayout { int n[3]; int kind[3]; int offset; };
 
 // Component layouts (Eqs. 2.17, 2.33, 2.52-2.53, 2.70-2.71).
-static int layout(int space, int q, int p, CompLayout c[3]) {
+static int layout(int space, int q, int p, CompLayout c[4]) {
     if (space == S_H1) { c[0] = { { q + 1, q + 1, q + 1 }, { KW, KW, KW }, 0 }; return 1; }
     if (space == S_L2) { c[0] = { { q, q, q }, { KY, KY, KY }, 0 }; return 1; }
     if (space == -S_B) {           // vector-L2 trial of order p
         for (int k = 0; k < 3; ++k) c[k] = { { p, p, p }, { KY, KY, KY }, k * p * p * p };
         return 3;
+    }
+    if (space == -S_AB) {          // acoustics trial: scalar L2 then vector L2, order p
+        for (int k = 0; k < 4; ++k) c[k] = { { p, p, p }, { KY, KY, KY }, k * p * p * p };
+        return 4;
+    }
+    if (space == S_AB) {           // acoustics test: H1 then H(div), order q
+        c[0] = { { q + 1, q + 1, q + 1 }, { KW, KW, KW }, 0 };
+        layout(S_HDIV, q, 0, c + 1);
+        for (int k = 1; k < 4; ++k) c[k].offset += (q + 1) * (q + 1) * (q + 1);
+        return 4;
     }
     int off = 0;
     for (int a = 0; a < 3; ++a) {
@@ -140,7 +150,7 @@ static int layout(int space, int q, int p, CompLayout c[3]) {
 }
 
 static int dim_of(int space, int q, int p) {
-    CompLayout c[3];
+    CompLayout c[4];
     int nc = layout(space, q, p, c);
     int n = 0;
     for (int k = 0; k < nc; ++k) n += c[k].n[0] * c[k].n[1] * c[k].n[2];
@@ -150,15 +160,18 @@ static int dim_of(int space, int q, int p) {
 int64_t rows_of(int space, int q) {
     if (q < 1 || q > MAXQ) return -1;
     if (space == S_B) return dim_of(S_HCURL, q, 0);
+    if (space == S_AX) return dim_of(S_HDIV, q, 0);
+    if (space == S_AB) return dim_of(S_AB, q, 0);
     if (space < S_H1 || space > S_L2) return -1;
     return dim_of(space, q, 0);
 }
 
 int64_t cols_of(int space, int p, int q) {
-    if (space == S_B) {
-        if (p < 1 || p > q || q > MAXQ) return -1;
-        return 3LL * p * p * p;
+    if (space == S_B || space == S_AB) {
+        if (p < 1 || p > q || q < 1 || q > MAXQ) return -1;
+        return (space == S_B ? 3LL : 4LL) * p * p * p;
     }
+    if (space == S_AX) return rows_of(S_H1, q);
     return rows_of(space, q);
 }
 
@@ -239,17 +252,19 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     pr.space = space; pr.q = q; pr.L = L; pr.p = p; pr.split = split;
     pr.rows = (int)rows_of(space, q);
     pr.cols = (int)cols_of(space, p, q);
-    pr.parts = (space == S_B && split) ? 2 : 1;
+    pr.parts = ((space == S_B && split) || space == S_AB) ? 2 : 1;
     pr.nfields = nfields_of(space);
     pr.nblock = 0;
 
-    CompLayout R[3], C[3];
-    int nR = layout(space == S_B ? S_HCURL : space, q, 0, R);
-    int nC = space == S_B ? layout(-S_B, q, p, C) : layout(space, q, 0, C);
+    CompLayout R[4], C[4];
+    const int rspace = space == S_B ? S_HCURL : (space == S_AX ? S_HDIV : space);
+    const int cspace = space == S_B ? -S_B : (space == S_AX ? S_H1 : (space == S_AB ? -S_AB : space));
+    int nR = layout(rspace, q, 0, R);
+    int nC = layout(cspace, q, p, C);
 
     for (int a = 0; a < nR; ++a)
     for (int b = 0; b < nC; ++b) {
-        bool symmetric = space != S_B && order != ORDER_PANEL;
+        bool symmetric = space <= S_L2 && order != ORDER_PANEL;
         if (symmetric && b < a) continue;             // lower blocks come from mirroring
         for (int part = 0; part < pr.parts; ++part) {
             std::vector<TermSpec> ts;
@@ -288,6 +303,36 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
                 for (int al = 0; al < 2; ++al)
                 for (int be = 0; be < 2; ++be)
                     add(6 + sym_index(ca[al], cb[be]), sa[al] * sb[be], kra[al], krb[be]);
+                break;
+            }
+            case S_AX: {                               // Eq. 3.18: -div^v^ q^ + v^ . grad^ q^
+                int kr[3], kc[3];
+                for (int d = 0; d < 3; ++d) { kr[d] = d == a ? KD : ka[d]; kc[d] = kb[d]; }
+                add(0, -1, kr, kc);
+                for (int d = 0; d < 3; ++d) { kr[d] = ka[d]; kc[d] = d == a ? KD : kb[d]; }
+                add(0, 1, kr, kc);
+                break;
+            }
+            case S_AB: {                               // Eq. 3.16, part 0 / part 1 (i omega)
+                // rows: a = 0 the H1 test, a = 1..3 H(div) component a-1;
+                // columns: b = 0 the scalar L2 trial, b = 1..3 vector component b-1
+                const int ra = a - 1, cb = b - 1;
+                int kr[3];
+                if (a == 0 && b == 0) { if (part == 1) add(0, 1, ka, kb); }          // (p, q)
+                else if (a == 0) {                                                  // -(u, grad q)
+                    if (part == 0)
+                        for (int d = 0; d < 3; ++d) {
+                            for (int e = 0; e < 3; ++e) kr[e] = e == d ? KD : ka[e];
+                            add(1 + 3 * d + cb, -1, kr, kb);
+                        }
+                } else if (b == 0) {                                                // -(p, div v)
+                    if (part == 0) {
+                        for (int e = 0; e < 3; ++e) kr[e] = e == ra ? KD : ka[e];
+                        add(10, -1, kr, kb);
+                    }
+                } else if (part == 1) {                                             // (u, v)
+                    add(11 + 3 * cb + ra, 1, ka, kb);
+                }
                 break;
             }
             case S_B: {                                // u^.J^-T psi^ + u^.J curl^psi^ / |J|

@@ -49,6 +49,13 @@ def test_matrix_sizes(lib, q):
         assert dpg.dpg_matrix_cols("B", p, q) == 3 * p ** 3
     assert dpg.dpg_matrix_cols("B", q + 1, q) == -1
     assert dpg.dpg_matrix_rows("B", q) == 3 * q * (q + 1) ** 2
+    # ultraweak acoustics: cross block H(div) x H1, stiffness (H1 + H(div)) x 4 p^3
+    assert dpg.dpg_matrix_rows("ACOUSTIC_CROSS", q) == oracle.dim("HDIV", q)
+    assert dpg.dpg_matrix_cols("ACOUSTIC_CROSS", 0, q) == oracle.dim("H1", q)
+    assert dpg.dpg_matrix_rows("ACOUSTIC_B", q) == oracle.dim("H1", q) + oracle.dim("HDIV", q)
+    for p in range(1, q + 1):
+        assert dpg.dpg_matrix_cols("ACOUSTIC_B", p, q) == 4 * p ** 3
+    assert dpg.dpg_matrix_cols("ACOUSTIC_B", q + 1, q) == -1
 
 
 def test_bad_arguments_rejected_on_host(lib):
