@@ -365,10 +365,21 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ultraweak acoustics (Sec. 3.3): the adjoint graph norm's diagonal blocks are H1 and H(div)
+# Gram matrices with coefficients (omega^2 + alpha, 1) (Eq. 3.17); omega = 4 pi, alpha = 1
+ACOUSTIC_OMEGA, ACOUSTIC_ALPHA = 4.0 * 3.141592653589793, 1.0
+_AC = (ACOUSTIC_OMEGA ** 2 + ACOUSTIC_ALPHA, 1.0)
+
 SECONDARY = {
-    # name: (meshgen workload, q, L, [(space, p_trial, affine)])
-    "hcurl_q6_p4_16x16x16": ("hcurl_q6_p4_16x16x16", 6, 8, [("HCURL", 0, False), ("B", 4, False)]),
-    "q9_8x8x4": ("q9_8x8x4", 9, 11, [("H1", 0, False), ("HDIV", 0, False), ("H1", 0, True), ("HDIV", 0, True)]),
+    # name: (meshgen workload, q, L, [(space, p_trial, affine, coefficients or None)])
+    "hcurl_q6_p4_16x16x16": ("hcurl_q6_p4_16x16x16", 6, 8, [("HCURL", 0, False, None), ("B", 4, False, None)]),
+    "q9_8x8x4": ("q9_8x8x4", 9, 11, [("H1", 0, False, None), ("HDIV", 0, False, None),
+                                     ("H1", 0, True, None), ("HDIV", 0, True, None)]),
+    # the full element routine of the ultraweak acoustics formulation at the paper's
+    # p0 = 4, p_r = 6 (Table 5) on the 16^3 jittered mesh: Gram blocks, cross block, stiffness
+    "acoustics_q6_p4_16x16x16": ("hcurl_q6_p4_16x16x16", 6, 8,
+                                 [("H1", 0, False, _AC), ("HDIV", 0, False, _AC),
+                                  ("ACOUSTIC_CROSS", 0, False, None), ("ACOUSTIC_B", 4, False, None)]),
 }
 
 
@@ -396,11 +407,15 @@ def run_secondary(args):
     except Exception:
         pass
     rec = {"workload": wname, "q": q, "L": L, "calls": []}
-    for space, p, aff in calls:
+    for space, p, aff, cf in calls:
         dpg.dpg_tables_init_L(q, L, space)
         v = torch.from_numpy(w["verts_affine" if aff else "verts"]).to(dev)
         ne = v.shape[0]
+        ct = None if cf is None else torch.tensor([list(cf)] * ne, dtype=torch.float64, device=dev)
+        cptr = 0 if ct is None else ct.data_ptr()
         res = {"space": space, "p_trial": p, "map": "affine" if aff else "general", "elements": ne}
+        if cf is not None:
+            res["coeffs"] = list(cf)
         outs = {}
         for fp32 in (False, True):
             sid = dpg.space_id(space, fp32=fp32, affine=aff)
@@ -408,7 +423,7 @@ def run_secondary(args):
             out = torch.empty(shape, dtype=torch.float32 if fp32 else torch.float64, device=dev)
 
             def call():
-                code = dpg.dpg_integrate(sid, p, q, ne, v.data_ptr(), 0, out.data_ptr(), sh)
+                code = dpg.dpg_integrate(sid, p, q, ne, v.data_ptr(), cptr, out.data_ptr(), sh)
                 if code:
                     raise dpg.DpgError(code, "dpg_integrate")
             for _ in range(args.warmup):
@@ -443,7 +458,36 @@ def run_secondary(args):
         del outs
         torch.cuda.empty_cache()
     rec["measured_alu_peaks_tflops"] = {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12}
+    if args.workload.startswith("acoustics"):
+        ne = rec["calls"][0]["elements"]
+        tot64 = sum(c["fp64"]["ms"] for c in rec["calls"])
+        tot32 = sum(c["fp32"]["ms"] for c in rec["calls"])
+        rec["element_routine"] = {
+            "calls": [c["space"] for c in rec["calls"]], "omega": ACOUSTIC_OMEGA, "alpha": ACOUSTIC_ALPHA,
+            "fp64_ms": tot64, "fp32_ms": tot32, "fp64_s_per_element": tot64 * 1e-3 / ne,
+            "fp32_s_per_element": tot32 * 1e-3 / ne,
+            "paper_table5_context": {"p0": 4, "p_r": 6, "tensorization_s_per_element": 8.08e-2,
+                                     "conventional_s_per_element": 1.900,
+                                     "note": "G, B and l on the paper's CPU; here the G blocks, X and B (no load vector)"}}
+        if not args.no_cpu:
+            rec["element_routine"]["cpu_baseline"] = _acoustics_oracle_rate(w["verts"], q, L)
     print(json.dumps(rec), flush=True)
+
+
+def _acoustics_oracle_rate(verts, q, L):
+    """The oracle's rate for the same four calls on a bounded sample (2 elements)."""
+    import numpy as np
+    import oracle
+    sample = np.ascontiguousarray(verts[:2])
+    c = np.tile(np.array(_AC), (2, 1))
+    t0 = time.perf_counter()
+    oracle.gram("H1", q, L, sample, c)
+    oracle.gram("HDIV", q, L, sample, c)
+    oracle.acoustic_cross(q, L, sample)
+    oracle.acoustic_b(q, 4, L, sample)
+    dt = time.perf_counter() - t0
+    return {"value": sample.shape[0] / dt, "unit": "element routines/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": "2 elements of the workload, the four calls"}
 
 
 def run_hp(args):
