@@ -88,8 +88,11 @@ typedef enum {
     DPG_ERR_DEGENERATE = 5,  /* device: |J| <= 0 or not finite at a quadrature point    */
     DPG_ERR_NOT_AFFINE = 6,  /* device: element is not a parallelepiped (affine path)   */
     DPG_ERR_NOMEM = 7,       /* device or host allocation failed                        */
-    DPG_ERR_SCRATCH = 8      /* dpg_integrate_noalloc: the call needs more metric-field
+    DPG_ERR_SCRATCH = 8,     /* dpg_integrate_noalloc: the call needs more metric-field
                                 scratch than DPG_NOALLOC_SCRATCH_BYTES                  */
+    DPG_ERR_TIMEOUT = 9      /* device: a bounded wait of the FP32 tensor-core kernel for
+                                its own MMAs ran out; the CTA stopped, the matrices of the
+                                call are not valid (first_bad = first element of the CTA) */
 } dpg_status;
 
 #define DPG_MAX_Q 12           /* supported test orders: 1 <= q <= DPG_MAX_Q           */

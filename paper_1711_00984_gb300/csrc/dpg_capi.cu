@@ -24,7 +24,9 @@ using namespace dpg;
 namespace {
 
 constexpr size_t kWorkspaceLimit = size_t(512) << 20;   // metric fields per launch chunk
+enum { K32_MIRROR = 0, K32_PANEL = 1, K32_TC = 2 };      // FP32 general-path kernels
 int g_max_dyn_smem = 0;                                  // per launch, set at device set-up
+int g_max_dyn_smem_tc = 0;                               // the same for the tensor-core kernel
 int g_num_sms = 152;                                     // set at device set-up
 
 struct TableEntry {
@@ -49,11 +51,12 @@ struct ProgEntry {
     // SM), [1] FP32 kernel (the larger chunk that fits two)
     AffProg aff[2];
     double flops_aff = 0.0;         // algorithmic flops of the affine path
-    Program prog32;                 // FP32 general path: row-panel program (panel32) or
-                                    // the mirrored-tile program with stage A on xi_3
-    bool panel32 = false;
-    float *d_ctab32 = nullptr;      // panel32: constant operands of every block
-    int *d_ctab_off32 = nullptr;    // panel32: [nblock] offsets into d_ctab32
+    Program prog32;                 // FP32 general path: tensor-core program (kind32 = K32_TC),
+                                    // row-panel program (K32_PANEL) or the mirrored-tile
+                                    // program with stage A on xi_3 (K32_MIRROR)
+    int kind32 = 0;
+    float *d_ctab32 = nullptr;      // K32_TC / K32_PANEL: constant operands of every block
+    int *d_ctab_off32 = nullptr;    // [nblock] offsets into d_ctab32
     BlockDesc *d_blocks32 = nullptr;
     Unit *d_units32 = nullptr;
     int max_nc1_32 = 0;             // largest stage-C column extent of prog32
@@ -116,7 +119,7 @@ int upload(const T *src, size_t n, T **dst) {
 
 void reset_host_status(DevStatus &s) {
     std::memset(&s, 0, sizeof(s));
-    for (int i = 0; i < 8; ++i) s.first_bad[i] = ULLONG_MAX;
+    for (int i = 0; i < 16; ++i) s.first_bad[i] = ULLONG_MAX;
 }
 
 int device_state(DeviceState **out) {
@@ -141,6 +144,8 @@ int device_state(DeviceState **out) {
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CK(init_kernel_attributes(optin));
     g_max_dyn_smem = max_dynamic_smem(optin);
+    CK(init_tc_attributes(optin));
+    g_max_dyn_smem_tc = optin - tc_static_smem();
     CK(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
     for (auto &cs : st->copy_streams) CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -170,12 +175,20 @@ int get_tables(DeviceState *ds, int q, int L, TableEntry **out) {
 }
 
 // Build and upload the FP32 general-path program of pe with stage-A chunk nj (0: largest
-// that fits): the row-panel program where its shared memory fits a CTA, else the
-// mirrored-tile program.  The previous device copies are freed (the caller synchronises).
+// that fits): the tensor-core program where every block fits the tcgen05 kernel, else the
+// row-panel program where its shared memory fits a CTA, else the mirrored-tile program.
+// The previous device copies are freed (the caller synchronises).
 int setup_prog32(ProgEntry *pe, int space, int q, int L, int p, bool split, const HostTables &tab, int nj) {
-    Program np = make_program(space, q, L, p, split, tab, ORDER_PANEL, nj);
-    const bool panel = np.smem_bytes <= (size_t)g_max_dyn_smem;
-    if (!panel) np = make_program(space, q, L, p, split, tab, ORDER_A3, nj);
+    int kind = K32_TC;
+    Program np = make_program(space, q, L, p, split, tab, ORDER_TC, nj, (size_t)g_max_dyn_smem_tc);
+    if (np.smem_bytes > (size_t)g_max_dyn_smem_tc) {
+        kind = K32_PANEL;
+        np = make_program(space, q, L, p, split, tab, ORDER_PANEL, nj);
+        if (np.smem_bytes > (size_t)g_max_dyn_smem) {
+            kind = K32_MIRROR;
+            np = make_program(space, q, L, p, split, tab, ORDER_A3, nj);
+        }
+    }
     if (np.smem_bytes > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     BlockDesc *db = nullptr;
     Unit *du = nullptr;
@@ -188,10 +201,11 @@ int setup_prog32(ProgEntry *pe, int space, int q, int L, int p, bool split, cons
     for (const Unit &u : np.units) ub[u.block + 1]++;
     for (int k = 0; k < np.nblock; ++k) ub[k + 1] += ub[k];
     if ((r = upload(ub.data(), ub.size(), &dbu))) return r;
-    if (panel) {
+    if (kind != K32_MIRROR) {
         std::vector<float> ct;
         std::vector<int> off;
-        build_panel_tables(np, tab, ct, off);
+        if (kind == K32_TC) build_tc_tables(np, tab, ct, off);
+        else build_panel_tables(np, tab, ct, off);
         if ((r = upload(ct.data(), ct.size(), &dct))) return r;
         if ((r = upload(off.data(), off.size(), &doff))) return r;
     }
@@ -199,7 +213,7 @@ int setup_prog32(ProgEntry *pe, int space, int q, int L, int p, bool split, cons
     cudaFree(pe->d_ctab32); cudaFree(pe->d_ctab_off32);
     pe->d_blocks32 = db; pe->d_units32 = du; pe->d_block_units32 = dbu;
     pe->d_ctab32 = dct; pe->d_ctab_off32 = doff;
-    pe->panel32 = panel;
+    pe->kind32 = kind;
     pe->prog32 = np;
     pe->max_nc1_32 = 0;
     for (int k = 0; k < np.nblock; ++k) pe->max_nc1_32 = std::max(pe->max_nc1_32, np.blocks[k].nc[np.blocks[k].dir[0]]);
@@ -365,7 +379,26 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
         g.fields = ws; g.status = ds->status;
         cudaError_t le = launch_geom<T>(g, s);
         if (le != cudaSuccess) { rc = cuda_fail(le, "geom_kernel launch", __LINE__); break; }
-        if constexpr (f32) if (pe->panel32) {
+        if constexpr (f32) if (pe->kind32 == K32_TC) {
+            TcParams tp;
+            tp.blocks = pe->d_blocks32; tp.units = pe->d_units32; tp.block_unit_begin = pe->d_block_units32;
+            tp.ctab = pe->d_ctab32; tp.ctab_off = pe->d_ctab_off32;
+            tp.nblock = pr.nblock; tp.nj_max = pr.nj;
+            // about four waves of one CTA per SM, each CTA a chunk of elements of one block
+            const int64_t target = (int64_t)g_num_sms * 4;
+            int64_t epc = (ne * pr.nblock + target - 1) / target;
+            tp.elems_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(epc, 1 << 20));
+            tp.L = L; tp.nfields = pr.nfields;
+            tp.pp = te->pp32;
+            tp.fields = reinterpret_cast<const float *>(ws);
+            tp.out = reinterpret_cast<float *>(out + e0 * mat);
+            tp.mat_stride = mat; tp.ld = pr.cols; tp.n_elem = ne;
+            tp.status = ds->status;
+            le = launch_tc_f32(tp, pr.smem_bytes, s);
+            if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
+            continue;
+        }
+        if constexpr (f32) if (pe->kind32 == K32_PANEL) {
             PanelParams pp;
             pp.blocks = pe->d_blocks32; pp.units = pe->d_units32; pp.block_unit_begin = pe->d_block_units32;
             pp.ctab = pe->d_ctab32; pp.ctab_off = pe->d_ctab_off32;
@@ -541,7 +574,7 @@ int read_status(DeviceState *ds, int64_t *first_bad) {
     CK(cudaMemcpy(ds->status, &z, sizeof(z), cudaMemcpyHostToDevice));
     if (first_bad) *first_bad = -1;
     if (h.code != 0) {
-        if (first_bad && h.code > 0 && h.code < 8 && h.first_bad[h.code] != ULLONG_MAX)
+        if (first_bad && h.code > 0 && h.code < 16 && h.first_bad[h.code] != ULLONG_MAX)
             *first_bad = (int64_t)h.first_bad[h.code];
         return h.code;
     }
@@ -838,6 +871,7 @@ const char *dpg_strerror(int code) {
     case DPG_ERR_NOT_AFFINE: return "element is not a parallelepiped";
     case DPG_ERR_NOMEM: return "out of memory";
     case DPG_ERR_SCRATCH: return "request larger than the fixed scratch of dpg_integrate_noalloc";
+    case DPG_ERR_TIMEOUT: return "a bounded tensor-core wait ran out (the call's matrices are not valid)";
     }
     return "unknown status";
 }

@@ -166,6 +166,100 @@ DPG_HD inline PanelLayout panel_layout(const BlockDesc &b, int L, int nj) {
     return f;
 }
 
+// Shared-memory and tensor-memory layout of the FP32 tensor-core kernel (tcgen05) for one
+// block in the paper's direction order and a chunk of nj stage-A partners.  Stages B and
+// C are tcgen05 kind::tf32 products (M = 128 rows per instruction, operands split into
+// TF32 high and low parts, three products per operand pair, FP32 accumulation in tensor
+// memory):
+//   stage B: D_B,g[(i2,j2)][(jj,l)]   = sum_{h in g} sum_m P2_h[(i2,j2)][m] A_h[(jj,l)][m]
+//   stage C: D_C[(i2,x)][(i1,j1)]     = sum_{g,l} A_C[(i2,x)][(g,l)] P1[(i1,j1)][(g,l)]
+// with x = j2 + nc2 jj and the stage-C columns (i1, j1) at i1 nc1p + j1 (j1 padded to a
+// multiple of 8).  Every operand is stored K-major in the canonical no-swizzle layout:
+// 8-row x 16-byte core matrices, element (r, k) at byte
+//   (r / 8) * sbo + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4,
+// sbo = 32 * (row length in k) bytes; one instruction consumes k = 8 (two core-matrix
+// columns, 128 bytes apart).  An instruction reads 128 rows of its A operand and N rows of
+// its B operand; rows past the stored ones only feed output rows / columns that are never
+// read, so stored regions are padded to 8 rows only and the allocation covers the reads.
+// The stage-A output A_h is double-buffered (the kernel pipelines consecutive work units).
+// The metric fields the block's terms use are staged per element (F), the stage-A factors
+// of every unit of the block are resident (P3T: [t][i3][j3][n], signs folded in).  Output
+// tile rows start at a shift of 0..3 floats so that each has the 16-byte alignment of its
+// destination row (vector write-out).  Byte offsets are from the start of dynamic shared
+// memory.
+struct TcLayout {
+    int lpad, lsh, ksh;            // L rounded up to 8, its log2, k-steps of 8 per group
+    int nr1, nr2, nc1, nc2, n22;   // stage-C / stage-B extents, (i2, j2) pairs (<= 128)
+    int nc1p;                      // j1 range padded to a multiple of 8
+    int NB, NC;                    // N of the stage-B (nj lpad, to 16) / stage-C (nr1 nc1p, to 16) products
+    int mc, mt;                    // stage-C rows (i2, x) and 128-row tiles (chunk nj)
+    int nrow, ncol, ldt;           // output tile [nrow][ldt]: rows i1 + nr1 i2, columns nc1 x + j1
+    int nbB;                       // stage-B accumulators (2: double-buffered when TMEM allows)
+    int tcolC, tneed, tcols;       // TMEM: D_B,g of buffer u at column (u ng + g) NB, D_C tile t
+                                   // at tcolC + t NC; columns used, allocated (power of two >= 32)
+    int sbo2, sboC;                // row-group strides: K = lpad (P2, A_h), K = ng lpad (P1, A_C)
+    int nfs;                       // distinct metric fields of the block's terms
+    int oP1, p1b;                  // P1 high part at oP1, low part at oP1 + p1b
+    int oP2, p2b;                  // slot s: high at oP2 + 2 s p2b, low at + p2b
+    int oAh, ahb, ahbuf;           // buffer u, h group: high at oAh + u ahbuf + 2 h ahb, low at + ahb
+    int oAC, acb;                  // high at oAC, low at oAC + acb
+    int oP3, p3b;                  // stage-A factors of a unit, two buffers [t][n][8] floats
+    int oP3T;                      // stage-A factors of every unit [t][i3][j3][n]
+    int oF;                        // metric fields of the current element [nfs][L^3]
+    int oT;                        // output tile
+    int total;                     // dynamic shared memory (bytes)
+    int ok;                        // the block fits the tensor-core kernel
+};
+constexpr int TC_TMEM_COLS = 512;
+constexpr int TC_MAXROW = 128;     // output-tile rows (nr1 nr2) of the tensor-core kernel
+DPG_HD inline int tc_distinct_fields(const BlockDesc &b) {
+    int n = 0;
+    for (int t = 0; t < b.nterm; ++t) {
+        bool seen = false;
+        for (int u = 0; u < t; ++u) seen = seen || b.term[u].field == b.term[t].field;
+        if (!seen) ++n;
+    }
+    return n;
+}
+DPG_HD inline TcLayout tc_layout(const BlockDesc &b, int L, int nj) {
+    TcLayout f;
+    auto r8 = [](int v) { return (v + 7) & ~7; };
+    auto r16 = [](int v) { return (v + 15) & ~15; };
+    f.lpad = r8(L); f.lsh = f.lpad == 8 ? 3 : 4; f.ksh = f.lpad >> 3;
+    f.nr1 = b.nr[0]; f.nr2 = b.nr[1]; f.nc1 = b.nc[0]; f.nc2 = b.nc[1];
+    f.n22 = f.nr2 * f.nc2; f.nc1p = r8(f.nc1);
+    f.NB = r16(nj * f.lpad); f.NC = r16(f.nr1 * f.nc1p);
+    f.mc = f.nr2 * f.nc2 * nj; f.mt = (f.mc + 127) >> 7;
+    f.nrow = f.nr1 * f.nr2; f.ncol = f.nc1 * f.nc2 * nj; f.ldt = (f.ncol + 6) & ~3;
+    f.nbB = 2 * b.ng * f.NB + f.mt * f.NC <= TC_TMEM_COLS ? 2 : 1;
+    f.tcolC = f.nbB * b.ng * f.NB; f.tneed = f.tcolC + f.mt * f.NC;
+    f.tcols = 32;
+    while (f.tcols < f.tneed && f.tcols < TC_TMEM_COLS) f.tcols <<= 1;
+    f.sbo2 = 32 * f.lpad; f.sboC = 32 * b.ng * f.lpad;
+    f.nfs = tc_distinct_fields(b);
+    f.oP1 = 0; f.p1b = (f.NC >> 3) * f.sboC;
+    f.oP2 = f.oP1 + 2 * f.p1b; f.p2b = (r8(f.n22) >> 3) * f.sbo2;
+    f.oAh = f.oP2 + 2 * b.np2 * f.p2b; f.ahb = nj * f.lpad / 8 * f.sbo2; f.ahbuf = 2 * b.nh * f.ahb;
+    f.oAC = f.oAh + 2 * f.ahbuf; f.acb = (r8(f.mc) >> 3) * f.sboC;
+    f.oP3 = f.oAC + 2 * f.acb; f.p3b = b.nterm * L * 8 * 4;
+    f.oP3T = f.oP3 + 2 * f.p3b;
+    f.oF = f.oP3T + ((b.nterm * b.nr[2] * b.nc[2] * L * 4 + 15) & ~15);
+    f.oT = f.oF + ((f.nfs * L * L * L * 4 + 15) & ~15);
+    int end = f.oT + f.nrow * f.ldt * 4;
+    // reads past the stored rows: 128 rows of the last P2 slot and of the last A_C tile,
+    // NB rows of the last A_h slot
+    const int e2 = f.oP2 + (2 * b.np2 - 1) * f.p2b + 16 * f.sbo2;
+    const int eh = f.oAh + f.ahbuf + (2 * b.nh - 1) * f.ahb + (f.NB >> 3) * f.sbo2;
+    const int ec = f.oAC + f.acb + f.mt * 16 * f.sboC;
+    if (e2 > end) end = e2;
+    if (eh > end) end = eh;
+    if (ec > end) end = ec;
+    f.total = (end + 127) & ~127;
+    f.ok = f.n22 <= 128 && f.NB <= 256 && f.NC <= 256 && f.tneed <= TC_TMEM_COLS && f.lpad <= 16 &&
+           f.nrow <= TC_MAXROW && (b.ng == 0 || (b.nh >= 1 && b.np2 >= 1));   // a block without terms: zeros
+    return f;
+}
+
 // Device-resident tables of one (q, L).
 struct DevTables {
     int q, L;

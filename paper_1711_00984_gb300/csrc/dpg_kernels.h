@@ -11,7 +11,7 @@ namespace dpg {
 struct DevStatus {
     int code;
     int pad;
-    unsigned long long first_bad[8];
+    unsigned long long first_bad[16];
 };
 
 struct GeomParams {
@@ -79,6 +79,22 @@ struct PanelParams {
     int64_t mat_stride, ld, n_elem;
 };
 
+// FP32 tensor-core kernel (tcgen05): one CTA per (block, chunk of elements).
+struct TcParams {
+    const BlockDesc *blocks;
+    const Unit *units;
+    const int *block_unit_begin;   // [nblock + 1]
+    const float *ctab;             // constant operands of every block (build_tc_tables)
+    const int *ctab_off;           // [nblock], in floats
+    int nblock, nj_max, elems_per_cta;
+    int L, nfields;
+    const float *pp;               // pair products [NPAIR][NQ1][NQ1][L]
+    const float *fields;           // [n_elem][nfields][L^3]
+    float *out;
+    int64_t mat_stride, ld, n_elem;
+    DevStatus *status;
+};
+
 template <typename T>
 struct AffParams {
     const BlockDesc *blocks;
@@ -128,6 +144,9 @@ template <typename TF> cudaError_t launch_geom(const GeomParams &p, cudaStream_t
 template <typename T> cudaError_t launch_general(const SfParams<T> &p, size_t smem, cudaStream_t s);
 cudaError_t launch_general_f32(const SfParams32 &p, size_t smem, int max_nc1, cudaStream_t s);
 cudaError_t launch_panel_f32(const PanelParams &p, size_t smem, cudaStream_t s);
+cudaError_t launch_tc_f32(const TcParams &p, size_t smem, cudaStream_t s);
+cudaError_t init_tc_attributes(int optin_smem);
+int tc_static_smem();
 cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);

@@ -264,7 +264,7 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
 
     for (int a = 0; a < nR; ++a)
     for (int b = 0; b < nC; ++b) {
-        bool symmetric = space <= S_L2 && order != ORDER_PANEL;
+        bool symmetric = space <= S_L2 && order != ORDER_PANEL && order != ORDER_TC;
         if (symmetric && b < a) continue;             // lower blocks come from mirroring
         for (int part = 0; part < pr.parts; ++part) {
             std::vector<TermSpec> ts;
@@ -356,7 +356,8 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             // ORDER_A3 keeps stage A on xi_3, ORDER_NATURAL keeps the paper's order
             static const int perms[6][3] = { { 0, 1, 2 }, { 1, 0, 2 }, { 0, 2, 1 },
                                              { 2, 0, 1 }, { 1, 2, 0 }, { 2, 1, 0 } };
-            const int nperm = (order == ORDER_NATURAL || order == ORDER_PANEL) ? 1 : (order == ORDER_A3 ? 2 : 6);
+            const int nperm = (order == ORDER_NATURAL || order == ORDER_PANEL || order == ORDER_TC) ? 1
+                                                                                                  : (order == ORDER_A3 ? 2 : 6);
             double best = 0.0; int bi = 0;
             for (int k = 0; k < nperm; ++k) {
                 finish_block(bd, ts, perms[k]);
@@ -372,6 +373,10 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     auto smem_bytes = [&](const BlockDesc &b, int njv) -> size_t {
         if (order == ORDER_A3) return (size_t)f32_layout(b, L, njv).total * sizeof(float);
         if (order == ORDER_PANEL) return (size_t)panel_layout(b, L, njv).total * sizeof(float);
+        if (order == ORDER_TC) {
+            const TcLayout t = tc_layout(b, L, njv);
+            return t.ok ? (size_t)t.total : SIZE_MAX;
+        }
         if (order == ORDER_NATURAL)
             return (size_t)aff_layout(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], njv).total * sizeof(double);
         return smem_values(b, L, njv) * sizeof(double);
@@ -379,7 +384,9 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     // (ORDER_PANEL: the largest chunk that fits one CTA per SM; the launch takes two
     // 8-warp CTAs per SM where the chunk fits PANEL_SMEM_2CTA, else one of 16 warps)
     const size_t budget = smem_budget ? smem_budget
-                                      : (order == ORDER_BEST ? 160 * 1024 : (order == ORDER_PANEL ? (size_t)200 * 1024 : 110 * 1024));
+                                      : (order == ORDER_BEST ? 160 * 1024
+                                         : (order == ORDER_PANEL ? (size_t)200 * 1024
+                                         : (order == ORDER_TC ? (size_t)220 * 1024 : 110 * 1024)));
     int maxnA = 1;
     for (int k = 0; k < pr.nblock; ++k) maxnA = std::max(maxnA, pr.blocks[k].nc[pr.blocks[k].dir[2]]);
     int nj = std::min(NJMAX, maxnA);
@@ -513,6 +520,42 @@ void build_panel_tables(const Program &pr, const HostTables &tab, std::vector<fl
                     }
         ctab.insert(ctab.end(), t.begin(), t.end());
     }
+}
+
+void build_tc_tables(const Program &pr, const HostTables &tab, std::vector<float> &ctab, std::vector<int> &off) {
+    ctab.clear();
+    off.assign(pr.nblock, 0);
+    const int L = pr.L;
+    auto ppv = [&](int pair, int i, int j, int l) -> float {
+        return (float)tab.pp[(((size_t)pair * NQ1 + i) * NQ1 + j) * L + l];
+    };
+    // float index of element (r, k) of a K-major canonical operand with row-group stride sbo
+    auto at = [](int r, int k, int sbo) { return ((r >> 3) * sbo + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4) / 4; };
+    for (int k = 0; k < pr.nblock; ++k) {
+        const BlockDesc &b = pr.blocks[k];
+        off[k] = (int)ctab.size();
+        if (b.ng == 0) continue;                          // no terms: the kernel writes zeros
+        const TcLayout f = tc_layout(b, L, pr.nj);
+        std::vector<float> t((size_t)f.oAh / 4, 0.0f);
+        // P1 (B operand of stage C): row n = i1 nc1p + j1, k = g lpad + l
+        for (int n = 0; n < f.NC; ++n)
+            for (int kk = 0; kk < b.ng * f.lpad; ++kk) {
+                const int g = kk / f.lpad, l = kk % f.lpad, i1 = n / f.nc1p, j1 = n % f.nc1p;
+                const float v = (i1 < f.nr1 && j1 < f.nc1 && l < L) ? ppv(b.g_pair[g], i1, j1, l) : 0.0f;
+                const int i = at(n, kk, f.sboC);
+                split_tf32(v, t[f.oP1 / 4 + i], t[(f.oP1 + f.p1b) / 4 + i]);
+            }
+        // P2 slots (A operand of stage B): row r = i2 nc2 + j2, k = m
+        for (int s2 = 0; s2 < b.np2; ++s2)
+            for (int r = 0; r < ((f.n22 + 7) & ~7); ++r)
+                for (int m = 0; m < f.lpad; ++m) {
+                    const float v = (r < f.n22 && m < L) ? ppv(b.p2_pair[s2], r / f.nc2, r % f.nc2, m) : 0.0f;
+                    const int i = at(r, m, f.sbo2);
+                    split_tf32(v, t[(f.oP2 + 2 * s2 * f.p2b) / 4 + i], t[(f.oP2 + (2 * s2 + 1) * f.p2b) / 4 + i]);
+                }
+        ctab.insert(ctab.end(), t.begin(), t.end());
+    }
+    if (ctab.empty()) ctab.push_back(0.0f);
 }
 
 }  // namespace dpg

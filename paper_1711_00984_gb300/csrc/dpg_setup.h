@@ -37,7 +37,10 @@ HostTables make_tables(int q, int L);
 // (stage A over xi_3, B over xi_2, C over xi_1; affine kernel).
 // ORDER_PANEL: the paper's order and every (a, b) block of a symmetric matrix built (no
 // mirrored tiles): the FP32 row-panel kernel writes every output row itself.
-enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3 };
+// ORDER_TC: the same blocks as ORDER_PANEL, sized for the FP32 tensor-core (tcgen05)
+// kernel (tc_layout); a block that does not fit it makes the program's smem_bytes
+// SIZE_MAX.
+enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3, ORDER_TC = 4 };
 // force_nj > 0 fixes the stage-A chunk (autotuner); otherwise the largest chunk whose
 // shared memory fits the kernel's budget (smem_budget bytes, or the order's default when
 // 0) is taken.
@@ -47,6 +50,11 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
 // program (the shared-memory image [0, oA) of panel_layout), concatenated; off[k] is the
 // first float of block k.
 void build_panel_tables(const Program &pr, const HostTables &tab, std::vector<float> &ctab, std::vector<int> &off);
+// Constant operands of the FP32 tensor-core kernel for every block of an ORDER_TC program:
+// P1 and the P2 slots, each split into TF32 high and low parts, in the canonical K-major
+// layout of tc_layout (the shared-memory image [0, oAh)); off[k] is the first float of
+// block k.
+void build_tc_tables(const Program &pr, const HostTables &tab, std::vector<float> &ctab, std::vector<int> &off);
 int64_t rows_of(int space, int q);
 int64_t cols_of(int space, int p, int q);
 
