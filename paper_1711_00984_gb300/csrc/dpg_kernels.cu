@@ -1005,6 +1005,20 @@ __device__ __forceinline__ bool is_zero(float x) {
     return (b << 1) == 0u;
 }
 
+// Slot of this lane's item in a list compacted by a whole warp: one shared atomic per warp
+// and list (the lanes of a warp may append to different lists g); -1 when keep is false.
+__device__ __forceinline__ int warp_append(int *count, bool keep) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned all = __activemask();
+    const unsigned peers = __match_any_sync(all, reinterpret_cast<uintptr_t>(count));
+    const unsigned want = __ballot_sync(all, keep) & peers;
+    int base = 0;
+    const int leader = want ? __ffs(want) - 1 : -1;
+    if ((int)lane == leader) base = atomicAdd(count, __popc(want));
+    base = __shfl_sync(peers, base, leader < 0 ? (__ffs(peers) - 1) : leader);
+    return keep ? base + __popc(want & ((1u << lane) - 1u)) : -1;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1059,8 +1073,8 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         const int g = fdiv(it, mn11), ij = it - g * n11;
         const int i1 = fdiv(ij, mnc1), j1 = ij - i1 * nc1;
         const T v = Fv(bd.g_pair[g], i1, j1);
-        if (!is_zero(v)) {
-            const int slot = atomicAdd(&f1c[g], 1);
+        const int slot = warp_append(&f1c[g], !is_zero(v));
+        if (slot >= 0) {
             f1v[g * n11 + slot] = v;
             f1i[g * n11 + slot] = i1 * lay.ldt + j1;
         }
@@ -1111,8 +1125,8 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
                 const T f2 = F2[t * n22 + ij2];
                 if (!is_zero(f2)) { acc = fma(sv, f2, acc); any = true; }
             }
-            if (any && !is_zero(acc)) {
-                const int slot = atomicAdd(&qc[g], 1);
+            const int slot = warp_append(&qc[g], any && !is_zero(acc));
+            if (slot >= 0) {
                 const int i2 = fdiv(ij2, mnc2), j2 = ij2 - i2 * nc2;
                 qv[g * n22 * njm + slot] = acc;
                 qi[g * n22 * njm + slot] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
