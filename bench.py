@@ -371,7 +371,8 @@ ACOUSTIC_OMEGA, ACOUSTIC_ALPHA = 4.0 * 3.141592653589793, 1.0
 _AC = (ACOUSTIC_OMEGA ** 2 + ACOUSTIC_ALPHA, 1.0)
 
 SECONDARY = {
-    # name: (meshgen workload, q, L, [(space, p_trial, affine, coefficients or None)])
+    # name: (meshgen workload, q, L, [(space, p_trial, map, coefficients or None)]); map is
+    # False (general), True (affine) or "extruded"
     "hcurl_q6_p4_16x16x16": ("hcurl_q6_p4_16x16x16", 6, 8, [("HCURL", 0, False, None), ("B", 4, False, None)]),
     "q9_8x8x4": ("q9_8x8x4", 9, 11, [("H1", 0, False, None), ("HDIV", 0, False, None),
                                      ("H1", 0, True, None), ("HDIV", 0, True, None)]),
@@ -380,6 +381,10 @@ SECONDARY = {
     "acoustics_q6_p4_16x16x16": ("hcurl_q6_p4_16x16x16", 6, 8,
                                  [("H1", 0, False, _AC), ("HDIV", 0, False, _AC),
                                   ("ACOUSTIC_CROSS", 0, False, None), ("ACOUSTIC_B", 4, False, None)]),
+    # 512 elements extruded along x1 (Eq. 2.89, right): the O(p^6) extruded-map path
+    # (Algorithm 11) and, on the same elements, the general O(p^7) path; unit coefficients
+    "ext_q5_8x8x8": ("ext_q5_8x8x8", 5, 7, [(s_, 0, m_, None) for m_ in ("extruded", False)
+                                            for s_ in ("H1", "HCURL", "HDIV", "L2")]),
 }
 
 
@@ -408,17 +413,20 @@ def run_secondary(args):
         pass
     rec = {"workload": wname, "q": q, "L": L, "calls": []}
     for space, p, aff, cf in calls:
+        ext = aff == "extruded"
+        aff = aff is True
         dpg.dpg_tables_init_L(q, L, space)
         v = torch.from_numpy(w["verts_affine" if aff else "verts"]).to(dev)
         ne = v.shape[0]
         ct = None if cf is None else torch.tensor([list(cf)] * ne, dtype=torch.float64, device=dev)
         cptr = 0 if ct is None else ct.data_ptr()
-        res = {"space": space, "p_trial": p, "map": "affine" if aff else "general", "elements": ne}
+        res = {"space": space, "p_trial": p, "map": "affine" if aff else ("extruded" if ext else "general"),
+               "elements": ne}
         if cf is not None:
             res["coeffs"] = list(cf)
         outs = {}
         for fp32 in (False, True):
-            sid = dpg.space_id(space, fp32=fp32, affine=aff)
+            sid = dpg.space_id(space, fp32=fp32, affine=aff, extruded=ext)
             shape = (ne,) + dpg.matrix_shape(space, q, p)
             out = torch.empty(shape, dtype=torch.float32 if fp32 else torch.float64, device=dev)
 

@@ -77,6 +77,16 @@ extern "C" {
 #define DPG_FP32        0x100  /* FP32 form (above) */
 #define DPG_MAP_AFFINE  0x200  /* elements are parallelepipeds: O(p^6) path, Sec. 2.8.1 */
 #define DPG_B_SPLIT     0x400  /* B only: write [2][rows][cols] = (mass part, curl part) */
+/* DPG_MAP_EXTRUDED: the elements are extrusions along x1 of a bilinear quadrilateral in
+ * (x2, x3), the second map of Eq. 2.89: x1 = x1(v0) + lambda1 xi1 with lambda1 the same on
+ * all four xi1-edges, and (x2, x3) independent of xi1, so J(xi2, xi3) =
+ * [[lambda1, 0, 0], [0, eta(xi2, xi3)]].  The metric fields then do not depend on xi1: the
+ * xi1 integrals are taken exactly from the 1D integrals F (Eq. 2.90) and the quadrature
+ * runs in (xi2, xi3) only (Algorithm 11, O(p^6)).  On such elements the result is the
+ * general path's discrete sum (a Gauss rule with L >= q + 1 points is exact in xi1).
+ * Elements that are not of this form are reported as DPG_ERR_NOT_EXTRUDED (relative
+ * tolerance 1e-10 on the vertices) and NaN-filled.  Not combinable with DPG_MAP_AFFINE. */
+#define DPG_MAP_EXTRUDED 0x800
 
 /* ---- status codes ---- */
 typedef enum {
@@ -90,9 +100,11 @@ typedef enum {
     DPG_ERR_NOMEM = 7,       /* device or host allocation failed                        */
     DPG_ERR_SCRATCH = 8,     /* dpg_integrate_noalloc: the call needs more metric-field
                                 scratch than DPG_NOALLOC_SCRATCH_BYTES                  */
-    DPG_ERR_TIMEOUT = 9      /* device: a bounded wait of the FP32 tensor-core kernel for
+    DPG_ERR_TIMEOUT = 9,     /* device: a bounded wait of the FP32 tensor-core kernel for
                                 its own MMAs ran out; the CTA stopped, the matrices of the
                                 call are not valid (first_bad = first element of the CTA) */
+    DPG_ERR_NOT_EXTRUDED = 10 /* device: element is not an extrusion along x1
+                                (DPG_MAP_EXTRUDED)                                       */
 } dpg_status;
 
 #define DPG_MAX_Q 12           /* supported test orders: 1 <= q <= DPG_MAX_Q           */
@@ -127,8 +139,8 @@ int64_t dpg_matrix_cols(int space, int p_trial, int q);
 
 /* Integrate the element matrices of n_elem elements (the paper's per-element routine
  * PROC(mid, G) of Algorithms 2-11, batched; problem statement Eq. 2.13).
- *   space    : DPG_H1 .. DPG_B_L2VEC_HCURL, ORed with DPG_FP32 / DPG_MAP_AFFINE /
- *              DPG_B_SPLIT (B only).
+ *   space    : DPG_H1 .. DPG_ACOUSTIC_B, ORed with DPG_FP32 / DPG_MAP_AFFINE or
+ *              DPG_MAP_EXTRUDED / DPG_B_SPLIT (B only).
  *   p_trial  : trial order for DPG_B_L2VEC_HCURL and DPG_ACOUSTIC_B
  *              (1 <= p_trial <= q_test); ignored (pass 0) otherwise.
  *   q_test   : test order; tables for (space, q_test) must be initialised.
@@ -189,8 +201,8 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj);
  * instead uses one file-scope device array of DPG_NOALLOC_SCRATCH_BYTES (32 MiB), which
  * every GPU that loads the library reserves until the process exits.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
- *   Arguments, layouts and results are those of dpg_integrate; DPG_MAP_AFFINE is
- *   rejected (DPG_ERR_ARG): the affine path needs no scratch, use dpg_integrate.
+ *   Arguments, layouts and results are those of dpg_integrate for the general map;
+ *   DPG_MAP_AFFINE and DPG_MAP_EXTRUDED are rejected (DPG_ERR_ARG).
  *   Limit: n_elem * nfields * L^3 * (8 or 4 bytes) must fit the array (nfields = 7, 12,
  *   7, 1, 18 for H1, H(curl), H(div), L2, B; 4 bytes with DPG_FP32), else the call
  *   returns DPG_ERR_SCRATCH before launching anything.  Example: H(curl), q = 5, L = 7,

@@ -20,12 +20,12 @@ LIB_PATH = os.path.join(HERE, "_build", "libdpg.so")
 # spaces and flags (include/dpg.h)
 DPG_H1, DPG_HCURL, DPG_HDIV, DPG_L2, DPG_B_L2VEC_HCURL = 1, 2, 3, 4, 5
 DPG_ACOUSTIC_CROSS, DPG_ACOUSTIC_B = 6, 7
-DPG_FP32, DPG_MAP_AFFINE, DPG_B_SPLIT = 0x100, 0x200, 0x400
+DPG_FP32, DPG_MAP_AFFINE, DPG_B_SPLIT, DPG_MAP_EXTRUDED = 0x100, 0x200, 0x400, 0x800
 SPACE_IDS = {"H1": DPG_H1, "HCURL": DPG_HCURL, "HDIV": DPG_HDIV, "L2": DPG_L2, "B": DPG_B_L2VEC_HCURL,
              "ACOUSTIC_CROSS": DPG_ACOUSTIC_CROSS, "ACOUSTIC_B": DPG_ACOUSTIC_B}
 STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANGE", 4: "DPG_ERR_CUDA",
           5: "DPG_ERR_DEGENERATE", 6: "DPG_ERR_NOT_AFFINE", 7: "DPG_ERR_NOMEM", 8: "DPG_ERR_SCRATCH",
-          9: "DPG_ERR_TIMEOUT"}
+          9: "DPG_ERR_TIMEOUT", 10: "DPG_ERR_NOT_EXTRUDED"}
 
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
            "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",
@@ -93,9 +93,10 @@ def _check(code: int, where: str) -> int:
     return code
 
 
-def space_id(space, fp32: bool = False, affine: bool = False, split: bool = False) -> int:
+def space_id(space, fp32: bool = False, affine: bool = False, split: bool = False, extruded: bool = False) -> int:
     s = SPACE_IDS[space] if isinstance(space, str) else int(space)
-    return s | (DPG_FP32 if fp32 else 0) | (DPG_MAP_AFFINE if affine else 0) | (DPG_B_SPLIT if split else 0)
+    return (s | (DPG_FP32 if fp32 else 0) | (DPG_MAP_AFFINE if affine else 0) | (DPG_B_SPLIT if split else 0)
+            | (DPG_MAP_EXTRUDED if extruded else 0))
 
 
 # ---- the C ABI, name for name ---------------------------------------------------------
@@ -226,7 +227,7 @@ def matrix_shape(space, q: int, p: int = 0, split: bool = False) -> tuple[int, .
 
 
 def integrate(space, q: int, verts, coeffs=None, *, p: int = 0, fp32: bool = False, affine: bool = False,
-              split: bool = False, out=None, stream=None):
+              split: bool = False, extruded: bool = False, out=None, stream=None):
     """Integrate element matrices of device tensors ``verts[n, 8, 3]`` (float64, CUDA).
 
     Returns ``out[n, rows, cols]`` (``[n, 2, rows, cols]`` with ``split``) in float64, or
@@ -244,7 +245,7 @@ def integrate(space, q: int, verts, coeffs=None, *, p: int = 0, fp32: bool = Fal
         out = torch.empty(shape, dtype=dt, device=verts.device)
     elif out.dtype != dt or tuple(out.shape) != shape or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous {dt} tensor of shape {shape}")
-    sid = space_id(space, fp32, affine, split)
+    sid = space_id(space, fp32, affine, split, extruded)
     code = dpg_integrate(sid, p, q, n, verts.data_ptr(), coeffs.data_ptr() if coeffs is not None else 0,
                          out.data_ptr(), _stream_handle(stream))
     _check(code, "dpg_integrate")

@@ -51,6 +51,8 @@ struct ProgEntry {
     // SM), [1] FP32 kernel (the larger chunk that fits two)
     AffProg aff[2];
     double flops_aff = 0.0;         // algorithmic flops of the affine path
+    AffProg ext[2];                 // extruded-map path, [0] FP64, [1] FP32
+    double flops_ext = 0.0;         // algorithmic flops of the extruded-map path
     Program prog32;                 // FP32 general path: tensor-core program (kind32 = K32_TC),
                                     // row-panel program (K32_PANEL) or the mirrored-tile
                                     // program with stage A on xi_3 (K32_MIRROR)
@@ -250,6 +252,28 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         ap.smem_values = m;
     }
     pe->flops_aff = pe->aff[0].prog.flops_affine;
+    for (int prec = 0; prec < 2; ++prec) {
+        AffProg &ap = pe->ext[prec];
+        const size_t esz = prec ? sizeof(float) : sizeof(double);
+        // the largest chunk whose shared memory fits three CTAs per SM, else the largest that fits
+        size_t budget = (size_t)72 * 1024 * sizeof(double) / esz;
+        ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0, budget);
+        if (ap.prog.smem_bytes > budget)
+            ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0,
+                                   (size_t)g_max_dyn_smem * sizeof(double) / esz);
+        const Program &pa = ap.prog;
+        if ((r = upload(pa.blocks, (size_t)pa.nblock, &ap.d_blocks))) return r;
+        if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
+        size_t m = 0;
+        for (int k = 0; k < pa.nblock; ++k) m = std::max(m, extruded_smem_values(pa.blocks[k], L, pa.nj));
+        std::vector<int> ub(pa.nblock + 1, 0);
+        for (const Unit &u : pa.units) ub[u.block + 1]++;
+        for (int k = 0; k < pa.nblock; ++k) ub[k + 1] += ub[k];
+        if ((r = upload(ub.data(), ub.size(), &ap.d_block_units))) return r;
+        if (m * esz > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
+        ap.smem_values = m;
+    }
+    pe->flops_ext = pe->ext[0].prog.flops_extruded;
     if ((r = setup_prog32(pe.get(), space, q, L, p, split != 0, tab, 0))) return r;
     *out = pe.get();
     ds->progs[key] = std::move(pe);
@@ -300,6 +324,7 @@ void free_device_state(DeviceState &ds) {
     for (auto &kv : ds.progs) {
         cudaFree(kv.second->d_blocks); cudaFree(kv.second->d_units);
         for (AffProg &ap : kv.second->aff) { cudaFree(ap.d_blocks); cudaFree(ap.d_units); cudaFree(ap.d_block_units); }
+        for (AffProg &ap : kv.second->ext) { cudaFree(ap.d_blocks); cudaFree(ap.d_units); cudaFree(ap.d_block_units); }
         cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
         cudaFree(kv.second->d_ctab32); cudaFree(kv.second->d_ctab_off32);
     }
@@ -320,7 +345,8 @@ bool valid_space(int space) {
     const int base = space & 0xff;
     const int flags = space & ~0xff;
     if (base < S_H1 || base > S_AB) return false;
-    if (flags & ~(DPG_FP32 | DPG_MAP_AFFINE | DPG_B_SPLIT)) return false;
+    if (flags & ~(DPG_FP32 | DPG_MAP_AFFINE | DPG_MAP_EXTRUDED | DPG_B_SPLIT)) return false;
+    if ((flags & DPG_MAP_AFFINE) && (flags & DPG_MAP_EXTRUDED)) return false;
     if ((flags & DPG_B_SPLIT) && base != S_B) return false;
     return true;
 }
@@ -490,6 +516,64 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
     return rc;
 }
 
+// Extruded maps (Eq. 2.89, right; Algorithm 11): 2D geometry and metric fields per element,
+// then the extruded-mode contraction, chunked like the general path.
+template <typename T>
+int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
+                 const double *coeffs, T *out, cudaStream_t s) {
+    const AffProg &aprog = pe->ext[sizeof(T) == 4 ? 1 : 0];
+    const Program &pr = aprog.prog;
+    const int L = pr.L, L2 = L * L;
+    const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
+    int max_units_block = 1;
+    for (int k = 0; k < pr.nblock; ++k) {
+        int c = 0;
+        for (const Unit &u : pr.units) c += u.block == k;
+        max_units_block = std::max(max_units_block, c);
+    }
+    const size_t per_elem = (size_t)pr.nfields * L2 * sizeof(T) + sizeof(int);
+    int64_t chunk = std::max<int64_t>(1, (int64_t)(kWorkspaceLimit / per_elem));
+    const int64_t target = (int64_t)g_num_sms * 6 * 4;
+    const int64_t ne_all = std::min(chunk, n_elem);
+    const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_units_block,
+                                              (target + ne_all * pr.nblock - 1) / (ne_all * pr.nblock)));
+    chunk = std::min<int64_t>(chunk, INT_MAX / ((int64_t)pr.nblock * nsplit));
+    if (chunk > n_elem) chunk = n_elem;
+    void *ws = nullptr;
+    CK(cudaMallocFromPoolAsync(&ws, (size_t)chunk * per_elem + 16, ds->pool, s));
+    T *fields = reinterpret_cast<T *>(ws);
+    int *est = reinterpret_cast<int *>(reinterpret_cast<char *>(ws) + (((size_t)chunk * pr.nfields * L2 * sizeof(T) + 15) & ~size_t(15)));
+    int rc = DPG_OK;
+    for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK; e0 += chunk) {
+        const int64_t ne = std::min(chunk, n_elem - e0);
+        cudaError_t le = cudaMemsetAsync(est, 0, (size_t)ne * sizeof(int), s);
+        if (le != cudaSuccess) { rc = cuda_fail(le, "cudaMemsetAsync", __LINE__); break; }
+        Geom2dParams g;
+        g.space = pr.space; g.L = L; g.nfields = pr.nfields;
+        g.n_elem = ne; g.elem_base = e0;
+        g.verts = verts + 24 * e0;
+        g.coeffs = coeffs ? coeffs + 2 * e0 : nullptr;
+        g.zeta = te->zeta; g.w = te->w;
+        g.fields = fields; g.estatus = est; g.status = ds->status;
+        le = launch_geom2d<T>(g, s);
+        if (le != cudaSuccess) { rc = cuda_fail(le, "geom2d_kernel launch", __LINE__); break; }
+        AffParams<T> ap;
+        ap.blocks = aprog.d_blocks; ap.units = aprog.d_units; ap.block_unit_begin = aprog.d_block_units;
+        ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit;
+        if constexpr (sizeof(T) == 8) { ap.F = te->F64; ap.pp = te->pp64; } else { ap.F = te->F32; ap.pp = te->pp32; }
+        ap.consts = nullptr;
+        ap.xfields = fields; ap.estatus = est;
+        ap.L = L; ap.nfields = pr.nfields;
+        ap.out = out + e0 * mat;
+        ap.mat_stride = mat; ap.ld = pr.cols; ap.n_elem = ne;
+        le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
+        if (le != cudaSuccess) { rc = cuda_fail(le, "extruded contraction launch", __LINE__); break; }
+    }
+    cudaError_t fe = cudaFreeAsync(ws, s);
+    if (fe != cudaSuccess && rc == DPG_OK) rc = cuda_fail(fe, "cudaFreeAsync", __LINE__);
+    return rc;
+}
+
 int integrate_locked(int space, int p_trial, int q_test, int64_t n_elem, const double *vertices,
                      const double *coeffs, void *out, cudaStream_t s) {
     ProgEntry *pe; TableEntry *te; DeviceState *ds;
@@ -504,6 +588,10 @@ int integrate_locked(int space, int p_trial, int q_test, int64_t n_elem, const d
     if (affine) {
         return fp32 ? run_affine<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
                     : run_affine<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s);
+    }
+    if (space & DPG_MAP_EXTRUDED) {
+        return fp32 ? run_extruded<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
+                    : run_extruded<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s);
     }
     return fp32 ? run_general<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
                 : run_general<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s);
@@ -872,6 +960,7 @@ const char *dpg_strerror(int code) {
     case DPG_ERR_NOMEM: return "out of memory";
     case DPG_ERR_SCRATCH: return "request larger than the fixed scratch of dpg_integrate_noalloc";
     case DPG_ERR_TIMEOUT: return "a bounded tensor-core wait ran out (the call's matrices are not valid)";
+    case DPG_ERR_NOT_EXTRUDED: return "element is not an extrusion along x1";
     }
     return "unknown status";
 }
@@ -881,6 +970,7 @@ double dpg_flops_per_element(int space, int p_trial, int q_test) {
     ProgEntry *pe; TableEntry *te; DeviceState *ds;
     if (resolve(space, p_trial, q_test, &pe, &te, &ds) != DPG_OK) return -1.0;
     if (space & DPG_MAP_AFFINE) return pe->flops_aff;
+    if (space & DPG_MAP_EXTRUDED) return pe->flops_ext;
     // the same algorithmic count for both forms (the FP32 row-panel kernel also computes
     // the mirrored blocks; that extra work is not counted)
     return pe->prog.flops;

@@ -123,6 +123,36 @@ DPG_HD inline AffLayout aff_layout(int ng, int nterm, int nr1, int nr2, int nc1,
     return a;
 }
 
+// Shared-memory layout (in values of the output type) of the extruded-map kernel: the
+// affine layout (Q as a dense list, the stage-C non-zeros, the output tile) followed by the
+// element's 2D metric fields of the block's terms [nfs][L][L], the stage-A factors of the
+// unit S3[t][jj][n], the stage-A output A[h][m][jj] and the stage-B pair products of the
+// block P2[slot][(i2,j2)][m].
+struct ExtLayout {
+    AffLayout a;
+    int nfs, oFx, oS3, oA, oP2, total;
+};
+DPG_HD inline int distinct_fields(const BlockDesc &b) {
+    int n = 0;
+    for (int t = 0; t < b.nterm; ++t) {
+        bool seen = false;
+        for (int u = 0; u < t; ++u) seen = seen || b.term[u].field == b.term[t].field;
+        if (!seen) ++n;
+    }
+    return n;
+}
+DPG_HD inline ExtLayout ext_layout(const BlockDesc &b, int L, int nj) {
+    ExtLayout x;
+    x.a = aff_layout(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], nj);
+    x.nfs = distinct_fields(b);
+    x.oFx = x.a.total;
+    x.oS3 = x.oFx + r4i(x.nfs * L * L);
+    x.oA = x.oS3 + r4i(b.nterm * nj * L);
+    x.oP2 = x.oA + r4i(b.nh * L * nj);
+    x.total = x.oP2 + r4i(b.np2 * b.nr[1] * b.nc[1] * L);
+    return x;
+}
+
 // Shared-memory layout (in floats, every region 16-byte aligned) of the FP32 row-panel
 // kernel for one block in the paper's direction order (stage C over xi_1, B over xi_2, A
 // over xi_3) and a chunk of nj stage-A partners.  Stages B and C are tensor-core
@@ -212,15 +242,6 @@ struct TcLayout {
 };
 constexpr int TC_TMEM_COLS = 512;
 constexpr int TC_MAXROW = 128;     // output-tile rows (nr1 nr2) of the tensor-core kernel
-DPG_HD inline int tc_distinct_fields(const BlockDesc &b) {
-    int n = 0;
-    for (int t = 0; t < b.nterm; ++t) {
-        bool seen = false;
-        for (int u = 0; u < t; ++u) seen = seen || b.term[u].field == b.term[t].field;
-        if (!seen) ++n;
-    }
-    return n;
-}
 DPG_HD inline TcLayout tc_layout(const BlockDesc &b, int L, int nj) {
     TcLayout f;
     auto r8 = [](int v) { return (v + 7) & ~7; };
@@ -236,7 +257,7 @@ DPG_HD inline TcLayout tc_layout(const BlockDesc &b, int L, int nj) {
     f.tcols = 32;
     while (f.tcols < f.tneed && f.tcols < TC_TMEM_COLS) f.tcols <<= 1;
     f.sbo2 = 32 * f.lpad; f.sboC = 32 * b.ng * f.lpad;
-    f.nfs = tc_distinct_fields(b);
+    f.nfs = distinct_fields(b);
     f.oP1 = 0; f.p1b = (f.NC >> 3) * f.sboC;
     f.oP2 = f.oP1 + 2 * f.p1b; f.p2b = (r8(f.n22) >> 3) * f.sbo2;
     f.oAh = f.oP2 + 2 * b.np2 * f.p2b; f.ahb = nj * f.lpad / 8 * f.sbo2; f.ahbuf = 2 * b.nh * f.ahb;

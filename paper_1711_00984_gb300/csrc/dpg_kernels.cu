@@ -172,6 +172,50 @@ __global__ void __launch_bounds__(256) geom_kernel(GeomParams p) {
     for (int k = 0; k < nf; ++k) dst[(int64_t)k * L3] = bad ? qnan<TF>() : (TF)f[k];
 }
 
+// Extruded elements (the second map of Eq. 2.89): one thread per (element, xi2 point m, xi3
+// point n).  J does not depend on xi1 and is taken at xi1 = 1/2; the weight is w_m w_n (the
+// xi1 integrals are exact 1D integrals).  The thread of point (0, 0) checks that the
+// element is an extrusion along x1: x1 = x1(v0) + lambda1 v1 at every vertex v and (x2, x3)
+// the same at v and its xi1 neighbour.
+template <typename TF>
+__global__ void __launch_bounds__(256) geom2d_kernel(Geom2dParams p) {
+    const int L = p.L, L2 = L * L;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= p.n_elem * L2) return;
+    const int64_t e = gid / L2;
+    const int pt = (int)(gid - e * L2);
+    const int m = pt / L, n = pt - (pt / L) * L;
+    const double *v = p.verts + 24 * e;
+    int flag = 0;
+    if (pt == 0) {
+        double scale = 0.0;
+        for (int c = 1; c < 8; ++c)
+            for (int i = 0; i < 3; ++i) scale = fmax(scale, fabs(v[3 * c + i] - v[i]));
+        const double lam = v[3] - v[0], tol = 1e-10 * scale;
+        for (int c = 0; c < 8; ++c) {
+            if (!(fabs(v[3 * c] - (v[0] + lam * (c & 1))) <= tol)) flag = 10; /*DPG_ERR_NOT_EXTRUDED*/
+            if (c & 1)
+                for (int i = 1; i < 3; ++i)
+                    if (!(fabs(v[3 * c + i] - v[3 * (c - 1) + i]) <= tol)) flag = 10;
+        }
+    }
+    const double wt = p.w[m] * p.w[n];
+    Jac g;
+    trilinear_jac(v, 0.5, p.zeta[m], p.zeta[n], g);
+    finish_jac(g);
+    if (flag == 0 && (!(g.det > 0.0) || !isfinite(g.det))) flag = 5; /*DPG_ERR_DEGENERATE*/
+    const double c0 = p.coeffs ? p.coeffs[2 * e] : 1.0;
+    const double c1 = p.coeffs ? p.coeffs[2 * e + 1] : 1.0;
+    double f[MAXFIELDS];
+    const int nf = metric_fields(p.space, g, wt, c0, c1, f);
+    TF *dst = reinterpret_cast<TF *>(p.fields) + (e * p.nfields) * L2 + pt;
+    for (int k = 0; k < nf; ++k) dst[(int64_t)k * L2] = flag ? qnan<TF>() : (TF)f[k];
+    if (flag) {
+        atomicMax(&p.estatus[e], flag);
+        report(p.status, flag, p.elem_base + e);
+    }
+}
+
 // --------------------------------------------------------------------------------------
 // general sum factorization
 // --------------------------------------------------------------------------------------
@@ -1019,12 +1063,22 @@ __device__ __forceinline__ int warp_append(int *count, bool keep) {
     return keep ? base + __popc(want & ((1u << lane) - 1u)) : -1;
 }
 
-template <typename T>
+// EXT = false: affine elements (Sec. 2.8.1, Algorithm 10), Q_g from exact 1D integrals and
+// the element's constant metric.  EXT = true: extruded elements (Algorithm 11), Q_g = the
+// stage-B result of a 2D sum factorization over (xi2, xi3): A_h[m][jj] = sum_{t in h} sum_n
+// M_t(m, n) S3_t(jj, n) (Eq. 2.23 on the 2D fields), Q_g[(i2,j2)][jj] = sum_{h in g} sum_m
+// P2_h[(i2,j2)][m] A_h[m][jj] (Eq. 2.24); stage C is the same Kronecker scatter with the
+// exact integrals F1 in both cases.
+template <typename T, bool EXT>
 __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockDesc bd;
     __shared__ T cf[MAXFIELDS];
     __shared__ int flag;
+    __shared__ signed char hterm[MAXH][MAXT], tfs[MAXT], fsrc[MAXT];   // EXT: h groups, field slots
+    __shared__ int hcount[MAXH];
+    __shared__ signed char ghl[MAXG][MAXH];
+    __shared__ int ghn[MAXG];
     __shared__ T st[MAXT * NJMAX];             // s_t = sign_t c_t F3_t(i3, j3) of the current unit
     __shared__ int f1c[MAXG], qc[MAXG];        // non-zero counts per group
     __shared__ signed char gt[MAXG][MAXT];     // terms of each group
@@ -1037,8 +1091,12 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     const int64_t e = blockIdx.x / (p.nblock * nsplit);
     if (e >= p.n_elem) return;
     load_block(p.blocks + k, bd);
-    if (tid < MAXFIELDS) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
-    if (tid == MAXFIELDS) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
+    if constexpr (!EXT) {
+        if (tid < MAXFIELDS) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
+        if (tid == MAXFIELDS) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
+    } else {
+        if (tid == 0) flag = p.estatus[e];
+    }
     if (tid < MAXG) f1c[tid] = 0;
     __syncthreads();
     if (tid == 0) {
@@ -1047,6 +1105,28 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             for (int t = 0; t < bd.nterm; ++t)
                 if (bd.h_g[bd.term[t].h] == g) gt[g][n++] = (signed char)t;
             gtn[g] = n;
+        }
+        if constexpr (EXT) {
+            for (int h = 0; h < bd.nh; ++h) {
+                int n = 0;
+                for (int t = 0; t < bd.nterm; ++t)
+                    if (bd.term[t].h == h) hterm[h][n++] = (signed char)t;
+                hcount[h] = n;
+            }
+            for (int g = 0; g < bd.ng; ++g) {
+                int n = 0;
+                for (int h = 0; h < bd.nh; ++h)
+                    if (bd.h_g[h] == g) ghl[g][n++] = (signed char)h;
+                ghn[g] = n;
+            }
+            int ns = 0;
+            for (int t = 0; t < bd.nterm; ++t) {
+                int sl = -1;
+                for (int u = 0; u < ns; ++u)
+                    if (fsrc[u] == bd.term[t].field) sl = u;
+                if (sl < 0) { sl = ns; fsrc[ns++] = (signed char)bd.term[t].field; }
+                tfs[t] = (signed char)sl;
+            }
         }
     }
 
@@ -1079,11 +1159,32 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             f1i[g * n11 + slot] = i1 * lay.ldt + j1;
         }
     }
-    for (int it = tid; it < nterm * n22; it += nth) {                   // F2_t(i2, j2)
-        const int t = fdiv(it, mn22t), ij = it - t * n22;
-        const TermDesc &td = bd.term[t];
-        const int i2 = fdiv(ij, mnc2);
-        F2[it] = Fv(3 * td.kr[1] + td.kc[1], i2, ij - i2 * nc2);
+    const int L = p.L, L2 = L * L;
+    [[maybe_unused]] T *Fx = nullptr, *S3 = nullptr, *Ah = nullptr, *P2 = nullptr;
+    if constexpr (!EXT) {
+        for (int it = tid; it < nterm * n22; it += nth) {               // F2_t(i2, j2)
+            const int t = fdiv(it, mn22t), ij = it - t * n22;
+            const TermDesc &td = bd.term[t];
+            const int i2 = fdiv(ij, mnc2);
+            F2[it] = Fv(3 * td.kr[1] + td.kc[1], i2, ij - i2 * nc2);
+        }
+    } else {
+        const ExtLayout xl = ext_layout(bd, L, njm);
+        Fx = reinterpret_cast<T *>(smem_raw) + xl.oFx;                 // [nfs][L][L]
+        S3 = reinterpret_cast<T *>(smem_raw) + xl.oS3;                 // [nterm][nj][L]
+        Ah = reinterpret_cast<T *>(smem_raw) + xl.oA;                  // [nh][L][nj]
+        P2 = reinterpret_cast<T *>(smem_raw) + xl.oP2;                 // [np2][n22][L]
+        __syncthreads();                                               // fsrc, tfs
+        const T *src = p.xfields + (size_t)e * p.nfields * L2;
+        for (int it = tid; it < xl.nfs * L2; it += nth) {
+            const int sl = it / L2;
+            Fx[it] = src[(size_t)fsrc[sl] * L2 + (it - sl * L2)];
+        }
+        for (int it = tid; it < bd.np2 * n22 * L; it += nth) {
+            const int r = it / L, m = it - r * L, s2 = r / n22, ij = r - s2 * n22;
+            const int i2 = fdiv(ij, mnc2);
+            P2[it] = p.pp[(((size_t)bd.p2_pair[s2] * NQ1 + i2) * NQ1 + ij - i2 * nc2) * L + m];
+        }
     }
 
     T *o = p.out + (size_t)e * p.mat_stride + bd.base;
@@ -1097,13 +1198,23 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         const unsigned mnj = div_magic(nj);
         const int ldt = lay.ldt;
         __syncthreads();                                                // previous unit done
-        for (int it = tid; it < nterm * nj; it += nth) {
-            const int t = fdiv(it, mnj), jj = it - t * nj;
-            const TermDesc &td = bd.term[t];
-            const T f3 = Fv(3 * td.kr[2] + td.kc[2], i3, j3b + jj);
-            st[it] = is_zero(f3) ? T(0) : (td.sign > 0 ? cf[td.field] : -cf[td.field]) * f3;
+        if constexpr (!EXT) {
+            for (int it = tid; it < nterm * nj; it += nth) {
+                const int t = fdiv(it, mnj), jj = it - t * nj;
+                const TermDesc &td = bd.term[t];
+                const T f3 = Fv(3 * td.kr[2] + td.kc[2], i3, j3b + jj);
+                st[it] = is_zero(f3) ? T(0) : (td.sign > 0 ? cf[td.field] : -cf[td.field]) * f3;
+            }
+            if (tid < MAXG) qc[tid] = 0;
+        } else {
+            for (int it = tid; it < nterm * nj * L; it += nth) {      // S3_t(jj, n), sign folded in
+                const int r = it / L, n = it - r * L, t = fdiv(r, mnj), jj = r - t * nj;
+                const TermDesc &td = bd.term[t];
+                const T v = p.pp[(((size_t)(3 * td.kr[2] + td.kc[2]) * NQ1 + i3) * NQ1 + j3b + jj) * L + n];
+                S3[it] = td.sign > 0 ? v : -v;
+            }
+            if (tid < MAXG) qc[tid] = n22 * nj;
         }
-        if (tid < MAXG) qc[tid] = 0;
         {
             float4 *t4 = reinterpret_cast<float4 *>(tile);            // tile is 16-byte aligned
             const int n4 = (int)((nrow * ldt * sizeof(T)) / 16);
@@ -1111,7 +1222,38 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             for (int it = n4 * (16 / (int)sizeof(T)) + tid; it < nrow * ldt; it += nth) tile[it] = T(0);
         }
         __syncthreads();
+        if constexpr (EXT) {
+            // stage A over xi3 (Eq. 2.23 on the 2D fields): A_h[m][jj]
+            for (int it = tid; it < bd.nh * L * nj; it += nth) {
+                const int r = fdiv(it, mnj), jj = it - r * nj, h = r / L, m = r - h * L;
+                T acc = T(0);
+                for (int ti = 0; ti < hcount[h]; ++ti) {
+                    const int t = hterm[h][ti];
+                    const T *M = Fx + tfs[t] * L2 + m * L;
+                    const T *s3 = S3 + (t * nj + jj) * L;
+                    for (int n = 0; n < L; ++n) acc = fma(M[n], s3[n], acc);
+                }
+                Ah[it] = acc;
+            }
+            __syncthreads();
+            // stage B over xi2 (Eq. 2.24): Q_g[(i2,j2)][jj], dense, at its tile offset
+            for (int it = tid; it < ng * n22 * nj; it += nth) {
+                const int r = fdiv(it, mnj), jj = it - r * nj;
+                const int g = fdiv(r, mn22), ij2 = r - g * n22;
+                T acc = T(0);
+                for (int hi = 0; hi < ghn[g]; ++hi) {
+                    const int h = ghl[g][hi];
+                    const T *p2 = P2 + (bd.h_p2[h] * n22 + ij2) * L;
+                    const T *a = Ah + h * L * nj + jj;
+                    for (int m = 0; m < L; ++m) acc = fma(p2[m], a[m * nj], acc);
+                }
+                const int i2 = fdiv(ij2, mnc2), j2 = ij2 - i2 * nc2;
+                qv[g * n22 * njm + ij2 * nj + jj] = acc;
+                qi[g * n22 * njm + ij2 * nj + jj] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
+            }
+        }
         // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2), kept as a list of its non-zeros
+        if constexpr (!EXT)
         for (int it = tid; it < ng * n22 * nj; it += nth) {
             const int r = fdiv(it, mnj), jj = it - r * nj;
             const int g = fdiv(r, mn22), ij2 = r - g * n22;
@@ -1496,11 +1638,33 @@ template <typename T>
 cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s) {
     const int64_t ctas = (int64_t)p.nblock * p.nsplit * p.n_elem;
     if (ctas == 0) return cudaSuccess;
-    sf_affine_kernel<T><<<(unsigned)ctas, 256, smem, s>>>(p);
+    sf_affine_kernel<T, false><<<(unsigned)ctas, 256, smem, s>>>(p);
     return cudaGetLastError();
 }
 template cudaError_t launch_affine<double>(const AffParams<double> &, size_t, cudaStream_t);
 template cudaError_t launch_affine<float>(const AffParams<float> &, size_t, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_extruded(const AffParams<T> &p, size_t smem, cudaStream_t s) {
+    const int64_t ctas = (int64_t)p.nblock * p.nsplit * p.n_elem;
+    if (ctas == 0) return cudaSuccess;
+    sf_affine_kernel<T, true><<<(unsigned)ctas, 256, smem, s>>>(p);
+    return cudaGetLastError();
+}
+template cudaError_t launch_extruded<double>(const AffParams<double> &, size_t, cudaStream_t);
+template cudaError_t launch_extruded<float>(const AffParams<float> &, size_t, cudaStream_t);
+
+template <typename TF>
+cudaError_t launch_geom2d(const Geom2dParams &p, cudaStream_t s) {
+    const int64_t n = p.n_elem * (int64_t)p.L * p.L;
+    if (n == 0) return cudaSuccess;
+    geom2d_kernel<TF><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+template cudaError_t launch_geom2d<double>(const Geom2dParams &, cudaStream_t);
+template cudaError_t launch_geom2d<float>(const Geom2dParams &, cudaStream_t);
+
+size_t extruded_smem_values(const BlockDesc &b, int L, int nj) { return (size_t)ext_layout(b, L, nj).total; }
 
 // Opt every kernel into the large shared-memory carve-out once per device (host call,
 // done at table set-up so that integration calls stay pure launches).
@@ -1521,8 +1685,10 @@ cudaError_t init_kernel_attributes(int optin_smem) {
     if (e == cudaSuccess) e = one((const void *)sf_general_f32_kernel<4>);
     if (e == cudaSuccess) e = one((const void *)sf_panel_f32_kernel<8>);
     if (e == cudaSuccess) e = one((const void *)sf_panel_f32_kernel<16>);
-    if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<double>);
-    if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<float>);
+    if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<double, false>);
+    if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<float, false>);
+    if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<double, true>);
+    if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<float, true>);
     return e;
 }
 
@@ -1530,7 +1696,7 @@ cudaError_t init_kernel_attributes(int optin_smem) {
 int max_dynamic_smem(int optin_smem) {
     cudaFuncAttributes a, b;
     if (cudaFuncGetAttributes(&a, (const void *)sf_general_kernel<double>) != cudaSuccess) return 0;
-    if (cudaFuncGetAttributes(&b, (const void *)sf_affine_kernel<double>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&b, (const void *)sf_affine_kernel<double, true>) != cudaSuccess) return 0;
     return optin_smem - (int)(a.sharedSizeBytes > b.sharedSizeBytes ? a.sharedSizeBytes : b.sharedSizeBytes);
 }
 

@@ -103,9 +103,26 @@ struct AffParams {
     int nblock, nj_max;
     int nsplit;                    // CTAs per (element, block): each takes every nsplit-th unit
     const T *F;                // exact 1D integrals [NPAIR][NQ1][NQ1]
-    const double *consts;      // [n_elem][AFF_CONST_STRIDE] from affine_const_kernel
+    const double *consts;      // [n_elem][AFF_CONST_STRIDE] from affine_const_kernel (affine)
+    // extruded maps: 2D metric fields [n_elem][nfields][L][L] (xi2, xi3) from geom2d_kernel,
+    // per-element status, pair products at the Gauss points [NPAIR][NQ1][NQ1][L]
+    const T *xfields;
+    const int *estatus;
+    const T *pp;
+    int L, nfields;
     T *out;
     int64_t mat_stride, ld, n_elem;
+};
+
+// Geometry of extruded elements: metric fields at the (xi2, xi3) Gauss points.
+struct Geom2dParams {
+    int space, L, nfields;
+    int64_t n_elem, elem_base;
+    const double *verts, *coeffs;
+    const double *zeta, *w;
+    void *fields;              // [n_elem][nfields][L][L] of the stage type
+    int *estatus;              // [n_elem], zeroed by the caller; set to the element's error
+    DevStatus *status;
 };
 
 // hp batching: per-q programs in device memory, indexed by q (entry 0 unused).
@@ -149,6 +166,9 @@ cudaError_t init_tc_attributes(int optin_smem);
 int tc_static_smem();
 cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s);
+template <typename T> cudaError_t launch_extruded(const AffParams<T> &p, size_t smem, cudaStream_t s);
+template <typename TF> cudaError_t launch_geom2d(const Geom2dParams &p, cudaStream_t s);
+size_t extruded_smem_values(const BlockDesc &b, int L, int nj);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
 cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);

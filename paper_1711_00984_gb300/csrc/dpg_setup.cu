@@ -356,8 +356,8 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             // ORDER_A3 keeps stage A on xi_3, ORDER_NATURAL keeps the paper's order
             static const int perms[6][3] = { { 0, 1, 2 }, { 1, 0, 2 }, { 0, 2, 1 },
                                              { 2, 0, 1 }, { 1, 2, 0 }, { 2, 1, 0 } };
-            const int nperm = (order == ORDER_NATURAL || order == ORDER_PANEL || order == ORDER_TC) ? 1
-                                                                                                  : (order == ORDER_A3 ? 2 : 6);
+            const int nperm = (order == ORDER_NATURAL || order == ORDER_PANEL || order == ORDER_TC ||
+                               order == ORDER_EXTRUDED) ? 1 : (order == ORDER_A3 ? 2 : 6);
             double best = 0.0; int bi = 0;
             for (int k = 0; k < nperm; ++k) {
                 finish_block(bd, ts, perms[k]);
@@ -379,6 +379,7 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
         }
         if (order == ORDER_NATURAL)
             return (size_t)aff_layout(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], njv).total * sizeof(double);
+        if (order == ORDER_EXTRUDED) return (size_t)ext_layout(b, L, njv).total * sizeof(double);
         return smem_values(b, L, njv) * sizeof(double);
     };
     // (ORDER_PANEL: the largest chunk that fits one CTA per SM; the launch takes two
@@ -460,6 +461,24 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
         }
     }
     pr.flops_affine = aff;
+
+    // extruded-map path: per (i3, j3) tile stage A over xi_3 (2D fields), stage B over xi_2,
+    // stage C by the exact 1D integrals of xi_1 (non-zero products only)
+    double ext = 0.0;
+    for (int k = 0; k < pr.nblock; ++k) {
+        const BlockDesc &b = pr.blocks[k];
+        const int dC = b.dir[0], dB = b.dir[1], dA = b.dir[2];
+        const double n22 = (double)b.nr[dB] * b.nc[dB];
+        double nzC = 0.0;
+        for (int g = 0; g < b.ng; ++g)
+            for (int i1 = 0; i1 < b.nr[dC]; ++i1)
+                for (int j1 = 0; j1 < b.nc[dC]; ++j1)
+                    if (Fv(b.g_pair[g], i1, j1) != 0.0) nzC += 1.0;
+        double tiles = 0.0;
+        for (int i3 = 0; i3 < b.nr[dA]; ++i3) tiles += b.sym == 1 ? b.nc[dA] - i3 : b.nc[dA];
+        ext += 2.0 * tiles * ((double)b.nterm * L * L + (double)b.nh * n22 * L + nzC * n22);
+    }
+    pr.flops_extruded = ext;
     return pr;
 }
 

@@ -27,6 +27,7 @@ struct Program {
     size_t smem_bytes = 0;         // shared memory of the kernel this program is built for
     double flops = 0.0;            // algorithmic flops per element, general path
     double flops_affine = 0.0;     // algorithmic flops per element, affine path
+    double flops_extruded = 0.0;   // algorithmic flops per element, extruded-map path
 };
 
 void gauss_rule(int L, double *z, double *w);
@@ -40,7 +41,8 @@ HostTables make_tables(int q, int L);
 // ORDER_TC: the same blocks as ORDER_PANEL, sized for the FP32 tensor-core (tcgen05)
 // kernel (tc_layout); a block that does not fit it makes the program's smem_bytes
 // SIZE_MAX.
-enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3, ORDER_TC = 4 };
+// ORDER_EXTRUDED: the paper's order, sized for the extruded-map kernel (ext_layout).
+enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3, ORDER_TC = 4, ORDER_EXTRUDED = 5 };
 // force_nj > 0 fixes the stage-A chunk (autotuner); otherwise the largest chunk whose
 // shared memory fits the kernel's budget (smem_budget bytes, or the order's default when
 // 0) is taken.

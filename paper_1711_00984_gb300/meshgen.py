@@ -16,6 +16,10 @@ Workloads (shapes follow the paper's element-level experiments, Sec. 3, scaled t
 * ``affine_parallelepipeds(n, seed)``: the same grid origins, each element mapped by
   ``x = x0 + h (I + S) xi`` with ``S`` off-diagonal ``U[-0.2, 0.2]`` (constant Jacobian,
   the case of Sec. 2.8.1 with a full matrix).
+* ``extruded_prisms(n, seed)``: a jittered ``n x n`` quadrilateral grid of the unit
+  square in (x2, x3) extruded along x1 in ``n`` layers of thickness ``h``: every element
+  has x1 = x1_0 + h xi1 and (x2, x3) a bilinear function of (xi2, xi3), the second
+  Jacobian form of Eq. 2.89.  Interior 2D vertices move by ``U[-0.1h, 0.1h]^2``.
 * per-element coefficient ``k_e ~ U[0.5, 2]`` (the Poisson diffusivity of Eq. 3.9).
 
 Random draws use numpy's PCG64 (``numpy.random.default_rng``) in a fixed order, so every
@@ -89,6 +93,33 @@ def affine_parallelepipeds(n: int, seed: int, shear: float = 0.2, nz: int | None
     return np.ascontiguousarray(verts)
 
 
+def extruded_prisms(n: int, seed: int, jitter: float = 0.1, nz: int | None = None,
+                    rng: np.random.Generator | None = None) -> np.ndarray:
+    """Elements of an ``n x n`` jittered quadrilateral grid in (x2, x3) extruded along x1.
+
+    The 2D grid of [0,1]^2 has its interior vertices moved by ``U[-jitter*h, jitter*h]^2``
+    (one draw, vertex order with the x2 index fastest); the extrusion has ``nz`` (default
+    ``n``) uniform layers of thickness ``h`` along x1.  Element index
+    ``e = i1 + nz (i2 + n i3)`` for layer i1 and quadrilateral (i2, i3).  Returns
+    ``verts[n_elem, 8, 3]``.
+    """
+    rng = np.random.default_rng(seed) if rng is None else rng
+    nz = n if nz is None else nz
+    h = 1.0 / n
+    b, a = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")      # a: x2 index
+    q2 = np.stack([a * h, b * h], axis=-1).reshape(-1, 2).astype(np.float64)
+    interior = ((a > 0) & (a < n) & (b > 0) & (b < n)).reshape(-1)
+    q2[interior] += rng.uniform(-jitter * h, jitter * h, size=(int(interior.sum()), 2))
+    i3, i2, i1 = np.meshgrid(np.arange(n), np.arange(n), np.arange(nz), indexing="ij")
+    i1, i2, i3 = i1.reshape(-1), i2.reshape(-1), i3.reshape(-1)
+    verts = np.empty((i1.shape[0], 8, 3), dtype=np.float64)
+    for v in range(8):
+        c1, c2, c3 = CORNERS[v]
+        verts[:, v, 0] = (i1 + c1) * h
+        verts[:, v, 1:] = q2[(i2 + c2) + (n + 1) * (i3 + c3)]
+    return np.ascontiguousarray(verts)
+
+
 def uniform_coefficients(n_elem: int, rng: np.random.Generator, lo: float = 0.5,
                          hi: float = 2.0) -> np.ndarray:
     """Per-element scalar k_e ~ U[lo, hi]."""
@@ -152,7 +183,15 @@ def workload(name: str) -> dict:
         v = jittered_grid(8, seed=5, nz=4, rng=rng)
         va = affine_parallelepipeds(8, seed=5, nz=4, rng=rng)
         return dict(verts=v, verts_affine=va, k=None, q=9, L=11, spaces=["H1", "HDIV"])
+    if name == "ext_q5_8x8x8":
+        # the 8^3 mesh of seq_q5_8x8x8 as an extrusion: 8 layers along x1 of a jittered
+        # 8 x 8 quadrilateral grid, k_e ~ U[0.5, 2]
+        rng = np.random.default_rng(6)
+        v = extruded_prisms(8, seed=6, rng=rng)
+        k = uniform_coefficients(v.shape[0], rng)
+        return dict(verts=v, k=k, q=5, L=7, spaces=["H1", "HCURL", "HDIV", "L2"])
     raise KeyError(name)
 
 
-WORKLOADS = ["h1_q3_2x2x2", "seq_q5_8x8x8", "hcurl_q6_p4_16x16x16", "hp_q2to8_16x16x16", "q9_8x8x4"]
+WORKLOADS = ["h1_q3_2x2x2", "seq_q5_8x8x8", "hcurl_q6_p4_16x16x16", "hp_q2to8_16x16x16", "q9_8x8x4",
+             "ext_q5_8x8x8"]
