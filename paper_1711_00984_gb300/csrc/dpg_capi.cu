@@ -40,6 +40,8 @@ struct AffProg {
     BlockDesc *d_blocks = nullptr;
     Unit *d_units = nullptr;
     int *d_block_units = nullptr;   // [nblock + 1] unit ranges
+    unsigned char *d_img = nullptr; // constant shared-memory images of the blocks
+    int *d_img_off = nullptr;       // [nblock + 1], 16-byte units
     size_t smem_values = 0;         // values of the kernel's shared memory
 };
 
@@ -116,6 +118,18 @@ template <typename T>
 int upload(const T *src, size_t n, T **dst) {
     CK(cudaMalloc(dst, n * sizeof(T)));
     CK(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return DPG_OK;
+}
+
+// Device copy of the constant images of an affine / extruded program in precision prec.
+int upload_aff_image(AffProg &ap, const HostTables &tab, bool extruded, int prec) {
+    std::vector<unsigned char> img;
+    std::vector<int> off;
+    if (prec) build_aff_image<float>(ap.prog, tab, extruded, img, off);
+    else build_aff_image<double>(ap.prog, tab, extruded, img, off);
+    int r;
+    if ((r = upload(img.data(), img.size(), &ap.d_img))) return r;
+    if ((r = upload(off.data(), off.size(), &ap.d_img_off))) return r;
     return DPG_OK;
 }
 
@@ -240,10 +254,8 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         if ((r = upload(pa.blocks, (size_t)pa.nblock, &ap.d_blocks))) return r;
         if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
         size_t m = 0;
-        for (int k = 0; k < pa.nblock; ++k) {
-            const BlockDesc &b = pa.blocks[k];
-            m = std::max(m, affine_smem_values(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], pa.nj));
-        }
+        for (int k = 0; k < pa.nblock; ++k) m = std::max(m, affine_smem_values(pa.blocks[k], pa.nj));
+        if ((r = upload_aff_image(ap, tab, false, prec))) return r;
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
         for (int k = 0; k < pa.nblock; ++k) ub[k + 1] += ub[k];
@@ -266,6 +278,7 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
         size_t m = 0;
         for (int k = 0; k < pa.nblock; ++k) m = std::max(m, extruded_smem_values(pa.blocks[k], L, pa.nj));
+        if ((r = upload_aff_image(ap, tab, true, prec))) return r;
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
         for (int k = 0; k < pa.nblock; ++k) ub[k + 1] += ub[k];
@@ -323,8 +336,12 @@ void free_device_state(DeviceState &ds) {
     }
     for (auto &kv : ds.progs) {
         cudaFree(kv.second->d_blocks); cudaFree(kv.second->d_units);
-        for (AffProg &ap : kv.second->aff) { cudaFree(ap.d_blocks); cudaFree(ap.d_units); cudaFree(ap.d_block_units); }
-        for (AffProg &ap : kv.second->ext) { cudaFree(ap.d_blocks); cudaFree(ap.d_units); cudaFree(ap.d_block_units); }
+        for (AffProg *aps : { kv.second->aff, kv.second->ext })
+            for (int i = 0; i < 2; ++i) {
+                AffProg &ap = aps[i];
+                cudaFree(ap.d_blocks); cudaFree(ap.d_units); cudaFree(ap.d_block_units);
+                cudaFree(ap.d_img); cudaFree(ap.d_img_off);
+            }
         cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
         cudaFree(kv.second->d_ctab32); cudaFree(kv.second->d_ctab_off32);
     }
@@ -474,6 +491,19 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
     return rc;
 }
 
+// Elements per CTA of the affine / extruded kernels.  A CTA that would hold a single small
+// work unit (the block split over several CTAs, under 8000 output values per unit) takes
+// a chunk of up to four elements so that its block set-up is amortised, as long as about
+// four waves of three CTAs per SM remain; otherwise one element (longer CTAs would only
+// lengthen the tail).
+int aff_elems_per_cta(const Program &pr, int64_t n_elem, int nsplit) {
+    const double values_per_unit = (double)pr.parts * pr.rows * pr.cols / std::max<size_t>(pr.units.size(), 1);
+    if (nsplit == 1 || values_per_unit >= 8000.0) return 1;
+    const int64_t ctas_wanted = (int64_t)g_num_sms * 3 * 4;
+    const int64_t work = n_elem * pr.nblock * nsplit;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(work / ctas_wanted, 4));
+}
+
 template <typename T>
 int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
                const double *coeffs, T *out, cudaStream_t s) {
@@ -490,7 +520,9 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
     const int64_t target = (int64_t)g_num_sms * 6 * 4;
     const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_units_block,
                                               (target + n_elem * pr.nblock - 1) / (n_elem * pr.nblock)));
-    const int64_t per_launch = INT_MAX / ((int64_t)pr.nblock * nsplit);
+    // elements per CTA: about four waves of three CTAs per SM, the block set-up amortised
+    const int epc = aff_elems_per_cta(pr, n_elem, nsplit);
+    const int64_t per_launch = (int64_t)epc * (INT_MAX / ((int64_t)pr.nblock * nsplit));
     void *consts = nullptr;
     CK(cudaMallocFromPoolAsync(&consts, (size_t)n_elem * AFF_CONST_STRIDE * sizeof(double), ds->pool, s));
     AffConstParams cp;
@@ -503,7 +535,9 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         const int64_t ne = std::min(per_launch, n_elem - e0);
         AffParams<T> ap;
         ap.blocks = aprog.d_blocks; ap.units = aprog.d_units; ap.block_unit_begin = aprog.d_block_units;
-        ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit;
+        ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit; ap.elems_per_cta = epc;
+        ap.img = aprog.d_img; ap.img_off16 = aprog.d_img_off;
+        ap.xfields = nullptr; ap.estatus = nullptr; ap.pp = nullptr; ap.L = pr.L; ap.nfields = pr.nfields;
         if constexpr (sizeof(T) == 8) ap.F = te->F64; else ap.F = te->F32;
         ap.consts = (const double *)consts + AFF_CONST_STRIDE * e0;
         ap.out = out + e0 * mat;
@@ -537,7 +571,8 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
     const int64_t ne_all = std::min(chunk, n_elem);
     const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_units_block,
                                               (target + ne_all * pr.nblock - 1) / (ne_all * pr.nblock)));
-    chunk = std::min<int64_t>(chunk, INT_MAX / ((int64_t)pr.nblock * nsplit));
+    const int epc = aff_elems_per_cta(pr, ne_all, nsplit);
+    chunk = std::min<int64_t>(chunk, (int64_t)epc * (INT_MAX / ((int64_t)pr.nblock * nsplit)));
     if (chunk > n_elem) chunk = n_elem;
     void *ws = nullptr;
     CK(cudaMallocFromPoolAsync(&ws, (size_t)chunk * per_elem + 16, ds->pool, s));
@@ -559,7 +594,8 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         if (le != cudaSuccess) { rc = cuda_fail(le, "geom2d_kernel launch", __LINE__); break; }
         AffParams<T> ap;
         ap.blocks = aprog.d_blocks; ap.units = aprog.d_units; ap.block_unit_begin = aprog.d_block_units;
-        ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit;
+        ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit; ap.elems_per_cta = epc;
+        ap.img = aprog.d_img; ap.img_off16 = aprog.d_img_off;
         if constexpr (sizeof(T) == 8) { ap.F = te->F64; ap.pp = te->pp64; } else { ap.F = te->F32; ap.pp = te->pp32; }
         ap.consts = nullptr;
         ap.xfields = fields; ap.estatus = est;

@@ -67,6 +67,16 @@ struct BlockDesc {
     int g_pair[MAXG];        // pair type of each g group (dir1)
     int h_pair2[MAXH];       // pair type of each h group's dir2 pair
     int h_pair1[MAXH];       // pair type of each h group's dir1 pair
+    // lists derived from the above on the host, read by the kernels as they are
+    signed char g_terms[MAXG][MAXT];   // terms of each g group, in term order
+    signed char g_nterm[MAXG];
+    signed char h_terms[MAXH][MAXT];   // terms of each h group, in term order
+    signed char h_nterm[MAXH];
+    signed char g_hs[MAXG][MAXH];      // h groups of each g group, in h order
+    signed char g_nh[MAXG];
+    signed char term_slot[MAXT];       // slot of each term's metric field among the block's
+    signed char slot_field[MAXT];      // distinct fields (first-use order) and the field of
+    signed char nslot;                 // each slot
 };
 
 struct Unit {
@@ -102,35 +112,43 @@ DPG_HD inline F32Layout f32_layout(const BlockDesc &b, int L, int nj) {
 }
 
 // Shared-memory layout (in values of the output type, every region a multiple of 4) of the
-// affine kernel for one block and a chunk of nj partners: Q and its non-zero list, F2, the
-// non-zero stage-C factors, and the output tile [nrow][ldt].  Index lists are ints stored
-// in value-sized slots.
+// affine kernel for one block and a chunk of nj partners.  The constant part [0, oC) is a
+// per-block image built on the host (build_aff_image) and copied in one pass: the counts of
+// the non-zero stage-C factors per group (ints), their values and tile offsets
+// i1 ldt + j1 (ints), the stage-B factors F2 (affine: exact 1D integrals per term) or P2
+// (extruded maps: pair products at the Gauss points per dir-2 slot).  Then per unit: the
+// non-zero list of Q (values, tile offsets) and the output tile [nrow][ldt].  Index lists
+// are ints packed at the start of their value-sized regions.
 struct AffLayout {
-    int ldt, oQ, oF2, oQV, oQI, oF1V, oF1I, oT, total;
+    int ldt, oF1C, oF1V, oF1I, oF2, oP2, oC, oQV, oQI, oT, total;
 };
-DPG_HD inline AffLayout aff_layout(int ng, int nterm, int nr1, int nr2, int nc1, int nc2, int nj) {
+DPG_HD inline AffLayout aff_layout(int ng, int nr1, int nr2, int nc1, int nc2, int nj, int f2vals, int p2vals) {
     AffLayout a;
     const int n22 = nr2 * nc2, n11 = nr1 * nc1, nrow = nr1 * nr2, ncol = nc1 * nc2 * nj;
     a.ldt = ncol | 1;
-    a.oQ = 0;
-    a.oF2 = a.oQ + r4i(ng * n22 * nj);
-    a.oQV = a.oF2 + r4i(nterm * n22);
-    a.oQI = a.oQV + r4i(ng * n22 * nj);
-    a.oF1V = a.oQI + r4i(ng * n22 * nj);
+    a.oF1C = 0;
+    a.oF1V = a.oF1C + r4i(MAXG);
     a.oF1I = a.oF1V + r4i(ng * n11);
-    a.oT = a.oF1I + r4i(ng * n11);
+    a.oF2 = a.oF1I + r4i(ng * n11);
+    a.oP2 = a.oF2 + r4i(f2vals);
+    a.oC = a.oP2 + r4i(p2vals);
+    a.oQV = a.oC;
+    a.oQI = a.oQV + r4i(ng * n22 * nj);
+    a.oT = a.oQI + r4i(ng * n22 * nj);
     a.total = a.oT + r4i(nrow * a.ldt);
     return a;
 }
+DPG_HD inline AffLayout aff_layout_block(const BlockDesc &b, int nj) {
+    return aff_layout(b.ng, b.nr[0], b.nr[1], b.nc[0], b.nc[1], nj, b.nterm * b.nr[1] * b.nc[1], 0);
+}
 
 // Shared-memory layout (in values of the output type) of the extruded-map kernel: the
-// affine layout (Q as a dense list, the stage-C non-zeros, the output tile) followed by the
-// element's 2D metric fields of the block's terms [nfs][L][L], the stage-A factors of the
-// unit S3[t][jj][n], the stage-A output A[h][m][jj] and the stage-B pair products of the
-// block P2[slot][(i2,j2)][m].
+// affine layout with the stage-B pair products P2[slot][(i2,j2)][m] in its constant part
+// (and no F2), followed by the element's 2D metric fields of the block's terms [nfs][L][L],
+// the stage-A factors of the unit S3[t][jj][n] and the stage-A output A[h][m][jj].
 struct ExtLayout {
     AffLayout a;
-    int nfs, oFx, oS3, oA, oP2, total;
+    int nfs, oFx, oS3, oA, total;
 };
 DPG_HD inline int distinct_fields(const BlockDesc &b) {
     int n = 0;
@@ -143,13 +161,12 @@ DPG_HD inline int distinct_fields(const BlockDesc &b) {
 }
 DPG_HD inline ExtLayout ext_layout(const BlockDesc &b, int L, int nj) {
     ExtLayout x;
-    x.a = aff_layout(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], nj);
+    x.a = aff_layout(b.ng, b.nr[0], b.nr[1], b.nc[0], b.nc[1], nj, 0, b.np2 * b.nr[1] * b.nc[1] * L);
     x.nfs = distinct_fields(b);
     x.oFx = x.a.total;
     x.oS3 = x.oFx + r4i(x.nfs * L * L);
     x.oA = x.oS3 + r4i(b.nterm * nj * L);
-    x.oP2 = x.oA + r4i(b.nh * L * nj);
-    x.total = x.oP2 + r4i(b.np2 * b.nr[1] * b.nc[1] * L);
+    x.total = x.oA + r4i(b.nh * L * nj);
     return x;
 }
 

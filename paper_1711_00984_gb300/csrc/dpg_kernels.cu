@@ -1069,129 +1069,82 @@ __device__ __forceinline__ int warp_append(int *count, bool keep) {
 // M_t(m, n) S3_t(jj, n) (Eq. 2.23 on the 2D fields), Q_g[(i2,j2)][jj] = sum_{h in g} sum_m
 // P2_h[(i2,j2)][m] A_h[m][jj] (Eq. 2.24); stage C is the same Kronecker scatter with the
 // exact integrals F1 in both cases.
+template <typename T> struct Vec16;
+template <> struct Vec16<double> { using type = double2; };
+template <> struct Vec16<float> { using type = float4; };
+
 template <typename T, bool EXT>
 __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockDesc bd;
     __shared__ T cf[MAXFIELDS];
     __shared__ int flag;
-    __shared__ signed char hterm[MAXH][MAXT], tfs[MAXT], fsrc[MAXT];   // EXT: h groups, field slots
-    __shared__ int hcount[MAXH];
-    __shared__ signed char ghl[MAXG][MAXH];
-    __shared__ int ghn[MAXG];
+
     __shared__ T st[MAXT * NJMAX];             // s_t = sign_t c_t F3_t(i3, j3) of the current unit
-    __shared__ int f1c[MAXG], qc[MAXG];        // non-zero counts per group
-    __shared__ signed char gt[MAXG][MAXT];     // terms of each group
-    __shared__ int gtn[MAXG];
+    __shared__ int qc[MAXG];                   // non-zero counts of Q per group
+
     const int tid = threadIdx.x, nth = blockDim.x;
     // CTA = (element, block, share of the block's units): the block's tables are built once
     const int nsplit = p.nsplit;
     const int ks = blockIdx.x % (p.nblock * nsplit);
     const int k = ks / nsplit, split = ks - k * nsplit;
-    const int64_t e = blockIdx.x / (p.nblock * nsplit);
-    if (e >= p.n_elem) return;
+    const int64_t e0 = (int64_t)(blockIdx.x / (p.nblock * nsplit)) * p.elems_per_cta;
+    const int64_t e1 = min(e0 + (int64_t)p.elems_per_cta, p.n_elem);
+    if (e0 >= e1) return;
     load_block(p.blocks + k, bd);
-    if constexpr (!EXT) {
-        if (tid < MAXFIELDS) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
-        if (tid == MAXFIELDS) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
-    } else {
-        if (tid == 0) flag = p.estatus[e];
+    {                                   // the block's constant image, one coalesced copy
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.img) + p.img_off16[k];
+        uint4 *dst = reinterpret_cast<uint4 *>(smem_raw);
+        const int n16 = p.img_off16[k + 1] - p.img_off16[k];
+        for (int i = tid; i < n16; i += nth) dst[i] = src[i];
     }
-    if (tid < MAXG) f1c[tid] = 0;
     __syncthreads();
-    if (tid == 0) {
-        for (int g = 0; g < bd.ng; ++g) {
-            int n = 0;
-            for (int t = 0; t < bd.nterm; ++t)
-                if (bd.h_g[bd.term[t].h] == g) gt[g][n++] = (signed char)t;
-            gtn[g] = n;
-        }
-        if constexpr (EXT) {
-            for (int h = 0; h < bd.nh; ++h) {
-                int n = 0;
-                for (int t = 0; t < bd.nterm; ++t)
-                    if (bd.term[t].h == h) hterm[h][n++] = (signed char)t;
-                hcount[h] = n;
-            }
-            for (int g = 0; g < bd.ng; ++g) {
-                int n = 0;
-                for (int h = 0; h < bd.nh; ++h)
-                    if (bd.h_g[h] == g) ghl[g][n++] = (signed char)h;
-                ghn[g] = n;
-            }
-            int ns = 0;
-            for (int t = 0; t < bd.nterm; ++t) {
-                int sl = -1;
-                for (int u = 0; u < ns; ++u)
-                    if (fsrc[u] == bd.term[t].field) sl = u;
-                if (sl < 0) { sl = ns; fsrc[ns++] = (signed char)bd.term[t].field; }
-                tfs[t] = (signed char)sl;
-            }
-        }
-    }
 
     const int nr1 = bd.nr[0], nr2 = bd.nr[1], nc1 = bd.nc[0], nc2 = bd.nc[1];
     const int ng = bd.ng, nterm = bd.nterm, njm = p.nj_max;
     const int n11 = nr1 * nc1, n22 = nr2 * nc2, ncj = nc1 * nc2, nrow = nr1 * nr2;
     const T *F = p.F;
     auto Fv = [&](int pair, int i, int j) -> T { return F[((size_t)pair * NQ1 + i) * NQ1 + j]; };
-    const AffLayout lay = aff_layout(ng, nterm, nr1, nr2, nc1, nc2, njm);
-    T *Q = reinterpret_cast<T *>(smem_raw) + lay.oQ;                   // [ng][nr2][nc2][nj]
-    T *F2 = reinterpret_cast<T *>(smem_raw) + lay.oF2;                 // [nterm][nr2][nc2]
+    const int L = p.L, L2 = L * L;
+    const AffLayout lay = EXT ? ext_layout(bd, L, njm).a : aff_layout_block(bd, njm);
+    const T *F2 = reinterpret_cast<const T *>(smem_raw) + lay.oF2;     // [nterm][nr2][nc2] (affine)
+    const T *P2 = reinterpret_cast<const T *>(smem_raw) + lay.oP2;     // [np2][n22][L] (extruded)
     T *qv = reinterpret_cast<T *>(smem_raw) + lay.oQV;                 // [ng][n22 nj] non-zero Q
-    T *f1v = reinterpret_cast<T *>(smem_raw) + lay.oF1V;               // [ng][n11] non-zero F1
+    const T *f1v = reinterpret_cast<const T *>(smem_raw) + lay.oF1V;   // [ng][n11] non-zero F1
     T *tile = reinterpret_cast<T *>(smem_raw) + lay.oT;                // [nrow][ldt]
     // tile offsets of the non-zeros: a product F1(i1,j1) Q(i2,j2,jj) lands at
     // (i1 ldt + j1) + (nr1 i2 ldt + nc1 (j2 + nc2 jj))
     int *qi = reinterpret_cast<int *>(reinterpret_cast<T *>(smem_raw) + lay.oQI);
-    int *f1i = reinterpret_cast<int *>(reinterpret_cast<T *>(smem_raw) + lay.oF1I);
-    const unsigned mnc1 = div_magic(nc1), mnc2 = div_magic(nc2), mn22 = div_magic(n22);
-
-    // stage-C factors: compact non-zero lists per group
-    const unsigned mn11 = div_magic(n11), mn22t = div_magic(n22);
-    for (int it = tid; it < ng * n11; it += nth) {
-        const int g = fdiv(it, mn11), ij = it - g * n11;
-        const int i1 = fdiv(ij, mnc1), j1 = ij - i1 * nc1;
-        const T v = Fv(bd.g_pair[g], i1, j1);
-        const int slot = warp_append(&f1c[g], !is_zero(v));
-        if (slot >= 0) {
-            f1v[g * n11 + slot] = v;
-            f1i[g * n11 + slot] = i1 * lay.ldt + j1;
-        }
-    }
-    const int L = p.L, L2 = L * L;
-    [[maybe_unused]] T *Fx = nullptr, *S3 = nullptr, *Ah = nullptr, *P2 = nullptr;
-    if constexpr (!EXT) {
-        for (int it = tid; it < nterm * n22; it += nth) {               // F2_t(i2, j2)
-            const int t = fdiv(it, mn22t), ij = it - t * n22;
-            const TermDesc &td = bd.term[t];
-            const int i2 = fdiv(ij, mnc2);
-            F2[it] = Fv(3 * td.kr[1] + td.kc[1], i2, ij - i2 * nc2);
-        }
-    } else {
+    const int *f1i = reinterpret_cast<const int *>(reinterpret_cast<const T *>(smem_raw) + lay.oF1I);
+    const int *f1c = reinterpret_cast<const int *>(reinterpret_cast<const T *>(smem_raw) + lay.oF1C);
+    const unsigned mnc2 = div_magic(nc2), mn22 = div_magic(n22);
+    [[maybe_unused]] T *Fx = nullptr, *S3 = nullptr, *Ah = nullptr;
+    if constexpr (EXT) {
         const ExtLayout xl = ext_layout(bd, L, njm);
         Fx = reinterpret_cast<T *>(smem_raw) + xl.oFx;                 // [nfs][L][L]
         S3 = reinterpret_cast<T *>(smem_raw) + xl.oS3;                 // [nterm][nj][L]
         Ah = reinterpret_cast<T *>(smem_raw) + xl.oA;                  // [nh][L][nj]
-        P2 = reinterpret_cast<T *>(smem_raw) + xl.oP2;                 // [np2][n22][L]
-        __syncthreads();                                               // fsrc, tfs
-        const T *src = p.xfields + (size_t)e * p.nfields * L2;
-        for (int it = tid; it < xl.nfs * L2; it += nth) {
-            const int sl = it / L2;
-            Fx[it] = src[(size_t)fsrc[sl] * L2 + (it - sl * L2)];
-        }
-        for (int it = tid; it < bd.np2 * n22 * L; it += nth) {
-            const int r = it / L, m = it - r * L, s2 = r / n22, ij = r - s2 * n22;
-            const int i2 = fdiv(ij, mnc2);
-            P2[it] = p.pp[(((size_t)bd.p2_pair[s2] * NQ1 + i2) * NQ1 + ij - i2 * nc2) * L + m];
-        }
     }
 
-    T *o = p.out + (size_t)e * p.mat_stride + bd.base;
     const int64_t ld = p.ld;
-    const bool bad = flag != 0;
     const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
     const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
+    for (int64_t e = e0; e < e1; ++e) {                               // the CTA's chunk of elements
+    __syncthreads();                                                  // previous element done
+    if constexpr (!EXT) {                                             // the element's constants
+        if (tid < MAXFIELDS) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
+        if (tid == MAXFIELDS) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
+    } else {                                                          // its 2D metric fields
+        if (tid == 0) flag = p.estatus[e];
+        const T *src = p.xfields + (size_t)e * p.nfields * L2;
+        for (int it = tid; it < bd.nslot * L2; it += nth) {
+            const int sl = it / L2;
+            Fx[it] = src[(size_t)bd.slot_field[sl] * L2 + (it - sl * L2)];
+        }
+    }
+    __syncthreads();
+    T *o = p.out + (size_t)e * p.mat_stride + bd.base;
+    const bool bad = flag != 0;
     for (int ui = ub + split; ui < ue; ui += nsplit) {               // this CTA's share of the units
         const Unit u = p.units[ui];
         const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
@@ -1227,9 +1180,9 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             for (int it = tid; it < bd.nh * L * nj; it += nth) {
                 const int r = fdiv(it, mnj), jj = it - r * nj, h = r / L, m = r - h * L;
                 T acc = T(0);
-                for (int ti = 0; ti < hcount[h]; ++ti) {
-                    const int t = hterm[h][ti];
-                    const T *M = Fx + tfs[t] * L2 + m * L;
+                for (int ti = 0; ti < bd.h_nterm[h]; ++ti) {
+                    const int t = bd.h_terms[h][ti];
+                    const T *M = Fx + bd.term_slot[t] * L2 + m * L;
                     const T *s3 = S3 + (t * nj + jj) * L;
                     for (int n = 0; n < L; ++n) acc = fma(M[n], s3[n], acc);
                 }
@@ -1241,8 +1194,8 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
                 const int r = fdiv(it, mnj), jj = it - r * nj;
                 const int g = fdiv(r, mn22), ij2 = r - g * n22;
                 T acc = T(0);
-                for (int hi = 0; hi < ghn[g]; ++hi) {
-                    const int h = ghl[g][hi];
+                for (int hi = 0; hi < bd.g_nh[g]; ++hi) {
+                    const int h = bd.g_hs[g][hi];
                     const T *p2 = P2 + (bd.h_p2[h] * n22 + ij2) * L;
                     const T *a = Ah + h * L * nj + jj;
                     for (int m = 0; m < L; ++m) acc = fma(p2[m], a[m * nj], acc);
@@ -1259,9 +1212,9 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             const int g = fdiv(r, mn22), ij2 = r - g * n22;
             T acc = T(0);
             bool any = false;
-            const int ngt = gtn[g];
+            const int ngt = bd.g_nterm[g];
             for (int k2 = 0; k2 < ngt; ++k2) {
-                const int t = gt[g][k2];
+                const int t = bd.g_terms[g][k2];
                 const T sv = st[t * nj + jj];
                 if (is_zero(sv)) continue;
                 const T f2 = F2[t * n22 + ij2];
@@ -1298,14 +1251,30 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
         const T nanv = qnan<T>();
         const int ncolu = ncj * nj, cb = jd * ncj;
+        // 16-byte vector stores of VW values where the destination is aligned, plain stores
+        // for the unaligned head and the tail of each run
+        constexpr int VW = 16 / (int)sizeof(T);
+        using V16 = typename Vec16<T>::type;
         for (int row = warp; row < nrow; row += nwarp) {
             T *orow = o + (R0 + row) * ld + C0;
             const T *trw = tile + row * ldt;
-            for (int c = lane; c < ncolu; c += 32) {
+            auto val = [&](int c) -> T {
                 T v = trw[c];
                 const unsigned cc = (unsigned)(c - cb);
                 if (jd >= 0 && cc < (unsigned)row) v = tile[cc * ldt + cb + row];
-                orow[c] = bad ? nanv : v;
+                return bad ? nanv : v;
+            };
+            const int head = min((int)((VW - (int)((reinterpret_cast<uintptr_t>(orow) / sizeof(T)) % VW)) % VW), ncolu);
+            const int nvec = (ncolu - head) / VW, tail0 = head + VW * nvec;
+            if (lane < head) orow[lane] = val(lane);
+            if (lane < ncolu - tail0) orow[tail0 + lane] = val(tail0 + lane);
+            V16 *o16 = reinterpret_cast<V16 *>(orow + head);
+            for (int i = lane; i < nvec; i += 32) {
+                V16 w;
+                T *wv = reinterpret_cast<T *>(&w);
+#pragma unroll
+                for (int x = 0; x < VW; ++x) wv[x] = val(head + VW * i + x);
+                o16[i] = w;
             }
         }
         if (bd.sym != 0) {
@@ -1314,6 +1283,8 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             const int nmc = jd >= 0 ? ncolu - ncj : ncolu;
             T *mbase = o + C0 * ld + R0;
             if (nrow >= 64) {                                   // long runs: a warp per column
+                // (plain stores: lanes reading consecutive tile rows keep the shared-memory
+                // reads conflict-free, which measured faster than 16-byte stores here)
                 for (int mcix = warp; mcix < nmc; mcix += nwarp) {
                     const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
                     T *mrow = mbase + (int64_t)c * ld;
@@ -1329,11 +1300,10 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             }
         }
     }
+    }                                                                 // element loop
 }
 
-size_t affine_smem_values(int ng, int nterm, int nr1, int nr2, int nc1, int nc2, int nj) {
-    return (size_t)aff_layout(ng, nterm, nr1, nr2, nc1, nc2, nj).total;
-}
+size_t affine_smem_values(const BlockDesc &b, int nj) { return (size_t)aff_layout_block(b, nj).total; }
 
 
 // --------------------------------------------------------------------------------------
@@ -1636,7 +1606,7 @@ cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s) {
-    const int64_t ctas = (int64_t)p.nblock * p.nsplit * p.n_elem;
+    const int64_t ctas = (int64_t)p.nblock * p.nsplit * ((p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta);
     if (ctas == 0) return cudaSuccess;
     sf_affine_kernel<T, false><<<(unsigned)ctas, 256, smem, s>>>(p);
     return cudaGetLastError();
@@ -1646,7 +1616,7 @@ template cudaError_t launch_affine<float>(const AffParams<float> &, size_t, cuda
 
 template <typename T>
 cudaError_t launch_extruded(const AffParams<T> &p, size_t smem, cudaStream_t s) {
-    const int64_t ctas = (int64_t)p.nblock * p.nsplit * p.n_elem;
+    const int64_t ctas = (int64_t)p.nblock * p.nsplit * ((p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta);
     if (ctas == 0) return cudaSuccess;
     sf_affine_kernel<T, true><<<(unsigned)ctas, 256, smem, s>>>(p);
     return cudaGetLastError();

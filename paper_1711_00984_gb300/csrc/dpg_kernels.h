@@ -101,8 +101,11 @@ struct AffParams {
     const Unit *units;
     const int *block_unit_begin;   // [nblock + 1]
     int nblock, nj_max;
-    int nsplit;                    // CTAs per (element, block): each takes every nsplit-th unit
+    int nsplit;                    // CTAs per (element chunk, block): each takes every nsplit-th unit
+    int elems_per_cta;             // elements of a CTA's chunk
     const T *F;                // exact 1D integrals [NPAIR][NQ1][NQ1]
+    const void *img;           // constant shared-memory images of the blocks (build_aff_image)
+    const int *img_off16;      // [nblock + 1], in 16-byte units
     const double *consts;      // [n_elem][AFF_CONST_STRIDE] from affine_const_kernel (affine)
     // extruded maps: 2D metric fields [n_elem][nfields][L][L] (xi2, xi3) from geom2d_kernel,
     // per-element status, pair products at the Gauss points [NPAIR][NQ1][NQ1][L]
@@ -172,7 +175,7 @@ size_t extruded_smem_values(const BlockDesc &b, int L, int nj);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
 cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);
-size_t affine_smem_values(int ng, int nterm, int nr1, int nr2, int nc1, int nc2, int nj);
+size_t affine_smem_values(const BlockDesc &b, int nj);
 int max_dynamic_smem(int optin_smem);
 
 }  // namespace dpg

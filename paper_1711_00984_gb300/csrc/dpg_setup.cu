@@ -215,6 +215,20 @@ static void finish_block(BlockDesc &b, const std::vector<TermSpec> &ts, const in
         }
         d.h = hmap[key];
     }
+    for (int g = 0; g < MAXG; ++g) b.g_nterm[g] = b.g_nh[g] = 0;
+    for (int h = 0; h < MAXH; ++h) b.h_nterm[h] = 0;
+    b.nslot = 0;
+    for (int t = 0; t < b.nterm; ++t) {
+        const int h = b.term[t].h, g = b.h_g[h];
+        b.g_terms[g][b.g_nterm[g]++] = (signed char)t;
+        b.h_terms[h][b.h_nterm[h]++] = (signed char)t;
+        int sl = -1;
+        for (int u = 0; u < b.nslot; ++u)
+            if (b.slot_field[u] == b.term[t].field) sl = u;
+        if (sl < 0) { sl = b.nslot; b.slot_field[b.nslot++] = (signed char)b.term[t].field; }
+        b.term_slot[t] = (signed char)sl;
+    }
+    for (int h = 0; h < b.nh; ++h) b.g_hs[b.h_g[h]][b.g_nh[b.h_g[h]]++] = (signed char)h;
 }
 
 // Multiply-adds of one block of the general path: per tile (iA, jA) stage A costs
@@ -377,8 +391,7 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             const TcLayout t = tc_layout(b, L, njv);
             return t.ok ? (size_t)t.total : SIZE_MAX;
         }
-        if (order == ORDER_NATURAL)
-            return (size_t)aff_layout(b.ng, b.nterm, b.nr[0], b.nr[1], b.nc[0], b.nc[1], njv).total * sizeof(double);
+        if (order == ORDER_NATURAL) return (size_t)aff_layout_block(b, njv).total * sizeof(double);
         if (order == ORDER_EXTRUDED) return (size_t)ext_layout(b, L, njv).total * sizeof(double);
         return smem_values(b, L, njv) * sizeof(double);
     };
@@ -576,5 +589,55 @@ void build_tc_tables(const Program &pr, const HostTables &tab, std::vector<float
     }
     if (ctab.empty()) ctab.push_back(0.0f);
 }
+
+template <typename T>
+void build_aff_image(const Program &pr, const HostTables &tab, bool extruded, std::vector<unsigned char> &img,
+                     std::vector<int> &off16) {
+    img.clear();
+    off16.assign(pr.nblock + 1, 0);
+    const int L = pr.L;
+    auto Fv = [&](int pair, int i, int j) { return (T)tab.F[((size_t)pair * NQ1 + i) * NQ1 + j]; };
+    auto ppv = [&](int pair, int i, int j, int l) { return (T)tab.pp[(((size_t)pair * NQ1 + i) * NQ1 + j) * L + l]; };
+    for (int k = 0; k < pr.nblock; ++k) {
+        const BlockDesc &b = pr.blocks[k];
+        const AffLayout a = extruded ? ext_layout(b, L, pr.nj).a : aff_layout_block(b, pr.nj);
+        off16[k] = (int)(img.size() / 16);
+        std::vector<unsigned char> t((size_t)a.oC * sizeof(T), 0);
+        T *tv = reinterpret_cast<T *>(t.data());
+        auto iat = [&](int off_values) { return reinterpret_cast<int *>(t.data() + (size_t)off_values * sizeof(T)); };
+        const int n11 = b.nr[0] * b.nc[0], n22 = b.nr[1] * b.nc[1];
+        // stage-C factors: the non-zero exact integrals F1_g(i1, j1), row-major order
+        for (int g = 0; g < b.ng; ++g) {
+            int c = 0;
+            for (int i1 = 0; i1 < b.nr[0]; ++i1)
+                for (int j1 = 0; j1 < b.nc[0]; ++j1) {
+                    const T v = Fv(b.g_pair[g], i1, j1);
+                    if (v != T(0)) {
+                        tv[a.oF1V + g * n11 + c] = v;
+                        iat(a.oF1I)[g * n11 + c] = i1 * a.ldt + j1;
+                        ++c;
+                    }
+                }
+            iat(a.oF1C)[g] = c;
+        }
+        if (!extruded)                                  // F2_t(i2, j2), exact integrals
+            for (int t2 = 0; t2 < b.nterm; ++t2)
+                for (int ij = 0; ij < n22; ++ij)
+                    tv[a.oF2 + t2 * n22 + ij] = Fv(3 * b.term[t2].kr[1] + b.term[t2].kc[1], ij / b.nc[1], ij % b.nc[1]);
+        else                                            // P2[slot][(i2, j2)][m] at the Gauss points
+            for (int s2 = 0; s2 < b.np2; ++s2)
+                for (int ij = 0; ij < n22; ++ij)
+                    for (int m = 0; m < L; ++m)
+                        tv[a.oP2 + (s2 * n22 + ij) * L + m] = ppv(b.p2_pair[s2], ij / b.nc[1], ij % b.nc[1], m);
+        t.resize((t.size() + 15) & ~size_t(15), 0);
+        img.insert(img.end(), t.begin(), t.end());
+    }
+    off16[pr.nblock] = (int)(img.size() / 16);
+    if (img.empty()) img.resize(16, 0);
+}
+template void build_aff_image<double>(const Program &, const HostTables &, bool, std::vector<unsigned char> &,
+                                      std::vector<int> &);
+template void build_aff_image<float>(const Program &, const HostTables &, bool, std::vector<unsigned char> &,
+                                     std::vector<int> &);
 
 }  // namespace dpg

@@ -57,6 +57,12 @@ void build_panel_tables(const Program &pr, const HostTables &tab, std::vector<fl
 // layout of tc_layout (the shared-memory image [0, oAh)); off[k] is the first float of
 // block k.
 void build_tc_tables(const Program &pr, const HostTables &tab, std::vector<float> &ctab, std::vector<int> &off);
+// Constant shared-memory image of the affine (extruded = false) or extruded-map kernel for
+// every block of an ORDER_NATURAL / ORDER_EXTRUDED program in the value type T: the region
+// [0, oC) of its layout; block k occupies bytes [16 off16[k], 16 off16[k + 1]).
+template <typename T>
+void build_aff_image(const Program &pr, const HostTables &tab, bool extruded, std::vector<unsigned char> &img,
+                     std::vector<int> &off16);
 int64_t rows_of(int space, int q);
 int64_t cols_of(int space, int p, int q);
 

@@ -183,12 +183,6 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
     extern __shared__ __align__(1024) unsigned char smb[];
     __shared__ BlockDesc bd;
     __shared__ TcLayout f;
-    __shared__ signed char hterm[MAXH][MAXT];
-    __shared__ int hcount[MAXH];
-    __shared__ signed char gh[MAXG][MAXH];
-    __shared__ int ghcount[MAXG];
-    __shared__ signed char tfs[MAXT];               // staged-field slot of each term
-    __shared__ signed char fsrc[MAXT];              // metric field of each slot
     __shared__ int rsh[2][TC_MAXROW];               // tile row r of unit parity u at float r ldt + shift
     __shared__ uint32_t tslot;
     // mbarriers (the first three per unit parity): A_h written, stage B done, stage-B
@@ -218,26 +212,6 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
 
     if (tid == 0) {
         f = tc_layout(bd, p.L, p.nj_max);
-        for (int h = 0; h < bd.nh; ++h) {
-            int n = 0;
-            for (int t = 0; t < bd.nterm; ++t)
-                if (bd.term[t].h == h) hterm[h][n++] = (signed char)t;
-            hcount[h] = n;
-        }
-        for (int g = 0; g < bd.ng; ++g) {
-            int n = 0;
-            for (int h = 0; h < bd.nh; ++h)
-                if (bd.h_g[h] == g) gh[g][n++] = (signed char)h;
-            ghcount[g] = n;
-        }
-        int ns = 0;
-        for (int t = 0; t < bd.nterm; ++t) {
-            int sl = -1;
-            for (int u = 0; u < ns; ++u)
-                if (fsrc[u] == bd.term[t].field) sl = u;
-            if (sl < 0) { sl = ns; fsrc[ns++] = (signed char)bd.term[t].field; }
-            tfs[t] = (signed char)sl;
-        }
         fail = 0;
         mbar_init(&bar_ah[0], TC_NP);
         mbar_init(&bar_ah[1], TC_NP);
@@ -377,7 +351,7 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
             if (e != fe_loaded) {                  // metric fields of the element's terms
                 const float *src = p.fields + (size_t)e * p.nfields * L3;
                 for (int sl = 0; sl < f.nfs; ++sl) {
-                    const float *fs = src + (size_t)fsrc[sl] * L3;
+                    const float *fs = src + (size_t)bd.slot_field[sl] * L3;
                     for (int i = tid; i < L3; i += TC_NP * 32) cp_async4(F + sl * L3 + i, fs + i);
                 }
                 cp_async_wait_all();
@@ -394,10 +368,10 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
                     float acc[8];
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) acc[jj] = 0.0f;
-                    const int nt = hcount[h];
+                    const int nt = bd.h_nterm[h];
                     for (int ti = 0; ti < nt; ++ti) {
-                        const int t = hterm[h][ti];
-                        const float *M = F + tfs[t] * L3 + l * L2 + m * L;
+                        const int t = bd.h_terms[h][ti];
+                        const float *M = F + bd.term_slot[t] * L3 + l * L2 + m * L;
                         const float4 *Pt = reinterpret_cast<const float4 *>(P3 + t * L * 8);
 #pragma unroll 4
                         for (int n = 0; n < L; ++n) {
@@ -545,8 +519,8 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
                 const uint32_t dB = (f.nbB == 2 ? (v & 1) : 0) * bd.ng * f.NB;
                 for (int g = par; g < bd.ng; g += 2) {
                     uint32_t acc = 0;
-                    for (int hi = 0; hi < ghcount[g]; ++hi) {
-                        const int h = gh[g][hi];
+                    for (int hi = 0; hi < bd.g_nh[g]; ++hi) {
+                        const int h = bd.g_hs[g][hi];
                         const uint32_t oa = 2 * bd.h_p2[h] * f.p2b, ob = oab + 2 * h * f.ahb;
                         for (int ks = 0; ks < ksh; ++ks) {
                             umma3(tbase + dB + g * f.NB, adv(dP2, oa + ks * 256), adv(dP2, oa + f.p2b + ks * 256),
