@@ -87,6 +87,14 @@ extern "C" {
  * Elements that are not of this form are reported as DPG_ERR_NOT_EXTRUDED (relative
  * tolerance 1e-10 on the vertices) and NaN-filled.  Not combinable with DPG_MAP_AFFINE. */
 #define DPG_MAP_EXTRUDED 0x800
+/* DPG_VEC3: the vector- / matrix-valued version V^3 of a Gram space V (H1, H(curl),
+ * H(div), L2; Sec. 2.7): test functions e_a (x) v_i with the physical unit vectors e_a,
+ * a = 1..3, numbered I = (a - 1) n + i (component-major, n = dim V).  Their inner product
+ * is delta_ab (v_i, v_j)_V (Eqs. 2.86, 2.88), so the element matrix is [3n][3n] with the
+ * Gram matrix of V in the three diagonal blocks and zeros elsewhere; dpg_matrix_rows /
+ * cols return 3n.  Combinable with DPG_FP32 and either map flag; not with the mixed
+ * stiffness, the acoustics blocks, dpg_integrate_hp or dpg_integrate_noalloc. */
+#define DPG_VEC3 0x1000
 
 /* ---- status codes ---- */
 typedef enum {
@@ -140,7 +148,7 @@ int64_t dpg_matrix_cols(int space, int p_trial, int q);
 /* Integrate the element matrices of n_elem elements (the paper's per-element routine
  * PROC(mid, G) of Algorithms 2-11, batched; problem statement Eq. 2.13).
  *   space    : DPG_H1 .. DPG_ACOUSTIC_B, ORed with DPG_FP32 / DPG_MAP_AFFINE or
- *              DPG_MAP_EXTRUDED / DPG_B_SPLIT (B only).
+ *              DPG_MAP_EXTRUDED / DPG_B_SPLIT (B only) / DPG_VEC3 (Gram spaces).
  *   p_trial  : trial order for DPG_B_L2VEC_HCURL and DPG_ACOUSTIC_B
  *              (1 <= p_trial <= q_test); ignored (pass 0) otherwise.
  *   q_test   : test order; tables for (space, q_test) must be initialised.
@@ -202,7 +210,7 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj);
  * every GPU that loads the library reserves until the process exits.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
  *   Arguments, layouts and results are those of dpg_integrate for the general map;
- *   DPG_MAP_AFFINE and DPG_MAP_EXTRUDED are rejected (DPG_ERR_ARG).
+ *   DPG_MAP_AFFINE, DPG_MAP_EXTRUDED and DPG_VEC3 are rejected (DPG_ERR_ARG).
  *   Limit: n_elem * nfields * L^3 * (8 or 4 bytes) must fit the array (nfields = 7, 12,
  *   7, 1, 18 for H1, H(curl), H(div), L2, B; 4 bytes with DPG_FP32), else the call
  *   returns DPG_ERR_SCRATCH before launching anything.  Example: H(curl), q = 5, L = 7,

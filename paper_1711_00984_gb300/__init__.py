@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libdpg.so")
 # spaces and flags (include/dpg.h)
 DPG_H1, DPG_HCURL, DPG_HDIV, DPG_L2, DPG_B_L2VEC_HCURL = 1, 2, 3, 4, 5
 DPG_ACOUSTIC_CROSS, DPG_ACOUSTIC_B = 6, 7
-DPG_FP32, DPG_MAP_AFFINE, DPG_B_SPLIT, DPG_MAP_EXTRUDED = 0x100, 0x200, 0x400, 0x800
+DPG_FP32, DPG_MAP_AFFINE, DPG_B_SPLIT, DPG_MAP_EXTRUDED, DPG_VEC3 = 0x100, 0x200, 0x400, 0x800, 0x1000
 SPACE_IDS = {"H1": DPG_H1, "HCURL": DPG_HCURL, "HDIV": DPG_HDIV, "L2": DPG_L2, "B": DPG_B_L2VEC_HCURL,
              "ACOUSTIC_CROSS": DPG_ACOUSTIC_CROSS, "ACOUSTIC_B": DPG_ACOUSTIC_B}
 STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANGE", 4: "DPG_ERR_CUDA",
@@ -93,10 +93,11 @@ def _check(code: int, where: str) -> int:
     return code
 
 
-def space_id(space, fp32: bool = False, affine: bool = False, split: bool = False, extruded: bool = False) -> int:
+def space_id(space, fp32: bool = False, affine: bool = False, split: bool = False, extruded: bool = False,
+             vec3: bool = False) -> int:
     s = SPACE_IDS[space] if isinstance(space, str) else int(space)
     return (s | (DPG_FP32 if fp32 else 0) | (DPG_MAP_AFFINE if affine else 0) | (DPG_B_SPLIT if split else 0)
-            | (DPG_MAP_EXTRUDED if extruded else 0))
+            | (DPG_MAP_EXTRUDED if extruded else 0) | (DPG_VEC3 if vec3 else 0))
 
 
 # ---- the C ABI, name for name ---------------------------------------------------------
@@ -217,17 +218,18 @@ def _stream_handle(stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def matrix_shape(space, q: int, p: int = 0, split: bool = False) -> tuple[int, ...]:
+def matrix_shape(space, q: int, p: int = 0, split: bool = False, vec3: bool = False) -> tuple[int, ...]:
     """Per-element output shape: (rows, cols), or (2, rows, cols) for split B and for the
-    acoustics stiffness (part 0 and the coefficient of i*omega)."""
-    r = dpg_matrix_rows(space, q)
-    c = dpg_matrix_cols(space, p, q)
+    acoustics stiffness (part 0 and the coefficient of i*omega); (3n, 3n) with vec3."""
+    sid = space_id(space, vec3=vec3)
+    r = dpg_matrix_rows(sid, q)
+    c = dpg_matrix_cols(sid, p, q)
     two = split or (space_id(space) & 0xff) == DPG_ACOUSTIC_B
     return (2, r, c) if two else (r, c)
 
 
 def integrate(space, q: int, verts, coeffs=None, *, p: int = 0, fp32: bool = False, affine: bool = False,
-              split: bool = False, extruded: bool = False, out=None, stream=None):
+              split: bool = False, extruded: bool = False, vec3: bool = False, out=None, stream=None):
     """Integrate element matrices of device tensors ``verts[n, 8, 3]`` (float64, CUDA).
 
     Returns ``out[n, rows, cols]`` (``[n, 2, rows, cols]`` with ``split``) in float64, or
@@ -239,13 +241,13 @@ def integrate(space, q: int, verts, coeffs=None, *, p: int = 0, fp32: bool = Fal
     n = verts.shape[0]
     if coeffs is not None and (not coeffs.is_cuda or coeffs.dtype != torch.float64 or not coeffs.is_contiguous()):
         raise ValueError("coeffs must be a contiguous float64 CUDA tensor [n, 2]")
-    shape = (n,) + matrix_shape(space, q, p, split)
+    shape = (n,) + matrix_shape(space, q, p, split, vec3)
     dt = torch.float32 if fp32 else torch.float64
     if out is None:
         out = torch.empty(shape, dtype=dt, device=verts.device)
     elif out.dtype != dt or tuple(out.shape) != shape or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous {dt} tensor of shape {shape}")
-    sid = space_id(space, fp32, affine, split, extruded)
+    sid = space_id(space, fp32, affine, split, extruded, vec3)
     code = dpg_integrate(sid, p, q, n, verts.data_ptr(), coeffs.data_ptr() if coeffs is not None else 0,
                          out.data_ptr(), _stream_handle(stream))
     _check(code, "dpg_integrate")

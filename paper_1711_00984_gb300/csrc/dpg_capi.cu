@@ -362,7 +362,8 @@ bool valid_space(int space) {
     const int base = space & 0xff;
     const int flags = space & ~0xff;
     if (base < S_H1 || base > S_AB) return false;
-    if (flags & ~(DPG_FP32 | DPG_MAP_AFFINE | DPG_MAP_EXTRUDED | DPG_B_SPLIT)) return false;
+    if (flags & ~(DPG_FP32 | DPG_MAP_AFFINE | DPG_MAP_EXTRUDED | DPG_B_SPLIT | DPG_VEC3)) return false;
+    if ((flags & DPG_VEC3) && base > S_L2) return false;
     if ((flags & DPG_MAP_AFFINE) && (flags & DPG_MAP_EXTRUDED)) return false;
     if ((flags & DPG_B_SPLIT) && base != S_B) return false;
     return true;
@@ -395,13 +396,19 @@ int resolve(int space, int p_trial, int q, ProgEntry **pe, TableEntry **te, Devi
     return DPG_OK;
 }
 
+// Leading dimension and per-element stride of the output a call writes (the program's own,
+// or those of the (0, 0) block of a DPG_VEC3 matrix).
+struct OutGeom {
+    int64_t ld, mat;
+};
+
 template <typename T>
 int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
-                const double *coeffs, T *out, cudaStream_t s) {
+                const double *coeffs, T *out, cudaStream_t s, OutGeom og) {
     constexpr bool f32 = sizeof(T) == 4;
     const Program &pr = f32 ? pe->prog32 : pe->prog;
     const int L = pr.L, L3 = L * L * L;
-    const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
+    const int64_t mat = og.mat;
     const size_t per_elem = (size_t)pr.nfields * L3 * sizeof(T);
     int64_t chunk = (int64_t)(kWorkspaceLimit / per_elem);
     if (chunk < 1) chunk = 1;
@@ -435,7 +442,7 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             tp.pp = te->pp32;
             tp.fields = reinterpret_cast<const float *>(ws);
             tp.out = reinterpret_cast<float *>(out + e0 * mat);
-            tp.mat_stride = mat; tp.ld = pr.cols; tp.n_elem = ne;
+            tp.mat_stride = mat; tp.ld = og.ld; tp.n_elem = ne;
             tp.status = ds->status;
             le = launch_tc_f32(tp, pr.smem_bytes, s);
             if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
@@ -454,7 +461,7 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             pp.pp = te->pp32;
             pp.fields = reinterpret_cast<const float *>(ws);
             pp.out = reinterpret_cast<float *>(out + e0 * mat);
-            pp.mat_stride = mat; pp.ld = pr.cols; pp.n_elem = ne;
+            pp.mat_stride = mat; pp.ld = og.ld; pp.n_elem = ne;
             le = launch_panel_f32(pp, pr.smem_bytes, s);
             if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
             continue;
@@ -471,7 +478,7 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             sp.pp = te->pp32;
             sp.fields = reinterpret_cast<const float *>(ws);
             sp.out = reinterpret_cast<float *>(out + e0 * mat);
-            sp.mat_stride = mat; sp.ld = pr.cols; sp.n_elem = ne;
+            sp.mat_stride = mat; sp.ld = og.ld; sp.n_elem = ne;
             le = launch_general_f32(sp, pr.smem_bytes, pe->max_nc1_32, s);
         } else {
             SfParams<T> sp;
@@ -481,7 +488,7 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             sp.pp = te->pp64;
             sp.fields = reinterpret_cast<const T *>(ws);
             sp.out = out + e0 * mat;
-            sp.mat_stride = mat; sp.ld = pr.cols; sp.n_elem = ne;
+            sp.mat_stride = mat; sp.ld = og.ld; sp.n_elem = ne;
             le = launch_general<T>(sp, pr.smem_values * sizeof(T), s);
         }
         if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
@@ -506,10 +513,10 @@ int aff_elems_per_cta(const Program &pr, int64_t n_elem, int nsplit) {
 
 template <typename T>
 int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
-               const double *coeffs, T *out, cudaStream_t s) {
+               const double *coeffs, T *out, cudaStream_t s, OutGeom og) {
     const AffProg &aprog = pe->aff[sizeof(T) == 4 ? 1 : 0];
     const Program &pr = aprog.prog;
-    const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
+    const int64_t mat = og.mat;
     // CTAs per (element, block): enough for about six waves of the SMs, at most one per unit
     int max_units_block = 1;
     for (int k = 0; k < pr.nblock; ++k) {
@@ -541,7 +548,7 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         if constexpr (sizeof(T) == 8) ap.F = te->F64; else ap.F = te->F32;
         ap.consts = (const double *)consts + AFF_CONST_STRIDE * e0;
         ap.out = out + e0 * mat;
-        ap.mat_stride = mat; ap.ld = pr.cols; ap.n_elem = ne;
+        ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne;
         le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
         if (le != cudaSuccess) rc = cuda_fail(le, "sf_affine_kernel launch", __LINE__);
     }
@@ -554,11 +561,11 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
 // then the extruded-mode contraction, chunked like the general path.
 template <typename T>
 int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
-                 const double *coeffs, T *out, cudaStream_t s) {
+                 const double *coeffs, T *out, cudaStream_t s, OutGeom og) {
     const AffProg &aprog = pe->ext[sizeof(T) == 4 ? 1 : 0];
     const Program &pr = aprog.prog;
     const int L = pr.L, L2 = L * L;
-    const int64_t mat = (int64_t)pr.parts * pr.rows * pr.cols;
+    const int64_t mat = og.mat;
     int max_units_block = 1;
     for (int k = 0; k < pr.nblock; ++k) {
         int c = 0;
@@ -601,7 +608,7 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         ap.xfields = fields; ap.estatus = est;
         ap.L = L; ap.nfields = pr.nfields;
         ap.out = out + e0 * mat;
-        ap.mat_stride = mat; ap.ld = pr.cols; ap.n_elem = ne;
+        ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne;
         le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
         if (le != cudaSuccess) { rc = cuda_fail(le, "extruded contraction launch", __LINE__); break; }
     }
@@ -621,16 +628,27 @@ int integrate_locked(int space, int p_trial, int q_test, int64_t n_elem, const d
     const bool fp32 = (space & DPG_FP32) != 0, affine = (space & DPG_MAP_AFFINE) != 0;
     const bool use_coeffs = (space & 0xff) <= S_L2;            // Gram matrices only
     const double *c = use_coeffs ? coeffs : nullptr;
-    if (affine) {
-        return fp32 ? run_affine<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
-                    : run_affine<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s);
+    const Program &pr = pe->prog;
+    const bool vec3 = (space & DPG_VEC3) != 0;
+    // DPG_VEC3: the scalar Gram matrix goes to the (0, 0) block of the [3n][3n] matrix,
+    // then it is replicated on the diagonal (Eqs. 2.86, 2.88)
+    const OutGeom og = vec3 ? OutGeom{ 3 * (int64_t)pr.cols, 9 * (int64_t)pr.rows * pr.cols }
+                            : OutGeom{ pr.cols, (int64_t)pr.parts * pr.rows * pr.cols };
+    if (affine)
+        r = fp32 ? run_affine<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s, og)
+                 : run_affine<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s, og);
+    else if (space & DPG_MAP_EXTRUDED)
+        r = fp32 ? run_extruded<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s, og)
+                 : run_extruded<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s, og);
+    else
+        r = fp32 ? run_general<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s, og)
+                 : run_general<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s, og);
+    if (r == DPG_OK && vec3) {
+        const cudaError_t le = fp32 ? launch_vec3_fill<float>((float *)out, n_elem, pr.rows, s)
+                                    : launch_vec3_fill<double>((double *)out, n_elem, pr.rows, s);
+        if (le != cudaSuccess) r = cuda_fail(le, "vec3_fill_kernel launch", __LINE__);
     }
-    if (space & DPG_MAP_EXTRUDED) {
-        return fp32 ? run_extruded<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
-                    : run_extruded<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s);
-    }
-    return fp32 ? run_general<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s)
-                : run_general<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s);
+    return r;
 }
 
 // The hp sequence (workspace, work generation, geometry, persistent contraction) on s.
@@ -779,12 +797,16 @@ int dpg_tables_free(void) {
     return DPG_OK;
 }
 
-int64_t dpg_matrix_rows(int space, int q) { return rows_of(space & 0xff, q); }
+int64_t dpg_matrix_rows(int space, int q) {
+    const int64_t r = rows_of(space & 0xff, q);
+    return (r > 0 && (space & DPG_VEC3)) ? 3 * r : r;
+}
 
 int64_t dpg_matrix_cols(int space, int p_trial, int q) {
     const int base = space & 0xff;
     if (rows_of(base, q) < 0) return -1;
-    return cols_of(base, p_trial, q);
+    const int64_t c = cols_of(base, p_trial, q);
+    return (c > 0 && (space & DPG_VEC3)) ? 3 * c : c;
 }
 
 int dpg_integrate(int space, int p_trial, int q_test, int64_t n_elem, const double *vertices,
@@ -840,7 +862,7 @@ int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem, const
     if (!vertices || !out) return DPG_ERR_ARG;
     const Program &pr = pe->prog;
     const size_t esz = (space & DPG_FP32) ? sizeof(float) : sizeof(double);
-    const size_t per_out = (size_t)pr.parts * pr.rows * pr.cols * esz;
+    const size_t per_out = (size_t)pr.parts * pr.rows * pr.cols * esz * ((space & DPG_VEC3) ? 9 : 1);
     const size_t out_bytes = (size_t)n_elem * per_out;
     const size_t v_bytes = (size_t)n_elem * 24 * sizeof(double);
     const size_t c_bytes = coeffs ? (size_t)n_elem * 2 * sizeof(double) : 0;
@@ -957,8 +979,9 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
         bool ok = true;
         for (int rep = 0; rep < 4 && ok; ++rep) {
             cudaEventRecord(a, s);
-            const int rr = fp32 ? run_general<float>(ds, pe, te, ne, dv, nullptr, (float *)dout, s)
-                                : run_general<double>(ds, pe, te, ne, dv, nullptr, (double *)dout, s);
+            const OutGeom og{ pe->prog.cols, (int64_t)pe->prog.parts * pe->prog.rows * pe->prog.cols };
+            const int rr = fp32 ? run_general<float>(ds, pe, te, ne, dv, nullptr, (float *)dout, s, og)
+                                : run_general<double>(ds, pe, te, ne, dv, nullptr, (double *)dout, s, og);
             cudaEventRecord(b, s);
             cudaEventSynchronize(b);
             float ms = 0.f;

@@ -1636,6 +1636,36 @@ template cudaError_t launch_geom2d<float>(const Geom2dParams &, cudaStream_t);
 
 size_t extruded_smem_values(const BlockDesc &b, int L, int nj) { return (size_t)ext_layout(b, L, nj).total; }
 
+// Sec. 2.7: block-replicated Gram matrix of V^3.  A warp per output row; rows of the first
+// row block keep their diagonal part (the source) and get zeros beyond it.
+template <typename T>
+__global__ void __launch_bounds__(256) vec3_fill_kernel(T *out, int64_t n_elem, int n) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n3 = 3 * n;
+    const int64_t gr = (int64_t)blockIdx.x * 8 + warp;          // global row over all elements
+    if (gr >= n_elem * n3) return;
+    const int64_t e = gr / n3;
+    const int r = (int)(gr - e * n3), a = r / n, i = r - a * n;
+    T *m = out + (size_t)e * n3 * n3;
+    const T *src = m + (size_t)i * n3;                           // row i of block (0, 0)
+    T *dst = m + (size_t)r * n3;
+    for (int c = lane; c < n3; c += 32) {
+        const int b = c / n;
+        if (a == 0 && b == 0) continue;
+        dst[c] = (a == b) ? src[c - b * n] : T(0);
+    }
+}
+
+template <typename T>
+cudaError_t launch_vec3_fill(T *out, int64_t n_elem, int n, cudaStream_t s) {
+    const int64_t rows = n_elem * 3 * (int64_t)n;
+    if (rows == 0) return cudaSuccess;
+    vec3_fill_kernel<T><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(out, n_elem, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_vec3_fill<double>(double *, int64_t, int, cudaStream_t);
+template cudaError_t launch_vec3_fill<float>(float *, int64_t, int, cudaStream_t);
+
 // Opt every kernel into the large shared-memory carve-out once per device (host call,
 // done at table set-up so that integration calls stay pure launches).
 cudaError_t init_kernel_attributes(int optin_smem) {

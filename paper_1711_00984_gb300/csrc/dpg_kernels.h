@@ -171,6 +171,10 @@ cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s);
 template <typename T> cudaError_t launch_extruded(const AffParams<T> &p, size_t smem, cudaStream_t s);
 template <typename TF> cudaError_t launch_geom2d(const Geom2dParams &p, cudaStream_t s);
+// Vector-valued Gram matrices (DPG_VEC3): the scalar Gram matrix of each element sits in the
+// (0, 0) block of its [3n][3n] matrix; copy it to the (1, 1) and (2, 2) blocks and zero the
+// off-diagonal blocks.
+template <typename T> cudaError_t launch_vec3_fill(T *out, int64_t n_elem, int n, cudaStream_t s);
 size_t extruded_smem_values(const BlockDesc &b, int L, int nj);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);

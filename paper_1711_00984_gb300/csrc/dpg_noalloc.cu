@@ -65,7 +65,7 @@ int run(const dpg::ProgramView &v, int64_t n_elem, const double *verts, const do
 
 extern "C" int dpg_integrate_noalloc(int space, int p_trial, int q_test, int64_t n_elem,
                                      const double *vertices, const double *coeffs, void *out, void *stream) {
-    if (space & (DPG_MAP_AFFINE | DPG_MAP_EXTRUDED)) return DPG_ERR_ARG;
+    if (space & (DPG_MAP_AFFINE | DPG_MAP_EXTRUDED | DPG_VEC3)) return DPG_ERR_ARG;
     dpg::ProgramView v;
     int r = dpg::lookup_program_view(space, p_trial, q_test, &v);
     if (r) return r;
