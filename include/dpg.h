@@ -235,6 +235,14 @@ int dpg_integrate_noalloc(int space, int p_trial, int q_test, int64_t n_elem,
 int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem,
                        const double *vertices, const double *coeffs, void *out, void *stream);
 
+/* Test hook (not part of the method): the next launch of the FP32 tensor-core kernel
+ * (DPG_FP32, general map) runs with its first CTA issuing no stage-B MMA, so that CTA's
+ * bounded mbarrier waits run out (after about a second), the CTA releases its tensor
+ * memory and records DPG_ERR_TIMEOUT (first_bad = its first element); the other CTAs and
+ * later calls are unaffected.  Exercises the kernel's failure path without a GPU fault.
+ * Returns DPG_OK. */
+int dpg_test_stall_tc_once(void);
+
 /* Synchronise `stream`, read and clear the device status word of the current device.
  * Returns DPG_OK or the first device-detected error; *first_bad_elem (if not NULL)
  * receives the smallest offending element index of that error, or -1. */

@@ -29,7 +29,8 @@ STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANG
 
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
            "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",
-           "dpg_strerror", "dpg_last_cuda_error", "dpg_autotune", "dpg_flops_per_element", "dpg_measure_fma_peak"]
+           "dpg_strerror", "dpg_last_cuda_error", "dpg_autotune", "dpg_flops_per_element", "dpg_measure_fma_peak",
+           "dpg_test_stall_tc_once"]
 
 _lib = None
 _lock = threading.Lock()
@@ -76,6 +77,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_flops_per_element.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.dpg_flops_per_element.restype = ctypes.c_double
         lib.dpg_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp]
+        lib.dpg_test_stall_tc_once.argtypes = []
+        lib.dpg_test_stall_tc_once.restype = ctypes.c_int
         for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp",
                      "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak"]:
             getattr(lib, name).restype = ctypes.c_int
@@ -183,6 +186,11 @@ def dpg_sync_status(stream: int = 0) -> tuple[int, int]:
     bad = ctypes.c_int64(-1)
     code = _L().dpg_sync_status(stream or None, ctypes.byref(bad))
     return int(code), int(bad.value)
+
+
+def dpg_test_stall_tc_once() -> int:
+    """Test hook: the next FP32 tensor-core launch stalls its first CTA (see include/dpg.h)."""
+    return _check(_L().dpg_test_stall_tc_once(), "dpg_test_stall_tc_once")
 
 
 def dpg_strerror(code: int) -> str:

@@ -27,6 +27,7 @@ constexpr size_t kWorkspaceLimit = size_t(512) << 20;   // metric fields per lau
 enum { K32_MIRROR = 0, K32_PANEL = 1, K32_TC = 2 };      // FP32 general-path kernels
 int g_max_dyn_smem = 0;                                  // per launch, set at device set-up
 int g_max_dyn_smem_tc = 0;                               // the same for the tensor-core kernel
+int g_tc_stall_once = 0;                                 // test hook, see dpg_test_stall_tc_once
 int g_num_sms = 152;                                     // set at device set-up
 
 struct TableEntry {
@@ -444,6 +445,8 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             tp.out = reinterpret_cast<float *>(out + e0 * mat);
             tp.mat_stride = mat; tp.ld = og.ld; tp.n_elem = ne;
             tp.status = ds->status;
+            tp.stall_cta = g_tc_stall_once ? 0 : -1;
+            g_tc_stall_once = 0;
             le = launch_tc_f32(tp, pr.smem_bytes, s);
             if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
             continue;
@@ -907,6 +910,12 @@ int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem, const
     for (auto ev : evs) cudaEventDestroy(ev);
     if (r) return r;
     return read_status(ds, nullptr);
+}
+
+int dpg_test_stall_tc_once(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tc_stall_once = 1;
+    return DPG_OK;
 }
 
 int dpg_sync_status(void *stream, int64_t *first_bad_elem) {

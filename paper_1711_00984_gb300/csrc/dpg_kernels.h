@@ -93,6 +93,7 @@ struct TcParams {
     float *out;
     int64_t mat_stride, ld, n_elem;
     DevStatus *status;
+    int stall_cta;                 // test hook: this CTA issues no stage-B MMA (-1: none)
 };
 
 template <typename T>

@@ -505,7 +505,10 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
         int ui = ub;
         if (mw < 2) {
             const uint64_t dP2 = sdesc(sbase + f.oP2, f.sbo2), dAh = sdesc(sbase + f.oAh, f.sbo2);
-            for (int v = 0; v < nv; ++v) {
+            // test hook (dpg_test_stall_tc_once): the stage-B completion of this CTA never
+            // arrives, so its bounded waits run out and the CTA reports DPG_ERR_TIMEOUT
+            const int nvB = (int)blockIdx.x == p.stall_cta ? 0 : nv;
+            for (int v = 0; v < nvB; ++v) {
                 const Unit u = p.units[ui];
                 mbar_wait(&bar_ah[v & 1], (uint32_t)((v >> 1) & 1), &fail);
                 // the D_B buffer of this unit has been read out (unit v - 2, or v - 1 when
