@@ -69,6 +69,9 @@ def _load():
             lib.oracle_gram.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                         dp, dp, dp, ctypes.c_int]
             lib.oracle_gram.restype = ctypes.c_int64
+            lib.oracle_load.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                        dp, dp, dp, ctypes.c_int]
+            lib.oracle_load.restype = ctypes.c_int64
             lib.oracle_mixed_b.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                            dp, dp, ctypes.c_int, ctypes.c_int]
             lib.oracle_mixed_b.restype = ctypes.c_int64
@@ -151,6 +154,26 @@ def gram(space, q: int, L: int, verts: np.ndarray, coeffs: np.ndarray | None = N
     r = _load().oracle_gram(sid, q, L, ne, _ptr(v), _ptr(c), _ptr(out), nthreads)
     if r < 0:
         raise ValueError("oracle_gram: bad arguments")
+    return out, int(r) - 1
+
+
+def load(space, q: int, L: int, verts: np.ndarray, coef, nthreads: int = 0) -> tuple[np.ndarray, int]:
+    """Load vectors ``[n_elem, n]``, l_I = (f, v_I)_K by conventional FP64 quadrature.
+
+    ``coef``: 10 (H1, L2) or 30 (H(curl), H(div)) coefficients of the source, component c
+    being sum_k coef[10 c + k] m_k(x) with m = (1, x1, x2, x3, x1^2, x2^2, x3^2, x1 x2,
+    x1 x3, x2 x3).  Returns (l, first_bad) like ``gram``.
+    """
+    sid = _sid(space)
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    c = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+    if c.size != (10 if sid in (1, 4) else 30):
+        raise ValueError("coef: 10 values for H1 / L2, 30 for H(curl) / H(div)")
+    ne = v.shape[0]
+    out = np.empty((ne, dim(sid, q)))
+    r = _load().oracle_load(sid, q, L, ne, _ptr(v), _ptr(c), _ptr(out), nthreads)
+    if r < 0:
+        raise ValueError("oracle_load: bad arguments")
     return out, int(r) - 1
 
 

@@ -415,6 +415,80 @@ int64_t oracle_gram(int space, int q, int L, int64_t n_elem, const double *verts
     return first_bad;
 }
 
+/* Polynomial source of total degree <= 2 in the physical coordinates: component c is
+ * f_c(x) = sum_k coef[10 c + k] m_k(x) with the monomials
+ * m = (1, x1, x2, x3, x1^2, x2^2, x3^2, x1 x2, x1 x3, x2 x3). */
+static double source_value(const double *coef, int c, const double *x) {
+    const double m[10] = { 1.0, x[0], x[1], x[2], x[0] * x[0], x[1] * x[1], x[2] * x[2],
+                           x[0] * x[1], x[0] * x[2], x[1] * x[2] };
+    double f = 0.0;
+    for (int k = 0; k < 10; ++k) f += coef[10 * c + k] * m[k];
+    return f;
+}
+
+/* Load vector of the test space (the right-hand side l_I = ell(v_I) of the DPG system,
+ * Sec. 3, Eq. 3.2): l_I = (f, v_I)_K = sum_lmn w_lmn |J| f(x) . phys0_I with the physical
+ * test functions of map_to_physical (Eqs. 2.3-2.6); f is scalar for H1 and L2 (coef[10]),
+ * a vector for H(curl) and H(div) (coef[30]).  verts: [n_elem][8][3]; out: [n_elem][n].
+ * Returns the index of the first element with det J <= 0 at a point + 1 (NaN-filled), or 0. */
+int64_t oracle_load(int space, int q, int L, int64_t n_elem, const double *verts, const double *coef,
+                    double *out, int nthreads) {
+    if (space < OR_H1 || space > OR_L2 || q < 1 || L < 1 || !coef) return -1;
+    int64_t n = space_dim(space, q, 0);
+    double zeta[64], wq[64];
+    if (oracle_gauss(L, zeta, wq) != 0) return -1;
+    const int nc = ncomp_value(space);
+    int64_t first_bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    #pragma omp parallel
+    {
+        double *val = (double *)malloc(sizeof(double) * 3 * n);
+        double *der = (double *)malloc(sizeof(double) * 9 * n);
+        double *p0 = (double *)malloc(sizeof(double) * 3 * n);
+        double *p1 = (double *)malloc(sizeof(double) * 3 * n);
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t e = 0; e < n_elem; ++e) {
+            const double *ve = verts + 24 * e;
+            double *l_e = out + e * n;
+            memset(l_e, 0, sizeof(double) * n);
+            int bad = 0;
+            for (int l = 0; l < L && !bad; ++l)
+            for (int m = 0; m < L && !bad; ++m)
+            for (int k = 0; k < L && !bad; ++k) {
+                double xi[3] = { zeta[l], zeta[m], zeta[k] };
+                double x[3], J9[9];
+                double det = oracle_geometry(ve, xi, x, J9);
+                if (!(det > 0.0) || !isfinite(det)) { bad = 1; break; }
+                double J[3][3], Ji[3][3];
+                for (int i = 0; i < 3; ++i)
+                    for (int d = 0; d < 3; ++d) J[i][d] = J9[3 * i + d];
+                inverse3(J, det, Ji);
+                shape3(space, q, 0, xi, val, der);
+                map_to_physical(space, n, val, der, J, det, Ji, p0, p1);
+                double f[3];
+                for (int c = 0; c < nc; ++c) f[c] = source_value(coef, c, x);
+                const double s = wq[l] * wq[m] * wq[k] * det;
+                for (int64_t I = 0; I < n; ++I) {
+                    double t = 0.0;
+                    for (int c = 0; c < nc; ++c) t += f[c] * p0[3 * I + c];
+                    l_e[I] += s * t;
+                }
+            }
+            if (bad) {
+                for (int64_t i = 0; i < n; ++i) l_e[i] = NAN;
+                #pragma omp critical
+                { if (first_bad == 0 || e + 1 < first_bad) first_bad = e + 1; }
+            }
+        }
+        free(val); free(der); free(p0); free(p1);
+    }
+    return first_bad;
+}
+
 /* Mixed stiffness B (pattern of Eqs. 3.15-3.16 for a vector-L2 trial u of order p and an
  * H(curl) test psi of order q):  B_IK = (u_K, psi_I)_K + (u_K, curl psi_I)_K, with
  * u_K = T(P_k1 P_k2 P_k3) e_c componentwise (Eq. 2.6) and psi_I = T^curl psi^_I.
