@@ -235,6 +235,30 @@ int dpg_integrate_noalloc(int space, int p_trial, int q_test, int64_t n_elem,
 int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem,
                        const double *vertices, const double *coeffs, void *out, void *stream);
 
+/* Load vector of a test space: l_I = (f, v_I)_K for every test function v_I of order q_test
+ * (the right-hand side ell(v_I) of the DPG system, Sec. 3, e.g. the (f, q) of Eq. 3.13 with
+ * v = q), by conventional Gauss quadrature on the active rule of (space, q_test) evaluated by
+ * sum factorization (Eqs. 2.23-2.25 with a single test index).  The source is a polynomial
+ * of total degree <= 2 in the physical coordinates x:
+ *   f_c(x) = sum_k src_coef[10 c + k] m_k(x),  m = (1, x1, x2, x3, x1^2, x2^2, x3^2,
+ *   x1 x2, x1 x3, x2 x3),
+ * scalar (c = 0) for H1 and L2, a vector (c = 0, 1, 2) for H(curl) and H(div); test
+ * functions are mapped by Eqs. 2.3-2.6, so the integrand is w |J| f v^ (H1), w f q^ (L2),
+ * w |J| (J^-1 f) . psi^ (H(curl)), w (J^T f) . theta^ (H(div)).
+ *   space       : DPG_H1 .. DPG_L2, optionally | DPG_FP32 (geometry and source in FP64,
+ *                 contractions and output in FP32).  Tables for (space, q_test) must be
+ *                 initialised (DPG_ERR_NOT_INIT).
+ *   vertices    : device, double[n_elem][8][3].
+ *   src_coef    : device, double: 10 (H1, L2) or 30 (H(curl), H(div)) values shared by all
+ *                 elements when coef_stride = 0, else element e reads
+ *                 src_coef + e * coef_stride (coef_stride >= 10 or 30).
+ *   out         : device, double or float [n_elem][dpg_matrix_rows(space, q_test)].
+ * An element with |J| <= 0 at a point is NaN-filled and reported as DPG_ERR_DEGENERATE
+ * through dpg_sync_status.  No workspace is allocated.
+ * Errors: DPG_ERR_ARG, DPG_ERR_NOT_INIT, DPG_ERR_RANGE, DPG_ERR_CUDA. */
+int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vertices,
+                       const double *src_coef, int64_t coef_stride, void *out, void *stream);
+
 /* Test hook (not part of the method): the next launch of the FP32 tensor-core kernel
  * (DPG_FP32, general map) runs with its first CTA issuing no stage-B MMA, so that CTA's
  * bounded mbarrier waits run out (after about a second), the CTA releases its tensor

@@ -30,7 +30,7 @@ STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANG
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
            "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",
            "dpg_strerror", "dpg_last_cuda_error", "dpg_autotune", "dpg_flops_per_element", "dpg_measure_fma_peak",
-           "dpg_test_stall_tc_once"]
+           "dpg_test_stall_tc_once", "dpg_integrate_load"]
 
 _lib = None
 _lock = threading.Lock()
@@ -77,10 +77,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_flops_per_element.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.dpg_flops_per_element.restype = ctypes.c_double
         lib.dpg_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp]
+        lib.dpg_integrate_load.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, i64, vp, vp]
         lib.dpg_test_stall_tc_once.argtypes = []
         lib.dpg_test_stall_tc_once.restype = ctypes.c_int
         for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp",
-                     "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak"]:
+                     "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak", "dpg_integrate_load"]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -259,6 +260,47 @@ def integrate(space, q: int, verts, coeffs=None, *, p: int = 0, fp32: bool = Fal
     code = dpg_integrate(sid, p, q, n, verts.data_ptr(), coeffs.data_ptr() if coeffs is not None else 0,
                          out.data_ptr(), _stream_handle(stream))
     _check(code, "dpg_integrate")
+    return out
+
+
+def dpg_integrate_load(space: int, q_test: int, n_elem: int, vertices: int, src_coef: int, coef_stride: int,
+                       out: int, stream: int) -> int:
+    """Raw call of the load-vector entry point (integer device pointers)."""
+    return _L().dpg_integrate_load(space, q_test, n_elem, vertices or None, src_coef or None, coef_stride,
+                                   out or None, stream or None)
+
+
+def integrate_load(space, q: int, verts, src_coef, *, fp32: bool = False, out=None, stream=None):
+    """Load vectors ``out[n, rows]`` of device tensors ``verts[n, 8, 3]`` (float64, CUDA).
+
+    ``src_coef``: float64 CUDA tensor of the degree-2 source's coefficients, ``[10 nc]``
+    (one source for all elements) or ``[n, 10 nc]`` (one per element), nc = 1 for H1 and
+    L2, 3 for H(curl) and H(div).  Tables for (space, q) must have been initialised.
+    """
+    import torch
+    if not verts.is_cuda or verts.dtype != torch.float64 or not verts.is_contiguous():
+        raise ValueError("verts must be a contiguous float64 CUDA tensor [n, 8, 3]")
+    if not src_coef.is_cuda or src_coef.dtype != torch.float64 or not src_coef.is_contiguous():
+        raise ValueError("src_coef must be a contiguous float64 CUDA tensor")
+    n = verts.shape[0]
+    nc = 3 if (SPACE_IDS[space] if isinstance(space, str) else int(space) & 0xFF) in (2, 3) else 1
+    if src_coef.dim() == 1:
+        if src_coef.numel() != 10 * nc:
+            raise ValueError(f"src_coef must hold {10 * nc} values")
+        stride = 0
+    else:
+        if tuple(src_coef.shape) != (n, 10 * nc):
+            raise ValueError(f"src_coef must have shape [{n}, {10 * nc}]")
+        stride = 10 * nc
+    shape = (n, dpg_matrix_rows(space, q))
+    dt = torch.float32 if fp32 else torch.float64
+    if out is None:
+        out = torch.empty(shape, dtype=dt, device=verts.device)
+    elif out.dtype != dt or tuple(out.shape) != shape or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous {dt} tensor of shape {shape}")
+    code = dpg_integrate_load(space_id(space, fp32), q, n, verts.data_ptr(), src_coef.data_ptr(), stride,
+                              out.data_ptr(), _stream_handle(stream))
+    _check(code, "dpg_integrate_load")
     return out
 
 

@@ -912,6 +912,31 @@ int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem, const
     return read_status(ds, nullptr);
 }
 
+int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vertices,
+                       const double *src_coef, int64_t coef_stride, void *out, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int base = space & 0xff;
+    if (base < S_H1 || base > S_L2 || (space & ~(0xff | DPG_FP32))) return DPG_ERR_ARG;
+    ProgEntry *pe; TableEntry *te; DeviceState *ds;
+    int r = resolve(base, 0, q_test, &pe, &te, &ds);
+    if (r) return r;
+    const int nc = (base == S_HCURL || base == S_HDIV) ? 3 : 1;
+    if (n_elem < 0 || (coef_stride != 0 && coef_stride < 10 * nc)) return DPG_ERR_ARG;
+    if (n_elem == 0) return DPG_OK;
+    if (!vertices || !src_coef || !out) return DPG_ERR_ARG;
+    LoadParams p;
+    p.space = base; p.q = q_test; p.L = te->host.L;
+    p.n_elem = n_elem; p.elem_base = 0;
+    p.verts = vertices; p.coef = src_coef; p.coef_stride = coef_stride;
+    p.zeta = te->zeta; p.w = te->w;
+    p.out = out; p.status = ds->status;
+    cudaError_t le;
+    if (space & DPG_FP32) { p.pp = te->pp32; le = launch_load<float>(p, g_num_sms, (cudaStream_t)stream); }
+    else { p.pp = te->pp64; le = launch_load<double>(p, g_num_sms, (cudaStream_t)stream); }
+    if (le != cudaSuccess) return cuda_fail(le, "load_kernel launch", __LINE__);
+    return DPG_OK;
+}
+
 int dpg_test_stall_tc_once(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_tc_stall_once = 1;

@@ -9,6 +9,7 @@
 //                        then the symmetric fill of both triangles (fillsymmetric3*).
 //   sf_affine_kernel   : constant-Jacobian path (Sec. 2.8.1, Algorithm 10 with a full J):
 //                        G = sum_t c_t F^{t1} (x) F^{t2} (x) F^{t3} from exact 1D integrals.
+//   load_kernel        : load vector (f, v_I)_K of a test space by sum factorization.
 //   fma_peak_kernel    : FMA-rate probe for the ALU roofline (not part of the method).
 #include "dpg_kernels.h"
 
@@ -1666,6 +1667,165 @@ cudaError_t launch_vec3_fill(T *out, int64_t n_elem, int n, cudaStream_t s) {
 template cudaError_t launch_vec3_fill<double>(double *, int64_t, int, cudaStream_t);
 template cudaError_t launch_vec3_fill<float>(float *, int64_t, int, cudaStream_t);
 
+// --------------------------------------------------------------------------------------
+// load vector l_I = (f, v_I)_K of a test space (the right-hand side of the DPG system,
+// Sec. 3): the pulled-back source at every Gauss point, then sum factorization over the
+// three directions with the 1D factors of the index maps (Eqs. 2.17, 2.33, 2.53, 2.71)
+// --------------------------------------------------------------------------------------
+constexpr int LOAD_NTH = 128;
+
+// Per-direction extent and family of component a: kind 0 = chi (integrated Legendre),
+// 1 = nu (Legendre).
+__device__ __forceinline__ void load_comp(int space, int q, int a, int d, int &n, int &k) {
+    switch (space) {
+    case S_H1: n = q + 1; k = 0; return;
+    case S_L2: n = q; k = 1; return;
+    case S_HCURL: n = d == a ? q : q + 1; k = d == a ? 1 : 0; return;
+    default: n = d == a ? q + 1 : q; k = d == a ? 0 : 1; return;     // H(div)
+    }
+}
+
+// Shared values of the kernel (in T): 1D factors [2][q+1][L], point values / stage-B
+// result [max(nc L^3, nc L (q+1)^2)], stage-A result [nc L^2 (q+1)].
+DPG_HD inline int64_t load_smem_values(int nc, int q, int L) {
+    const int64_t n = q + 1, L3 = (int64_t)L * L * L;
+    const int64_t r0 = nc * L3 > nc * L * n * n ? nc * L3 : nc * L * n * n;
+    return 2 * n * L + r0 + nc * (int64_t)L * L * n;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(LOAD_NTH) load_kernel(LoadParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sv[24], scoef[30], szeta[MAXL], sw[MAXL];
+    __shared__ int sbad;
+    const int q = p.q, L = p.L, L2 = L * L, L3 = L2 * L, n = q + 1;
+    const int space = p.space, nc = (space == S_HCURL || space == S_HDIV) ? 3 : 1;
+    T *phi = reinterpret_cast<T *>(smem_raw);                  // [2][n][L]
+    T *wf = phi + 2 * n * L;                                   // [nc][L^3], then [nc][L][n][n]
+    const int r0 = nc * L3 > nc * L * n * n ? nc * L3 : nc * L * n * n;
+    T *t1 = wf + r0;                                           // [nc][L^2][n]
+    const T *pp = static_cast<const T *>(p.pp);
+    // f_k(i, l) = pp[pair (k, nu)][i][j = 0][l] since nu_0 = P_0 = 1
+    for (int t = threadIdx.x; t < 2 * n * L; t += LOAD_NTH) {
+        const int k = t / (n * L), i = (t / L) % n, l = t % L;
+        const int pair = 3 * (k ? KY : KW) + KY;
+        phi[t] = pp[((pair * NQ1 + i) * NQ1) * L + l];
+    }
+    for (int t = threadIdx.x; t < L; t += LOAD_NTH) { szeta[t] = p.zeta[t]; sw[t] = p.w[t]; }
+    if (p.coef_stride == 0)
+        for (int t = threadIdx.x; t < 10 * nc; t += LOAD_NTH) scoef[t] = p.coef[t];
+    for (int64_t e = blockIdx.x; e < p.n_elem; e += gridDim.x) {
+        if (threadIdx.x < 24) sv[threadIdx.x] = p.verts[24 * e + threadIdx.x];
+        if (p.coef_stride != 0)
+            for (int t = threadIdx.x; t < 10 * nc; t += LOAD_NTH) scoef[t] = p.coef[e * p.coef_stride + t];
+        if (threadIdx.x == 0) sbad = 0;
+        __syncthreads();
+        // point values W_a(l, m, n) = w |J| f . (pulled-back a-th unit vector), FP64
+        for (int pt = threadIdx.x; pt < L3; pt += LOAD_NTH) {
+            const int l = pt / L2, m = (pt / L) % L, k = pt % L;
+            const double x1 = szeta[l], x2 = szeta[m], x3 = szeta[k];
+            Jac g;
+            trilinear_jac(sv, x1, x2, x3, g);
+            finish_jac(g);
+            double x[3] = { 0.0, 0.0, 0.0 };
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const double N = ((c & 1) ? x1 : 1.0 - x1) * ((c & 2) ? x2 : 1.0 - x2) * ((c & 4) ? x3 : 1.0 - x3);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) x[i] += sv[3 * c + i] * N;
+            }
+            const double mono[10] = { 1.0, x[0], x[1], x[2], x[0] * x[0], x[1] * x[1], x[2] * x[2],
+                                      x[0] * x[1], x[0] * x[2], x[1] * x[2] };
+            double f[3] = { 0.0, 0.0, 0.0 };
+            for (int c = 0; c < nc; ++c)
+#pragma unroll
+                for (int t = 0; t < 10; ++t) f[c] += scoef[10 * c + t] * mono[t];
+            const double wt = sw[l] * sw[m] * sw[k];
+            if (!(g.det > 0.0) || !isfinite(g.det)) sbad = 1;
+            if (space == S_H1) {
+                wf[pt] = (T)(wt * g.det * f[0]);                           // Eq. 2.3
+            } else if (space == S_L2) {
+                wf[pt] = (T)(wt * f[0]);                                   // Eq. 2.6: |J|^-1 |J|
+            } else if (space == S_HCURL) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)                                // Eq. 2.4: (J^-1 f)_a |J|
+                    wf[a * L3 + pt] = (T)(wt * g.det * (g.Ji[a][0] * f[0] + g.Ji[a][1] * f[1] + g.Ji[a][2] * f[2]));
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)                                // Eq. 2.5: (J^T f)_a
+                    wf[a * L3 + pt] = (T)(wt * (g.J[0][a] * f[0] + g.J[1][a] * f[1] + g.J[2][a] * f[2]));
+            }
+        }
+        __syncthreads();
+        // stage A: contract xi_3, t1[a][l m][i3] = sum_k W_a(l, m, k) f3_{i3}(k)
+        for (int a = 0; a < nc; ++a) {
+            int n3, k3;
+            load_comp(space, q, a, 2, n3, k3);
+            const T *src = wf + a * L3, *f3 = phi + k3 * n * L;
+            T *dst = t1 + a * L2 * n;
+            for (int it = threadIdx.x; it < L2 * n3; it += LOAD_NTH) {
+                const int lm = it / n3, i3 = it - lm * n3;
+                T s = 0;
+                for (int k = 0; k < L; ++k) s += src[lm * L + k] * f3[i3 * L + k];
+                dst[lm * n + i3] = s;
+            }
+        }
+        __syncthreads();
+        // stage B: contract xi_2, t2[a][l][i2][i3] = sum_m t1[a][l m][i3] f2_{i2}(m)
+        for (int a = 0; a < nc; ++a) {
+            int n2, k2, n3, k3;
+            load_comp(space, q, a, 1, n2, k2);
+            load_comp(space, q, a, 2, n3, k3);
+            const T *src = t1 + a * L2 * n, *f2 = phi + k2 * n * L;
+            T *dst = wf + a * L * n * n;
+            for (int it = threadIdx.x; it < L * n2 * n3; it += LOAD_NTH) {
+                const int i3 = it % n3, i2 = (it / n3) % n2, l = it / (n2 * n3);
+                T s = 0;
+                for (int m = 0; m < L; ++m) s += src[(l * L + m) * n + i3] * f2[i2 * L + m];
+                dst[(l * n + i2) * n + i3] = s;
+            }
+        }
+        __syncthreads();
+        // stage C: contract xi_1 and write l[off_a + i1 + n1 (i2 + n2 i3)], i1 fastest
+        T *out = static_cast<T *>(p.out);
+        int off = 0;
+        for (int a = 0; a < nc; ++a) {
+            int n1, k1, n2, k2, n3, k3;
+            load_comp(space, q, a, 0, n1, k1);
+            load_comp(space, q, a, 1, n2, k2);
+            load_comp(space, q, a, 2, n3, k3);
+            const T *src = wf + a * L * n * n, *f1 = phi + k1 * n * L;
+            const int na = n1 * n2 * n3;
+            const int64_t rows = nc == 1 ? na : 3 * (int64_t)na;
+            for (int it = threadIdx.x; it < na; it += LOAD_NTH) {
+                const int i1 = it % n1, i2 = (it / n1) % n2, i3 = it / (n1 * n2);
+                T s = 0;
+                for (int l = 0; l < L; ++l) s += src[(l * n + i2) * n + i3] * f1[i1 * L + l];
+                out[e * rows + off + it] = sbad ? qnan<T>() : s;
+            }
+            off += na;
+        }
+        if (threadIdx.x == 0 && sbad) report(p.status, 5 /*DPG_ERR_DEGENERATE*/, p.elem_base + e);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_load(const LoadParams &p, int num_sms, cudaStream_t s) {
+    if (p.n_elem == 0) return cudaSuccess;
+    const int nc = (p.space == S_HCURL || p.space == S_HDIV) ? 3 : 1;
+    const size_t smem = (size_t)load_smem_values(nc, p.q, p.L) * sizeof(T);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, load_kernel<T>, LOAD_NTH, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = p.n_elem < (int64_t)per_sm * num_sms ? p.n_elem : (int64_t)per_sm * num_sms;
+    load_kernel<T><<<(unsigned)grid, LOAD_NTH, smem, s>>>(p);
+    return cudaGetLastError();
+}
+template cudaError_t launch_load<double>(const LoadParams &, int, cudaStream_t);
+template cudaError_t launch_load<float>(const LoadParams &, int, cudaStream_t);
+
 // Opt every kernel into the large shared-memory carve-out once per device (host call,
 // done at table set-up so that integration calls stay pure launches).
 cudaError_t init_kernel_attributes(int optin_smem) {
@@ -1689,6 +1849,8 @@ cudaError_t init_kernel_attributes(int optin_smem) {
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<float, false>);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<double, true>);
     if (e == cudaSuccess) e = one((const void *)sf_affine_kernel<float, true>);
+    if (e == cudaSuccess) e = one((const void *)load_kernel<double>);
+    if (e == cudaSuccess) e = one((const void *)load_kernel<float>);
     return e;
 }
 

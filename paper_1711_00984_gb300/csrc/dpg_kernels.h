@@ -129,6 +129,19 @@ struct Geom2dParams {
     DevStatus *status;
 };
 
+// Load vector of a test space (dpg_integrate_load): one CTA per element at a time.
+struct LoadParams {
+    int space, q, L;
+    int64_t n_elem, elem_base;
+    const double *verts;       // chunk start, [n_elem][8][3]
+    const double *coef;        // source coefficients: [10 ncomp] shared, or per element
+    int64_t coef_stride;       // 0: one source for every element; else values per element
+    const double *zeta, *w;    // Gauss rule
+    const void *pp;            // pair products of the stage type [NPAIR][NQ1][NQ1][L]
+    void *out;                 // chunk start, [n_elem][rows] of the stage type
+    DevStatus *status;
+};
+
 // hp batching: per-q programs in device memory, indexed by q (entry 0 unused).
 struct HpProg {
     const BlockDesc *blocks;
@@ -177,6 +190,7 @@ template <typename TF> cudaError_t launch_geom2d(const Geom2dParams &p, cudaStre
 // off-diagonal blocks.
 template <typename T> cudaError_t launch_vec3_fill(T *out, int64_t n_elem, int n, cudaStream_t s);
 size_t extruded_smem_values(const BlockDesc &b, int L, int nj);
+template <typename T> cudaError_t launch_load(const LoadParams &p, int num_sms, cudaStream_t s);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
 cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);
