@@ -17,6 +17,10 @@ Functions and the passages they follow:
                             (the coefficient of i*omega).
 * ``acoustic_b(...)``    -- ultraweak acoustics stiffness, Eqs. 3.14-3.16, as (part without
                             i*omega, coefficient of i*omega).
+* ``load(space, ...)``   -- load vector l_I = (f, v_I)_K (the right-hand side of Eq. 3.7).
+* ``condense(G, B, l)``  -- static condensation of the test variables, Eq. 3.8 from Eq. 3.7:
+                            B^T G^-1 B and B^T G^-1 l through a Cholesky factorization of G
+                            (numpy / scipy routines as the steps).
 """
 from __future__ import annotations
 
@@ -216,3 +220,35 @@ def acoustic_b(q: int, p: int, L: int, verts: np.ndarray, nthreads: int = 0) -> 
     if r < 0:
         raise ValueError("oracle_acoustic_b: bad arguments")
     return out, int(r) - 1
+
+
+def condense(G: np.ndarray, B: np.ndarray, l: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray | None, int]:
+    """Static condensation of Eq. 3.8 per element: K = B^T G^-1 B and F = B^T G^-1 l.
+
+    ``G[n_elem, n, n]`` symmetric positive definite, ``B[n_elem, n, m]``, ``l[n_elem, n]`` or
+    None.  Steps as the paper names them: Cholesky factorization G = L L^T, the substitutions
+    W = L^-1 B and y = L^-1 l, then the products K = W^T W and F = W^T y (so K = B^T L^-T
+    L^-1 B = B^T G^-1 B).  An element whose G is not positive definite (the factorization
+    fails) gets NaN in K and F.  Returns (K, F or None, first such element or -1).
+    """
+    from scipy.linalg import solve_triangular
+    G = np.asarray(G, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    ne, n, m = B.shape
+    K = np.empty((ne, m, m))
+    F = None if l is None else np.empty((ne, m))
+    bad = -1
+    for e in range(ne):
+        try:
+            Lf = np.linalg.cholesky(G[e])
+        except np.linalg.LinAlgError:
+            K[e] = np.nan
+            if F is not None:
+                F[e] = np.nan
+            bad = e if bad < 0 else bad
+            continue
+        W = solve_triangular(Lf, B[e], lower=True)
+        K[e] = W.T @ W
+        if F is not None:
+            F[e] = W.T @ solve_triangular(Lf, np.asarray(l[e], dtype=np.float64), lower=True)
+    return K, F, bad
