@@ -111,8 +111,10 @@ typedef enum {
     DPG_ERR_TIMEOUT = 9,     /* device: a bounded wait of the FP32 tensor-core kernel for
                                 its own MMAs ran out; the CTA stopped, the matrices of the
                                 call are not valid (first_bad = first element of the CTA) */
-    DPG_ERR_NOT_EXTRUDED = 10 /* device: element is not an extrusion along x1
+    DPG_ERR_NOT_EXTRUDED = 10, /* device: element is not an extrusion along x1
                                 (DPG_MAP_EXTRUDED)                                       */
+    DPG_ERR_NOT_SPD = 11     /* device: dpg_condense met a Gram matrix that is not positive
+                                definite (a pivot <= 0 or not finite)                    */
 } dpg_status;
 
 #define DPG_MAX_Q 12           /* supported test orders: 1 <= q <= DPG_MAX_Q           */
@@ -258,6 +260,31 @@ int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem,
  * Errors: DPG_ERR_ARG, DPG_ERR_NOT_INIT, DPG_ERR_RANGE, DPG_ERR_CUDA. */
 int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vertices,
                        const double *src_coef, int64_t coef_stride, void *out, void *stream);
+
+/* Static condensation of the test variables, element by element (Eq. 3.8 from Eq. 3.7):
+ *   K = B^T G^-1 B   and   F = B^T G^-1 l,
+ * with G the Gram matrix of the test space (n x n, symmetric positive definite), B the
+ * enriched stiffness (n x m; the skeleton block B~ of Eq. 3.8 is handled by passing the
+ * columns [B | B~] as one matrix) and l the load vector.  Steps as the paper names them:
+ * Cholesky factorization G = L L^T, the substitutions W = L^-1 B and y = L^-1 l, and the
+ * products K = W^T W, F = W^T y.  FP64 throughout.
+ *   n_elem   : number of elements (0 does nothing).
+ *   n, m     : 1 <= n <= 8192, 1 <= m <= 8192.
+ *   G        : device, double[n_elem][n][n] row-major.  Only the lower triangle is read;
+ *              it is OVERWRITTEN with the Cholesky factor L (the strict upper triangle is
+ *              left as it was).
+ *   B        : device, double[n_elem][n][m] row-major (rows: test functions, e.g. the
+ *              output of DPG_B_L2VEC_HCURL); OVERWRITTEN with W = L^-1 B.
+ *   l        : device, double[n_elem][n], or NULL; OVERWRITTEN with y = L^-1 l.
+ *   K        : device, double[n_elem][m][m], both triangles written.
+ *   F        : device, double[n_elem][m]; must be NULL exactly when l is NULL.
+ *   stream   : cudaStream_t.
+ * An element whose G is not positive definite gets NaN in K (and F) and is reported as
+ * DPG_ERR_NOT_SPD through dpg_sync_status; its G, B, l are left partially factored.
+ * No workspace is allocated (everything happens in place).
+ * Errors: DPG_ERR_ARG, DPG_ERR_RANGE (n or m), DPG_ERR_CUDA. */
+int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, double *K, double *F,
+                 void *stream);
 
 /* Test hook (not part of the method): the next launch of the FP32 tensor-core kernel
  * (DPG_FP32, general map) runs with its first CTA issuing no stage-B MMA, so that CTA's

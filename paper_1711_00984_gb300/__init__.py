@@ -25,12 +25,13 @@ SPACE_IDS = {"H1": DPG_H1, "HCURL": DPG_HCURL, "HDIV": DPG_HDIV, "L2": DPG_L2, "
              "ACOUSTIC_CROSS": DPG_ACOUSTIC_CROSS, "ACOUSTIC_B": DPG_ACOUSTIC_B}
 STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANGE", 4: "DPG_ERR_CUDA",
           5: "DPG_ERR_DEGENERATE", 6: "DPG_ERR_NOT_AFFINE", 7: "DPG_ERR_NOMEM", 8: "DPG_ERR_SCRATCH",
-          9: "DPG_ERR_TIMEOUT", 10: "DPG_ERR_NOT_EXTRUDED"}
+          9: "DPG_ERR_TIMEOUT", 10: "DPG_ERR_NOT_EXTRUDED",
+          11: "DPG_ERR_NOT_SPD"}
 
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
            "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",
            "dpg_strerror", "dpg_last_cuda_error", "dpg_autotune", "dpg_flops_per_element", "dpg_measure_fma_peak",
-           "dpg_test_stall_tc_once", "dpg_integrate_load"]
+           "dpg_test_stall_tc_once", "dpg_integrate_load", "dpg_condense"]
 
 _lib = None
 _lock = threading.Lock()
@@ -78,10 +79,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_flops_per_element.restype = ctypes.c_double
         lib.dpg_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp]
         lib.dpg_integrate_load.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, i64, vp, vp]
+        lib.dpg_condense.argtypes = [i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         lib.dpg_test_stall_tc_once.argtypes = []
         lib.dpg_test_stall_tc_once.restype = ctypes.c_int
         for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp",
-                     "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak", "dpg_integrate_load"]:
+                     "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak", "dpg_integrate_load",
+                     "dpg_condense"]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -302,6 +305,35 @@ def integrate_load(space, q: int, verts, src_coef, *, fp32: bool = False, out=No
                               out.data_ptr(), _stream_handle(stream))
     _check(code, "dpg_integrate_load")
     return out
+
+
+def dpg_condense(n_elem: int, n: int, m: int, G: int, B: int, l: int, K: int, F: int, stream: int) -> int:
+    """Raw call of the static condensation (integer device pointers, in place on G, B, l)."""
+    return _L().dpg_condense(n_elem, n, m, G or None, B or None, l or None, K or None, F or None,
+                             stream or None)
+
+
+def condense(G, B, l=None, *, K=None, F=None, stream=None):
+    """K = B^T G^-1 B (and F = B^T G^-1 l) per element; G, B, l are overwritten in place.
+
+    ``G[ne, n, n]``, ``B[ne, n, m]``, ``l[ne, n]`` contiguous float64 CUDA tensors.
+    Returns ``(K[ne, m, m], F[ne, m] or None)``.
+    """
+    import torch
+    for name, t in (("G", G), ("B", B), ("l", l)):
+        if t is not None and (not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    ne, n, m = B.shape
+    if tuple(G.shape) != (ne, n, n) or (l is not None and tuple(l.shape) != (ne, n)):
+        raise ValueError("shapes: G[ne, n, n], B[ne, n, m], l[ne, n]")
+    if K is None:
+        K = torch.empty((ne, m, m), dtype=torch.float64, device=B.device)
+    if l is not None and F is None:
+        F = torch.empty((ne, m), dtype=torch.float64, device=B.device)
+    code = dpg_condense(ne, n, m, G.data_ptr(), B.data_ptr(), l.data_ptr() if l is not None else 0,
+                        K.data_ptr(), F.data_ptr() if l is not None else 0, _stream_handle(stream))
+    _check(code, "dpg_condense")
+    return K, (F if l is not None else None)
 
 
 def sync_status(stream=None) -> tuple[int, int]:

@@ -937,6 +937,26 @@ int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vert
     return DPG_OK;
 }
 
+int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, double *K, double *F,
+                 void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (n_elem < 0) return DPG_ERR_ARG;
+    if (n < 1 || n > 8192 || m < 1 || m > 8192) return DPG_ERR_RANGE;
+    if ((l == nullptr) != (F == nullptr)) return DPG_ERR_ARG;
+    if (n_elem == 0) return DPG_OK;
+    if (!G || !B || !K) return DPG_ERR_ARG;
+    DeviceState *ds = nullptr;
+    int r = device_state(&ds);
+    if (r) return r;
+    CondParams p;
+    p.n_elem = n_elem; p.elem_base = 0; p.n = n; p.m = m;
+    p.G = G; p.B = B; p.l = l; p.K = K; p.F = F;
+    p.status = ds->status;
+    const cudaError_t le = launch_condense(p, g_num_sms, (cudaStream_t)stream);
+    if (le != cudaSuccess) return cuda_fail(le, "condense_kernel launch", __LINE__);
+    return DPG_OK;
+}
+
 int dpg_test_stall_tc_once(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_tc_stall_once = 1;
@@ -1054,6 +1074,7 @@ const char *dpg_strerror(int code) {
     case DPG_ERR_SCRATCH: return "request larger than the fixed scratch of dpg_integrate_noalloc";
     case DPG_ERR_TIMEOUT: return "a bounded tensor-core wait ran out (the call's matrices are not valid)";
     case DPG_ERR_NOT_EXTRUDED: return "element is not an extrusion along x1";
+    case DPG_ERR_NOT_SPD: return "Gram matrix is not positive definite";
     }
     return "unknown status";
 }

@@ -1,0 +1,300 @@
+// dpg_condense.cu -- static condensation of the DPG test variables, per element.
+//
+// Eq. 3.7 couples the test-space unknowns s to the trial unknowns through the Gram matrix G
+// and the enriched stiffness B; eliminating s (G is positive definite) gives the condensed
+// system of Eq. 3.8 with K = B^T G^-1 B and F = B^T G^-1 l.  The paper's route: a Cholesky
+// factorization G = L L^T, the substitutions W = L^-1 B and y = L^-1 l, then the products
+// K = W^T W and F = W^T y.
+//
+// condense_kernel: one CTA per element at a time (persistent over the batch), FP64.
+//   * Right-looking blocked Cholesky, panels of CD_NB columns, in place in the lower
+//     triangle of G.  The diagonal block is factored in shared memory by one warp, which
+//     also forms L11^-1; the panel rows below it (L21 = A21 L11^-T) and the matching CD_NB
+//     rows of [B | l] (W1 = L11^-1 B1) are products with that inverse; the trailing lower triangle of G and the rows of [B | l] below the panel are updated
+//     by CD_TM x CD_TM tiles, 4 x 4 outputs per thread.
+//   * The substitution of [B | l] rides along with the factorization (same panel loop),
+//     so W and y overwrite B and l in place.
+//   * K and F: the lower tiles of [W | y]^T [W | y] over all n rows, mirrored into K; the
+//     row of y gives F.
+// Every step is multiply-add work on the FP64 pipe: the kernel is bound by the FP64
+// FMA rate (2 per clock per SM on GB300), not by memory -- one element's G is read and
+// written O(n / CD_NB) times through L2 while it takes O(n^3) multiply-adds.
+#include "dpg_kernels.h"
+
+#include <cuda_runtime.h>
+
+namespace dpg {
+
+constexpr int CD_NB = 32;          // panel width
+constexpr int CD_TM = 64;          // tile edge of the updates
+constexpr int CD_NTH = 256;        // 16 x 16 threads, 4 x 4 outputs each
+constexpr int CD_LDS = CD_TM + 1;  // padded row of the staged operands
+
+__device__ __forceinline__ void report_cd(DevStatus *st, int code, long long elem) {
+    atomicCAS(&st->code, 0, code);
+    atomicMin(&st->first_bad[code], (unsigned long long)elem);
+}
+
+// Column c of the right-hand side [B | l] at row i (c == m: the load vector).
+struct Rhs {
+    double *B, *l;
+    int m;
+    __device__ __forceinline__ double &at(int i, int c) const {
+        return c < m ? B[(size_t)i * m + c] : l[i];
+    }
+};
+
+__global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
+    __shared__ double srd[CD_NB];               // reciprocals of the factor's diagonal
+    __shared__ double sIT[CD_NB][CD_NB + 1];    // (L11^-1)^T
+    __shared__ double sA[CD_NB][CD_LDS];        // staged operand rows (k-major)
+    __shared__ double sB[CD_NB][CD_LDS];
+    // the diagonal block and its factor share sA's storage: they are last read before the
+    // barrier that precedes the first staging into sA of the same panel step
+    double (*sD)[CD_NB + 1] = reinterpret_cast<double (*)[CD_NB + 1]>(&sA[0][0]);
+    __shared__ int sbad;
+    const int n = p.n, m = p.m, mc = m + (p.l ? 1 : 0);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int64_t e = blockIdx.x; e < p.n_elem; e += gridDim.x) {
+        double *G = p.G + (size_t)e * n * n;
+        const Rhs R{ p.B + (size_t)e * n * m, p.l ? p.l + (size_t)e * n : nullptr, m };
+        if (tid == 0) sbad = 0;
+        for (int kb = 0; kb < n; kb += CD_NB) {
+            const int w = n - kb < CD_NB ? n - kb : CD_NB;
+            // 1. the diagonal block (lower triangle), factored by warp 0
+            for (int idx = tid; idx < w * w; idx += CD_NTH) {
+                const int r = idx / w, c = idx - r * w;
+                sD[r][c] = c <= r ? G[(size_t)(kb + r) * n + kb + c] : 0.0;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                for (int j = 0; j < w; ++j) {
+                    if (lane == j) {
+                        const double d = sD[j][j];
+                        if (!(d > 0.0) || !isfinite(d)) sbad = 1;
+                        const double piv = sqrt(d);
+                        sD[j][j] = piv;
+                        srd[j] = 1.0 / piv;
+                    }
+                    __syncwarp();
+                    if (lane > j && lane < w) sD[lane][j] *= srd[j];
+                    __syncwarp();
+                    if (lane > j && lane < w)
+                        for (int c = j + 1; c <= lane; ++c) sD[lane][c] -= sD[lane][j] * sD[c][j];
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            if (sbad) break;
+            for (int idx = tid; idx < w * w; idx += CD_NTH) {
+                const int r = idx / w, c = idx - r * w;
+                if (c <= r) G[(size_t)(kb + r) * n + kb + c] = sD[r][c];
+            }
+            // 2. the panel rows below the block, L21 = A21 L11^-T, and the block's rows of
+            //    [B | l], W1 = L11^-1 B1, as products with L11^-1.  Lane c of warp 0 forms
+            //    column c of L11^-1 by forward substitution (stored transposed: sIT[t][j] =
+            //    (L11^-1)_jt); each warp then owns 4 columns (rows) of the product, so the
+            //    triangular bound t <= j of its sums is the same for all its lanes.
+            if (warp == 0) {
+                const int c = lane;
+                for (int j = 0; j < CD_NB; ++j) {
+                    double v = 0.0;
+                    if (c < w && j < w && j >= c) {
+                        if (j == c) {
+                            v = srd[c];
+                        } else {
+                            double s = 0.0;
+                            for (int t = c; t < j; ++t) s = fma(sD[j][t], sIT[c][t], s);
+                            v = -s * srd[j];
+                        }
+                    }
+                    sIT[c][j] = v;
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            const int r0 = kb + w, nr = n - r0;
+            const int jw = 4 * warp, tmax = jw + 4 < w ? jw + 4 : w;      // t < tmax
+            for (int gi0 = r0; gi0 < n; gi0 += CD_TM) {
+                for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
+                    const int r = idx / CD_NB, t = idx - r * CD_NB;
+                    sA[t][r] = (t < w && gi0 + r < n) ? G[(size_t)(gi0 + r) * n + kb + t] : 0.0;
+                }
+                __syncthreads();
+                double o[2][4] = {};
+                for (int t = 0; t < tmax; ++t) {
+                    const double a0 = sA[t][2 * lane], a1 = sA[t][2 * lane + 1];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const double li = sIT[t][jw + b];                 // (L11^-1)_{jw+b, t}
+                        o[0][b] = fma(a0, li, o[0][b]);
+                        o[1][b] = fma(a1, li, o[1][b]);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int gi = gi0 + 2 * lane + a, j = jw + b;
+                        if (gi < n && j < w) G[(size_t)gi * n + kb + j] = o[a][b];
+                    }
+                __syncthreads();
+            }
+            for (int gj0 = 0; gj0 < mc; gj0 += CD_TM) {
+                for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
+                    const int t = idx / CD_TM, c = idx - t * CD_TM;
+                    sB[t][c] = (t < w && gj0 + c < mc) ? R.at(kb + t, gj0 + c) : 0.0;
+                }
+                __syncthreads();
+                double o[4][2] = {};
+                for (int t = 0; t < tmax; ++t) {
+                    const double b0 = sB[t][2 * lane], b1 = sB[t][2 * lane + 1];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const double li = sIT[t][jw + a];
+                        o[a][0] = fma(li, b0, o[a][0]);
+                        o[a][1] = fma(li, b1, o[a][1]);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int j = jw + a, gj = gj0 + 2 * lane + b;
+                        if (j < w && gj < mc) R.at(kb + j, gj) = o[a][b];
+                    }
+                __syncthreads();
+            }
+            // 3. trailing update: G22 -= L21 L21^T (lower tiles), [B | l]_2 -= L21 W1
+            const int ntr = (nr + CD_TM - 1) / CD_TM, ntc = (mc + CD_TM - 1) / CD_TM;
+            const int tilesA = ntr * (ntr + 1) / 2, tiles = tilesA + ntr * ntc;
+            for (int tile = 0; tile < tiles; ++tile) {
+                int I, J;
+                const bool isA = tile < tilesA;
+                if (isA) {                                 // lower tiles, row by row
+                    I = 0;
+                    while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+                    J = tile - I * (I + 1) / 2;
+                } else {
+                    I = (tile - tilesA) / ntc;
+                    J = (tile - tilesA) - I * ntc;
+                }
+                const int gi0 = r0 + I * CD_TM;                           // rows of G / rhs
+                const int gj0 = isA ? r0 + J * CD_TM : J * CD_TM;         // columns
+                for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
+                    const int r = idx / CD_NB, t = idx - r * CD_NB;
+                    const bool tv = t < w;
+                    sA[t][r] = (tv && gi0 + r < n) ? G[(size_t)(gi0 + r) * n + kb + t] : 0.0;
+                    if (isA) sB[t][r] = (tv && gj0 + r < n) ? G[(size_t)(gj0 + r) * n + kb + t] : 0.0;
+                }
+                if (!isA)
+                    for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
+                        const int t = idx / CD_TM, c = idx - t * CD_TM;
+                        sB[t][c] = (t < w && gj0 + c < mc) ? R.at(kb + t, gj0 + c) : 0.0;
+                    }
+                __syncthreads();
+                double acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int gi = gi0 + ty * 4 + a, gj = gj0 + tx * 4 + b;
+                        const bool ok = gi < n && (isA ? (gj < n && gj <= gi) : gj < mc);
+                        acc[a][b] = ok ? (isA ? G[(size_t)gi * n + gj] : R.at(gi, gj)) : 0.0;
+                    }
+                for (int t = 0; t < w; ++t) {
+                    double av[4], bv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) av[a] = sA[t][ty * 4 + a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) bv[b] = sB[t][tx * 4 + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(-av[a], bv[b], acc[a][b]);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int gi = gi0 + ty * 4 + a, gj = gj0 + tx * 4 + b;
+                        if (gi >= n) continue;
+                        if (isA) {
+                            if (gj < n && gj <= gi) G[(size_t)gi * n + gj] = acc[a][b];
+                        } else if (gj < mc) {
+                            R.at(gi, gj) = acc[a][b];
+                        }
+                    }
+                __syncthreads();
+            }
+        }
+        double *K = p.K + (size_t)e * m * m;
+        double *F = p.F ? p.F + (size_t)e * m : nullptr;
+        if (sbad) {
+            for (int idx = tid; idx < m * m; idx += CD_NTH) K[idx] = __longlong_as_double(0x7ff8000000000000LL);
+            if (F)
+                for (int idx = tid; idx < m; idx += CD_NTH) F[idx] = __longlong_as_double(0x7ff8000000000000LL);
+            if (tid == 0) report_cd(p.status, 11 /*DPG_ERR_NOT_SPD*/, p.elem_base + e);
+            __syncthreads();
+            continue;
+        }
+        // 4. [W | y]^T [W | y], lower tiles over all n rows; K mirrored, F from the y row
+        const int nt = (mc + CD_TM - 1) / CD_TM;
+        for (int tile = 0; tile < nt * (nt + 1) / 2; ++tile) {
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+            const int J = tile - I * (I + 1) / 2;
+            const int ci0 = I * CD_TM, cj0 = J * CD_TM;
+            double acc[4][4] = {};
+            for (int i0 = 0; i0 < n; i0 += CD_NB) {
+                const int h = n - i0 < CD_NB ? n - i0 : CD_NB;
+                for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
+                    const int t = idx / CD_TM, c = idx - t * CD_TM;
+                    sA[t][c] = (t < h && ci0 + c < mc) ? R.at(i0 + t, ci0 + c) : 0.0;
+                    sB[t][c] = (t < h && cj0 + c < mc) ? R.at(i0 + t, cj0 + c) : 0.0;
+                }
+                __syncthreads();
+                for (int t = 0; t < h; ++t) {
+                    double av[4], bv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) av[a] = sA[t][ty * 4 + a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) bv[b] = sB[t][tx * 4 + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int ci = ci0 + ty * 4 + a, cj = cj0 + tx * 4 + b;
+                    if (ci >= mc || cj > ci) continue;
+                    if (ci < m) {
+                        K[(size_t)ci * m + cj] = acc[a][b];
+                        K[(size_t)cj * m + ci] = acc[a][b];
+                    } else if (F && cj < m) {
+                        F[cj] = acc[a][b];                                 // row of y: F = W^T y
+                    }
+                }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_condense(const CondParams &p, int num_sms, cudaStream_t s) {
+    if (p.n_elem == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, condense_kernel, CD_NTH, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t cap = (int64_t)per_sm * num_sms;
+    condense_kernel<<<(unsigned)(p.n_elem < cap ? p.n_elem : cap), CD_NTH, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace dpg

@@ -142,6 +142,18 @@ struct LoadParams {
     DevStatus *status;
 };
 
+// Static condensation (dpg_condense), FP64, in place on G, B and l.
+struct CondParams {
+    int64_t n_elem, elem_base;
+    int n, m;
+    double *G;                 // [n_elem][n][n], lower triangle -> Cholesky factor
+    double *B;                 // [n_elem][n][m] -> L^-1 B
+    double *l;                 // [n_elem][n] -> L^-1 l, or NULL
+    double *K;                 // [n_elem][m][m]
+    double *F;                 // [n_elem][m], NULL when l is NULL
+    DevStatus *status;
+};
+
 // hp batching: per-q programs in device memory, indexed by q (entry 0 unused).
 struct HpProg {
     const BlockDesc *blocks;
@@ -191,6 +203,7 @@ template <typename TF> cudaError_t launch_geom2d(const Geom2dParams &p, cudaStre
 template <typename T> cudaError_t launch_vec3_fill(T *out, int64_t n_elem, int n, cudaStream_t s);
 size_t extruded_smem_values(const BlockDesc &b, int L, int nj);
 template <typename T> cudaError_t launch_load(const LoadParams &p, int num_sms, cudaStream_t s);
+cudaError_t launch_condense(const CondParams &p, int num_sms, cudaStream_t s);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
 cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);

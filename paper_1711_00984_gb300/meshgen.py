@@ -142,6 +142,20 @@ def coeff_pairs(space: str, k: np.ndarray | None, n_elem: int) -> np.ndarray:
     return c
 
 
+def spd_batch(n_elem: int, n: int, cond: float, seed: int) -> np.ndarray:
+    """Symmetric positive definite matrices ``[n_elem, n, n]`` with eigenvalues spaced
+    geometrically in [1, cond] and a random orthogonal eigenbasis (QR of a standard normal
+    draw per matrix), symmetrised exactly: test inputs of the static condensation."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((n_elem, n, n))
+    lam = np.geomspace(1.0, cond, n)
+    for e in range(n_elem):
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        A = (Q * lam) @ Q.T
+        out[e] = 0.5 * (A + A.T)
+    return out
+
+
 def reference_cube(h: float = 1.0, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
     """One axis-aligned cube of side h: ``verts[1, 8, 3]``."""
     o = np.asarray(origin, dtype=np.float64)

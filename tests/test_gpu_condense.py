@@ -1,0 +1,105 @@
+"""Static condensation (Eq. 3.8 from Eq. 3.7) through the C ABI against the oracle.
+
+Both sides factor G by Cholesky and substitute, in FP64 with different summation orders,
+so they differ by the forward error of a Cholesky solve: the test allows
+||K_gpu - K_oracle||_F <= 8 n eps cond(G) ||K_oracle||_F (and the same for F), with
+cond(G) computed here for every element.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1711_00984_gb300 import meshgen
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+
+
+def run(dpg, G, B, l=None):
+    g = torch.from_numpy(np.ascontiguousarray(G)).cuda()
+    b = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    lt = None if l is None else torch.from_numpy(np.ascontiguousarray(l)).cuda()
+    K, F = dpg.condense(g, b, lt)
+    code, bad = dpg.sync_status()
+    return K.cpu().numpy(), (None if F is None else F.cpu().numpy()), g.cpu().numpy(), code, bad
+
+
+def check(G, K, F, Kr, Fr):
+    n = G.shape[1]
+    for e in range(G.shape[0]):
+        tol = max(8 * n * EPS * np.linalg.cond(G[e]), 1e-14)
+        assert np.linalg.norm(K[e] - Kr[e]) <= tol * np.linalg.norm(Kr[e])
+        assert np.array_equal(K[e], K[e].T)
+        if F is not None:
+            assert np.linalg.norm(F[e] - Fr[e]) <= tol * max(np.linalg.norm(Fr[e]), 1e-300)
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (5, 3), (31, 7), (32, 64), (33, 65), (64, 1), (100, 130), (150, 24)])
+@pytest.mark.parametrize("with_l", [False, True])
+def test_condense_random(gpu_lib, n, m, with_l):
+    ne = 5
+    G = meshgen.spd_batch(ne, n, 1e3, seed=n * 1000 + m)
+    rng = np.random.default_rng(n + m)
+    B = rng.standard_normal((ne, n, m))
+    l = rng.standard_normal((ne, n)) if with_l else None
+    K, F, Lg, code, _ = run(gpu_lib, G, B, l)
+    Kr, Fr, bad = oracle.condense(G, B, l)
+    assert code == 0 and bad == -1
+    check(G, K, F, Kr, Fr)
+    # G's lower triangle now holds the Cholesky factor; the strict upper triangle is untouched
+    iu = np.triu_indices(n, 1)
+    for e in range(ne):
+        Lr = np.linalg.cholesky(G[e])
+        assert np.abs(np.tril(Lg[e]) - Lr).max() <= 8 * n * EPS * np.linalg.cond(G[e]) * np.abs(Lr).max()
+        assert np.array_equal(Lg[e][iu], G[e][iu])
+
+
+def test_condense_element_matrices(gpu_lib):
+    """H(curl) Gram (q = 3), mixed B (p = 2) and load vector of oracle-built elements."""
+    v = meshgen.jittered_grid(2, seed=80)[:6]
+    G, _ = oracle.gram("HCURL", 3, 5, v)
+    B, _ = oracle.mixed_b(3, 2, 5, v)
+    l, _ = oracle.load("HCURL", 3, 5, v, np.random.default_rng(81).uniform(-1, 1, 30))
+    K, F, _, code, _ = run(gpu_lib, G, B, l)
+    Kr, Fr, _ = oracle.condense(G, B, l)
+    assert code == 0
+    check(G, K, F, Kr, Fr)
+
+
+def test_condense_config_sizes(gpu_lib):
+    """The sizes of the mixed-stiffness workload: H(curl) q = 6 (n = 882), p = 4 (m = 192),
+    L = 8, two elements."""
+    v = meshgen.jittered_grid(16, seed=3)[[0, 4095]]
+    G, _ = oracle.gram("HCURL", 6, 8, v)
+    B, _ = oracle.mixed_b(6, 4, 8, v)
+    l, _ = oracle.load("HCURL", 6, 8, v, np.random.default_rng(82).uniform(-1, 1, 30))
+    K, F, _, code, _ = run(gpu_lib, G, B, l)
+    Kr, Fr, _ = oracle.condense(G, B, l)
+    assert code == 0
+    check(G, K, F, Kr, Fr)
+
+
+def test_condense_not_spd_and_args(gpu_lib):
+    dpg = gpu_lib
+    G = meshgen.spd_batch(4, 40, 1e2, seed=83)
+    G[2, 35, 35] = -5.0                                   # a negative pivot late in the factorization
+    rng = np.random.default_rng(84)
+    B = rng.standard_normal((4, 40, 9))
+    l = rng.standard_normal((4, 40))
+    K, F, _, code, bad = run(dpg, G, B, l)
+    assert dpg.STATUS[code] == "DPG_ERR_NOT_SPD" and bad == 2
+    assert np.isnan(K[2]).all() and np.isnan(F[2]).all()
+    ok = [0, 1, 3]
+    Kr, Fr, _ = oracle.condense(G[ok], B[ok], l[ok])
+    check(G[ok], K[ok], F[ok], Kr, Fr)
+    g = torch.zeros((1, 4, 4), dtype=torch.float64, device="cuda")
+    b = torch.zeros((1, 4, 2), dtype=torch.float64, device="cuda")
+    k = torch.zeros((1, 2, 2), dtype=torch.float64, device="cuda")
+    f = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
+    L = dpg._L()
+    assert L.dpg_condense(1, 4, 2, g.data_ptr(), b.data_ptr(), None, k.data_ptr(), f.data_ptr(), None) == 1
+    assert L.dpg_condense(1, 0, 2, g.data_ptr(), b.data_ptr(), None, k.data_ptr(), None, None) == 3
+    assert L.dpg_condense(1, 4, 2, None, b.data_ptr(), None, k.data_ptr(), None, None) == 1
+    assert L.dpg_condense(0, 4, 2, None, None, None, None, None, None) == 0
+    assert dpg.sync_status()[0] == 0
