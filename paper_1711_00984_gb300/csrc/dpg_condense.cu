@@ -8,10 +8,10 @@
 //
 // condense_kernel: one CTA per element at a time (persistent over the batch), FP64.
 //   * Right-looking blocked Cholesky, panels of CD_NB columns, in place in the lower
-//     triangle of G.  The diagonal block is factored in shared memory by one warp, which
-//     also forms L11^-1; the panel rows below it (L21 = A21 L11^-T) and the matching CD_NB
+//     triangle of G.  The diagonal block is factored in shared memory by all threads,
+//     which then form L11^-1; the panel rows below it (L21 = A21 L11^-T) and the matching CD_NB
 //     rows of [B | l] (W1 = L11^-1 B1) are products with that inverse; the trailing lower triangle of G and the rows of [B | l] below the panel are updated
-//     by CD_TM x CD_TM tiles, 4 x 4 outputs per thread.
+//     by CD_TM x CD_TM tiles, 16 outputs per thread (TileSpan).
 //   * The substitution of [B | l] rides along with the factorization (same panel loop),
 //     so W and y overwrite B and l in place.
 //   * K and F: the lower tiles of [W | y]^T [W | y] over all n rows, mirrored into K; the
@@ -27,7 +27,7 @@ namespace dpg {
 
 constexpr int CD_NB = 32;          // panel width
 constexpr int CD_TM = 64;          // tile edge of the updates
-constexpr int CD_NTH = 256;        // 16 x 16 threads, 4 x 4 outputs each
+constexpr int CD_NTH = 256;        // 16 outputs of a 64 x 64 tile per thread
 constexpr int CD_LDS = CD_TM + 1;  // padded row of the staged operands
 
 __device__ __forceinline__ void report_cd(DevStatus *st, int code, long long elem) {
@@ -44,6 +44,34 @@ struct Rhs {
     }
 };
 
+// Outputs of one CD_TM x CD_TM tile owned by a thread: column c = tid % 64 and rows
+// rw + 4 k, k < 16, rw = tid / 64 -- the row is the same for a whole warp, so a group of
+// four k whose rows are all outside the tile (or, on a diagonal tile, above the first
+// column of the warp) is skipped by the warp as a whole: on a part with 2 FP64 FMAs per
+// clock per SM the tiles' ragged edges would otherwise cost more than the loads.
+struct TileSpan {
+    int c, rw, rows_v, cols_v, c0;
+    bool lower;
+    __device__ __forceinline__ bool ok(int k) const {
+        const int r = rw + 4 * k;
+        return r < rows_v && c < cols_v && (!lower || c <= r);
+    }
+    __device__ __forceinline__ bool group(int q4) const {
+        const int rlo = rw + 16 * q4, rhi = rlo + 12;                  // rows of k = 4 q4 .. 4 q4 + 3
+        return c0 < cols_v && rlo < rows_v && (!lower || c0 <= rhi);
+    }
+};
+__device__ __forceinline__ TileSpan tile_span(int rows_v, int cols_v, bool lower) {
+    TileSpan s;
+    s.c = threadIdx.x & (CD_TM - 1);
+    s.c0 = threadIdx.x & 32;
+    s.rw = threadIdx.x >> 6;
+    s.rows_v = rows_v < CD_TM ? rows_v : CD_TM;
+    s.cols_v = cols_v < CD_TM ? cols_v : CD_TM;
+    s.lower = lower;
+    return s;
+}
+
 __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
     __shared__ double srd[CD_NB];               // reciprocals of the factor's diagonal
     __shared__ double sIT[CD_NB][CD_NB + 1];    // (L11^-1)^T
@@ -54,8 +82,8 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
     double (*sD)[CD_NB + 1] = reinterpret_cast<double (*)[CD_NB + 1]>(&sA[0][0]);
     __shared__ int sbad;
     const int n = p.n, m = p.m, mc = m + (p.l ? 1 : 0);
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;   // phase 2: warp -> 4 columns, lane -> 2 rows
     for (int64_t e = blockIdx.x; e < p.n_elem; e += gridDim.x) {
         double *G = p.G + (size_t)e * n * n;
         const Rhs R{ p.B + (size_t)e * n * m, p.l ? p.l + (size_t)e * n : nullptr, m };
@@ -68,52 +96,55 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
                 sD[r][c] = c <= r ? G[(size_t)(kb + r) * n + kb + c] : 0.0;
             }
             __syncthreads();
-            if (warp == 0) {
-                for (int j = 0; j < w; ++j) {
-                    if (lane == j) {
-                        const double d = sD[j][j];
-                        if (!(d > 0.0) || !isfinite(d)) sbad = 1;
-                        const double piv = sqrt(d);
-                        sD[j][j] = piv;
-                        srd[j] = 1.0 / piv;
-                    }
-                    __syncwarp();
-                    if (lane > j && lane < w) sD[lane][j] *= srd[j];
-                    __syncwarp();
-                    if (lane > j && lane < w)
-                        for (int c = j + 1; c <= lane; ++c) sD[lane][c] -= sD[lane][j] * sD[c][j];
-                    __syncwarp();
+            // right-looking unblocked factorization of the block by all threads: per column
+            // j, the pivot, then the rank-1 update of the trailing lower triangle with the
+            // column still unscaled (A_rc -= A_rj A_cj / piv^2); the columns are scaled at
+            // the end
+            for (int j = 0; j < w; ++j) {
+                if (tid == 0) {
+                    const double d = sD[j][j];
+                    if (!(d > 0.0) || !isfinite(d)) sbad = 1;
+                    const double piv = sqrt(d);
+                    sD[j][j] = piv;
+                    srd[j] = 1.0 / piv;
                 }
+                __syncthreads();
+                const int nb = w - j - 1;
+                const double rd2 = srd[j] * srd[j];
+                for (int idx = tid; idx < nb * nb; idx += CD_NTH) {
+                    const int r = j + 1 + idx / nb, c = j + 1 + idx % nb;
+                    if (c <= r) sD[r][c] = fma(-sD[r][j] * rd2, sD[c][j], sD[r][c]);
+                }
+                __syncthreads();
+            }
+            if (sbad) break;
+            for (int idx = tid; idx < w * w; idx += CD_NTH) {
+                const int r = idx / w, c = idx - r * w;
+                if (c < r) sD[r][c] *= srd[c];
             }
             __syncthreads();
-            if (sbad) break;
             for (int idx = tid; idx < w * w; idx += CD_NTH) {
                 const int r = idx / w, c = idx - r * w;
                 if (c <= r) G[(size_t)(kb + r) * n + kb + c] = sD[r][c];
             }
             // 2. the panel rows below the block, L21 = A21 L11^-T, and the block's rows of
-            //    [B | l], W1 = L11^-1 B1, as products with L11^-1.  Lane c of warp 0 forms
-            //    column c of L11^-1 by forward substitution (stored transposed: sIT[t][j] =
-            //    (L11^-1)_jt); each warp then owns 4 columns (rows) of the product, so the
-            //    triangular bound t <= j of its sums is the same for all its lanes.
-            if (warp == 0) {
-                const int c = lane;
-                for (int j = 0; j < CD_NB; ++j) {
-                    double v = 0.0;
-                    if (c < w && j < w && j >= c) {
-                        if (j == c) {
-                            v = srd[c];
-                        } else {
-                            double s = 0.0;
-                            for (int t = c; t < j; ++t) s = fma(sD[j][t], sIT[c][t], s);
-                            v = -s * srd[j];
-                        }
-                    }
-                    sIT[c][j] = v;
-                    __syncwarp();
+            //    [B | l], W1 = L11^-1 B1, as products with X = L11^-1.  X is formed row by
+            //    row, X_jj = 1 / L_jj and X_jc = -(sum_{c <= t < j} L_jt X_tc) / L_jj, with 8
+            //    threads per column c summing every 8th term (stored transposed:
+            //    sIT[c][j] = X_jc).  Each warp then owns 4 columns (rows) of the products, so
+            //    the triangular bound t <= j of its sums is the same for all its lanes.
+            {
+                const int cc = tid >> 3, sl = tid & 7;
+                for (int j = 0; j < w; ++j) {
+                    double part = 0.0;
+                    for (int t = cc + sl; t < j; t += 8) part = fma(sD[j][t], sIT[cc][t], part);
+                    part += __shfl_xor_sync(0xffffffffu, part, 1);
+                    part += __shfl_xor_sync(0xffffffffu, part, 2);
+                    part += __shfl_xor_sync(0xffffffffu, part, 4);
+                    if (sl == 0) sIT[cc][j] = cc < j ? -part * srd[j] : (cc == j ? srd[j] : 0.0);
+                    __syncthreads();
                 }
             }
-            __syncthreads();
             const int r0 = kb + w, nr = n - r0;
             const int jw = 4 * warp, tmax = jw + 4 < w ? jw + 4 : w;      // t < tmax
             for (int gi0 = r0; gi0 < n; gi0 += CD_TM) {
@@ -194,38 +225,32 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
                         sB[t][c] = (t < w && gj0 + c < mc) ? R.at(kb + t, gj0 + c) : 0.0;
                     }
                 __syncthreads();
-                double acc[4][4];
+                const TileSpan sp = tile_span(n - gi0, (isA ? n : mc) - gj0, isA && I == J);
+                double acc[16];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int gi = gi0 + ty * 4 + a, gj = gj0 + tx * 4 + b;
-                        const bool ok = gi < n && (isA ? (gj < n && gj <= gi) : gj < mc);
-                        acc[a][b] = ok ? (isA ? G[(size_t)gi * n + gj] : R.at(gi, gj)) : 0.0;
-                    }
-                for (int t = 0; t < w; ++t) {
-                    double av[4], bv[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) av[a] = sA[t][ty * 4 + a];
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) bv[b] = sB[t][tx * 4 + b];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(-av[a], bv[b], acc[a][b]);
+                for (int k = 0; k < 16; ++k) {
+                    const int gi = gi0 + sp.rw + 4 * k, gj = gj0 + sp.c;
+                    acc[k] = sp.ok(k) ? (isA ? G[(size_t)gi * n + gj] : R.at(gi, gj)) : 0.0;
                 }
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    if (!sp.group(q4)) continue;                          // the same for the warp
+                    for (int t = 0; t < w; ++t) {
+                        const double bv = sB[t][sp.c];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int gi = gi0 + ty * 4 + a, gj = gj0 + tx * 4 + b;
-                        if (gi >= n) continue;
-                        if (isA) {
-                            if (gj < n && gj <= gi) G[(size_t)gi * n + gj] = acc[a][b];
-                        } else if (gj < mc) {
-                            R.at(gi, gj) = acc[a][b];
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = 4 * q4 + u;
+                            acc[k] = fma(-sA[t][sp.rw + 4 * k], bv, acc[k]);
                         }
                     }
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if (!sp.ok(k)) continue;
+                    const int gi = gi0 + sp.rw + 4 * k, gj = gj0 + sp.c;
+                    if (isA) G[(size_t)gi * n + gj] = acc[k];
+                    else R.at(gi, gj) = acc[k];
+                }
                 __syncthreads();
             }
         }
@@ -246,7 +271,8 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
             while ((I + 1) * (I + 2) / 2 <= tile) ++I;
             const int J = tile - I * (I + 1) / 2;
             const int ci0 = I * CD_TM, cj0 = J * CD_TM;
-            double acc[4][4] = {};
+            const TileSpan sp = tile_span(mc - ci0, mc - cj0, I == J);
+            double acc[16] = {};
             for (int i0 = 0; i0 < n; i0 += CD_NB) {
                 const int h = n - i0 < CD_NB ? n - i0 : CD_NB;
                 for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
@@ -255,32 +281,31 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
                     sB[t][c] = (t < h && cj0 + c < mc) ? R.at(i0 + t, cj0 + c) : 0.0;
                 }
                 __syncthreads();
-                for (int t = 0; t < h; ++t) {
-                    double av[4], bv[4];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) av[a] = sA[t][ty * 4 + a];
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    if (!sp.group(q4)) continue;
+                    for (int t = 0; t < h; ++t) {
+                        const double bv = sB[t][sp.c];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) bv[b] = sB[t][tx * 4 + b];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = 4 * q4 + u;
+                            acc[k] = fma(sA[t][sp.rw + 4 * k], bv, acc[k]);
+                        }
+                    }
                 }
                 __syncthreads();
             }
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int ci = ci0 + ty * 4 + a, cj = cj0 + tx * 4 + b;
-                    if (ci >= mc || cj > ci) continue;
-                    if (ci < m) {
-                        K[(size_t)ci * m + cj] = acc[a][b];
-                        K[(size_t)cj * m + ci] = acc[a][b];
-                    } else if (F && cj < m) {
-                        F[cj] = acc[a][b];                                 // row of y: F = W^T y
-                    }
+            for (int k = 0; k < 16; ++k) {
+                if (!sp.ok(k)) continue;
+                const int ci = ci0 + sp.rw + 4 * k, cj = cj0 + sp.c;
+                if (ci < m) {
+                    K[(size_t)ci * m + cj] = acc[k];
+                    K[(size_t)cj * m + ci] = acc[k];
+                } else if (F && cj < m) {
+                    F[cj] = acc[k];                                        // row of y: F = W^T y
                 }
+            }
         }
         __syncthreads();
     }

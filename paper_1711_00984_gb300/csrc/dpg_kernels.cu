@@ -1696,7 +1696,7 @@ DPG_HD inline int64_t load_smem_values(int nc, int q, int L) {
 template <typename T>
 __global__ void __launch_bounds__(LOAD_NTH) load_kernel(LoadParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double sv[24], scoef[30], szeta[MAXL], sw[MAXL];
+    __shared__ double sv[24], sa[24], scoef[30], szeta[MAXL], sw[MAXL];
     __shared__ int sbad;
     const int q = p.q, L = p.L, L2 = L * L, L3 = L2 * L, n = q + 1;
     const int space = p.space, nc = (space == S_HCURL || space == S_HDIV) ? 3 : 1;
@@ -1720,20 +1720,37 @@ __global__ void __launch_bounds__(LOAD_NTH) load_kernel(LoadParams p) {
             for (int t = threadIdx.x; t < 10 * nc; t += LOAD_NTH) scoef[t] = p.coef[e * p.coef_stride + t];
         if (threadIdx.x == 0) sbad = 0;
         __syncthreads();
-        // point values W_a(l, m, n) = w |J| f . (pulled-back a-th unit vector), FP64
+        // point values W_a(l, m, n) = w |J| f . (pulled-back a-th unit vector), FP64.  The
+        // trilinear map in monomial form, x = sum_S a_S prod_{d in S} xi_d over the subsets
+        // S of {1, 2, 3} (bit d-1 of S), a_S = sum_{c subset of S} (-1)^{|S| - |c|} x_c
+        // (expanding prod_d (1 - xi_d or xi_d) of every vertex), so that x and the columns
+        // of J are a few multiply-adds per point.
+        for (int t = threadIdx.x; t < 24; t += LOAD_NTH) {
+            const int S = t / 3, i = t - 3 * (t / 3);
+            double a = 0.0;
+            for (int c = 0; c < 8; ++c)
+                if ((c & S) == c) a += ((__popc(S ^ c) & 1) ? -1.0 : 1.0) * sv[3 * c + i];
+            sa[t] = a;
+        }
+        __syncthreads();
         for (int pt = threadIdx.x; pt < L3; pt += LOAD_NTH) {
             const int l = pt / L2, m = (pt / L) % L, k = pt % L;
             const double x1 = szeta[l], x2 = szeta[m], x3 = szeta[k];
-            Jac g;
-            trilinear_jac(sv, x1, x2, x3, g);
-            finish_jac(g);
-            double x[3] = { 0.0, 0.0, 0.0 };
+            const double x12 = x1 * x2, x13 = x1 * x3, x23 = x2 * x3, x123 = x12 * x3;
+            double x[3], J[3][3];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const double N = ((c & 1) ? x1 : 1.0 - x1) * ((c & 2) ? x2 : 1.0 - x2) * ((c & 4) ? x3 : 1.0 - x3);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) x[i] += sv[3 * c + i] * N;
+            for (int i = 0; i < 3; ++i) {
+                const double *A = sa + i;              // a_S of component i at A[3 S]
+                x[i] = A[0] + A[3] * x1 + A[6] * x2 + A[12] * x3 + A[9] * x12 + A[15] * x13 + A[18] * x23 + A[21] * x123;
+                J[i][0] = A[3] + A[9] * x2 + A[15] * x3 + A[21] * x23;
+                J[i][1] = A[6] + A[9] * x1 + A[18] * x3 + A[21] * x13;
+                J[i][2] = A[12] + A[15] * x1 + A[18] * x2 + A[21] * x12;
             }
+            // cofactors: adj(J)_{di} = C_{id}; |J| = sum_d J_{0d} C_{0d}
+            const double C00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            const double C01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            const double C02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            const double det = J[0][0] * C00 + J[0][1] * C01 + J[0][2] * C02;
             const double mono[10] = { 1.0, x[0], x[1], x[2], x[0] * x[0], x[1] * x[1], x[2] * x[2],
                                       x[0] * x[1], x[0] * x[2], x[1] * x[2] };
             double f[3] = { 0.0, 0.0, 0.0 };
@@ -1741,19 +1758,26 @@ __global__ void __launch_bounds__(LOAD_NTH) load_kernel(LoadParams p) {
 #pragma unroll
                 for (int t = 0; t < 10; ++t) f[c] += scoef[10 * c + t] * mono[t];
             const double wt = sw[l] * sw[m] * sw[k];
-            if (!(g.det > 0.0) || !isfinite(g.det)) sbad = 1;
+            if (!(det > 0.0) || !isfinite(det)) sbad = 1;
             if (space == S_H1) {
-                wf[pt] = (T)(wt * g.det * f[0]);                           // Eq. 2.3
+                wf[pt] = (T)(wt * det * f[0]);                             // Eq. 2.3
             } else if (space == S_L2) {
                 wf[pt] = (T)(wt * f[0]);                                   // Eq. 2.6: |J|^-1 |J|
             } else if (space == S_HCURL) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a)                                // Eq. 2.4: (J^-1 f)_a |J|
-                    wf[a * L3 + pt] = (T)(wt * g.det * (g.Ji[a][0] * f[0] + g.Ji[a][1] * f[1] + g.Ji[a][2] * f[2]));
+                // Eq. 2.4: |J| (J^-1 f)_a = (adj(J) f)_a, adj(J)_{ai} = C_{ia}
+                const double C10 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+                const double C11 = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+                const double C12 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+                const double C20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+                const double C21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+                const double C22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+                wf[pt] = (T)(wt * (C00 * f[0] + C10 * f[1] + C20 * f[2]));
+                wf[L3 + pt] = (T)(wt * (C01 * f[0] + C11 * f[1] + C21 * f[2]));
+                wf[2 * L3 + pt] = (T)(wt * (C02 * f[0] + C12 * f[1] + C22 * f[2]));
             } else {
 #pragma unroll
                 for (int a = 0; a < 3; ++a)                                // Eq. 2.5: (J^T f)_a
-                    wf[a * L3 + pt] = (T)(wt * (g.J[0][a] * f[0] + g.J[1][a] * f[1] + g.J[2][a] * f[2]));
+                    wf[a * L3 + pt] = (T)(wt * (J[0][a] * f[0] + J[1][a] * f[1] + J[2][a] * f[2]));
             }
         }
         __syncthreads();
