@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-form sub-measurement")
-    ap.add_argument("--workload", default=None, choices=sorted(SECONDARY) + ["hp_q2to8_16x16x16"],
+    ap.add_argument("--workload", default=None,
+                    choices=sorted(SECONDARY) + ["hp_q2to8_16x16x16", "dpg_q6_p4_16x16x16"],
                     help="secondary workload record")
     ap.add_argument("--only", default=None, help="profiling case: run only this space's call (H1, HCURL, HDIV, L2)")
     ap.add_argument("--map", default="general", choices=["general", "affine"], help="map of the --only case")
@@ -581,6 +582,104 @@ def run_hp(args):
     print(json.dumps(rec), flush=True)
 
 
+def condense_flops(n: int, mc: int) -> float:
+    """Algorithmic flops of one condensation (2 per multiply-add): Cholesky n^3/6, the
+    substitutions of mc right-hand sides mc n^2/2, the lower triangle of W^T W n mc(mc+1)/2."""
+    return 2.0 * (n ** 3 / 6.0 + mc * n * n / 2.0 + n * mc * (mc + 1) / 2.0)
+
+
+def run_dpg_chain(args):
+    """The DPG element routine of the mixed-stiffness workload (Eqs. 3.7-3.8): Gram matrix G
+    of H(curl) q = 6, enriched stiffness B (vector-L2 trial p = 4), load vector l (a
+    degree-2 source), then the condensed K = B^T G^-1 B and F = B^T G^-1 l, per stage."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1711_00984_gb300 as dpg
+    from paper_1711_00984_gb300 import build as dbuild
+    from paper_1711_00984_gb300 import meshgen
+    dbuild.build()
+    dpg.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    q, p, L = 6, 4, 8
+    w = meshgen.workload("hcurl_q6_p4_16x16x16")
+    vn = np.ascontiguousarray(w["verts"])
+    v = torch.from_numpy(vn).to(dev)
+    ne = v.shape[0]
+    src = np.random.default_rng(6).uniform(-1.0, 1.0, 30)
+    ct = torch.from_numpy(src).to(dev)
+    dpg.dpg_tables_init_L(q, L, "HCURL")
+    dpg.dpg_tables_init_L(q, L, "B")
+    n, m = dpg.dpg_matrix_rows("HCURL", q), dpg.dpg_matrix_cols("B", p, q)
+    G = torch.empty((ne, n, n), dtype=torch.float64, device=dev)
+    B = torch.empty((ne, n, m), dtype=torch.float64, device=dev)
+    l = torch.empty((ne, n), dtype=torch.float64, device=dev)
+    K = torch.empty((ne, m, m), dtype=torch.float64, device=dev)
+    F = torch.empty((ne, m), dtype=torch.float64, device=dev)
+    G0, B0, l0 = torch.empty_like(G), torch.empty_like(B), torch.empty_like(l)
+    peak64 = dpg.dpg_measure_fma_peak(64, sh)
+    stages = {
+        "gram": lambda: dpg.integrate("HCURL", q, v, out=G0, stream=stream),
+        "stiffness_b": lambda: dpg.integrate("B", q, v, p=p, out=B0, stream=stream),
+        "load": lambda: dpg.integrate_load("HCURL", q, v, ct, out=l0, stream=stream),
+        "condense": lambda: dpg.condense(G, B, l, K=K, F=F, stream=stream),
+    }
+
+    def refresh():                           # the condensation works in place on G, B, l
+        G.copy_(G0); B.copy_(B0); l.copy_(l0)
+    for f in ("gram", "stiffness_b", "load"):
+        stages[f]()
+    refresh()
+    rec = {"workload": "dpg_q6_p4_16x16x16", "q": q, "p_trial": p, "L": L, "elements": ne, "n": n, "m": m,
+           "stages": {}}
+    steps = max(1, min(args.steps, 5))
+    for name, fn in stages.items():
+        for _ in range(max(1, min(args.warmup, 2))):
+            if name == "condense":
+                refresh()
+            fn()
+        ts = []
+        for _ in range(steps):
+            if name == "condense":
+                refresh()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        code, bad = dpg.dpg_sync_status(sh)
+        assert code == 0, (name, code, bad)
+        rec["stages"][name] = {"ms": float(np.median(ts))}
+    cf = condense_flops(n, m + 1) * ne
+    cms = rec["stages"]["condense"]["ms"]
+    rec["stages"]["condense"].update({"tflops": cf / (cms * 1e-3) / 1e12, "bound": "alu",
+                                      "roofline_frac": cf / (cms * 1e-3) / peak64,
+                                      "flops_per_element": cf / ne})
+    tot = sum(st["ms"] for st in rec["stages"].values())
+    rec["element_routine_ms"] = tot
+    rec["element_routines_per_s"] = ne / (tot * 1e-3)
+    rec["measured_fp64_fma_peak_tflops"] = peak64 / 1e12
+    # the oracle's chain on a bounded sample: its rate and the agreement of K and F
+    idx = [0, ne - 1]
+    t0 = time.perf_counter()
+    Go, _ = oracle.gram("HCURL", q, L, vn[idx])
+    Bo, _ = oracle.mixed_b(q, p, L, vn[idx])
+    lo, _ = oracle.load("HCURL", q, L, vn[idx], src)
+    Ko, Fo, _ = oracle.condense(Go, Bo, lo)
+    dt = time.perf_counter() - t0
+    Kg, Fg = K[idx].cpu().numpy(), F[idx].cpu().numpy()
+    rec["sample_rel_err"] = {"K": float(max(np.linalg.norm(Kg[i] - Ko[i]) / np.linalg.norm(Ko[i]) for i in range(2))),
+                             "F": float(max(np.linalg.norm(Fg[i] - Fo[i]) / np.linalg.norm(Fo[i]) for i in range(2)))}
+    rec["cpu_baseline"] = {"value": 2 / dt, "unit": "element routines/s", "cores": host_cores(), "kind": "oracle",
+                           "sample": "elements 0 and 4095: gram, mixed_b, load, condense"}
+    print(json.dumps(rec), flush=True)
+
+
 def run_case(args):
     """One (space, map, form) call of the workload on a subset of elements, for profilers."""
     import torch
@@ -612,6 +711,8 @@ def main():
         run_case(args)
     elif args.workload == "hp_q2to8_16x16x16":
         run_hp(args)
+    elif args.workload == "dpg_q6_p4_16x16x16":
+        run_dpg_chain(args)
     elif args.workload:
         run_secondary(args)
     elif args.impl == "reference":
