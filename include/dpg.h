@@ -286,6 +286,27 @@ int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vert
 int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, double *K, double *F,
                  void *stream);
 
+/* The DPG element routine of the mixed-stiffness pair in one call (Sec. 3, Eqs. 3.7-3.8):
+ * per element, the Gram matrix G of the H(curl) test space of order q_test (coefficients as
+ * in dpg_integrate), the enriched stiffness B of DPG_B_L2VEC_HCURL with trial order p_trial,
+ * the load vector l of dpg_integrate_load (optional), then K = B^T G^-1 B and F = B^T G^-1 l
+ * as in dpg_condense.  G, B and l live only in a library workspace (stream-ordered, from the
+ * library pool, processed in chunks of at most 8 GB): the caller receives K and F.
+ *   q_test, p_trial : tables for (DPG_HCURL, q_test) and (DPG_B_L2VEC_HCURL, q_test) must be
+ *                     initialised with the same rule L; 1 <= p_trial <= q_test.
+ *   vertices        : device, double[n_elem][8][3].
+ *   coeffs          : device, double[n_elem][2] (G's mass and curl weights) or NULL.
+ *   src_coef        : device, the source of dpg_integrate_load for H(curl) (30 values, or
+ *                     per element with coef_stride >= 30), or NULL for no load vector.
+ *   K               : device, double[n_elem][m][m], m = 3 p_trial^3.
+ *   F               : device, double[n_elem][m]; NULL exactly when src_coef is NULL.
+ * Device-detected errors (a degenerate element: DPG_ERR_DEGENERATE; G not positive definite:
+ * DPG_ERR_NOT_SPD) through dpg_sync_status, element indices relative to the call.
+ * Errors: DPG_ERR_ARG, DPG_ERR_NOT_INIT, DPG_ERR_RANGE, DPG_ERR_CUDA, DPG_ERR_NOMEM. */
+int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *vertices,
+                         const double *coeffs, const double *src_coef, int64_t coef_stride, double *K,
+                         double *F, void *stream);
+
 /* Test hook (not part of the method): the next launch of the FP32 tensor-core kernel
  * (DPG_FP32, general map) runs with its first CTA issuing no stage-B MMA, so that CTA's
  * bounded mbarrier waits run out (after about a second), the CTA releases its tensor

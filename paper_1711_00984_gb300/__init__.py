@@ -31,7 +31,8 @@ STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANG
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
            "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",
            "dpg_strerror", "dpg_last_cuda_error", "dpg_autotune", "dpg_flops_per_element", "dpg_measure_fma_peak",
-           "dpg_test_stall_tc_once", "dpg_integrate_load", "dpg_condense"]
+           "dpg_test_stall_tc_once", "dpg_integrate_load", "dpg_condense",
+           "dpg_condensed_system"]
 
 _lib = None
 _lock = threading.Lock()
@@ -80,11 +81,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp]
         lib.dpg_integrate_load.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, i64, vp, vp]
         lib.dpg_condense.argtypes = [i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+        lib.dpg_condensed_system.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, i64, vp, vp, vp]
         lib.dpg_test_stall_tc_once.argtypes = []
         lib.dpg_test_stall_tc_once.restype = ctypes.c_int
         for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp",
                      "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak", "dpg_integrate_load",
-                     "dpg_condense"]:
+                     "dpg_condense", "dpg_condensed_system"]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -334,6 +336,40 @@ def condense(G, B, l=None, *, K=None, F=None, stream=None):
                         K.data_ptr(), F.data_ptr() if l is not None else 0, _stream_handle(stream))
     _check(code, "dpg_condense")
     return K, (F if l is not None else None)
+
+
+def dpg_condensed_system(q_test: int, p_trial: int, n_elem: int, vertices: int, coeffs: int, src_coef: int,
+                         coef_stride: int, K: int, F: int, stream: int) -> int:
+    """Raw call of the one-call DPG element routine (integer device pointers)."""
+    return _L().dpg_condensed_system(q_test, p_trial, n_elem, vertices or None, coeffs or None, src_coef or None,
+                                     coef_stride, K or None, F or None, stream or None)
+
+
+def condensed_system(q: int, p: int, verts, coeffs=None, src_coef=None, *, K=None, F=None, stream=None):
+    """K[n, m, m] = B^T G^-1 B and F[n, m] = B^T G^-1 l of the H(curl) q / vector-L2 p pair.
+
+    ``src_coef``: None, a float64 CUDA tensor of 30 values, or ``[n, 30]`` (per element).
+    Tables for ("HCURL", q) and ("B", q) must have been initialised with the same rule.
+    """
+    import torch
+    if not verts.is_cuda or verts.dtype != torch.float64 or not verts.is_contiguous():
+        raise ValueError("verts must be a contiguous float64 CUDA tensor [n, 8, 3]")
+    n = verts.shape[0]
+    m = 3 * p ** 3
+    stride = 0
+    if src_coef is not None:
+        if not src_coef.is_cuda or src_coef.dtype != torch.float64 or not src_coef.is_contiguous():
+            raise ValueError("src_coef must be a contiguous float64 CUDA tensor")
+        stride = 0 if src_coef.dim() == 1 else 30
+    if K is None:
+        K = torch.empty((n, m, m), dtype=torch.float64, device=verts.device)
+    if src_coef is not None and F is None:
+        F = torch.empty((n, m), dtype=torch.float64, device=verts.device)
+    code = dpg_condensed_system(q, p, n, verts.data_ptr(), coeffs.data_ptr() if coeffs is not None else 0,
+                                src_coef.data_ptr() if src_coef is not None else 0, stride, K.data_ptr(),
+                                F.data_ptr() if src_coef is not None else 0, _stream_handle(stream))
+    _check(code, "dpg_condensed_system")
+    return K, (F if src_coef is not None else None)
 
 
 def sync_status(stream=None) -> tuple[int, int]:

@@ -405,7 +405,7 @@ struct OutGeom {
 
 template <typename T>
 int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
-                const double *coeffs, T *out, cudaStream_t s, OutGeom og) {
+                const double *coeffs, T *out, cudaStream_t s, OutGeom og, int64_t base = 0) {
     constexpr bool f32 = sizeof(T) == 4;
     const Program &pr = f32 ? pe->prog32 : pe->prog;
     const int L = pr.L, L3 = L * L * L;
@@ -423,7 +423,7 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
         const int64_t ne = std::min(chunk, n_elem - e0);
         GeomParams g;
         g.space = pr.space; g.L = L; g.nfields = pr.nfields;
-        g.n_elem = ne; g.elem_base = e0;
+        g.n_elem = ne; g.elem_base = base + e0;
         g.verts = verts + 24 * e0;
         g.coeffs = coeffs ? coeffs + 2 * e0 : nullptr;
         g.zeta = te->zeta; g.w = te->w;
@@ -955,6 +955,69 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
     const cudaError_t le = launch_condense(p, g_num_sms, (cudaStream_t)stream);
     if (le != cudaSuccess) return cuda_fail(le, "condense_kernel launch", __LINE__);
     return DPG_OK;
+}
+
+int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *vertices,
+                         const double *coeffs, const double *src_coef, int64_t coef_stride, double *K,
+                         double *F, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (n_elem < 0 || (coef_stride != 0 && coef_stride < 30)) return DPG_ERR_ARG;
+    if ((src_coef == nullptr) != (F == nullptr)) return DPG_ERR_ARG;
+    ProgEntry *pg, *pb; TableEntry *tg, *tb; DeviceState *ds;
+    int r = resolve(S_HCURL, 0, q_test, &pg, &tg, &ds);
+    if (r) return r;
+    if ((r = resolve(S_B, p_trial, q_test, &pb, &tb, &ds))) return r;
+    if (tg != tb) return DPG_ERR_NOT_INIT;          // G and B must use the same rule
+    if (n_elem == 0) return DPG_OK;
+    if (!vertices || !K) return DPG_ERR_ARG;
+    const int n = pg->prog.rows, m = pb->prog.cols;
+    const bool with_l = src_coef != nullptr;
+    // per element: G, B and l in a pool workspace; chunks of whole waves of the
+    // condensation kernel (two CTAs per SM) within about 8 GB, so that only the last
+    // chunk has a partial wave
+    const size_t per_elem = ((size_t)n * n + (size_t)n * m + (with_l ? n : 0)) * sizeof(double);
+    int64_t chunk = (int64_t)((size_t(8) << 30) / per_elem);
+    const int64_t wave = 2 * (int64_t)g_num_sms;
+    if (chunk >= wave) chunk -= chunk % wave;
+    if (chunk < 1) chunk = 1;
+    if (chunk > n_elem) chunk = n_elem;
+    void *ws = nullptr;
+    CK(cudaMallocFromPoolAsync(&ws, (size_t)chunk * per_elem, ds->pool, s));
+    double *G = static_cast<double *>(ws);
+    double *B = G + (size_t)chunk * n * n;
+    double *l = with_l ? B + (size_t)chunk * n * m : nullptr;
+    int rc = DPG_OK;
+    for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK; e0 += chunk) {
+        const int64_t ne = n_elem - e0 < chunk ? n_elem - e0 : chunk;
+        const double *v = vertices + 24 * e0;
+        rc = run_general<double>(ds, pg, tg, ne, v, coeffs ? coeffs + 2 * e0 : nullptr, G, s,
+                                 OutGeom{ n, (int64_t)n * n }, e0);
+        if (rc) break;
+        rc = run_general<double>(ds, pb, tb, ne, v, nullptr, B, s, OutGeom{ m, (int64_t)n * m }, e0);
+        if (rc) break;
+        if (with_l) {
+            LoadParams lp;
+            lp.space = S_HCURL; lp.q = q_test; lp.L = tg->host.L;
+            lp.n_elem = ne; lp.elem_base = e0;
+            lp.verts = v; lp.coef = coef_stride ? src_coef + e0 * coef_stride : src_coef;
+            lp.coef_stride = coef_stride;
+            lp.zeta = tg->zeta; lp.w = tg->w; lp.pp = tg->pp64;
+            lp.out = l; lp.status = ds->status;
+            const cudaError_t le = launch_load<double>(lp, g_num_sms, s);
+            if (le != cudaSuccess) { rc = cuda_fail(le, "load_kernel launch", __LINE__); break; }
+        }
+        CondParams cp;
+        cp.n_elem = ne; cp.elem_base = e0; cp.n = n; cp.m = m;
+        cp.G = G; cp.B = B; cp.l = l;
+        cp.K = K + (size_t)e0 * m * m; cp.F = with_l ? F + (size_t)e0 * m : nullptr;
+        cp.status = ds->status;
+        const cudaError_t le = launch_condense(cp, g_num_sms, s);
+        if (le != cudaSuccess) rc = cuda_fail(le, "condense_kernel launch", __LINE__);
+    }
+    const cudaError_t fe = cudaFreeAsync(ws, s);
+    if (fe != cudaSuccess && rc == DPG_OK) rc = cuda_fail(fe, "cudaFreeAsync", __LINE__);
+    return rc;
 }
 
 int dpg_test_stall_tc_once(void) {

@@ -72,6 +72,32 @@ __device__ __forceinline__ TileSpan tile_span(int rows_v, int cols_v, bool lower
     return s;
 }
 
+// acc[k] += (or -=) sum_{t < tn} sA[t][rw + 4 k] sB[t][c] over a thread's outputs.  The
+// active groups of four k form one contiguous range; when it is all four (every tile
+// but the ragged and diagonal ones) the sixteen chains advance together, else group by
+// group with the inactive groups skipped by the whole warp.
+template <bool NEG>
+__device__ __forceinline__ void tile_fma(double (&acc)[16], const double (*sA)[CD_LDS],
+                                         const double (*sB)[CD_LDS], const TileSpan &sp, int tn) {
+    if (sp.group(0) && sp.group(3)) {
+        for (int t = 0; t < tn; ++t) {
+            const double bv = NEG ? -sB[t][sp.c] : sB[t][sp.c];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc[k] = fma(sA[t][sp.rw + 4 * k], bv, acc[k]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+        if (!sp.group(q4)) continue;                                       // the same for the warp
+        for (int t = 0; t < tn; ++t) {
+            const double bv = NEG ? -sB[t][sp.c] : sB[t][sp.c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[4 * q4 + u] = fma(sA[t][sp.rw + 16 * q4 + 4 * u], bv, acc[4 * q4 + u]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
     __shared__ double srd[CD_NB];               // reciprocals of the factor's diagonal
     __shared__ double sIT[CD_NB][CD_NB + 1];    // (L11^-1)^T
@@ -232,18 +258,7 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
                     const int gi = gi0 + sp.rw + 4 * k, gj = gj0 + sp.c;
                     acc[k] = sp.ok(k) ? (isA ? G[(size_t)gi * n + gj] : R.at(gi, gj)) : 0.0;
                 }
-#pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    if (!sp.group(q4)) continue;                          // the same for the warp
-                    for (int t = 0; t < w; ++t) {
-                        const double bv = sB[t][sp.c];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = 4 * q4 + u;
-                            acc[k] = fma(-sA[t][sp.rw + 4 * k], bv, acc[k]);
-                        }
-                    }
-                }
+                tile_fma<true>(acc, sA, sB, sp, w);
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     if (!sp.ok(k)) continue;
@@ -281,18 +296,7 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
                     sB[t][c] = (t < h && cj0 + c < mc) ? R.at(i0 + t, cj0 + c) : 0.0;
                 }
                 __syncthreads();
-#pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    if (!sp.group(q4)) continue;
-                    for (int t = 0; t < h; ++t) {
-                        const double bv = sB[t][sp.c];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = 4 * q4 + u;
-                            acc[k] = fma(sA[t][sp.rw + 4 * k], bv, acc[k]);
-                        }
-                    }
-                }
+                tile_fma<false>(acc, sA, sB, sp, h);
                 __syncthreads();
             }
 #pragma unroll

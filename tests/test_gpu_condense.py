@@ -103,3 +103,67 @@ def test_condense_not_spd_and_args(gpu_lib):
     assert L.dpg_condense(1, 4, 2, None, b.data_ptr(), None, k.data_ptr(), None, None) == 1
     assert L.dpg_condense(0, 4, 2, None, None, None, None, None, None) == 0
     assert dpg.sync_status()[0] == 0
+
+
+def _chain(dpg, q, p, v, c, src):
+    """The stage-by-stage route through the separate entry points."""
+    G = dpg.integrate("HCURL", q, v, c)
+    B = dpg.integrate("B", q, v, p=p)
+    l = dpg.integrate_load("HCURL", q, v, src)
+    return dpg.condense(G, B, l)
+
+
+def test_condensed_system_one_call(gpu_lib):
+    """dpg_condensed_system equals the separate calls bit for bit, and the oracle's chain."""
+    dpg = gpu_lib
+    q, p = 3, 2
+    dpg.dpg_tables_init(q, "HCURL")
+    dpg.dpg_tables_init(q, "B")
+    vn = meshgen.jittered_grid(4, seed=85)[:37]
+    rng = np.random.default_rng(86)
+    cn = np.stack([rng.uniform(0.5, 2, 37), rng.uniform(0.5, 2, 37)], axis=1)
+    src = rng.uniform(-1, 1, 30)
+    v, c, s = (torch.from_numpy(a).cuda() for a in (vn, cn, src))
+    K, F = dpg.condensed_system(q, p, v, c, s)
+    K2, F2 = _chain(dpg, q, p, v, c, s)
+    code, _ = dpg.sync_status()
+    assert code == 0
+    assert torch.equal(K, K2) and torch.equal(F, F2)
+    idx = [0, 17, 36]
+    G, _ = oracle.gram("HCURL", q, q + 2, vn[idx], cn[idx])
+    B, _ = oracle.mixed_b(q, p, q + 2, vn[idx])
+    l, _ = oracle.load("HCURL", q, q + 2, vn[idx], src)
+    Kr, Fr, _ = oracle.condense(G, B, l)
+    check(G, K.cpu().numpy()[idx], F.cpu().numpy()[idx], Kr, Fr)
+    Kn, Fn = dpg.condensed_system(q, p, v, c)                 # no load vector
+    assert Fn is None and torch.equal(Kn, K)
+
+
+def test_condensed_system_chunks_and_errors(gpu_lib):
+    """1400 elements of the q = 6 / p = 4 pair run in two workspace chunks (912 and 488 on
+    152 SMs): equal to the separate calls; an inverted element in the second chunk is
+    reported by its index."""
+    dpg = gpu_lib
+    q, p = 6, 4
+    dpg.dpg_tables_init_L(q, 8, "HCURL")
+    dpg.dpg_tables_init_L(q, 8, "B")
+    vn = meshgen.jittered_grid(16, seed=3)[:1400].copy()
+    src = torch.from_numpy(np.random.default_rng(87).uniform(-1, 1, 30)).cuda()
+    v = torch.from_numpy(vn).cuda()
+    K, F = dpg.condensed_system(q, p, v, None, src)
+    K2, F2 = _chain(dpg, q, p, v, None, src)
+    assert dpg.sync_status()[0] == 0
+    assert torch.equal(K, K2) and torch.equal(F, F2)
+    del K2, F2
+    vn[1000] = vn[1000][[1, 0, 3, 2, 5, 4, 7, 6]]
+    v = torch.from_numpy(vn).cuda()
+    K, F = dpg.condensed_system(q, p, v, None, src)
+    code, bad = dpg.sync_status()
+    assert dpg.STATUS[code] == "DPG_ERR_DEGENERATE" and bad == 1000
+    assert torch.isnan(K[1000]).all() and torch.isfinite(K[999]).all() and torch.isfinite(K[1001]).all()
+    L = dpg._L()
+    k = torch.empty((1, 192, 192), dtype=torch.float64, device="cuda")
+    assert L.dpg_condensed_system(q, 7, 1, v.data_ptr(), None, None, 0, k.data_ptr(), None, None) == 1   # p > q
+    assert L.dpg_condensed_system(q, p, 1, v.data_ptr(), None, src.data_ptr(), 0, k.data_ptr(), None, None) == 1
+    assert L.dpg_condensed_system(q, p, 0, None, None, None, 0, None, None, None) == 0
+    assert dpg.sync_status()[0] == 0
