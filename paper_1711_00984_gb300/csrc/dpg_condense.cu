@@ -14,8 +14,8 @@
 //     by CD_TM x CD_TM tiles, 16 outputs per thread (TileSpan).
 //   * The substitution of [B | l] rides along with the factorization (same panel loop),
 //     so W and y overwrite B and l in place.
-//   * K and F: the lower tiles of [W | y]^T [W | y] over all n rows, mirrored into K; the
-//     row of y gives F.
+//   * K: the lower tiles of W^T W over all n rows, mirrored; F = W^T y by one dot product
+//     per column (the load column is likewise a dot product per row in the updates).
 // Every step is multiply-add work on the FP64 pipe: the kernel is bound by the FP64
 // FMA rate (2 per clock per SM on GB300), not by memory -- one element's G is read and
 // written O(n / CD_NB) times through L2 while it takes O(n^3) multiply-adds.
@@ -224,7 +224,21 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
                 __syncthreads();
             }
             // 3. trailing update: G22 -= L21 L21^T (lower tiles), [B | l]_2 -= L21 W1
-            const int ntr = (nr + CD_TM - 1) / CD_TM, ntc = (mc + CD_TM - 1) / CD_TM;
+            // the load column is a plain dot product per row (no 64-wide tile for one column):
+            // l_i -= sum_t L_{i, kb+t} y_{kb+t}, i >= r0
+            if (R.l)
+                for (int i = r0 + tid; i < n; i += CD_NTH) {
+                    const double *Li = G + (size_t)i * n + kb;
+                    double s0 = 0.0, s1 = 0.0;
+                    int t = 0;
+                    for (; t + 1 < w; t += 2) {
+                        s0 = fma(Li[t], R.l[kb + t], s0);
+                        s1 = fma(Li[t + 1], R.l[kb + t + 1], s1);
+                    }
+                    if (t < w) s0 = fma(Li[t], R.l[kb + t], s0);
+                    R.l[i] -= s0 + s1;
+                }
+            const int ntr = (nr + CD_TM - 1) / CD_TM, ntc = (m + CD_TM - 1) / CD_TM;
             const int tilesA = ntr * (ntr + 1) / 2, tiles = tilesA + ntr * ntc;
             for (int tile = 0; tile < tiles; ++tile) {
                 int I, J;
@@ -248,15 +262,15 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
                 if (!isA)
                     for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
                         const int t = idx / CD_TM, c = idx - t * CD_TM;
-                        sB[t][c] = (t < w && gj0 + c < mc) ? R.at(kb + t, gj0 + c) : 0.0;
+                        sB[t][c] = (t < w && gj0 + c < m) ? R.B[(size_t)(kb + t) * m + gj0 + c] : 0.0;
                     }
                 __syncthreads();
-                const TileSpan sp = tile_span(n - gi0, (isA ? n : mc) - gj0, isA && I == J);
+                const TileSpan sp = tile_span(n - gi0, (isA ? n : m) - gj0, isA && I == J);
                 double acc[16];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int gi = gi0 + sp.rw + 4 * k, gj = gj0 + sp.c;
-                    acc[k] = sp.ok(k) ? (isA ? G[(size_t)gi * n + gj] : R.at(gi, gj)) : 0.0;
+                    acc[k] = sp.ok(k) ? (isA ? G[(size_t)gi * n + gj] : R.B[(size_t)gi * m + gj]) : 0.0;
                 }
                 tile_fma<true>(acc, sA, sB, sp, w);
 #pragma unroll
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
                     if (!sp.ok(k)) continue;
                     const int gi = gi0 + sp.rw + 4 * k, gj = gj0 + sp.c;
                     if (isA) G[(size_t)gi * n + gj] = acc[k];
-                    else R.at(gi, gj) = acc[k];
+                    else R.B[(size_t)gi * m + gj] = acc[k];
                 }
                 __syncthreads();
             }
@@ -279,21 +293,23 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
             __syncthreads();
             continue;
         }
-        // 4. [W | y]^T [W | y], lower tiles over all n rows; K mirrored, F from the y row
-        const int nt = (mc + CD_TM - 1) / CD_TM;
+        // 4. K = W^T W, lower tiles over all n rows, mirrored; F = W^T y, one column of W
+        //    per thread
+        const int nt = (m + CD_TM - 1) / CD_TM;
         for (int tile = 0; tile < nt * (nt + 1) / 2; ++tile) {
             int I = 0;
             while ((I + 1) * (I + 2) / 2 <= tile) ++I;
             const int J = tile - I * (I + 1) / 2;
             const int ci0 = I * CD_TM, cj0 = J * CD_TM;
-            const TileSpan sp = tile_span(mc - ci0, mc - cj0, I == J);
+            const TileSpan sp = tile_span(m - ci0, m - cj0, I == J);
             double acc[16] = {};
             for (int i0 = 0; i0 < n; i0 += CD_NB) {
                 const int h = n - i0 < CD_NB ? n - i0 : CD_NB;
                 for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
                     const int t = idx / CD_TM, c = idx - t * CD_TM;
-                    sA[t][c] = (t < h && ci0 + c < mc) ? R.at(i0 + t, ci0 + c) : 0.0;
-                    sB[t][c] = (t < h && cj0 + c < mc) ? R.at(i0 + t, cj0 + c) : 0.0;
+                    const double *Wr = R.B + (size_t)(i0 + t) * m;
+                    sA[t][c] = (t < h && ci0 + c < m) ? Wr[ci0 + c] : 0.0;
+                    sB[t][c] = (t < h && cj0 + c < m) ? Wr[cj0 + c] : 0.0;
                 }
                 __syncthreads();
                 tile_fma<false>(acc, sA, sB, sp, h);
@@ -303,14 +319,21 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
             for (int k = 0; k < 16; ++k) {
                 if (!sp.ok(k)) continue;
                 const int ci = ci0 + sp.rw + 4 * k, cj = cj0 + sp.c;
-                if (ci < m) {
-                    K[(size_t)ci * m + cj] = acc[k];
-                    K[(size_t)cj * m + ci] = acc[k];
-                } else if (F && cj < m) {
-                    F[cj] = acc[k];                                        // row of y: F = W^T y
-                }
+                K[(size_t)ci * m + cj] = acc[k];
+                K[(size_t)cj * m + ci] = acc[k];
             }
         }
+        if (F)
+            for (int c = tid; c < m; c += CD_NTH) {
+                double s0 = 0.0, s1 = 0.0;
+                int i = 0;
+                for (; i + 1 < n; i += 2) {
+                    s0 = fma(R.B[(size_t)i * m + c], R.l[i], s0);
+                    s1 = fma(R.B[(size_t)(i + 1) * m + c], R.l[i + 1], s1);
+                }
+                if (i < n) s0 = fma(R.B[(size_t)i * m + c], R.l[i], s0);
+                F[c] = s0 + s1;
+            }
         __syncthreads();
     }
 }
