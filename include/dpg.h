@@ -193,7 +193,8 @@ int dpg_integrate_hp(int space, int64_t n_elem, const double *vertices, const do
 /* Autotuner (not in the paper): for the general path of (space, q) with its active rule,
  * time every stage-A chunk width nj (the number of partner indices j_A one work unit
  * produces: tile shape and stage schedule of the contraction kernels) on a synthetic batch
- * of 128 elements on `stream`, and install the fastest for dpg_integrate and
+ * of up to 512 elements (fewer where their output would pass 2 GB, at least 8; median of
+ * five runs) on `stream`, and install the fastest for dpg_integrate and
  * dpg_integrate_hp.  space = DPG_H1 .. DPG_L2, optionally | DPG_FP32 (tunes the FP32
  * kernel).  If the environment variable DPG_AUTOTUNE_CACHE names a file, a choice stored
  * there for (space, q, L, precision) is installed without timing, and new choices are

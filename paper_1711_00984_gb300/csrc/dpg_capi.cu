@@ -1070,9 +1070,12 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
             }
         }
     }
-    // synthetic batch: unit cubes (timing does not depend on the geometry values)
-    const int ne = 128;
-    std::vector<double> hv(24 * ne);
+    // synthetic batch: unit cubes (timing does not depend on the geometry values); up to
+    // 512 elements, fewer where their output would pass 2 GB (at least 8)
+    const Program &pz = (space & DPG_FP32) ? pe->prog32 : pe->prog;
+    const size_t out_elem = (size_t)pz.parts * pz.rows * pz.cols * ((space & DPG_FP32) ? sizeof(float) : sizeof(double));
+    const int ne = (int)std::max<size_t>(8, std::min<size_t>(512, (size_t(2) << 30) / out_elem));
+    std::vector<double> hv(24 * (size_t)ne);
     for (int e = 0; e < ne; ++e)
         for (int v = 0; v < 8; ++v)
             for (int d = 0; d < 3; ++d) hv[24 * e + 3 * v + d] = ((v >> d) & 1) + (d == 0 ? e : 0);
@@ -1092,9 +1095,10 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
     float best_ms = 1e30f;
     for (int nj = 1; nj <= std::min(NJMAX, maxnA); ++nj) {
         if (install_program(pe, te, base, q, L, fp32, nj) != DPG_OK) continue;
-        float tot = 0.f;
+        float ts[6];
+        int nt = 0;
         bool ok = true;
-        for (int rep = 0; rep < 4 && ok; ++rep) {
+        for (int rep = 0; rep < 6 && ok; ++rep) {
             cudaEventRecord(a, s);
             const OutGeom og{ pe->prog.cols, (int64_t)pe->prog.parts * pe->prog.rows * pe->prog.cols };
             const int rr = fp32 ? run_general<float>(ds, pe, te, ne, dv, nullptr, (float *)dout, s, og)
@@ -1104,9 +1108,12 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a, b);
             ok = rr == DPG_OK;
-            if (rep > 0) tot += ms;                       // the first run warms up
+            if (rep > 0) ts[nt++] = ms;                   // the first run warms up
         }
-        if (ok && tot < best_ms) { best_ms = tot; best = nj; }
+        if (!ok) continue;
+        std::sort(ts, ts + nt);
+        const float med = ts[nt / 2];                     // median of five
+        if (med < best_ms) { best_ms = med; best = nj; }
     }
     cudaEventDestroy(a); cudaEventDestroy(b);
     cudaFree(dv); cudaFree(dout);
@@ -1116,7 +1123,7 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
     if (cache) {
         if (FILE *f = std::fopen(cache, "a")) {
             std::fprintf(f, "{\"space\": %d, \"q\": %d, \"L\": %d, \"fp32\": %d, \"nj\": %d, \"ms\": %.6f}\n",
-                         base, q, L, (int)fp32, best, best_ms / 3.0);
+                         base, q, L, (int)fp32, best, (double)best_ms);
             std::fclose(f);
         }
     }
