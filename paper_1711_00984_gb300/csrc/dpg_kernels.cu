@@ -42,24 +42,25 @@ struct Jac {
     double J[3][3], Ji[3][3], det;
 };
 
+// J of the trilinear map at (x1, x2, x3).  The map in monomial form, x = sum_S a_S
+// prod_{d in S} xi_d over the subsets S of {1, 2, 3} (bit d-1 of S): a is the Moebius
+// transform of the vertex values (a_S = sum_{c subset of S} (-1)^{|S|-|c|} x_c, three
+// butterfly passes), so each column of J is four terms.
 __device__ __forceinline__ void trilinear_jac(const double *__restrict__ v, double x1, double x2, double x3, Jac &g) {
+    const double x12 = x1 * x2, x13 = x1 * x3, x23 = x2 * x3;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) {
+        double a[8];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) g.J[i][d] = 0.0;
+        for (int c = 0; c < 8; ++c) a[c] = v[3 * c + i];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int c1 = c & 1, c2 = (c >> 1) & 1, c3 = (c >> 2) & 1;
-        const double l1 = c1 ? x1 : 1.0 - x1, l2 = c2 ? x2 : 1.0 - x2, l3 = c3 ? x3 : 1.0 - x3;
-        const double d1 = c1 ? 1.0 : -1.0, d2 = c2 ? 1.0 : -1.0, d3 = c3 ? 1.0 : -1.0;
-        const double g1 = d1 * l2 * l3, g2 = l1 * d2 * l3, g3 = l1 * l2 * d3;
+        for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const double xv = v[3 * c + i];
-            g.J[i][0] += xv * g1;
-            g.J[i][1] += xv * g2;
-            g.J[i][2] += xv * g3;
-        }
+            for (int c = 0; c < 8; ++c)
+                if (c & (1 << d)) a[c] -= a[c ^ (1 << d)];
+        g.J[i][0] = a[1] + a[3] * x2 + a[5] * x3 + a[7] * x23;
+        g.J[i][1] = a[2] + a[3] * x1 + a[6] * x3 + a[7] * x13;
+        g.J[i][2] = a[4] + a[5] * x1 + a[6] * x2 + a[7] * x12;
     }
 }
 
