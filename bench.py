@@ -128,6 +128,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- multi-rank host logic
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (the step time the whole job waited for); a
+    no-op on one rank.  Any torch.distributed backend (NCCL on the GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: int, seconds: float) -> float:
+    """Whole-job rate of a weak-scaling step: every rank processes units_per_rank units, the
+    job takes the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------------------- GPU arm
 
 class ClockSampler:
@@ -261,17 +281,14 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
     dom_ms = float(np.mean([a.elapsed_time(b) for a, b in dom_ev]))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     code, bad = dpg.dpg_sync_status(sh)
     if code:
         raise RuntimeError(f"device status {dpg.STATUS.get(code)} at element {bad}")
 
     elems_per_step = ne * len(SPACES) * len(maps)
     ms_per_step = total_ms / args.steps
-    value = world * elems_per_step / (ms_per_step * 1e-3)
+    value = job_throughput(world, elems_per_step, ms_per_step * 1e-3)
 
     # ---- e2e through the host-buffer entry point (H2D + integrate + D2H per call)
     e2e = None
@@ -295,12 +312,9 @@ def run_gpu(args):
         for _ in range(ke):
             hstep()
         te = (time.perf_counter() - t0) / ke
-        if world > 1:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(te, world, dev)
         in_bytes = sum(v.numel() * 8 for v in hv.values()) * len(SPACES) + sum(c.numel() * 8 for c in hc.values()) * 2
-        e2e = {"value": world * elems_per_step / te, "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
+        e2e = {"value": job_throughput(world, elems_per_step, te), "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
                "d2h_bytes_per_step": int(out_bytes), "ms_per_step": 1e3 * te}
 
     # ---- roofline of the dominant kernel (H(curl) general: geometry + contraction launch pair)
@@ -341,13 +355,13 @@ def run_gpu(args):
             step32()
             ev32[i][1].record(stream)
         torch.cuda.synchronize()
-        ms32 = float(np.mean([a.elapsed_time(b) for a, b in ev32]))
+        ms32 = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev32])), world, dev)
         errs = {}
         for k in outs:
             ref = outs[k]
             d = (outs32[k].double() - ref).flatten(1).norm(dim=1) / ref.flatten(1).norm(dim=1)
             errs[f"{k[1]}_{k[0]}"] = float(d.max())
-        fp32 = {"ms_per_step": ms32, "value": world * elems_per_step / (ms32 * 1e-3), "unit": UNIT,
+        fp32 = {"ms_per_step": ms32, "value": job_throughput(world, elems_per_step, ms32 * 1e-3), "unit": UNIT,
                 "speedup_vs_fp64": ms_per_step / ms32, "max_rel_frobenius_err_vs_fp64": max(errs.values()),
                 "target_err": 1e-5, "err_per_call": errs}
 
