@@ -974,11 +974,10 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
     const int n = pg->prog.rows, m = pb->prog.cols;
     const bool with_l = src_coef != nullptr;
     // per element: G, B and l in a pool workspace; chunks of whole waves of the
-    // condensation kernel (two CTAs per SM) within about 8 GB, so that only the last
-    // chunk has a partial wave
+    // condensation kernel within about 8 GB, so that only the last chunk has a partial wave
     const size_t per_elem = ((size_t)n * n + (size_t)n * m + (with_l ? n : 0)) * sizeof(double);
     int64_t chunk = (int64_t)((size_t(8) << 30) / per_elem);
-    const int64_t wave = 2 * (int64_t)g_num_sms;
+    const int64_t wave = (int64_t)condense_ctas_per_sm() * g_num_sms;
     if (chunk >= wave) chunk -= chunk % wave;
     if (chunk < 1) chunk = 1;
     if (chunk > n_elem) chunk = n_elem;

@@ -6,7 +6,8 @@
 // factorization G = L L^T, the substitutions W = L^-1 B and y = L^-1 l, then the products
 // K = W^T W and F = W^T y.
 //
-// condense_kernel: one CTA per element at a time (persistent over the batch), FP64.
+// condense_kernel: one CTA per element at a time (persistent over the batch, three CTAs per
+// SM), FP64.
 //   * Right-looking blocked Cholesky, panels of CD_NB columns, in place in the lower
 //     triangle of G.  The diagonal block is factored in shared memory by all threads,
 //     which then form L11^-1; the panel rows below it (L21 = A21 L11^-T) and the matching CD_NB
@@ -98,7 +99,7 @@ __device__ __forceinline__ void tile_fma(double (&acc)[16], const double (*sA)[C
     }
 }
 
-__global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
+__global__ void __launch_bounds__(CD_NTH, 3) condense_kernel(CondParams p) {
     __shared__ double srd[CD_NB];               // reciprocals of the factor's diagonal
     __shared__ double sIT[CD_NB][CD_NB + 1];    // (L11^-1)^T
     __shared__ double sA[CD_NB][CD_LDS];        // staged operand rows (k-major)
@@ -338,13 +339,15 @@ __global__ void __launch_bounds__(CD_NTH, 2) condense_kernel(CondParams p) {
     }
 }
 
+int condense_ctas_per_sm() {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, condense_kernel, CD_NTH, 0) != cudaSuccess) return 1;
+    return per_sm < 1 ? 1 : per_sm;
+}
+
 cudaError_t launch_condense(const CondParams &p, int num_sms, cudaStream_t s) {
     if (p.n_elem == 0) return cudaSuccess;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, condense_kernel, CD_NTH, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t cap = (int64_t)per_sm * num_sms;
+    const int64_t cap = (int64_t)condense_ctas_per_sm() * num_sms;
     condense_kernel<<<(unsigned)(p.n_elem < cap ? p.n_elem : cap), CD_NTH, 0, s>>>(p);
     return cudaGetLastError();
 }
