@@ -195,10 +195,13 @@ int dpg_integrate_hp(int space, int64_t n_elem, const double *vertices, const do
  * produces: tile shape and stage schedule of the contraction kernels) on a synthetic batch
  * of up to 512 elements (fewer where their output would pass 2 GB, at least 8; median of
  * five runs) on `stream`, and install the fastest for dpg_integrate and
- * dpg_integrate_hp.  space = DPG_H1 .. DPG_L2, optionally | DPG_FP32 (tunes the FP32
- * kernel).  If the environment variable DPG_AUTOTUNE_CACHE names a file, a choice stored
+ * dpg_integrate_hp; for FP64 programs that hold both diagonal blocks of the symmetric
+ * matrix (their work units run from j_A = i_A up, so they are uneven) and full blocks
+ * (H(curl), H(div)), a second pass picks a smaller width for the diagonal blocks alone.
+ * space = DPG_H1 .. DPG_L2, optionally | DPG_FP32 (tunes the FP32 kernel).  If the environment variable DPG_AUTOTUNE_CACHE names a file, a choice stored
  * there for (space, q, L, precision) is installed without timing, and new choices are
- * appended as JSON lines.  Synchronous; allocates temporary device buffers; call it at
+ * appended as JSON lines ({"space", "q", "L", "fp32", "nj", "ms", "nj_sym"}; nj_sym = 0:
+ * the diagonal blocks use nj too).  Synchronous; allocates temporary device buffers; call it at
  * set-up, not inside stream capture.  *best_nj (if not NULL) receives the chosen width.
  * Errors: DPG_ERR_ARG, DPG_ERR_NOT_INIT, DPG_ERR_RANGE, DPG_ERR_CUDA. */
 int dpg_autotune(int q, int space, void *stream, int *best_nj);

@@ -692,12 +692,12 @@ int enqueue_hp(DeviceState *ds, int space, int64_t n, const double *verts, const
 
 // Replace the general-path program of pe (FP32 kernel's or FP64 kernel's) by one built
 // with stage-A chunk nj.  Synchronises the device (the old descriptors are freed).
-int install_program(ProgEntry *pe, TableEntry *te, int space, int q, int L, bool fp32, int nj) {
+int install_program(ProgEntry *pe, TableEntry *te, int space, int q, int L, bool fp32, int nj, int nj_sym = 0) {
     if (fp32) {
         CK(cudaDeviceSynchronize());
         return setup_prog32(pe, space, q, L, 0, false, te->host, nj);
     }
-    Program np = make_program(space, q, L, 0, false, te->host, ORDER_BEST, nj);
+    Program np = make_program(space, q, L, 0, false, te->host, ORDER_BEST, nj, 0, nj_sym);
     if (np.smem_values * sizeof(double) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
     BlockDesc *db = nullptr;
     Unit *du = nullptr;
@@ -1052,17 +1052,21 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
     if (cache) {
         if (FILE *f = std::fopen(cache, "r")) {
             char line[256];
-            int found = 0;
+            int found = 0, found_sym = 0;
             while (std::fgets(line, sizeof(line), f)) {
-                int cs, cq, cl, cf, cn;
+                int cs, cq, cl, cf, cn, cy = 0;
                 double cms;
-                if (std::sscanf(line, "{\"space\": %d, \"q\": %d, \"L\": %d, \"fp32\": %d, \"nj\": %d, \"ms\": %lf}",
-                                &cs, &cq, &cl, &cf, &cn, &cms) == 6 &&
-                    cs == base && cq == q && cl == L && cf == (int)fp32)
+                // {"space", "q", "L", "fp32", "nj", "ms"} and, in newer lines, "nj_sym"
+                const int got = std::sscanf(line,
+                    "{\"space\": %d, \"q\": %d, \"L\": %d, \"fp32\": %d, \"nj\": %d, \"ms\": %lf, \"nj_sym\": %d}",
+                    &cs, &cq, &cl, &cf, &cn, &cms, &cy);
+                if (got >= 6 && cs == base && cq == q && cl == L && cf == (int)fp32) {
                     found = cn;
+                    found_sym = got == 7 ? cy : 0;
+                }
             }
             std::fclose(f);
-            if (found > 0 && install_program(pe, te, base, q, L, fp32, found) == DPG_OK) {
+            if (found > 0 && install_program(pe, te, base, q, L, fp32, found, found_sym) == DPG_OK) {
                 if ((r = update_hp_table(ds, base, q, pe, te))) return r;
                 if (best_nj) *best_nj = found;
                 return DPG_OK;
@@ -1114,15 +1118,41 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
         const float med = ts[nt / 2];                     // median of five
         if (med < best_ms) { best_ms = med; best = nj; }
     }
+    // FP64 programs that mix diagonal blocks of the symmetric matrix (units from i_A up:
+    // uneven) with full blocks: a second pass over the diagonal blocks' own chunk
+    int best_sym = 0;
+    bool has_sym = false, has_full = false;
+    for (int k = 0; k < p0.nblock; ++k) (p0.blocks[k].sym == 1 ? has_sym : has_full) = true;
+    if (!fp32 && has_sym && has_full && best > 1) {
+        for (int nj_sym = 1; nj_sym < best; ++nj_sym) {
+            if (install_program(pe, te, base, q, L, fp32, best, nj_sym) != DPG_OK) continue;
+            float ts[6];
+            int nt = 0;
+            bool ok = true;
+            for (int rep = 0; rep < 6 && ok; ++rep) {
+                cudaEventRecord(a, s);
+                const OutGeom og{ pe->prog.cols, (int64_t)pe->prog.parts * pe->prog.rows * pe->prog.cols };
+                ok = run_general<double>(ds, pe, te, ne, dv, nullptr, (double *)dout, s, og) == DPG_OK;
+                cudaEventRecord(b, s);
+                cudaEventSynchronize(b);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) ts[nt++] = ms;
+            }
+            if (!ok) continue;
+            std::sort(ts, ts + nt);
+            if (ts[nt / 2] < best_ms) { best_ms = ts[nt / 2]; best_sym = nj_sym; }
+        }
+    }
     cudaEventDestroy(a); cudaEventDestroy(b);
     cudaFree(dv); cudaFree(dout);
-    if ((r = install_program(pe, te, base, q, L, fp32, best))) return r;
+    if ((r = install_program(pe, te, base, q, L, fp32, best, best_sym))) return r;
     if ((r = update_hp_table(ds, base, q, pe, te))) return r;
     read_status(ds, nullptr);                             // the synthetic runs report nothing
     if (cache) {
         if (FILE *f = std::fopen(cache, "a")) {
-            std::fprintf(f, "{\"space\": %d, \"q\": %d, \"L\": %d, \"fp32\": %d, \"nj\": %d, \"ms\": %.6f}\n",
-                         base, q, L, (int)fp32, best, (double)best_ms);
+            std::fprintf(f, "{\"space\": %d, \"q\": %d, \"L\": %d, \"fp32\": %d, \"nj\": %d, \"ms\": %.6f, \"nj_sym\": %d}\n",
+                         base, q, L, (int)fp32, best, (double)best_ms, best_sym);
             std::fclose(f);
         }
     }

@@ -260,7 +260,7 @@ static size_t smem_values(const BlockDesc &b, int L, int nj) {
 }
 
 Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order, int force_nj,
-                     size_t smem_budget) {
+                     size_t smem_budget, int force_nj_sym) {
     Program pr;
     std::memset(pr.blocks, 0, sizeof(pr.blocks));
     pr.space = space; pr.q = q; pr.L = L; pr.p = p; pr.split = split;
@@ -414,10 +414,14 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
         }
     }
     pr.nj = nj;
+    // the diagonal blocks of a symmetric matrix may take a smaller chunk (general FP64
+    // kernel only: its units carry their own width)
+    pr.nj_sym = (order == ORDER_BEST && force_nj_sym > 0) ? std::min(force_nj_sym, nj) : nj;
+    auto njb = [&](const BlockDesc &b) { return b.sym == 1 ? pr.nj_sym : nj; };
     size_t m = 0, mb = 0;
     for (int k = 0; k < pr.nblock; ++k) {
-        m = std::max(m, smem_values(pr.blocks[k], L, nj));
-        mb = std::max(mb, smem_bytes(pr.blocks[k], nj));
+        m = std::max(m, smem_values(pr.blocks[k], L, njb(pr.blocks[k])));
+        mb = std::max(mb, smem_bytes(pr.blocks[k], njb(pr.blocks[k])));
     }
     pr.smem_values = m;
     pr.smem_bytes = mb;
@@ -428,12 +432,13 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     for (int k = 0; k < pr.nblock; ++k) {
         const BlockDesc &b = pr.blocks[k];
         const int dA = b.dir[2];
+        const int nju = njb(b);
         for (int i3 = 0; i3 < b.nr[dA]; ++i3) {
             int jlo = b.sym == 1 ? i3 : 0;
-            for (int j = jlo; j < b.nc[dA]; j += nj) {
+            for (int j = jlo; j < b.nc[dA]; j += nju) {
                 Unit u;
                 u.block = (int16_t)k; u.i3 = (int16_t)i3; u.j3b = (int16_t)j;
-                u.nj = (int16_t)std::min(nj, b.nc[dA] - j);
+                u.nj = (int16_t)std::min(nju, b.nc[dA] - j);
                 pr.units.push_back(u);
             }
         }

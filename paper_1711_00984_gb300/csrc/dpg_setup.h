@@ -23,6 +23,8 @@ struct Program {
     BlockDesc blocks[MAXBLK];
     std::vector<Unit> units;
     int nj = 1;
+    int nj_sym = 1;                // chunk of the diagonal blocks of a symmetric matrix (sym == 1;
+                                   // ORDER_BEST programs: may be below nj, their units are uneven)
     size_t smem_values = 0;        // shared-memory values of the FP64-model general kernel
     size_t smem_bytes = 0;         // shared memory of the kernel this program is built for
     double flops = 0.0;            // algorithmic flops per element, general path
@@ -47,7 +49,7 @@ enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3, ORDER_T
 // shared memory fits the kernel's budget (smem_budget bytes, or the order's default when
 // 0) is taken.
 Program make_program(int space, int q, int L, int p, bool split, const HostTables &tab, int order = ORDER_BEST,
-                     int force_nj = 0, size_t smem_budget = 0);
+                     int force_nj = 0, size_t smem_budget = 0, int force_nj_sym = 0);
 // Constant operands of the FP32 row-panel kernel for every block of an ORDER_PANEL
 // program (the shared-memory image [0, oA) of panel_layout), concatenated; off[k] is the
 // first float of block k.
