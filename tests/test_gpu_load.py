@@ -123,3 +123,24 @@ def test_load_degenerate_and_args(gpu_lib):
     assert L.dpg_integrate_load(sid, 11, 8, vt.data_ptr(), ct.data_ptr(), 0, o.data_ptr(), None) == 2   # no tables
     assert L.dpg_integrate_load(sid, 2, 0, None, None, 0, None, None) == 0                             # empty
     assert dpg.sync_status()[0] == 0
+
+
+@pytest.mark.parametrize("space,q", [("L2", 12), ("HDIV", 11)])
+def test_load_largest_orders(gpu_lib, space, q):
+    """The largest orders whose tables initialise for the space (L = 14 and 13 points)."""
+    v = meshgen.jittered_grid(2, seed=71)[:2]
+    c = source(space, 72)
+    L = min(q + 2, 14)
+    got, code, _ = run(gpu_lib, space, q, v, c, L=L)
+    ref, _ = oracle.load(space, q, L, v, c)
+    assert code == 0
+    assert rel_errs(got, ref).max() <= TOL64
+
+
+def test_load_fp32_per_element_source(gpu_lib):
+    v = meshgen.jittered_grid(2, seed=73)
+    c = np.random.default_rng(74).uniform(-1, 1, (v.shape[0], 30))
+    got, code, _ = run(gpu_lib, "HDIV", 4, v, c, fp32=True)
+    ref = np.stack([oracle.load("HDIV", 4, 6, v[e:e + 1], c[e])[0][0] for e in range(v.shape[0])])
+    assert code == 0
+    assert rel_errs(got, ref).max() <= TOL32
