@@ -284,11 +284,28 @@ int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vert
  *   F        : device, double[n_elem][m]; must be NULL exactly when l is NULL.
  *   stream   : cudaStream_t.
  * An element whose G is not positive definite gets NaN in K (and F) and is reported as
- * DPG_ERR_NOT_SPD through dpg_sync_status; its G, B, l are left partially factored.
+ * DPG_ERR_NOT_SPD through dpg_sync_status; its G, B, l are left partially factored.  With
+ * DPG_CONDENSE_TC, a value of B that is not finite is reported the same way (the FMA
+ * route lets it propagate as NaN into K and F without a status).
  * No workspace is allocated (everything happens in place).
  * Errors: DPG_ERR_ARG, DPG_ERR_RANGE (n or m), DPG_ERR_CUDA. */
 int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, double *K, double *F,
                  void *stream);
+
+/* Arithmetic of the condensation's trailing updates (the O(n^3) and O(n^2 m) part of
+ * dpg_condense and dpg_condensed_system), for every later call in the process:
+ *   DPG_CONDENSE_FMA: FP64 fused multiply-adds.
+ *   DPG_CONDENSE_TC : the same FP64 products from exact BF16 digits on the tensor cores --
+ *                     each operand row split as 2^e sum_{u<8} d_u 2^-7(u+1) with 7-bit
+ *                     digits d_u, the digit products summed exactly in FP32 and combined
+ *                     in a 64-bit integer, entering the FP64 result once per product; the
+ *                     digits dropped are below 2^-56 of the row maxima, so the results
+ *                     agree with the FMA route to FP64 rounding of the row-scaled sums.
+ * The factorization of the diagonal blocks, the panel substitutions and K = W^T W stay
+ * FP64 in both.  Errors: DPG_ERR_ARG. */
+#define DPG_CONDENSE_FMA 0
+#define DPG_CONDENSE_TC  1
+int dpg_condense_set_method(int method);
 
 /* The DPG element routine of the mixed-stiffness pair in one call (Sec. 3, Eqs. 3.7-3.8):
  * per element, the Gram matrix G of the H(curl) test space of order q_test (coefficients as

@@ -32,7 +32,7 @@ EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matri
            "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",
            "dpg_strerror", "dpg_last_cuda_error", "dpg_autotune", "dpg_flops_per_element", "dpg_measure_fma_peak",
            "dpg_test_stall_tc_once", "dpg_integrate_load", "dpg_condense",
-           "dpg_condensed_system"]
+           "dpg_condensed_system", "dpg_condense_set_method"]
 
 _lib = None
 _lock = threading.Lock()
@@ -82,11 +82,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_integrate_load.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, i64, vp, vp]
         lib.dpg_condense.argtypes = [i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         lib.dpg_condensed_system.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, i64, vp, vp, vp]
+        lib.dpg_condense_set_method.argtypes = [ctypes.c_int]
         lib.dpg_test_stall_tc_once.argtypes = []
         lib.dpg_test_stall_tc_once.restype = ctypes.c_int
         for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp",
                      "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak", "dpg_integrate_load",
-                     "dpg_condense", "dpg_condensed_system"]:
+                     "dpg_condense", "dpg_condensed_system", "dpg_condense_set_method"]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -313,6 +314,16 @@ def dpg_condense(n_elem: int, n: int, m: int, G: int, B: int, l: int, K: int, F:
     """Raw call of the static condensation (integer device pointers, in place on G, B, l)."""
     return _L().dpg_condense(n_elem, n, m, G or None, B or None, l or None, K or None, F or None,
                              stream or None)
+
+
+DPG_CONDENSE_FMA, DPG_CONDENSE_TC = 0, 1
+
+
+def dpg_condense_set_method(method) -> int:
+    """Arithmetic of the condensation's updates: "fma" / DPG_CONDENSE_FMA (FP64 FMA) or
+    "tc" / DPG_CONDENSE_TC (FP64 products from exact BF16 digits on the tensor cores)."""
+    m = {"fma": DPG_CONDENSE_FMA, "tc": DPG_CONDENSE_TC}.get(method, method)
+    return _check(_L().dpg_condense_set_method(int(m)), "dpg_condense_set_method")
 
 
 def condense(G, B, l=None, *, K=None, F=None, stream=None):

@@ -29,6 +29,7 @@ int g_max_dyn_smem = 0;                                  // per launch, set at d
 int g_max_dyn_smem_tc = 0;                               // the same for the tensor-core kernel
 int g_tc_stall_once = 0;                                 // test hook, see dpg_test_stall_tc_once
 int g_num_sms = 152;                                     // set at device set-up
+int g_condense_method = DPG_CONDENSE_FMA;                // see dpg_condense_set_method
 
 struct TableEntry {
     HostTables host;
@@ -160,6 +161,7 @@ int device_state(DeviceState **out) {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CK(init_kernel_attributes(optin));
+    CK(init_condense_attributes());
     g_max_dyn_smem = max_dynamic_smem(optin);
     CK(init_tc_attributes(optin));
     g_max_dyn_smem_tc = optin - tc_static_smem();
@@ -952,7 +954,7 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
     p.n_elem = n_elem; p.elem_base = 0; p.n = n; p.m = m;
     p.G = G; p.B = B; p.l = l; p.K = K; p.F = F;
     p.status = ds->status;
-    const cudaError_t le = launch_condense(p, g_num_sms, (cudaStream_t)stream);
+    const cudaError_t le = launch_condense(p, g_num_sms, g_condense_method == DPG_CONDENSE_TC, (cudaStream_t)stream);
     if (le != cudaSuccess) return cuda_fail(le, "condense_kernel launch", __LINE__);
     return DPG_OK;
 }
@@ -977,7 +979,7 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
     // condensation kernel within about 8 GB, so that only the last chunk has a partial wave
     const size_t per_elem = ((size_t)n * n + (size_t)n * m + (with_l ? n : 0)) * sizeof(double);
     int64_t chunk = (int64_t)((size_t(8) << 30) / per_elem);
-    const int64_t wave = (int64_t)condense_ctas_per_sm() * g_num_sms;
+    const int64_t wave = (int64_t)condense_ctas_per_sm(g_condense_method == DPG_CONDENSE_TC) * g_num_sms;
     if (chunk >= wave) chunk -= chunk % wave;
     if (chunk < 1) chunk = 1;
     if (chunk > n_elem) chunk = n_elem;
@@ -1011,12 +1013,19 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
         cp.G = G; cp.B = B; cp.l = l;
         cp.K = K + (size_t)e0 * m * m; cp.F = with_l ? F + (size_t)e0 * m : nullptr;
         cp.status = ds->status;
-        const cudaError_t le = launch_condense(cp, g_num_sms, s);
+        const cudaError_t le = launch_condense(cp, g_num_sms, g_condense_method == DPG_CONDENSE_TC, s);
         if (le != cudaSuccess) rc = cuda_fail(le, "condense_kernel launch", __LINE__);
     }
     const cudaError_t fe = cudaFreeAsync(ws, s);
     if (fe != cudaSuccess && rc == DPG_OK) rc = cuda_fail(fe, "cudaFreeAsync", __LINE__);
     return rc;
+}
+
+int dpg_condense_set_method(int method) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (method != DPG_CONDENSE_FMA && method != DPG_CONDENSE_TC) return DPG_ERR_ARG;
+    g_condense_method = method;
+    return DPG_OK;
 }
 
 int dpg_test_stall_tc_once(void) {

@@ -24,6 +24,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 namespace dpg {
 
 constexpr int CD_NB = 32;          // panel width
@@ -99,11 +101,111 @@ __device__ __forceinline__ void tile_fma(double (&acc)[16], const double (*sA)[C
     }
 }
 
-__global__ void __launch_bounds__(CD_NTH, 3) condense_kernel(CondParams p) {
+// ---- trailing update on the tensor cores: FP64 products from exact BF16 slices ----------
+// Every operand row of a 64 x 64 update tile (its <= 32 panel values) is written as
+// x = 2^e sum_{u<8} d_u 2^-7(u+1) with the row exponent e (|x| < 2^e over the row) and
+// 7-bit digits |d_u| <= 127 (exact in BF16), from the FP64 bits with integer operations
+// only; digits below 2^-56 of the row maximum are dropped.  A product of two rows is
+// then 2^(e_i+e_j) sum_D 2^-7(D+2) P_D with P_D = sum_{u+v=D} d_u(i) . d_v(j), and every
+// P_D is a sum of at most 8 x 32 integer products below 2^14, below 2^22 in all: the BF16
+// tensor-core products accumulate it exactly in FP32.  The diagonals D <= 7 (36 slice
+// products) keep the truncation near 2^-53 of the row maxima, which is FP64 rounding for
+// these sums; they are combined exactly in a 64-bit integer and enter the FP64 output
+// once, so the FP64 pipe sees two operations per output and panel instead of 32 FMAs.
+constexpr int EM_S = 8;                  // digits per value
+constexpr int EM_SK = 40;                // BF16 per digit row (32 used; 80-byte rows keep the
+                                         // fragment loads free of bank conflicts)
+constexpr int EM_ROWBYTES = EM_SK * 2;
+constexpr size_t EM_SIDE = (size_t)EM_S * CD_TM * EM_ROWBYTES;          // one operand side
+constexpr size_t EM_SMEM = 2 * EM_SIDE + 2 * CD_TM * sizeof(int);       // + row exponents
+constexpr size_t CD_SMEM = 2 * (size_t)CD_NB * CD_LDS * sizeof(double); // FP64 staging
+
+// Digits of one row held by a warp (lane t: value t of the row, zero beyond w).  Writes the
+// digits to dst[u * CD_TM * EM_SK + t] (BF16 bits) and, from lane 0, the row exponent;
+// returns true when a value of the row is not finite.
+__device__ __forceinline__ bool slice_row(double x, uint16_t *dst, int *e_out, int lane) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned eb = (unsigned)(bits >> 52) & 0x7ffu;
+    const unsigned emax = __reduce_max_sync(0xffffffffu, eb);
+    if (lane == 0) *e_out = emax ? (int)emax - 1022 : 0;
+    unsigned long long f = 0;
+    if (eb != 0 && eb != 0x7ffu) {
+        const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);
+        const int sh = (int)eb - (int)emax + 3;                 // <= 3: f < 2^56
+        f = sh >= 0 ? mant << sh : (sh > -56 ? mant >> (-sh) : 0ull);
+    }
+    const bool neg = (bits >> 63) != 0;
+#pragma unroll
+    for (int u = 0; u < EM_S; ++u) {
+        const int d = (int)((f >> (49 - 7 * u)) & 127ull);
+        const float fd = (float)(neg ? -d : d);
+        dst[(size_t)u * CD_TM * EM_SK] = (uint16_t)(__float_as_uint(fd) >> 16);
+    }
+    return __any_sync(0xffffffffu, eb == 0x7ffu);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// tot[4 nt + i] (the warp's 16 x 32 sub-tile, mma accumulator order) = sum_D P_D 2^(43-7D)
+// (D = 7: 2^-6, floor), from the digit planes of the I rows (rows rb ..) and J rows (cb ..).
+__device__ __forceinline__ void emu_products(long long (&tot)[16], const unsigned char *si,
+                                             const unsigned char *sj, int rb, int cb, int lane) {
+    const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) tot[k] = 0;
+#pragma unroll 1
+    for (int D = 0; D < EM_S; ++D) {
+        float acc[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+#pragma unroll 1
+        for (int u = 0; u <= D; ++u) {
+            const unsigned char *pa = si + (size_t)u * CD_TM * EM_ROWBYTES;
+            const unsigned char *pb = sj + (size_t)(D - u) * CD_TM * EM_ROWBYTES;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const int kbyte = (16 * ks + 2 * tq) * 2;
+                uint32_t a[4];
+                a[0] = *reinterpret_cast<const uint32_t *>(pa + (rb + g) * EM_ROWBYTES + kbyte);
+                a[1] = *reinterpret_cast<const uint32_t *>(pa + (rb + g + 8) * EM_ROWBYTES + kbyte);
+                a[2] = *reinterpret_cast<const uint32_t *>(pa + (rb + g) * EM_ROWBYTES + kbyte + 16);
+                a[3] = *reinterpret_cast<const uint32_t *>(pa + (rb + g + 8) * EM_ROWBYTES + kbyte + 16);
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const unsigned char *pr = pb + (cb + 8 * nt + g) * EM_ROWBYTES + kbyte;
+                    mma_bf16(acc[nt], a, *reinterpret_cast<const uint32_t *>(pr),
+                             *reinterpret_cast<const uint32_t *>(pr + 16));
+                }
+            }
+        }
+        // the exact integer sums into the 64-bit total (|P_D| < 2^22: the 1.5 2^23 shift
+        // puts the integer in the low mantissa bits)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const long long iv = (long long)(__float_as_int(acc[nt][i] + 12582912.0f) - 0x4B400000);
+                tot[4 * nt + i] += D < EM_S - 1 ? iv * (1ll << (43 - 7 * D)) : (iv >> 6);   // floor
+            }
+    }
+}
+
+template <bool EMU>
+__global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParams p) {
     __shared__ double srd[CD_NB];               // reciprocals of the factor's diagonal
     __shared__ double sIT[CD_NB][CD_NB + 1];    // (L11^-1)^T
-    __shared__ double sA[CD_NB][CD_LDS];        // staged operand rows (k-major)
-    __shared__ double sB[CD_NB][CD_LDS];
+    // dynamic arena: staged FP64 operand rows sA, sB (k-major), or, in the tensor-core
+    // updates, the digit planes of the two operand sides and their row exponents
+    extern __shared__ __align__(16) unsigned char cd_smem[];
+    double (*sA)[CD_LDS] = reinterpret_cast<double (*)[CD_LDS]>(cd_smem);
+    double (*sB)[CD_LDS] = sA + CD_NB;
     // the diagonal block and its factor share sA's storage: they are last read before the
     // barrier that precedes the first staging into sA of the same panel step
     double (*sD)[CD_NB + 1] = reinterpret_cast<double (*)[CD_NB + 1]>(&sA[0][0]);
@@ -254,6 +356,68 @@ __global__ void __launch_bounds__(CD_NTH, 3) condense_kernel(CondParams p) {
                 }
                 const int gi0 = r0 + I * CD_TM;                           // rows of G / rhs
                 const int gj0 = isA ? r0 + J * CD_TM : J * CD_TM;         // columns
+                if constexpr (EMU) {
+                    unsigned char *si = cd_smem, *sj = cd_smem + EM_SIDE;
+                    int *ei = reinterpret_cast<int *>(cd_smem + 2 * EM_SIDE), *ej = ei + CD_TM;
+                    // digits of the 64 I rows (L21 rows) and the 64 J rows (L21 rows, or
+                    // the columns of W1 for a right-hand-side tile): a warp per row
+                    // all 16 loads of a warp first (independent), then the digit splits
+                    constexpr int RPW = 2 * CD_TM / (CD_NTH / 32);            // rows per warp
+                    double xv[RPW];
+#pragma unroll
+                    for (int j = 0; j < RPW; ++j) {
+                        const int r = warp + (CD_NTH / 32) * j;
+                        const bool side_j = r >= CD_TM;
+                        const int rr = side_j ? r - CD_TM : r;
+                        double x = 0.0;
+                        if (lane < w) {
+                            if (!side_j) {
+                                if (gi0 + rr < n) x = G[(size_t)(gi0 + rr) * n + kb + lane];
+                            } else if (isA) {
+                                if (gj0 + rr < n) x = G[(size_t)(gj0 + rr) * n + kb + lane];
+                            } else if (gj0 + rr < m) {
+                                x = R.B[(size_t)(kb + lane) * m + gj0 + rr];
+                            }
+                        }
+                        xv[j] = x;
+                    }
+                    bool nonfinite = false;
+#pragma unroll
+                    for (int j = 0; j < RPW; ++j) {
+                        const int r = warp + (CD_NTH / 32) * j;
+                        const bool side_j = r >= CD_TM;
+                        const int rr = side_j ? r - CD_TM : r;
+                        unsigned char *base = (side_j ? sj : si) + (size_t)rr * EM_ROWBYTES;
+                        nonfinite |= slice_row(xv[j], reinterpret_cast<uint16_t *>(base) + lane,
+                                               (side_j ? ej : ei) + rr, lane);
+                    }
+                    if (nonfinite && lane == 0) sbad = 1;
+                    __syncthreads();
+                    // a 16 x 32 sub-tile per warp; sub-tiles outside the tile or above a
+                    // diagonal tile's diagonal are skipped by the whole warp
+                    const int rb = 16 * (warp & 3), cb = 32 * (warp >> 2);
+                    const int rows_v = n - gi0, cols_v = (isA ? n : m) - gj0;
+                    const bool diag = isA && I == J;
+                    if (rb < rows_v && cb < cols_v && !(diag && cb >= rb + 16)) {
+                        long long tot[16];
+                        emu_products(tot, si, sj, rb, cb, lane);
+                        const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int r = rb + g + 8 * (i >> 1), c = cb + 8 * nt + 2 * tq + (i & 1);
+                                if (r >= rows_v || c >= cols_v || (diag && c > r)) continue;
+                                // 2^(e_i + e_j - 57), a normal number for the exponents here
+                                const int se = min(max(ei[r] + ej[c] - 57, -1022), 1023);
+                                const double sc = __longlong_as_double((long long)(se + 1023) << 52);
+                                double *dst = isA ? G + (size_t)(gi0 + r) * n + gj0 + c
+                                                  : R.B + (size_t)(gi0 + r) * m + gj0 + c;
+                                *dst = fma(-(double)tot[4 * nt + i], sc, *dst);
+                            }
+                    }
+                    __syncthreads();
+                } else {
                 for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
                     const int r = idx / CD_NB, t = idx - r * CD_NB;
                     const bool tv = t < w;
@@ -282,6 +446,7 @@ __global__ void __launch_bounds__(CD_NTH, 3) condense_kernel(CondParams p) {
                     else R.B[(size_t)gi * m + gj] = acc[k];
                 }
                 __syncthreads();
+                }
             }
         }
         double *K = p.K + (size_t)e * m * m;
@@ -302,6 +467,68 @@ __global__ void __launch_bounds__(CD_NTH, 3) condense_kernel(CondParams p) {
             while ((I + 1) * (I + 2) / 2 <= tile) ++I;
             const int J = tile - I * (I + 1) / 2;
             const int ci0 = I * CD_TM, cj0 = J * CD_TM;
+            if constexpr (EMU) {
+                // the same digit products, the columns of W as the operand rows, in chunks
+                // of 32 rows of W (each chunk with its own column exponents)
+                unsigned char *si = cd_smem, *sj = cd_smem + EM_SIDE;
+                int *ei = reinterpret_cast<int *>(cd_smem + 2 * EM_SIDE), *ej = ei + CD_TM;
+                const int rb = 16 * (warp & 3), cb = 32 * (warp >> 2);
+                const int rows_v = m - ci0, cols_v = m - cj0;
+                const bool diag = I == J;
+                const bool active = rb < rows_v && cb < cols_v && !(diag && cb >= rb + 16);
+                const int g = lane >> 2, tq = lane & 3;
+                double out[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) out[k] = 0.0;
+                for (int i0 = 0; i0 < n; i0 += CD_NB) {
+                    constexpr int RPW = 2 * CD_TM / (CD_NTH / 32);            // rows per warp
+                    double xv[RPW];
+#pragma unroll
+                    for (int j = 0; j < RPW; ++j) {
+                        const int r = warp + (CD_NTH / 32) * j;
+                        const bool side_j = r >= CD_TM;
+                        const int col = (side_j ? cj0 + r - CD_TM : ci0 + r);
+                        xv[j] = (i0 + lane < n && col < m) ? R.B[(size_t)(i0 + lane) * m + col] : 0.0;
+                    }
+                    bool nonfinite = false;
+#pragma unroll
+                    for (int j = 0; j < RPW; ++j) {
+                        const int r = warp + (CD_NTH / 32) * j;
+                        const bool side_j = r >= CD_TM;
+                        const int rr = side_j ? r - CD_TM : r;
+                        unsigned char *base = (side_j ? sj : si) + (size_t)rr * EM_ROWBYTES;
+                        nonfinite |= slice_row(xv[j], reinterpret_cast<uint16_t *>(base) + lane,
+                                               (side_j ? ej : ei) + rr, lane);
+                    }
+                    if (nonfinite && lane == 0) sbad = 1;
+                    __syncthreads();
+                    if (active) {
+                        long long tot[16];
+                        emu_products(tot, si, sj, rb, cb, lane);
+#pragma unroll
+                        for (int nt2 = 0; nt2 < 4; ++nt2)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int r = rb + g + 8 * (i >> 1), c = cb + 8 * nt2 + 2 * tq + (i & 1);
+                                const int se = min(max(ei[r] + ej[c] - 57, -1022), 1023);
+                                const double sc = __longlong_as_double((long long)(se + 1023) << 52);
+                                out[4 * nt2 + i] = fma((double)tot[4 * nt2 + i], sc, out[4 * nt2 + i]);
+                            }
+                    }
+                    __syncthreads();
+                }
+                if (active)
+#pragma unroll
+                    for (int nt2 = 0; nt2 < 4; ++nt2)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int r = rb + g + 8 * (i >> 1), c = cb + 8 * nt2 + 2 * tq + (i & 1);
+                            if (r >= rows_v || c >= cols_v || (diag && c > r)) continue;
+                            K[(size_t)(ci0 + r) * m + cj0 + c] = out[4 * nt2 + i];
+                            K[(size_t)(cj0 + c) * m + ci0 + r] = out[4 * nt2 + i];
+                        }
+                continue;
+            }
             const TileSpan sp = tile_span(m - ci0, m - cj0, I == J);
             double acc[16] = {};
             for (int i0 = 0; i0 < n; i0 += CD_NB) {
@@ -336,19 +563,37 @@ __global__ void __launch_bounds__(CD_NTH, 3) condense_kernel(CondParams p) {
                 F[c] = s0 + s1;
             }
         __syncthreads();
+        if (EMU && sbad) {          // a value of W that is not finite, met by the digit split
+            for (int idx = tid; idx < m * m; idx += CD_NTH) K[idx] = __longlong_as_double(0x7ff8000000000000LL);
+            if (F)
+                for (int idx = tid; idx < m; idx += CD_NTH) F[idx] = __longlong_as_double(0x7ff8000000000000LL);
+            if (tid == 0) report_cd(p.status, 11 /*DPG_ERR_NOT_SPD*/, p.elem_base + e);
+            __syncthreads();
+        }
     }
 }
 
-int condense_ctas_per_sm() {
+int condense_ctas_per_sm(bool emu) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, condense_kernel, CD_NTH, 0) != cudaSuccess) return 1;
+    const cudaError_t e = emu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, condense_kernel<true>, CD_NTH, EM_SMEM)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, condense_kernel<false>, CD_NTH, CD_SMEM);
+    if (e != cudaSuccess) return 1;
     return per_sm < 1 ? 1 : per_sm;
 }
 
-cudaError_t launch_condense(const CondParams &p, int num_sms, cudaStream_t s) {
+cudaError_t init_condense_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(condense_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EM_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(condense_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CD_SMEM);
+    return e;
+}
+
+cudaError_t launch_condense(const CondParams &p, int num_sms, bool emu, cudaStream_t s) {
     if (p.n_elem == 0) return cudaSuccess;
-    const int64_t cap = (int64_t)condense_ctas_per_sm() * num_sms;
-    condense_kernel<<<(unsigned)(p.n_elem < cap ? p.n_elem : cap), CD_NTH, 0, s>>>(p);
+    const int64_t cap = (int64_t)condense_ctas_per_sm(emu) * num_sms;
+    const unsigned grid = (unsigned)(p.n_elem < cap ? p.n_elem : cap);
+    if (emu) condense_kernel<true><<<grid, CD_NTH, EM_SMEM, s>>>(p);
+    else condense_kernel<false><<<grid, CD_NTH, CD_SMEM, s>>>(p);
     return cudaGetLastError();
 }
 

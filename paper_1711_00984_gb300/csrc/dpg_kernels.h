@@ -203,8 +203,10 @@ template <typename TF> cudaError_t launch_geom2d(const Geom2dParams &p, cudaStre
 template <typename T> cudaError_t launch_vec3_fill(T *out, int64_t n_elem, int n, cudaStream_t s);
 size_t extruded_smem_values(const BlockDesc &b, int L, int nj);
 template <typename T> cudaError_t launch_load(const LoadParams &p, int num_sms, cudaStream_t s);
-cudaError_t launch_condense(const CondParams &p, int num_sms, cudaStream_t s);
-int condense_ctas_per_sm();
+// emu: trailing updates as exact BF16-digit products on the tensor cores (else FP64 FMA)
+cudaError_t launch_condense(const CondParams &p, int num_sms, bool emu, cudaStream_t s);
+int condense_ctas_per_sm(bool emu);
+cudaError_t init_condense_attributes();
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
 cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);

@@ -16,6 +16,15 @@ pytestmark = pytest.mark.gpu
 EPS = np.finfo(np.float64).eps
 
 
+@pytest.fixture(params=["fma", "tc"])
+def method(request, gpu_lib):
+    """Both arithmetics of the trailing updates (FP64 FMA; FP64 products from exact BF16
+    digits on the tensor cores) meet the same tolerance."""
+    gpu_lib.dpg_condense_set_method(request.param)
+    yield request.param
+    gpu_lib.dpg_condense_set_method("fma")
+
+
 def run(dpg, G, B, l=None):
     g = torch.from_numpy(np.ascontiguousarray(G)).cuda()
     b = torch.from_numpy(np.ascontiguousarray(B)).cuda()
@@ -37,7 +46,7 @@ def check(G, K, F, Kr, Fr):
 
 @pytest.mark.parametrize("n,m", [(1, 1), (5, 3), (31, 7), (32, 64), (33, 65), (64, 1), (100, 130), (150, 24)])
 @pytest.mark.parametrize("with_l", [False, True])
-def test_condense_random(gpu_lib, n, m, with_l):
+def test_condense_random(gpu_lib, method, n, m, with_l):
     ne = 5
     G = meshgen.spd_batch(ne, n, 1e3, seed=n * 1000 + m)
     rng = np.random.default_rng(n + m)
@@ -55,7 +64,7 @@ def test_condense_random(gpu_lib, n, m, with_l):
         assert np.array_equal(Lg[e][iu], G[e][iu])
 
 
-def test_condense_element_matrices(gpu_lib):
+def test_condense_element_matrices(gpu_lib, method):
     """H(curl) Gram (q = 3), mixed B (p = 2) and load vector of oracle-built elements."""
     v = meshgen.jittered_grid(2, seed=80)[:6]
     G, _ = oracle.gram("HCURL", 3, 5, v)
@@ -67,7 +76,7 @@ def test_condense_element_matrices(gpu_lib):
     check(G, K, F, Kr, Fr)
 
 
-def test_condense_config_sizes(gpu_lib):
+def test_condense_config_sizes(gpu_lib, method):
     """The sizes of the mixed-stiffness workload: H(curl) q = 6 (n = 882), p = 4 (m = 192),
     L = 8, two elements."""
     v = meshgen.jittered_grid(16, seed=3)[[0, 4095]]
@@ -80,7 +89,7 @@ def test_condense_config_sizes(gpu_lib):
     check(G, K, F, Kr, Fr)
 
 
-def test_condense_not_spd_and_args(gpu_lib):
+def test_condense_not_spd_and_args(gpu_lib, method):
     dpg = gpu_lib
     G = meshgen.spd_batch(4, 40, 1e2, seed=83)
     G[2, 35, 35] = -5.0                                   # a negative pivot late in the factorization
@@ -113,7 +122,7 @@ def _chain(dpg, q, p, v, c, src):
     return dpg.condense(G, B, l)
 
 
-def test_condensed_system_one_call(gpu_lib):
+def test_condensed_system_one_call(gpu_lib, method):
     """dpg_condensed_system equals the separate calls bit for bit, and the oracle's chain."""
     dpg = gpu_lib
     q, p = 3, 2
@@ -139,7 +148,7 @@ def test_condensed_system_one_call(gpu_lib):
     assert Fn is None and torch.equal(Kn, K)
 
 
-def test_condensed_system_chunks_and_errors(gpu_lib):
+def test_condensed_system_chunks_and_errors(gpu_lib, method):
     """1400 elements of the q = 6 / p = 4 pair run in two workspace chunks (912 and 488 on
     152 SMs): equal to the separate calls; an inverted element in the second chunk is
     reported by its index."""
@@ -167,3 +176,29 @@ def test_condensed_system_chunks_and_errors(gpu_lib):
     assert L.dpg_condensed_system(q, p, 1, v.data_ptr(), None, src.data_ptr(), 0, k.data_ptr(), None, None) == 1
     assert L.dpg_condensed_system(q, p, 0, None, None, None, 0, None, None, None) == 0
     assert dpg.sync_status()[0] == 0
+
+
+def test_condense_methods_agree_and_nonfinite(gpu_lib):
+    """The two arithmetics agree to FP64 rounding on the config-3 sizes; a NaN below the
+    first panel (met by the tensor-core digit split) is reported, not absorbed."""
+    dpg = gpu_lib
+    G = meshgen.spd_batch(3, 300, 1e4, seed=90)
+    B = np.random.default_rng(91).standard_normal((3, 300, 40))
+    out = {}
+    for meth in ("fma", "tc"):
+        dpg.dpg_condense_set_method(meth)
+        K, _, _, code, _ = run(dpg, G, B)
+        assert code == 0
+        out[meth] = K
+    dpg.dpg_condense_set_method("fma")
+    for e in range(3):
+        tol = 8 * 300 * EPS * np.linalg.cond(G[e])
+        assert np.linalg.norm(out["tc"][e] - out["fma"][e]) <= tol * np.linalg.norm(out["fma"][e])
+    G2 = G.copy()
+    G2[1, 200, 40] = G2[1, 40, 200] = np.nan
+    dpg.dpg_condense_set_method("tc")
+    K, _, _, code, bad = run(dpg, G2, B)
+    dpg.dpg_condense_set_method("fma")
+    assert dpg.STATUS[code] == "DPG_ERR_NOT_SPD" and bad == 1
+    assert np.isnan(K[1]).all() and np.isfinite(K[[0, 2]]).all()
+    assert dpg._L().dpg_condense_set_method(7) == 1
