@@ -271,7 +271,8 @@ int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vert
  * enriched stiffness (n x m; the skeleton block B~ of Eq. 3.8 is handled by passing the
  * columns [B | B~] as one matrix) and l the load vector.  Steps as the paper names them:
  * Cholesky factorization G = L L^T, the substitutions W = L^-1 B and y = L^-1 l, and the
- * products K = W^T W, F = W^T y.  FP64 throughout.
+ * products K = W^T W, F = W^T y.  FP64 results; the O(n^3) updates and W^T W run on the
+ * tensor cores as exact digit products unless dpg_condense_set_method selects FP64 FMA.
  *   n_elem   : number of elements (0 does nothing).
  *   n, m     : 1 <= n <= 8192, 1 <= m <= 8192.
  *   G        : device, double[n_elem][n][n] row-major.  Only the lower triangle is read;
@@ -293,16 +294,18 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
                  void *stream);
 
 /* Arithmetic of the condensation's trailing updates (the O(n^3) and O(n^2 m) part of
- * dpg_condense and dpg_condensed_system), for every later call in the process:
+ * dpg_condense and dpg_condensed_system) and of K = W^T W, for every later call in the
+ * process:
  *   DPG_CONDENSE_FMA: FP64 fused multiply-adds.
- *   DPG_CONDENSE_TC : the same FP64 products from exact BF16 digits on the tensor cores --
+ *   DPG_CONDENSE_TC : (the default) the same FP64 products from exact BF16 digits on the
+ *                     tensor cores --
  *                     each operand row split as 2^e sum_{u<8} d_u 2^-7(u+1) with 7-bit
  *                     digits d_u, the digit products summed exactly in FP32 and combined
  *                     in a 64-bit integer, entering the FP64 result once per product; the
  *                     digits dropped are below 2^-56 of the row maxima, so the results
  *                     agree with the FMA route to FP64 rounding of the row-scaled sums.
- * The factorization of the diagonal blocks, the panel substitutions and K = W^T W stay
- * FP64 in both.  Errors: DPG_ERR_ARG. */
+ * The factorization of the diagonal blocks, the panel substitutions and F = W^T y stay
+ * FP64 FMA in both.  Errors: DPG_ERR_ARG. */
 #define DPG_CONDENSE_FMA 0
 #define DPG_CONDENSE_TC  1
 int dpg_condense_set_method(int method);

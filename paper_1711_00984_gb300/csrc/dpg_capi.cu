@@ -29,7 +29,7 @@ int g_max_dyn_smem = 0;                                  // per launch, set at d
 int g_max_dyn_smem_tc = 0;                               // the same for the tensor-core kernel
 int g_tc_stall_once = 0;                                 // test hook, see dpg_test_stall_tc_once
 int g_num_sms = 152;                                     // set at device set-up
-int g_condense_method = DPG_CONDENSE_FMA;                // see dpg_condense_set_method
+int g_condense_method = DPG_CONDENSE_TC;                 // see dpg_condense_set_method
 
 struct TableEntry {
     HostTables host;

@@ -151,11 +151,21 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+
 // tot[4 nt + i] (the warp's 16 x 32 sub-tile, mma accumulator order) = sum_D P_D 2^(43-7D)
 // (D = 7: 2^-6, floor), from the digit planes of the I rows (rows rb ..) and J rows (cb ..).
+// Fragments come in with ldmatrix: lane L addresses row (L & 7) + 8 ((L >> 3) & 1) of the A
+// block at column 8 (L >> 4), and J row (L & 7) + 8 (L >> 4) at column 8 ((L >> 3) & 1)
+// (two n-tiles per load); 80-byte rows keep the eight rows of a phase on distinct banks.
 __device__ __forceinline__ void emu_products(long long (&tot)[16], const unsigned char *si,
                                              const unsigned char *sj, int rb, int cb, int lane) {
-    const int g = lane >> 2, tq = lane & 3;
+    const int arow = rb + (lane & 7) + 8 * ((lane >> 3) & 1), acol = 16 * (lane >> 4);       // bytes
+    const int brow = cb + (lane & 7) + 8 * (lane >> 4), bcol = 16 * ((lane >> 3) & 1);
 #pragma unroll
     for (int k = 0; k < 16; ++k) tot[k] = 0;
 #pragma unroll 1
@@ -167,22 +177,18 @@ __device__ __forceinline__ void emu_products(long long (&tot)[16], const unsigne
             for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
 #pragma unroll 1
         for (int u = 0; u <= D; ++u) {
-            const unsigned char *pa = si + (size_t)u * CD_TM * EM_ROWBYTES;
-            const unsigned char *pb = sj + (size_t)(D - u) * CD_TM * EM_ROWBYTES;
+            const unsigned char *pa = si + (size_t)u * CD_TM * EM_ROWBYTES + arow * EM_ROWBYTES + acol;
+            const unsigned char *pb = sj + (size_t)(D - u) * CD_TM * EM_ROWBYTES + brow * EM_ROWBYTES + bcol;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
-                const int kbyte = (16 * ks + 2 * tq) * 2;
-                uint32_t a[4];
-                a[0] = *reinterpret_cast<const uint32_t *>(pa + (rb + g) * EM_ROWBYTES + kbyte);
-                a[1] = *reinterpret_cast<const uint32_t *>(pa + (rb + g + 8) * EM_ROWBYTES + kbyte);
-                a[2] = *reinterpret_cast<const uint32_t *>(pa + (rb + g) * EM_ROWBYTES + kbyte + 16);
-                a[3] = *reinterpret_cast<const uint32_t *>(pa + (rb + g + 8) * EM_ROWBYTES + kbyte + 16);
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    const unsigned char *pr = pb + (cb + 8 * nt + g) * EM_ROWBYTES + kbyte;
-                    mma_bf16(acc[nt], a, *reinterpret_cast<const uint32_t *>(pr),
-                             *reinterpret_cast<const uint32_t *>(pr + 16));
-                }
+                uint32_t a[4], b01[4], b23[4];
+                ldsm_x4(a, pa + 32 * ks);
+                ldsm_x4(b01, pb + 32 * ks);                          // n-tiles 0, 1
+                ldsm_x4(b23, pb + 16 * EM_ROWBYTES + 32 * ks);       // n-tiles 2, 3
+                mma_bf16(acc[0], a, b01[0], b01[1]);
+                mma_bf16(acc[1], a, b01[2], b01[3]);
+                mma_bf16(acc[2], a, b23[0], b23[1]);
+                mma_bf16(acc[3], a, b23[2], b23[3]);
             }
         }
         // the exact integer sums into the 64-bit total (|P_D| < 2^22: the 1.5 2^23 shift
