@@ -121,9 +121,9 @@ constexpr size_t EM_SMEM = 2 * EM_SIDE + 2 * CD_TM * sizeof(int);       // + row
 constexpr size_t CD_SMEM = 2 * (size_t)CD_NB * CD_LDS * sizeof(double); // FP64 staging
 
 // Digits of one row held by a warp (lane t: value t of the row, zero beyond w).  Writes the
-// digits to dst[u * CD_TM * EM_SK + t] (BF16 bits) and, from lane 0, the row exponent;
+// digits to dst[u * plane_rows * EM_SK + t] (BF16 bits) and, from lane 0, the row exponent;
 // returns true when a value of the row is not finite.
-__device__ __forceinline__ bool slice_row(double x, uint16_t *dst, int *e_out, int lane) {
+__device__ __forceinline__ bool slice_row_planes(double x, uint16_t *dst, int *e_out, int lane, int plane_rows) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const unsigned eb = (unsigned)(bits >> 52) & 0x7ffu;
     const unsigned emax = __reduce_max_sync(0xffffffffu, eb);
@@ -139,9 +139,12 @@ __device__ __forceinline__ bool slice_row(double x, uint16_t *dst, int *e_out, i
     for (int u = 0; u < EM_S; ++u) {
         const int d = (int)((f >> (49 - 7 * u)) & 127ull);
         const float fd = (float)(neg ? -d : d);
-        dst[(size_t)u * CD_TM * EM_SK] = (uint16_t)(__float_as_uint(fd) >> 16);
+        dst[(size_t)u * plane_rows * EM_SK] = (uint16_t)(__float_as_uint(fd) >> 16);
     }
     return __any_sync(0xffffffffu, eb == 0x7ffu);
+}
+__device__ __forceinline__ bool slice_row(double x, uint16_t *dst, int *e_out, int lane) {
+    return slice_row_planes(x, dst, e_out, lane, CD_TM);
 }
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -162,8 +165,8 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
 // Fragments come in with ldmatrix: lane L addresses row (L & 7) + 8 ((L >> 3) & 1) of the A
 // block at column 8 (L >> 4), and J row (L & 7) + 8 (L >> 4) at column 8 ((L >> 3) & 1)
 // (two n-tiles per load); 80-byte rows keep the eight rows of a phase on distinct banks.
-__device__ __forceinline__ void emu_products(long long (&tot)[16], const unsigned char *si,
-                                             const unsigned char *sj, int rb, int cb, int lane) {
+__device__ __forceinline__ void emu_products_g(long long (&tot)[16], const unsigned char *si, int rows_i,
+                                               const unsigned char *sj, int rows_j, int rb, int cb, int lane) {
     const int arow = rb + (lane & 7) + 8 * ((lane >> 3) & 1), acol = 16 * (lane >> 4);       // bytes
     const int brow = cb + (lane & 7) + 8 * (lane >> 4), bcol = 16 * ((lane >> 3) & 1);
 #pragma unroll
@@ -177,8 +180,8 @@ __device__ __forceinline__ void emu_products(long long (&tot)[16], const unsigne
             for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
 #pragma unroll 1
         for (int u = 0; u <= D; ++u) {
-            const unsigned char *pa = si + (size_t)u * CD_TM * EM_ROWBYTES + arow * EM_ROWBYTES + acol;
-            const unsigned char *pb = sj + (size_t)(D - u) * CD_TM * EM_ROWBYTES + brow * EM_ROWBYTES + bcol;
+            const unsigned char *pa = si + (size_t)u * rows_i * EM_ROWBYTES + arow * EM_ROWBYTES + acol;
+            const unsigned char *pb = sj + (size_t)(D - u) * rows_j * EM_ROWBYTES + brow * EM_ROWBYTES + bcol;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 uint32_t a[4], b01[4], b23[4];
@@ -201,6 +204,11 @@ __device__ __forceinline__ void emu_products(long long (&tot)[16], const unsigne
                 tot[4 * nt + i] += D < EM_S - 1 ? iv * (1ll << (43 - 7 * D)) : (iv >> 6);   // floor
             }
     }
+}
+
+__device__ __forceinline__ void emu_products(long long (&tot)[16], const unsigned char *si,
+                                             const unsigned char *sj, int rb, int cb, int lane) {
+    emu_products_g(tot, si, CD_TM, sj, CD_TM, rb, cb, lane);
 }
 
 template <bool EMU>
@@ -281,6 +289,85 @@ __global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParam
                 }
             }
             const int r0 = kb + w, nr = n - r0;
+            if constexpr (EMU) {
+                // the same products from digits: X = L11^-1 (rows j, K = t) once per panel,
+                // then 64-row tiles of A21 (L21 = A21 X^T, warps 0-3) and 64-column tiles of
+                // [B | l]_1 (W1 = X B1, warps 0-3 in 2 x 2 sub-tiles)
+                unsigned char *sx = cd_smem, *so = cd_smem + (size_t)EM_S * CD_NB * EM_ROWBYTES;
+                int *ex = reinterpret_cast<int *>(cd_smem + 2 * EM_SIDE), *eo = ex + CD_TM;
+                bool nonfinite = false;
+                for (int jr = warp; jr < CD_NB; jr += CD_NTH / 32) {
+                    const double x = (lane < w && jr < w) ? sIT[lane][jr] : 0.0;   // X[jr][lane]
+                    unsigned char *base = sx + (size_t)jr * EM_ROWBYTES;
+                    nonfinite |= slice_row_planes(x, reinterpret_cast<uint16_t *>(base) + lane, ex + jr, lane, CD_NB);
+                }
+                for (int gi0 = r0; gi0 < n; gi0 += CD_TM) {
+                    constexpr int RPW = CD_TM / (CD_NTH / 32);
+                    double xv[RPW];
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) {
+                        const int rr = warp + (CD_NTH / 32) * q;
+                        xv[q] = (lane < w && gi0 + rr < n) ? G[(size_t)(gi0 + rr) * n + kb + lane] : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) {
+                        const int rr = warp + (CD_NTH / 32) * q;
+                        unsigned char *base = so + (size_t)rr * EM_ROWBYTES;
+                        nonfinite |= slice_row_planes(xv[q], reinterpret_cast<uint16_t *>(base) + lane, eo + rr, lane, CD_TM);
+                    }
+                    __syncthreads();
+                    if (warp < 4 && 16 * warp < n - gi0) {
+                        long long tot[16];
+                        emu_products_g(tot, so, CD_TM, sx, CD_NB, 16 * warp, 0, lane);
+                        const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int r = 16 * warp + g + 8 * (i >> 1), c = 8 * nt + 2 * tq + (i & 1);
+                                if (gi0 + r >= n || c >= w) continue;
+                                const int se = min(max(eo[r] + ex[c] - 57, -1022), 1023);
+                                G[(size_t)(gi0 + r) * n + kb + c] =
+                                    (double)tot[4 * nt + i] * __longlong_as_double((long long)(se + 1023) << 52);
+                            }
+                    }
+                    __syncthreads();
+                }
+                for (int gj0 = 0; gj0 < mc; gj0 += CD_TM) {
+                    constexpr int RPW = CD_TM / (CD_NTH / 32);
+                    double xv[RPW];
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) {
+                        const int cc = warp + (CD_NTH / 32) * q;
+                        xv[q] = (lane < w && gj0 + cc < mc) ? R.at(kb + lane, gj0 + cc) : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) {
+                        const int cc = warp + (CD_NTH / 32) * q;
+                        unsigned char *base = so + (size_t)cc * EM_ROWBYTES;
+                        nonfinite |= slice_row_planes(xv[q], reinterpret_cast<uint16_t *>(base) + lane, eo + cc, lane, CD_TM);
+                    }
+                    __syncthreads();
+                    const int rb = 16 * (warp & 1), cb = 32 * ((warp >> 1) & 1);
+                    if (warp < 4 && rb < w && gj0 + cb < mc) {
+                        long long tot[16];
+                        emu_products_g(tot, sx, CD_NB, so, CD_TM, rb, cb, lane);
+                        const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int r = rb + g + 8 * (i >> 1), c = cb + 8 * nt + 2 * tq + (i & 1);
+                                if (r >= w || gj0 + c >= mc) continue;
+                                const int se = min(max(ex[r] + eo[c] - 57, -1022), 1023);
+                                R.at(kb + r, gj0 + c) =
+                                    (double)tot[4 * nt + i] * __longlong_as_double((long long)(se + 1023) << 52);
+                            }
+                    }
+                    __syncthreads();
+                }
+                if (nonfinite && lane == 0) sbad = 1;
+            } else {
             const int jw = 4 * warp, tmax = jw + 4 < w ? jw + 4 : w;      // t < tmax
             for (int gi0 = r0; gi0 < n; gi0 += CD_TM) {
                 for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
@@ -333,6 +420,7 @@ __global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParam
                 __syncthreads();
             }
             // 3. trailing update: G22 -= L21 L21^T (lower tiles), [B | l]_2 -= L21 W1
+            }
             // the load column is a plain dot product per row (no 64-wide tile for one column):
             // l_i -= sum_t L_{i, kb+t} y_{kb+t}, i >= r0
             if (R.l)
