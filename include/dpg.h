@@ -298,14 +298,14 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
  * process:
  *   DPG_CONDENSE_FMA: FP64 fused multiply-adds.
  *   DPG_CONDENSE_TC : (the default) the same FP64 products from exact BF16 digits on the
- *                     tensor cores --
- *                     each operand row split as 2^e sum_{u<8} d_u 2^-7(u+1) with 7-bit
- *                     digits d_u, the digit products summed exactly in FP32 and combined
- *                     in a 64-bit integer, entering the FP64 result once per product; the
- *                     digits dropped are below 2^-56 of the row maxima, so the results
- *                     agree with the FMA route to FP64 rounding of the row-scaled sums.
- * The factorization of the diagonal blocks, the panel substitutions and F = W^T y stay
- * FP64 FMA in both.  Errors: DPG_ERR_ARG. */
+ *                     tensor cores -- each operand row split as 2^e sum_{u<7} d_u 2^-(8u+7)
+ *                     with balanced digits |d_u| <= 128, the digit products summed exactly
+ *                     in FP32 and combined in a 64-bit integer, entering the FP64 result
+ *                     once per product; what is dropped lies below 2^-55 of the row maxima,
+ *                     so the results agree with the FMA route to FP64 rounding of the
+ *                     row-scaled sums.
+ * The factorization of the diagonal blocks and F = W^T y stay FP64 FMA in both (the panel
+ * products with the inverse diagonal blocks follow the method).  Errors: DPG_ERR_ARG. */
 #define DPG_CONDENSE_FMA 0
 #define DPG_CONDENSE_TC  1
 int dpg_condense_set_method(int method);

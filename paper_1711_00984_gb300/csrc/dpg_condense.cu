@@ -101,18 +101,19 @@ __device__ __forceinline__ void tile_fma(double (&acc)[16], const double (*sA)[C
     }
 }
 
-// ---- trailing update on the tensor cores: FP64 products from exact BF16 slices ----------
+// ---- trailing update on the tensor cores: FP64 products from exact BF16 digits ---------
 // Every operand row of a 64 x 64 update tile (its <= 32 panel values) is written as
-// x = 2^e sum_{u<8} d_u 2^-7(u+1) with the row exponent e (|x| < 2^e over the row) and
-// 7-bit digits |d_u| <= 127 (exact in BF16), from the FP64 bits with integer operations
-// only; digits below 2^-56 of the row maximum are dropped.  A product of two rows is
-// then 2^(e_i+e_j) sum_D 2^-7(D+2) P_D with P_D = sum_{u+v=D} d_u(i) . d_v(j), and every
-// P_D is a sum of at most 8 x 32 integer products below 2^14, below 2^22 in all: the BF16
-// tensor-core products accumulate it exactly in FP32.  The diagonals D <= 7 (36 slice
-// products) keep the truncation near 2^-53 of the row maxima, which is FP64 rounding for
-// these sums; they are combined exactly in a 64-bit integer and enter the FP64 output
-// once, so the FP64 pipe sees two operations per output and panel instead of 32 FMAs.
-constexpr int EM_S = 8;                  // digits per value
+// x = 2^e sum_{u<7} d_u 2^-(8u+7) with the row exponent e (|x| < 2^e over the row) and
+// balanced base-256 digits |d_u| <= 128 (exact in BF16), from the FP64 bits with integer
+// operations only; what lies below 2^-55 of the row maximum is dropped.  A product of two
+// rows is then 2^(e_i+e_j) sum_D 2^-(8D+14) P_D with P_D = sum_{u+v=D} d_u(i) . d_v(j),
+// and every P_D is a sum of at most 7 x 32 integer products of at most 2^14, below 2^22
+// in all: the BF16 tensor-core products accumulate it exactly in FP32.  The diagonals
+// D <= 6 (28 digit products) keep the truncation near 2^-53 of the row maxima, which is
+// FP64 rounding for these sums; they are combined exactly in a 64-bit integer and enter
+// the FP64 output once, so the FP64 pipe sees two operations per output and panel instead
+// of 32 FMAs.
+constexpr int EM_S = 7;                  // digits per value
 constexpr int EM_SK = 40;                // BF16 per digit row (32 used; 80-byte rows keep the
                                          // fragment loads free of bank conflicts)
 constexpr int EM_ROWBYTES = EM_SK * 2;
@@ -131,14 +132,25 @@ __device__ __forceinline__ bool slice_row_planes(double x, uint16_t *dst, int *e
     unsigned long long f = 0;
     if (eb != 0 && eb != 0x7ffu) {
         const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);
-        const int sh = (int)eb - (int)emax + 3;                 // <= 3: f < 2^56
-        f = sh >= 0 ? mant << sh : (sh > -56 ? mant >> (-sh) : 0ull);
+        const int sh = (int)eb - (int)emax + 2;                 // <= 2: f < 2^55
+        f = sh >= 0 ? mant << sh : (sh > -55 ? mant >> (-sh) : 0ull);
     }
+    // balanced base-256 digits from the low end (a byte >= 128 becomes byte - 256 with a
+    // carry into the next); the top digit is below 2^7 plus the carry, so |d| <= 128
+    const unsigned lo = (unsigned)f, hi = (unsigned)(f >> 32);
+    int dig[EM_S];
+    unsigned carry = 0;
+#pragma unroll
+    for (int k = 0; k < EM_S - 1; ++k) {
+        const unsigned byte = ((k < 4 ? lo >> (8 * k) : hi >> (8 * (k - 4))) & 255u) + carry;
+        carry = byte >= 128u;
+        dig[EM_S - 1 - k] = (int)byte - (int)(carry << 8);
+    }
+    dig[0] = (int)((hi >> 16) + carry);
     const bool neg = (bits >> 63) != 0;
 #pragma unroll
     for (int u = 0; u < EM_S; ++u) {
-        const int d = (int)((f >> (49 - 7 * u)) & 127ull);
-        const float fd = (float)(neg ? -d : d);
+        const float fd = (float)(neg ? -dig[u] : dig[u]);
         dst[(size_t)u * plane_rows * EM_SK] = (uint16_t)(__float_as_uint(fd) >> 16);
     }
     return __any_sync(0xffffffffu, eb == 0x7ffu);
@@ -160,8 +172,8 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
                  : "r"((uint32_t)__cvta_generic_to_shared(p)));
 }
 
-// tot[4 nt + i] (the warp's 16 x 32 sub-tile, mma accumulator order) = sum_D P_D 2^(43-7D)
-// (D = 7: 2^-6, floor), from the digit planes of the I rows (rows rb ..) and J rows (cb ..).
+// tot[4 nt + i] (the warp's 16 x 32 sub-tile, mma accumulator order) = sum_D P_D 2^(43-8D)
+// (D = 6: 2^-5, floor), from the digit planes of the I rows (rows rb ..) and J rows (cb ..).
 // Fragments come in with ldmatrix: lane L addresses row (L & 7) + 8 ((L >> 3) & 1) of the A
 // block at column 8 (L >> 4), and J row (L & 7) + 8 (L >> 4) at column 8 ((L >> 3) & 1)
 // (two n-tiles per load); 80-byte rows keep the eight rows of a phase on distinct banks.
@@ -195,13 +207,13 @@ __device__ __forceinline__ void emu_products_g(long long (&tot)[16], const unsig
             }
         }
         // the exact integer sums into the 64-bit total (|P_D| < 2^22: the 1.5 2^23 shift
-        // puts the integer in the low mantissa bits)
+        // puts the integer in the low mantissa bits; |total| < 2^62)
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const long long iv = (long long)(__float_as_int(acc[nt][i] + 12582912.0f) - 0x4B400000);
-                tot[4 * nt + i] += D < EM_S - 1 ? iv * (1ll << (43 - 7 * D)) : (iv >> 6);   // floor
+                tot[4 * nt + i] += D < EM_S - 1 ? iv * (1ll << (43 - 8 * D)) : (iv >> 5);   // floor
             }
     }
 }
