@@ -6,20 +6,24 @@
 // factorization G = L L^T, the substitutions W = L^-1 B and y = L^-1 l, then the products
 // K = W^T W and F = W^T y.
 //
-// condense_kernel: one CTA per element at a time (persistent over the batch, three CTAs per
-// SM), FP64.
+// condense_kernel<EMU>: one CTA per element at a time, persistent over the batch.
 //   * Right-looking blocked Cholesky, panels of CD_NB columns, in place in the lower
 //     triangle of G.  The diagonal block is factored in shared memory by all threads,
-//     which then form L11^-1; the panel rows below it (L21 = A21 L11^-T) and the matching CD_NB
-//     rows of [B | l] (W1 = L11^-1 B1) are products with that inverse; the trailing lower triangle of G and the rows of [B | l] below the panel are updated
-//     by CD_TM x CD_TM tiles, 16 outputs per thread (TileSpan).
+//     which then form L11^-1; the panel rows below it (L21 = A21 L11^-T) and the matching
+//     CD_NB rows of [B | l] (W1 = L11^-1 B1) are products with that inverse; the trailing
+//     lower triangle of G and the rows of [B | l] below the panel are updated by
+//     CD_TM x CD_TM tiles.
 //   * The substitution of [B | l] rides along with the factorization (same panel loop),
 //     so W and y overwrite B and l in place.
 //   * K: the lower tiles of W^T W over all n rows, mirrored; F = W^T y by one dot product
 //     per column (the load column is likewise a dot product per row in the updates).
-// Every step is multiply-add work on the FP64 pipe: the kernel is bound by the FP64
-// FMA rate (2 per clock per SM on GB300), not by memory -- one element's G is read and
-// written O(n / CD_NB) times through L2 while it takes O(n^3) multiply-adds.
+// EMU = false (DPG_CONDENSE_FMA): every product is FP64 FMA work, 16 outputs of a tile per
+// thread (TileSpan), three CTAs per SM; the kernel is bound by the FP64 FMA rate (2 per
+// clock per SM on GB300), not by memory -- an element's G streams through L2 O(n / CD_NB)
+// times against O(n^3) multiply-adds.
+// EMU = true (DPG_CONDENSE_TC, the default): the panel products, the tile updates and
+// W^T W are exact BF16 digit products on the tensor cores (dpg_digits.cuh), a 16 x 32
+// sub-tile per warp, two CTAs per SM; the diagonal blocks and F stay FP64 FMA.
 #include "dpg_digits.cuh"
 #include "dpg_kernels.h"
 
