@@ -344,6 +344,83 @@ __global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParam
                     R.l[i] -= s0 + s1;
                 }
             const int ntr = (nr + CD_TM - 1) / CD_TM, ntc = (m + CD_TM - 1) / CD_TM;
+            if constexpr (EMU) {
+                // row block by row block: the digits of the 64 I rows (L21 rows) once per block,
+                // those of the J rows (L21 rows, or the columns of W1 for a right-hand-side
+                // tile) per tile; a warp per row, its loads issued before the digit splits
+                unsigned char *si = cd_smem, *sj = cd_smem + EM_SIDE;
+                int *ei = reinterpret_cast<int *>(cd_smem + 2 * EM_SIDE), *ej = ei + CD_TM;
+                constexpr int RPW = CD_TM / (CD_NTH / 32);                   // rows per warp
+                bool nonfinite = false;
+                for (int I = 0; I < ntr; ++I) {
+                    const int gi0 = r0 + I * CD_TM;
+                    {
+                        double xv[RPW];
+#pragma unroll
+                        for (int q = 0; q < RPW; ++q) {
+                            const int rr = warp + (CD_NTH / 32) * q;
+                            xv[q] = (lane < w && gi0 + rr < n) ? G[(size_t)(gi0 + rr) * n + kb + lane] : 0.0;
+                        }
+#pragma unroll
+                        for (int q = 0; q < RPW; ++q) {
+                            const int rr = warp + (CD_NTH / 32) * q;
+                            nonfinite |= slice_row(xv[q], reinterpret_cast<uint16_t *>(si + (size_t)rr * EM_ROWBYTES) + lane,
+                                                   ei + rr, lane);
+                        }
+                    }
+                    for (int jt = 0; jt < I + 1 + ntc; ++jt) {
+                        const bool isA = jt <= I;
+                        const int J = isA ? jt : jt - I - 1;
+                        const int gj0 = isA ? r0 + J * CD_TM : J * CD_TM;
+                        double xv[RPW];
+#pragma unroll
+                        for (int q = 0; q < RPW; ++q) {
+                            const int rr = warp + (CD_NTH / 32) * q;
+                            double x = 0.0;
+                            if (lane < w) {
+                                if (isA) {
+                                    if (gj0 + rr < n) x = G[(size_t)(gj0 + rr) * n + kb + lane];
+                                } else if (gj0 + rr < m) {
+                                    x = R.B[(size_t)(kb + lane) * m + gj0 + rr];
+                                }
+                            }
+                            xv[q] = x;
+                        }
+#pragma unroll
+                        for (int q = 0; q < RPW; ++q) {
+                            const int rr = warp + (CD_NTH / 32) * q;
+                            nonfinite |= slice_row(xv[q], reinterpret_cast<uint16_t *>(sj + (size_t)rr * EM_ROWBYTES) + lane,
+                                                   ej + rr, lane);
+                        }
+                        __syncthreads();
+                        // a 16 x 32 sub-tile per warp; sub-tiles outside the tile or above a
+                        // diagonal tile's diagonal are skipped by the whole warp
+                        const int rb = 16 * (warp & 3), cb = 32 * (warp >> 2);
+                        const int rows_v = n - gi0, cols_v = (isA ? n : m) - gj0;
+                        const bool diag = isA && I == J;
+                        if (rb < rows_v && cb < cols_v && !(diag && cb >= rb + 16)) {
+                            long long tot[16];
+                            emu_products(tot, si, sj, rb, cb, lane);
+                            const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+                            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    const int r = rb + g + 8 * (i >> 1), c = cb + 8 * nt + 2 * tq + (i & 1);
+                                    if (r >= rows_v || c >= cols_v || (diag && c > r)) continue;
+                                    // 2^(e_i + e_j - 57), a normal number for the exponents here
+                                    const int se = min(max(ei[r] + ej[c] - 57, -1022), 1023);
+                                    const double sc = __longlong_as_double((long long)(se + 1023) << 52);
+                                    double *dst = isA ? G + (size_t)(gi0 + r) * n + gj0 + c
+                                                      : R.B + (size_t)(gi0 + r) * m + gj0 + c;
+                                    *dst = fma(-(double)tot[4 * nt + i], sc, *dst);
+                                }
+                        }
+                        __syncthreads();
+                    }
+                }
+                if (nonfinite && lane == 0) sbad = 1;
+            } else {
             const int tilesA = ntr * (ntr + 1) / 2, tiles = tilesA + ntr * ntc;
             for (int tile = 0; tile < tiles; ++tile) {
                 int I, J;
@@ -358,68 +435,7 @@ __global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParam
                 }
                 const int gi0 = r0 + I * CD_TM;                           // rows of G / rhs
                 const int gj0 = isA ? r0 + J * CD_TM : J * CD_TM;         // columns
-                if constexpr (EMU) {
-                    unsigned char *si = cd_smem, *sj = cd_smem + EM_SIDE;
-                    int *ei = reinterpret_cast<int *>(cd_smem + 2 * EM_SIDE), *ej = ei + CD_TM;
-                    // digits of the 64 I rows (L21 rows) and the 64 J rows (L21 rows, or
-                    // the columns of W1 for a right-hand-side tile): a warp per row
-                    // all 16 loads of a warp first (independent), then the digit splits
-                    constexpr int RPW = 2 * CD_TM / (CD_NTH / 32);            // rows per warp
-                    double xv[RPW];
-#pragma unroll
-                    for (int j = 0; j < RPW; ++j) {
-                        const int r = warp + (CD_NTH / 32) * j;
-                        const bool side_j = r >= CD_TM;
-                        const int rr = side_j ? r - CD_TM : r;
-                        double x = 0.0;
-                        if (lane < w) {
-                            if (!side_j) {
-                                if (gi0 + rr < n) x = G[(size_t)(gi0 + rr) * n + kb + lane];
-                            } else if (isA) {
-                                if (gj0 + rr < n) x = G[(size_t)(gj0 + rr) * n + kb + lane];
-                            } else if (gj0 + rr < m) {
-                                x = R.B[(size_t)(kb + lane) * m + gj0 + rr];
-                            }
-                        }
-                        xv[j] = x;
-                    }
-                    bool nonfinite = false;
-#pragma unroll
-                    for (int j = 0; j < RPW; ++j) {
-                        const int r = warp + (CD_NTH / 32) * j;
-                        const bool side_j = r >= CD_TM;
-                        const int rr = side_j ? r - CD_TM : r;
-                        unsigned char *base = (side_j ? sj : si) + (size_t)rr * EM_ROWBYTES;
-                        nonfinite |= slice_row(xv[j], reinterpret_cast<uint16_t *>(base) + lane,
-                                               (side_j ? ej : ei) + rr, lane);
-                    }
-                    if (nonfinite && lane == 0) sbad = 1;
-                    __syncthreads();
-                    // a 16 x 32 sub-tile per warp; sub-tiles outside the tile or above a
-                    // diagonal tile's diagonal are skipped by the whole warp
-                    const int rb = 16 * (warp & 3), cb = 32 * (warp >> 2);
-                    const int rows_v = n - gi0, cols_v = (isA ? n : m) - gj0;
-                    const bool diag = isA && I == J;
-                    if (rb < rows_v && cb < cols_v && !(diag && cb >= rb + 16)) {
-                        long long tot[16];
-                        emu_products(tot, si, sj, rb, cb, lane);
-                        const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const int r = rb + g + 8 * (i >> 1), c = cb + 8 * nt + 2 * tq + (i & 1);
-                                if (r >= rows_v || c >= cols_v || (diag && c > r)) continue;
-                                // 2^(e_i + e_j - 57), a normal number for the exponents here
-                                const int se = min(max(ei[r] + ej[c] - 57, -1022), 1023);
-                                const double sc = __longlong_as_double((long long)(se + 1023) << 52);
-                                double *dst = isA ? G + (size_t)(gi0 + r) * n + gj0 + c
-                                                  : R.B + (size_t)(gi0 + r) * m + gj0 + c;
-                                *dst = fma(-(double)tot[4 * nt + i], sc, *dst);
-                            }
-                    }
-                    __syncthreads();
-                } else {
+                {
                 for (int idx = tid; idx < CD_TM * CD_NB; idx += CD_NTH) {
                     const int r = idx / CD_NB, t = idx - r * CD_NB;
                     const bool tv = t < w;
@@ -449,6 +465,7 @@ __global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParam
                 }
                 __syncthreads();
                 }
+            }
             }
         }
         double *K = p.K + (size_t)e * m * m;
