@@ -44,7 +44,7 @@ def _rank(rank, world, port, times, results):
 def test_max_over_ranks_gloo():
     world = 2
     times = [0.0031, 0.0047]               # seconds per step on each rank
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:       # no fork of a multi-threaded process
         results = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), times, results), nprocs=world, join=True)
         got = dict(results)
