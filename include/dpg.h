@@ -212,22 +212,26 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj);
  * and may not grow, code that runs inside another framework's allocator or memory
  * budget, or a call issued where an allocation would stall the stream or the device.
  * dpg_integrate takes its metric-field workspace from a memory pool; this entry point
- * instead uses one file-scope device array of DPG_NOALLOC_SCRATCH_BYTES (32 MiB), which
- * every GPU that loads the library reserves until the process exits.  It calls no
- * cudaMalloc, cudaFree or other allocating routine.
- *   Arguments, layouts and results are those of dpg_integrate for the general map;
- *   DPG_MAP_AFFINE, DPG_MAP_EXTRUDED and DPG_VEC3 are rejected (DPG_ERR_ARG).
+ * instead uses one file-scope device array of DPG_NOALLOC_SCRATCH_BYTES (32 MiB).  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   Arguments, layouts and results are those of dpg_integrate for the general map, FP64
+ *   and FP32 forms (the same programs and kernels); DPG_MAP_AFFINE, DPG_MAP_EXTRUDED and
+ *   DPG_VEC3 are rejected (DPG_ERR_ARG).
  *   Limit: n_elem * nfields * L^3 * (8 or 4 bytes) must fit the array (nfields = 7, 12,
  *   7, 1, 18 for H1, H(curl), H(div), L2, B; 4 bytes with DPG_FP32), else the call
  *   returns DPG_ERR_SCRATCH before launching anything.  Example: H(curl), q = 5, L = 7,
- *   FP64 fits 1019 elements per call.
- *   Set-up: the first call on a device (with that device current) looks up the array's
- *   device address (cudaGetSymbolAddress) and caches it; make that first call before
- *   any stream capture.  Tables must be initialised with dpg_tables_init beforehand.
+ *   FP64 fits 1019 elements per call, FP32 2038.
+ *   Set-up and memory: the array belongs to a module that CUDA loads lazily (by default),
+ *   so its 32 MiB are reserved on a device by the first call on that device -- the call
+ *   that looks up the array's device address (cudaGetSymbolAddress, with that device
+ *   current) -- and stay reserved until the process exits.  Make that first call at
+ *   set-up, within the caller's memory budget, and before any stream capture; later
+ *   calls reserve nothing.  Tables must be initialised with dpg_tables_init beforehand.
  *   Sharing: all calls use the same array and it keeps the last call's contents (every
  *   value a call reads is written by that call first, so nothing needs clearing); calls
  *   that overlap on the GPU, e.g. on two streams, race on it and must be serialised by
- *   the caller. */
+ *   the caller.  On the host, a call holds the library's lock from its program look-up to
+ *   its last launch, like dpg_integrate. */
 #define DPG_NOALLOC_SCRATCH_BYTES (32u << 20)
 int dpg_integrate_noalloc(int space, int p_trial, int q_test, int64_t n_elem,
                           const double *vertices, const double *coeffs, void *out, void *stream);
@@ -339,6 +343,13 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
  * Returns DPG_OK. */
 int dpg_test_stall_tc_once(void);
 
+/* Test hook (not part of the method): caps the metric-field workspace of one chunk of the
+ * general and extruded-map paths (dpg_integrate, dpg_integrate_host, dpg_autotune) at
+ * `bytes` (at least one element per chunk) instead of the library's 512 MB, so that a
+ * small call runs through several chunks; 0 restores the default.  Applies to every later
+ * call in the process.  Returns DPG_OK, or DPG_ERR_ARG for bytes < 0. */
+int dpg_test_set_workspace_limit(int64_t bytes);
+
 /* Synchronise `stream`, read and clear the device status word of the current device.
  * Returns DPG_OK or the first device-detected error; *first_bad_elem (if not NULL)
  * receives the smallest offending element index of that error, or -1. */
@@ -360,10 +371,12 @@ const char *dpg_last_cuda_error(void);
 double dpg_flops_per_element(int space, int p_trial, int q_test);
 
 /* Not part of the paper's method: measure the device's peak fused multiply-add rate in
- * FP64 (precision = 64) or FP32 (precision = 32) with a register-resident FMA loop, or
- * the FP64 tensor-core rate (precision = 65, mma.sync m8n8k4 FP64), on `stream`; writes
- * the flop rate (2 flops per multiply-add) in flop/s to *flops.  Synchronous.  Used only
- * to give the ALU roofline a measured denominator. */
+ * FP64 (precision = 64) or FP32 (precision = 32) with a register-resident FMA loop, the
+ * FP64 tensor-core rate (precision = 65, mma.sync m8n8k4 FP64), or the TF32 rate of the
+ * fifth-generation tensor cores (precision = 19: tcgen05 kind::tf32, 128 x 256 x 8
+ * products, one CTA per SM), on `stream`; writes the flop rate (2 flops per multiply-add)
+ * in flop/s to *flops.  Synchronous.  Used only to give the ALU and tensor rooflines a
+ * measured denominator.  DPG_ERR_TIMEOUT if the tensor-core probe's bounded wait ran out. */
 int dpg_measure_fma_peak(int precision, void *stream, double *flops);
 
 #ifdef __cplusplus

@@ -31,7 +31,7 @@ STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANG
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
            "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",
            "dpg_strerror", "dpg_last_cuda_error", "dpg_autotune", "dpg_flops_per_element", "dpg_measure_fma_peak",
-           "dpg_test_stall_tc_once", "dpg_integrate_load", "dpg_condense",
+           "dpg_test_stall_tc_once", "dpg_test_set_workspace_limit", "dpg_integrate_load", "dpg_condense",
            "dpg_condensed_system", "dpg_condense_set_method"]
 
 _lib = None
@@ -85,6 +85,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.dpg_condense_set_method.argtypes = [ctypes.c_int]
         lib.dpg_test_stall_tc_once.argtypes = []
         lib.dpg_test_stall_tc_once.restype = ctypes.c_int
+        lib.dpg_test_set_workspace_limit.argtypes = [i64]
+        lib.dpg_test_set_workspace_limit.restype = ctypes.c_int
         for name in ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp",
                      "dpg_integrate_host", "dpg_sync_status", "dpg_measure_fma_peak", "dpg_integrate_load",
                      "dpg_condense", "dpg_condensed_system", "dpg_condense_set_method"]:
@@ -198,6 +200,12 @@ def dpg_sync_status(stream: int = 0) -> tuple[int, int]:
 def dpg_test_stall_tc_once() -> int:
     """Test hook: the next FP32 tensor-core launch stalls its first CTA (see include/dpg.h)."""
     return _check(_L().dpg_test_stall_tc_once(), "dpg_test_stall_tc_once")
+
+
+def dpg_test_set_workspace_limit(nbytes: int) -> int:
+    """Test hook: cap the per-chunk metric-field workspace of the general and extruded
+    paths at nbytes (0 restores the default; see include/dpg.h)."""
+    return _check(_L().dpg_test_set_workspace_limit(int(nbytes)), "dpg_test_set_workspace_limit")
 
 
 def dpg_strerror(code: int) -> str:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libdpg.so")
 SOURCES = ["dpg_setup.cu", "dpg_kernels.cu", "dpg_tc.cu", "dpg_capi.cu", "dpg_noalloc.cu", "dpg_condense.cu"]
-HEADERS = ["dpg_internal.h", "dpg_setup.h", "dpg_kernels.h", "dpg_registry.h", "dpg_digits.cuh"]
+HEADERS = ["dpg_internal.h", "dpg_setup.h", "dpg_kernels.h", "dpg_registry.h", "dpg_digits.cuh", "dpg_trace.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -18,6 +18,7 @@
 #include "dpg_kernels.h"
 #include "dpg_registry.h"
 #include "dpg_setup.h"
+#include "dpg_trace.h"
 
 using namespace dpg;
 
@@ -30,6 +31,7 @@ int g_max_dyn_smem_tc = 0;                               // the same for the ten
 int g_tc_stall_once = 0;                                 // test hook, see dpg_test_stall_tc_once
 int g_num_sms = 152;                                     // set at device set-up
 int g_condense_method = DPG_CONDENSE_TC;                 // see dpg_condense_set_method
+size_t g_ws_limit_test = 0;                              // see dpg_test_set_workspace_limit
 
 struct TableEntry {
     HostTables host;
@@ -405,21 +407,37 @@ struct OutGeom {
     int64_t ld, mat;
 };
 
+// Metric-field bytes per element of the general-path program of the form T.
 template <typename T>
-int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
-                const double *coeffs, T *out, cudaStream_t s, OutGeom og, int64_t base = 0) {
-    constexpr bool f32 = sizeof(T) == 4;
-    const Program &pr = f32 ? pe->prog32 : pe->prog;
-    const int L = pr.L, L3 = L * L * L;
-    const int64_t mat = og.mat;
-    const size_t per_elem = (size_t)pr.nfields * L3 * sizeof(T);
-    int64_t chunk = (int64_t)(kWorkspaceLimit / per_elem);
+size_t general_field_bytes(const ProgEntry *pe) {
+    const Program &pr = sizeof(T) == 4 ? pe->prog32 : pe->prog;
+    return (size_t)pr.nfields * pr.L * pr.L * pr.L * sizeof(T);
+}
+
+// Elements per chunk of the general path: the workspace bound, the CTA-count bound of the
+// FP64 grid (one CTA per element and unit) and n_elem.
+template <typename T>
+int64_t general_chunk(const ProgEntry *pe, int64_t n_elem, size_t ws_limit) {
+    const Program &pr = sizeof(T) == 4 ? pe->prog32 : pe->prog;
+    int64_t chunk = (int64_t)(ws_limit / general_field_bytes<T>(pe));
     if (chunk < 1) chunk = 1;
     const int64_t max_ctas = INT_MAX / (int64_t)pr.units.size();
     if (chunk > max_ctas) chunk = max_ctas;
     if (chunk > n_elem) chunk = n_elem;
-    void *ws = nullptr;
-    CK(cudaMallocFromPoolAsync(&ws, (size_t)chunk * per_elem, ds->pool, s));
+    return chunk;
+}
+
+// The general path over n_elem elements in chunks of `chunk` elements, the metric fields
+// of a chunk in ws (at least chunk * general_field_bytes<T> bytes, reused by every chunk:
+// the launches are stream-ordered).
+template <typename T>
+int run_general_in(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
+                   const double *coeffs, T *out, cudaStream_t s, OutGeom og, int64_t base, void *ws,
+                   int64_t chunk) {
+    constexpr bool f32 = sizeof(T) == 4;
+    const Program &pr = f32 ? pe->prog32 : pe->prog;
+    const int L = pr.L;
+    const int64_t mat = og.mat;
     int rc = DPG_OK;
     for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK; e0 += chunk) {
         const int64_t ne = std::min(chunk, n_elem - e0);
@@ -430,7 +448,11 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
         g.coeffs = coeffs ? coeffs + 2 * e0 : nullptr;
         g.zeta = te->zeta; g.w = te->w;
         g.fields = ws; g.status = ds->status;
-        cudaError_t le = launch_geom<T>(g, s);
+        cudaError_t le;
+        {
+            TraceRange tr("dpg geometry");
+            le = launch_geom<T>(g, s);
+        }
         if (le != cudaSuccess) { rc = cuda_fail(le, "geom_kernel launch", __LINE__); break; }
         if constexpr (f32) if (pe->kind32 == K32_TC) {
             TcParams tp;
@@ -449,7 +471,10 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             tp.status = ds->status;
             tp.stall_cta = g_tc_stall_once ? 0 : -1;
             g_tc_stall_once = 0;
-            le = launch_tc_f32(tp, pr.smem_bytes, s);
+            {
+                TraceRange tr("dpg contraction: general, FP32, tcgen05");
+                le = launch_tc_f32(tp, pr.smem_bytes, s);
+            }
             if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
             continue;
         }
@@ -467,7 +492,10 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             pp.fields = reinterpret_cast<const float *>(ws);
             pp.out = reinterpret_cast<float *>(out + e0 * mat);
             pp.mat_stride = mat; pp.ld = og.ld; pp.n_elem = ne;
-            le = launch_panel_f32(pp, pr.smem_bytes, s);
+            {
+                TraceRange tr("dpg contraction: general, FP32, row panels");
+                le = launch_panel_f32(pp, pr.smem_bytes, s);
+            }
             if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
             continue;
         }
@@ -484,6 +512,7 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             sp.fields = reinterpret_cast<const float *>(ws);
             sp.out = reinterpret_cast<float *>(out + e0 * mat);
             sp.mat_stride = mat; sp.ld = og.ld; sp.n_elem = ne;
+            TraceRange tr("dpg contraction: general, FP32, mirrored tiles");
             le = launch_general_f32(sp, pr.smem_bytes, pe->max_nc1_32, s);
         } else {
             SfParams<T> sp;
@@ -494,10 +523,23 @@ int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, 
             sp.fields = reinterpret_cast<const T *>(ws);
             sp.out = out + e0 * mat;
             sp.mat_stride = mat; sp.ld = og.ld; sp.n_elem = ne;
+            TraceRange tr("dpg contraction: general, FP64");
             le = launch_general<T>(sp, pr.smem_values * sizeof(T), s);
         }
         if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
     }
+    return rc;
+}
+
+// The general path with its workspace from the library pool (chunks of at most
+// kWorkspaceLimit bytes of metric fields, or g_ws_limit_test when a test sets it).
+template <typename T>
+int run_general(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, const double *verts,
+                const double *coeffs, T *out, cudaStream_t s, OutGeom og, int64_t base = 0) {
+    const int64_t chunk = general_chunk<T>(pe, n_elem, g_ws_limit_test ? g_ws_limit_test : kWorkspaceLimit);
+    void *ws = nullptr;
+    CK(cudaMallocFromPoolAsync(&ws, (size_t)chunk * general_field_bytes<T>(pe), ds->pool, s));
+    int rc = run_general_in<T>(ds, pe, te, n_elem, verts, coeffs, out, s, og, base, ws, chunk);
     cudaError_t fe = cudaFreeAsync(ws, s);
     if (fe != cudaSuccess && rc == DPG_OK) rc = cuda_fail(fe, "cudaFreeAsync", __LINE__);
     return rc;
@@ -541,7 +583,11 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
     cp.space = pr.space; cp.n_elem = n_elem; cp.elem_base = 0;
     cp.verts = verts; cp.coeffs = coeffs; cp.consts = (double *)consts; cp.status = ds->status;
     int rc = DPG_OK;
-    cudaError_t le = launch_affine_const(cp, s);
+    cudaError_t le;
+    {
+        TraceRange tr("dpg geometry: affine constants");
+        le = launch_affine_const(cp, s);
+    }
     if (le != cudaSuccess) rc = cuda_fail(le, "affine_const_kernel launch", __LINE__);
     for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK; e0 += per_launch) {
         const int64_t ne = std::min(per_launch, n_elem - e0);
@@ -554,7 +600,10 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         ap.consts = (const double *)consts + AFF_CONST_STRIDE * e0;
         ap.out = out + e0 * mat;
         ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne;
-        le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
+        {
+            TraceRange tr("dpg contraction: affine");
+            le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
+        }
         if (le != cudaSuccess) rc = cuda_fail(le, "sf_affine_kernel launch", __LINE__);
     }
     cudaError_t fe = cudaFreeAsync(consts, s);
@@ -578,7 +627,8 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         max_units_block = std::max(max_units_block, c);
     }
     const size_t per_elem = (size_t)pr.nfields * L2 * sizeof(T) + sizeof(int);
-    int64_t chunk = std::max<int64_t>(1, (int64_t)(kWorkspaceLimit / per_elem));
+    const size_t ws_limit = g_ws_limit_test ? g_ws_limit_test : kWorkspaceLimit;
+    int64_t chunk = std::max<int64_t>(1, (int64_t)(ws_limit / per_elem));
     const int64_t target = (int64_t)g_num_sms * 6 * 4;
     const int64_t ne_all = std::min(chunk, n_elem);
     const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_units_block,
@@ -602,7 +652,10 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         g.coeffs = coeffs ? coeffs + 2 * e0 : nullptr;
         g.zeta = te->zeta; g.w = te->w;
         g.fields = fields; g.estatus = est; g.status = ds->status;
-        le = launch_geom2d<T>(g, s);
+        {
+            TraceRange tr("dpg geometry: extruded");
+            le = launch_geom2d<T>(g, s);
+        }
         if (le != cudaSuccess) { rc = cuda_fail(le, "geom2d_kernel launch", __LINE__); break; }
         AffParams<T> ap;
         ap.blocks = aprog.d_blocks; ap.units = aprog.d_units; ap.block_unit_begin = aprog.d_block_units;
@@ -614,7 +667,10 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         ap.L = L; ap.nfields = pr.nfields;
         ap.out = out + e0 * mat;
         ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne;
-        le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
+        {
+            TraceRange tr("dpg contraction: extruded");
+            le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
+        }
         if (le != cudaSuccess) { rc = cuda_fail(le, "extruded contraction launch", __LINE__); break; }
     }
     cudaError_t fe = cudaFreeAsync(ws, s);
@@ -649,6 +705,7 @@ int integrate_locked(int space, int p_trial, int q_test, int64_t n_elem, const d
         r = fp32 ? run_general<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s, og)
                  : run_general<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s, og);
     if (r == DPG_OK && vec3) {
+        TraceRange tr("dpg vec3 replication");
         const cudaError_t le = fp32 ? launch_vec3_fill<float>((float *)out, n_elem, pr.rows, s)
                                     : launch_vec3_fill<double>((double *)out, n_elem, pr.rows, s);
         if (le != cudaSuccess) r = cuda_fail(le, "vec3_fill_kernel launch", __LINE__);
@@ -686,7 +743,11 @@ int enqueue_hp(DeviceState *ds, int space, int64_t n, const double *verts, const
     const size_t smem = ds->hp_smem[fp32 ? 1 : 0][base];
     const int ctas = g_num_sms * hp_ctas_per_sm(fp32, smem);
     int rc = DPG_OK;
-    cudaError_t le = launch_hp(p, fp32, smem, ctas, s);
+    cudaError_t le;
+    {
+        TraceRange tr("dpg hp: work generation, geometry, persistent contraction");
+        le = launch_hp(p, fp32, smem, ctas, s);
+    }
     if (le != cudaSuccess) rc = cuda_fail(le, "hp launch sequence", __LINE__);
     for (void *w : { wfield, wtmp, wit, wf, wu, word, wsmall }) cudaFreeAsync(w, s);
     return rc;
@@ -730,37 +791,50 @@ int read_status(DeviceState *ds, int64_t *first_bad) {
 
 }  // namespace
 
-int dpg::lookup_program_view(int space, int p_trial, int q, ProgramView *view) {
+int dpg::integrate_in_scratch(int space, int p_trial, int q_test, int64_t n_elem, const double *vertices,
+                              const double *coeffs, void *out, void *scratch, size_t scratch_bytes, void *stream) {
+    if (space & (DPG_MAP_AFFINE | DPG_MAP_EXTRUDED | DPG_VEC3)) return DPG_ERR_ARG;
     if (!valid_space(space)) return DPG_ERR_ARG;
-    if (q < 1 || q > DPG_MAX_Q) return DPG_ERR_RANGE;
+    if (q_test < 1 || q_test > DPG_MAX_Q) return DPG_ERR_RANGE;
     const int base = space & 0xff;
     int p = 0, split = 0;
     if (base == S_B || base == S_AB) {
-        if (p_trial < 1 || p_trial > q) return DPG_ERR_ARG;
+        if (p_trial < 1 || p_trial > q_test) return DPG_ERR_ARG;
         p = p_trial;
         split = (space & DPG_B_SPLIT) ? 1 : 0;
     }
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    // the lock is held from the look-up to the last launch, so that no dpg_tables_init,
+    // dpg_tables_free or dpg_autotune on another thread replaces the program meanwhile;
+    // only existing state is looked up (nothing is created, nothing allocated)
     std::lock_guard<std::mutex> lk(g_mu);
     auto di = g_dev.find(dev);
     if (di == g_dev.end()) return DPG_ERR_NOT_INIT;
     DeviceState *ds = di->second.get();
-    auto it = ds->active_L.find(std::make_pair(base, q));
+    auto it = ds->active_L.find(std::make_pair(base, q_test));
     if (it == ds->active_L.end()) return DPG_ERR_NOT_INIT;
     const int L = it->second;
-    auto tt = ds->tables.find(std::make_pair(q, L));
-    auto pt = ds->progs.find(ProgKey{ base, q, L, p, split });
+    auto tt = ds->tables.find(std::make_pair(q_test, L));
+    auto pt = ds->progs.find(ProgKey{ base, q_test, L, p, split });
     if (tt == ds->tables.end() || pt == ds->progs.end()) return DPG_ERR_NOT_INIT;
-    view->prog = &pt->second->prog;
-    view->d_blocks = pt->second->d_blocks;
-    view->d_units = pt->second->d_units;
-    view->zeta = tt->second->zeta;
-    view->w = tt->second->w;
-    view->pp64 = tt->second->pp64;
-    view->pp32 = tt->second->pp32;
-    view->status = ds->status;
-    return DPG_OK;
+    ProgEntry *pe = pt->second.get();
+    TableEntry *te = tt->second.get();
+    if (n_elem < 0) return DPG_ERR_ARG;
+    const bool fp32 = (space & DPG_FP32) != 0;
+    // the whole call in one chunk: its metric fields must fit the scratch, and the FP64
+    // grid (one CTA per element and unit) must stay below 2^31 CTAs
+    const size_t per_elem = fp32 ? general_field_bytes<float>(pe) : general_field_bytes<double>(pe);
+    const Program &pr = fp32 ? pe->prog32 : pe->prog;
+    if ((size_t)n_elem > scratch_bytes / per_elem) return DPG_ERR_SCRATCH;
+    if ((int64_t)pr.units.size() * n_elem > INT_MAX) return DPG_ERR_SCRATCH;
+    if (n_elem == 0) return DPG_OK;
+    if (!vertices || !out || !scratch) return DPG_ERR_ARG;
+    const double *c = base <= S_L2 ? coeffs : nullptr;                 // Gram matrices only
+    const OutGeom og{ pe->prog.cols, (int64_t)pe->prog.parts * pe->prog.rows * pe->prog.cols };
+    cudaStream_t s = (cudaStream_t)stream;
+    return fp32 ? run_general_in<float>(ds, pe, te, n_elem, vertices, c, (float *)out, s, og, 0, scratch, n_elem)
+                : run_general_in<double>(ds, pe, te, n_elem, vertices, c, (double *)out, s, og, 0, scratch, n_elem);
 }
 
 extern "C" {
@@ -875,8 +949,11 @@ int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem, const
     CK(cudaMallocFromPoolAsync(&dv, v_bytes, ds->pool, s));
     if (c_bytes) CK(cudaMallocFromPoolAsync(&dc, c_bytes, ds->pool, s));
     CK(cudaMallocFromPoolAsync(&dout, out_bytes, ds->pool, s));
-    CK(cudaMemcpyAsync(dv, vertices, v_bytes, cudaMemcpyHostToDevice, s));
-    if (c_bytes) CK(cudaMemcpyAsync(dc, coeffs, c_bytes, cudaMemcpyHostToDevice, s));
+    {
+        TraceRange tr("dpg host-to-device inputs");
+        CK(cudaMemcpyAsync(dv, vertices, v_bytes, cudaMemcpyHostToDevice, s));
+        if (c_bytes) CK(cudaMemcpyAsync(dc, coeffs, c_bytes, cudaMemcpyHostToDevice, s));
+    }
     // stream the batch: chunk k is integrated on `s` while earlier chunks drain to the
     // host on the copy streams (about 64 MB per chunk, at most 64 chunks)
     const int64_t by_bytes = (int64_t)((out_bytes + (size_t(64) << 20) - 1) / (size_t(64) << 20));
@@ -893,6 +970,7 @@ int dpg_integrate_host(int space, int p_trial, int q_test, int64_t n_elem, const
         evs.push_back(ev);
         CK(cudaEventRecord(ev, s));
         cudaStream_t cs = ds->copy_streams[c % 4];
+        TraceRange tr("dpg device-to-host chunk");
         CK(cudaStreamWaitEvent(cs, ev, 0));
         CK(cudaMemcpyAsync((char *)out + e0 * per_out, (char *)dout + e0 * per_out, ne * per_out,
                            cudaMemcpyDeviceToHost, cs));
@@ -933,6 +1011,7 @@ int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vert
     p.zeta = te->zeta; p.w = te->w;
     p.out = out; p.status = ds->status;
     cudaError_t le;
+    TraceRange tr("dpg load vector");
     if (space & DPG_FP32) { p.pp = te->pp32; le = launch_load<float>(p, g_num_sms, (cudaStream_t)stream); }
     else { p.pp = te->pp64; le = launch_load<double>(p, g_num_sms, (cudaStream_t)stream); }
     if (le != cudaSuccess) return cuda_fail(le, "load_kernel launch", __LINE__);
@@ -954,6 +1033,7 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
     p.n_elem = n_elem; p.elem_base = 0; p.n = n; p.m = m;
     p.G = G; p.B = B; p.l = l; p.K = K; p.F = F;
     p.status = ds->status;
+    TraceRange tr("dpg condensation");
     const cudaError_t le = launch_condense(p, g_num_sms, g_condense_method == DPG_CONDENSE_TC, (cudaStream_t)stream);
     if (le != cudaSuccess) return cuda_fail(le, "condense_kernel launch", __LINE__);
     return DPG_OK;
@@ -1005,6 +1085,7 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
             lp.coef_stride = coef_stride;
             lp.zeta = tg->zeta; lp.w = tg->w; lp.pp = tg->pp64;
             lp.out = l; lp.status = ds->status;
+            TraceRange tr("dpg load vector");
             const cudaError_t le = launch_load<double>(lp, g_num_sms, s);
             if (le != cudaSuccess) { rc = cuda_fail(le, "load_kernel launch", __LINE__); break; }
         }
@@ -1013,6 +1094,7 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
         cp.G = G; cp.B = B; cp.l = l;
         cp.K = K + (size_t)e0 * m * m; cp.F = with_l ? F + (size_t)e0 * m : nullptr;
         cp.status = ds->status;
+        TraceRange tr("dpg condensation");
         const cudaError_t le = launch_condense(cp, g_num_sms, g_condense_method == DPG_CONDENSE_TC, s);
         if (le != cudaSuccess) rc = cuda_fail(le, "condense_kernel launch", __LINE__);
     }
@@ -1031,6 +1113,13 @@ int dpg_condense_set_method(int method) {
 int dpg_test_stall_tc_once(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_tc_stall_once = 1;
+    return DPG_OK;
+}
+
+int dpg_test_set_workspace_limit(int64_t bytes) {
+    if (bytes < 0) return DPG_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_ws_limit_test = (size_t)bytes;
     return DPG_OK;
 }
 
@@ -1199,14 +1288,16 @@ double dpg_flops_per_element(int space, int p_trial, int q_test) {
 }
 
 int dpg_measure_fma_peak(int precision, void *stream, double *flops) {
-    if (!flops || (precision != 32 && precision != 64 && precision != 65)) return DPG_ERR_ARG;
+    if (!flops || (precision != 32 && precision != 64 && precision != 65 && precision != 19)) return DPG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int blocks = sms * 8;
+    const bool tc = precision == 19;
+    const int blocks = tc ? sms : sms * 8;
     void *buf = nullptr;
     CK(cudaMalloc(&buf, 256 * sizeof(double)));
+    CK(cudaMemset(buf, 0, 256 * sizeof(double)));
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
@@ -1214,8 +1305,9 @@ int dpg_measure_fma_peak(int precision, void *stream, double *flops) {
         CK(cudaEventRecord(a, s));
         cudaError_t e = precision == 64 ? launch_fma_peak<double>((double *)buf, blocks, iters, s)
                       : precision == 65 ? launch_dmma_peak((double *)buf, blocks, iters, s)
+                      : tc             ? launch_tc_tf32_peak(blocks, iters, (int *)buf, s)
                                         : launch_fma_peak<float>((float *)buf, blocks, iters, s);
-        if (e != cudaSuccess) return DPG_ERR_CUDA;
+        if (e != cudaSuccess) return cuda_fail(e, "peak probe launch", __LINE__);
         CK(cudaEventRecord(b, s));
         CK(cudaEventSynchronize(b));
         CK(cudaEventElapsedTime(ms, a, b));
@@ -1228,10 +1320,17 @@ int dpg_measure_fma_peak(int precision, void *stream, double *flops) {
     double best = 0.0;
     for (int rep = 0; rep < 5 && r == DPG_OK; ++rep) {
         r = run(iters, &ms);
-        // flops per thread and iteration: 8 chains x 16 FMAs x 2, or 8 mma x 512 / 32 lanes
-        const double per = precision == 65 ? 128.0 : 256.0;
-        const double f = per * (double)iters * 256.0 * blocks / (ms * 1e-3);
+        // flops per CTA-thread and iteration: 8 chains x 16 FMAs x 2, or 8 mma x 512 / 32
+        // lanes; the tensor-core probe: 2 products of 2 x 128 x 256 x 8 per CTA
+        const double f = tc ? 2.0 * 2.0 * 128 * 256 * 8 * (double)iters * blocks / (ms * 1e-3)
+                            : (precision == 65 ? 128.0 : 256.0) * (double)iters * 256.0 * blocks / (ms * 1e-3);
         if (f > best) best = f;
+    }
+    int st = 0;
+    if (r == DPG_OK && tc) {
+        cudaError_t e = cudaMemcpy(&st, buf, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) r = cuda_fail(e, "cudaMemcpy", __LINE__);
+        else if (st) r = DPG_ERR_TIMEOUT;
     }
     cudaEventDestroy(a); cudaEventDestroy(b); cudaFree(buf);
     if (r) return r;

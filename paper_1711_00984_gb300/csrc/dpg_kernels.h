@@ -210,6 +210,9 @@ cudaError_t init_condense_attributes();
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
 cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);
+// TF32 tensor-core (tcgen05 kind::tf32) rate probe: `ctas` CTAs (one per SM), each 2 iters
+// products of 128 x 256 x 8; *status (device) is set to 1 if a bounded wait ran out.
+cudaError_t launch_tc_tf32_peak(int ctas, int iters, int *status, cudaStream_t s);
 size_t affine_smem_values(const BlockDesc &b, int nj);
 int max_dynamic_smem(int optin_smem);
 

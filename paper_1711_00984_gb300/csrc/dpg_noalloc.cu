@@ -5,11 +5,9 @@
 
 #include <cuda_runtime.h>
 
-#include <climits>
 #include <map>
 #include <mutex>
 
-#include "dpg_kernels.h"
 #include "dpg_registry.h"
 
 namespace {
@@ -22,7 +20,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[DPG_NOALLOC_SCR
 std::mutex g_na_mu;
 std::map<int, void *> g_na_addr;   // device ordinal -> device address of g_noalloc_scratch
 
-// Set-up, once per device, with that device current.
+// Set-up, once per device, with that device current.  Under CUDA's lazy module loading
+// this is also where the module holding the array is loaded, i.e. where the device
+// memory of the array is reserved.
 int scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DPG_ERR_CUDA;
@@ -37,50 +37,16 @@ int scratch_address(void **out) {
     return DPG_OK;
 }
 
-template <typename T>
-int run(const dpg::ProgramView &v, int64_t n_elem, const double *verts, const double *coeffs, T *out,
-        void *ws, cudaStream_t s) {
-    const dpg::Program &pr = *v.prog;
-    const int L = pr.L;
-    dpg::GeomParams g;
-    g.space = pr.space; g.L = L; g.nfields = pr.nfields;
-    g.n_elem = n_elem; g.elem_base = 0;
-    g.verts = verts; g.coeffs = coeffs;
-    g.zeta = v.zeta; g.w = v.w;
-    g.fields = ws; g.status = v.status;
-    if (dpg::launch_geom<T>(g, s) != cudaSuccess) return DPG_ERR_CUDA;
-    dpg::SfParams<T> sp;
-    sp.blocks = v.d_blocks; sp.units = v.d_units; sp.nunits = (int)pr.units.size();
-    sp.L = L; sp.nfields = pr.nfields;
-    if constexpr (sizeof(T) == 8) sp.pp = v.pp64; else sp.pp = v.pp32;
-    sp.fields = reinterpret_cast<const T *>(ws);
-    sp.out = out;
-    sp.mat_stride = (int64_t)pr.parts * pr.rows * pr.cols;
-    sp.ld = pr.cols; sp.n_elem = n_elem;
-    if (dpg::launch_general<T>(sp, pr.smem_values * sizeof(T), s) != cudaSuccess) return DPG_ERR_CUDA;
-    return DPG_OK;
-}
-
 }  // namespace
 
 extern "C" int dpg_integrate_noalloc(int space, int p_trial, int q_test, int64_t n_elem,
                                      const double *vertices, const double *coeffs, void *out, void *stream) {
     if (space & (DPG_MAP_AFFINE | DPG_MAP_EXTRUDED | DPG_VEC3)) return DPG_ERR_ARG;
-    dpg::ProgramView v;
-    int r = dpg::lookup_program_view(space, p_trial, q_test, &v);
-    if (r) return r;
-    if (n_elem < 0) return DPG_ERR_ARG;
-    if (n_elem == 0) return DPG_OK;
-    if (!vertices || !out) return DPG_ERR_ARG;
-    const bool fp32 = (space & DPG_FP32) != 0;
-    const int L = v.prog->L;
-    const size_t per_elem = (size_t)v.prog->nfields * L * L * L * (fp32 ? sizeof(float) : sizeof(double));
-    if ((size_t)n_elem > DPG_NOALLOC_SCRATCH_BYTES / per_elem) return DPG_ERR_SCRATCH;
-    if ((int64_t)v.prog->units.size() * n_elem > INT_MAX) return DPG_ERR_SCRATCH;
     void *ws = nullptr;
-    if ((r = scratch_address(&ws))) return r;
-    const double *c = (space & 0xff) > DPG_L2 ? nullptr : coeffs;          // Gram matrices only
-    cudaStream_t s = (cudaStream_t)stream;
-    return fp32 ? run<float>(v, n_elem, vertices, c, (float *)out, ws, s)
-                : run<double>(v, n_elem, vertices, c, (double *)out, ws, s);
+    const int r = scratch_address(&ws);
+    if (r) return r;
+    // the same programs and kernels as dpg_integrate (FP64 and FP32 forms), the metric
+    // fields in the array; the size check comes before any launch or pointer use
+    return dpg::integrate_in_scratch(space, p_trial, q_test, n_elem, vertices, coeffs, out, ws,
+                                     DPG_NOALLOC_SCRATCH_BYTES, stream);
 }

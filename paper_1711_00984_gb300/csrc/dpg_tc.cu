@@ -567,6 +567,72 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
     if (failed && tid == 0) report_tc(p.status, 9 /*DPG_ERR_TIMEOUT*/, e0);
 }
 
+// --------------------------------------------------------------------------------------
+// TF32 tensor-core rate probe (not part of the method): the denominator of the roofline of
+// the 3xTF32 stages.  One CTA per SM (its dynamic shared memory admits no second CTA);
+// one thread issues `iters` rounds of two kind::tf32 products of 128 x 256 x 8 into two
+// accumulators of 256 tensor-memory columns each, completion through one mbarrier (a
+// bounded wait: a wait that runs out sets *status and the CTA still releases its tensor
+// memory).  Operands are K-major no-swizzle tiles of zeros.
+// --------------------------------------------------------------------------------------
+constexpr int TCP_SMEM = 160 * 1024;
+
+__global__ void __launch_bounds__(128, 1) tc_tf32_peak_kernel(int iters, int *status) {
+    extern __shared__ __align__(1024) unsigned char smb[];
+    __shared__ uint32_t tslot;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int fail;
+    float *sA = reinterpret_cast<float *>(smb);            // 128 rows x 8: 4 KB
+    float *sB = sA + 128 * 8;                              // 256 rows x 8: 8 KB
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < 384 * 8; i += 128) sA[i] = 0.0f;
+    if (tid == 0) {
+        fail = 0;
+        mbar_init(&bar, 1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(saddr(&tslot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tslot;
+    if (tid == 0) {
+        const uint32_t id = idesc_tf32(128, 256);
+        const uint64_t dA = sdesc(saddr(sA), 256), dB = sdesc(saddr(sB), 256);
+        for (int i = 0; i < iters; ++i) {
+            umma(tbase, dA, dB, id, i > 0 ? 1u : 0u);
+            umma(tbase + 256, dA, dB, id, i > 0 ? 1u : 0u);
+        }
+        umma_commit(&bar);
+    }
+    __syncwarp();
+    mbar_wait(&bar, 0u, &fail);
+    tc_fence_before();
+    const int failed = __syncthreads_or(fail);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(512));
+    }
+    if (failed && tid == 0) atomicExch(status, 1);
+}
+
+cudaError_t launch_tc_tf32_peak(int ctas, int iters, int *status, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute((const void *)tc_tf32_peak_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TCP_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    tc_tf32_peak_kernel<<<ctas, 128, TCP_SMEM, s>>>(iters, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tc_f32(const TcParams &p, size_t smem, cudaStream_t s) {
     if (p.n_elem == 0) return cudaSuccess;
     const int64_t chunks = (p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta;
