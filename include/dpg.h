@@ -113,8 +113,12 @@ typedef enum {
                                 call are not valid (first_bad = first element of the CTA) */
     DPG_ERR_NOT_EXTRUDED = 10, /* device: element is not an extrusion along x1
                                 (DPG_MAP_EXTRUDED)                                       */
-    DPG_ERR_NOT_SPD = 11     /* device: dpg_condense met a Gram matrix that is not positive
+    DPG_ERR_NOT_SPD = 11,    /* device: dpg_condense met a Gram matrix that is not positive
                                 definite (a pivot <= 0 or not finite)                    */
+    DPG_ERR_BOUNDS = 12      /* device, bounds-checked build (libdpg_debug.so) only: a
+                                kernel's shared- or global-memory index, metric-field
+                                index or tensor-memory column left the extent it was
+                                given; the access was skipped (first_bad = the element) */
 } dpg_status;
 
 #define DPG_MAX_Q 12           /* supported test orders: 1 <= q <= DPG_MAX_Q           */

@@ -26,7 +26,7 @@ SPACE_IDS = {"H1": DPG_H1, "HCURL": DPG_HCURL, "HDIV": DPG_HDIV, "L2": DPG_L2, "
 STATUS = {0: "DPG_OK", 1: "DPG_ERR_ARG", 2: "DPG_ERR_NOT_INIT", 3: "DPG_ERR_RANGE", 4: "DPG_ERR_CUDA",
           5: "DPG_ERR_DEGENERATE", 6: "DPG_ERR_NOT_AFFINE", 7: "DPG_ERR_NOMEM", 8: "DPG_ERR_SCRATCH",
           9: "DPG_ERR_TIMEOUT", 10: "DPG_ERR_NOT_EXTRUDED",
-          11: "DPG_ERR_NOT_SPD"}
+          11: "DPG_ERR_NOT_SPD", 12: "DPG_ERR_BOUNDS"}
 
 EXPORTS = ["dpg_tables_init", "dpg_tables_init_L", "dpg_tables_free", "dpg_matrix_rows",
            "dpg_matrix_cols", "dpg_integrate", "dpg_integrate_noalloc", "dpg_integrate_hp", "dpg_integrate_host", "dpg_sync_status",

@@ -491,7 +491,7 @@ int run_general_in(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_ele
             pp.pp = te->pp32;
             pp.fields = reinterpret_cast<const float *>(ws);
             pp.out = reinterpret_cast<float *>(out + e0 * mat);
-            pp.mat_stride = mat; pp.ld = og.ld; pp.n_elem = ne;
+            pp.mat_stride = mat; pp.ld = og.ld; pp.n_elem = ne; pp.status = ds->status;
             {
                 TraceRange tr("dpg contraction: general, FP32, row panels");
                 le = launch_panel_f32(pp, pr.smem_bytes, s);
@@ -511,7 +511,7 @@ int run_general_in(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_ele
             sp.pp = te->pp32;
             sp.fields = reinterpret_cast<const float *>(ws);
             sp.out = reinterpret_cast<float *>(out + e0 * mat);
-            sp.mat_stride = mat; sp.ld = og.ld; sp.n_elem = ne;
+            sp.mat_stride = mat; sp.ld = og.ld; sp.n_elem = ne; sp.status = ds->status;
             TraceRange tr("dpg contraction: general, FP32, mirrored tiles");
             le = launch_general_f32(sp, pr.smem_bytes, pe->max_nc1_32, s);
         } else {
@@ -522,7 +522,7 @@ int run_general_in(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_ele
             sp.pp = te->pp64;
             sp.fields = reinterpret_cast<const T *>(ws);
             sp.out = out + e0 * mat;
-            sp.mat_stride = mat; sp.ld = og.ld; sp.n_elem = ne;
+            sp.mat_stride = mat; sp.ld = og.ld; sp.n_elem = ne; sp.status = ds->status;
             TraceRange tr("dpg contraction: general, FP64");
             le = launch_general<T>(sp, pr.smem_values * sizeof(T), s);
         }
@@ -599,7 +599,7 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         if constexpr (sizeof(T) == 8) ap.F = te->F64; else ap.F = te->F32;
         ap.consts = (const double *)consts + AFF_CONST_STRIDE * e0;
         ap.out = out + e0 * mat;
-        ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne;
+        ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne; ap.status = ds->status;
         {
             TraceRange tr("dpg contraction: affine");
             le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
@@ -666,7 +666,7 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         ap.xfields = fields; ap.estatus = est;
         ap.L = L; ap.nfields = pr.nfields;
         ap.out = out + e0 * mat;
-        ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne;
+        ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne; ap.status = ds->status;
         {
             TraceRange tr("dpg contraction: extruded");
             le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
@@ -1272,6 +1272,7 @@ const char *dpg_strerror(int code) {
     case DPG_ERR_TIMEOUT: return "a bounded tensor-core wait ran out (the call's matrices are not valid)";
     case DPG_ERR_NOT_EXTRUDED: return "element is not an extrusion along x1";
     case DPG_ERR_NOT_SPD: return "Gram matrix is not positive definite";
+    case DPG_ERR_BOUNDS: return "a kernel index left its extent (bounds-checked build)";
     }
     return "unknown status";
 }

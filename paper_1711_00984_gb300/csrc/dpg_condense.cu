@@ -134,6 +134,9 @@ __global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParam
     __shared__ int sbad;
     const int n = p.n, m = p.m, mc = m + (p.l ? 1 : 0);
     const int tid = threadIdx.x;
+#if defined(DPG_DEBUG_BOUNDS)
+    if (!DPG_INB((EMU ? EM_SMEM : CD_SMEM) <= dpg_dyn_smem_bytes(), p.status, p.elem_base)) return;   // uniform
+#endif
     const int warp = tid >> 5, lane = tid & 31;   // phase 2: warp -> 4 columns, lane -> 2 rows
     for (int64_t e = blockIdx.x; e < p.n_elem; e += gridDim.x) {
         double *G = p.G + (size_t)e * n * n;
@@ -543,6 +546,7 @@ __global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParam
                         for (int i = 0; i < 4; ++i) {
                             const int r = rb + g + 8 * (i >> 1), c = cb + 8 * nt2 + 2 * tq + (i & 1);
                             if (r >= rows_v || c >= cols_v || (diag && c > r)) continue;
+                            if (!DPG_INB(ci0 + r < m && cj0 + c < m, p.status, p.elem_base + e)) continue;
                             K[(size_t)(ci0 + r) * m + cj0 + c] = out[4 * nt2 + i];
                             K[(size_t)(cj0 + c) * m + ci0 + r] = out[4 * nt2 + i];
                         }
@@ -566,6 +570,7 @@ __global__ void __launch_bounds__(CD_NTH, EMU ? 2 : 3) condense_kernel(CondParam
             for (int k = 0; k < 16; ++k) {
                 if (!sp.ok(k)) continue;
                 const int ci = ci0 + sp.rw + 4 * k, cj = cj0 + sp.c;
+                if (!DPG_INB(ci < m && cj < m, p.status, p.elem_base + e)) continue;
                 K[(size_t)ci * m + cj] = acc[k];
                 K[(size_t)cj * m + ci] = acc[k];
             }

@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(256) geom_kernel(GeomParams p) {
     TF *dst = reinterpret_cast<TF *>(p.fields) + (e * p.nfields) * L3 + pt;
     const bool bad = !(g.det > 0.0) || !isfinite(g.det);
     if (bad) report(p.status, 5 /*DPG_ERR_DEGENERATE*/, p.elem_base + e);
-    for (int k = 0; k < nf; ++k) dst[(int64_t)k * L3] = bad ? qnan<TF>() : (TF)f[k];
+    const int nfw = DPG_INB(nf <= p.nfields, p.status, p.elem_base + e) ? nf : 0;
+    for (int k = 0; k < nfw; ++k) dst[(int64_t)k * L3] = bad ? qnan<TF>() : (TF)f[k];
 }
 
 // Extruded elements (the second map of Eq. 2.89): one thread per (element, xi2 point m, xi3
@@ -211,7 +212,8 @@ __global__ void __launch_bounds__(256) geom2d_kernel(Geom2dParams p) {
     double f[MAXFIELDS];
     const int nf = metric_fields(p.space, g, wt, c0, c1, f);
     TF *dst = reinterpret_cast<TF *>(p.fields) + (e * p.nfields) * L2 + pt;
-    for (int k = 0; k < nf; ++k) dst[(int64_t)k * L2] = flag ? qnan<TF>() : (TF)f[k];
+    const int nfw = DPG_INB(nf <= p.nfields, p.status, p.elem_base + e) ? nf : 0;
+    for (int k = 0; k < nfw; ++k) dst[(int64_t)k * L2] = flag ? qnan<TF>() : (TF)f[k];
     if (flag) {
         atomicMax(&p.estatus[e], flag);
         report(p.status, flag, p.elem_base + e);
@@ -233,9 +235,12 @@ __device__ __forceinline__ void load_block(const BlockDesc *src, BlockDesc &dst)
 // One work unit (block bd, stage-A index u.i3, partners u.j3b .. +u.nj) of one element:
 // fe = the element's metric fields, o = its output matrix (leading dimension ld).  All
 // threads of the CTA take part; bd must be in shared memory and visible to every thread.
+// st, elem, mat_size (values from o to the end of the element's matrix) and nfields serve
+// the bounds-checked build only.
 template <typename T>
 __device__ void sf_unit(const BlockDesc &bd, const Unit u, const T *__restrict__ fe, T *__restrict__ o,
-                        const T *__restrict__ pp, int L, int64_t ld, unsigned char *smem_raw) {
+                        const T *__restrict__ pp, int L, int64_t ld, unsigned char *smem_raw, DevStatus *st,
+                        long long elem, int64_t mat_size, int nfields) {
     const int tid = threadIdx.x, nth = blockDim.x;
     const int L2 = L * L;
     const int dC = bd.dir[0], dB = bd.dir[1], dA = bd.dir[2];
@@ -250,6 +255,15 @@ __device__ void sf_unit(const BlockDesc &bd, const Unit u, const T *__restrict__
     T *P3 = P2 + r4((size_t)np2 * n22 * L);                          // [nterm][nj][L]
     T *A = P3 + r4((size_t)nterm * nj * L);                          // [nh][L][L][nj]
     T *Bs = A + r4((size_t)nh * L2 * nj);                            // [ng][L][nr2][nc2][nj]
+#if defined(DPG_DEBUG_BOUNDS)
+    {
+        bool ok = (size_t)(Bs + (size_t)ng * L * n22 * nj - P1) * sizeof(T) <= dpg_dyn_smem_bytes();
+        for (int t = 0; t < nterm; ++t) ok = ok && bd.term[t].field >= 0 && bd.term[t].field < nfields;
+        if (!DPG_INB(ok, st, elem)) return;             // uniform over the CTA
+    }
+#else
+    (void)st; (void)elem; (void)mat_size; (void)nfields;
+#endif
 
     auto PP = [&](int pair, int i, int j) -> const T * {
         return pp + (((size_t)pair * NQ1 + i) * NQ1 + j) * L;
@@ -358,6 +372,7 @@ __device__ void sf_unit(const BlockDesc &bd, const Unit u, const T *__restrict__
         }
         const int64_t R = R0 + (int64_t)i1 * srC + (int64_t)i2 * srB;
         const int64_t C = C0 + (int64_t)j1 * scC + (int64_t)j2 * scB + (int64_t)jj * scA;
+        if (!DPG_INB(R * ld + C < mat_size && C * ld + R < mat_size, st, elem)) continue;
         o[R * ld + C] = acc;
         if (mirror_all || (mirror_off && R != C)) o[C * ld + R] = acc;
     }
@@ -377,7 +392,7 @@ __global__ void __launch_bounds__(256) sf_general_kernel(SfParams<T> p) {
     __syncthreads();
     const int L3 = p.L * p.L * p.L;
     sf_unit<T>(bd, u, p.fields + (size_t)e * p.nfields * L3, p.out + (size_t)e * p.mat_stride + bd.base, p.pp,
-               p.L, p.ld, smem_raw);
+               p.L, p.ld, smem_raw, p.status, e, p.mat_stride - bd.base, p.nfields);
 }
 
 
@@ -419,6 +434,10 @@ __global__ void __launch_bounds__(256, 2) sf_general_f32_kernel(SfParams32 p) {
     const int ng = bd.ng, nh = bd.nh, np2 = bd.np2, nterm = bd.nterm;
     const int nc1p = f.nc1p, n22 = f.n22, n22p = f.n22p, nx4 = f.nx4, ldt = f.ldt;
     float *P1 = sm + f.oP1, *P2 = sm + f.oP2, *P3 = sm + f.oP3, *A = sm + f.oA, *Bs = sm + f.oB, *tile = sm + f.oT;
+#if defined(DPG_DEBUG_BOUNDS)
+    if (!DPG_INB((size_t)f.total * 4 <= dpg_dyn_smem_bytes() && p.nj_max * nc2 <= F32_NXMAX && f.n22 <= F32_NIJMAX,
+                 p.status, e0)) return;                                 // uniform
+#endif
     const unsigned mL = div_magic(L), mL2 = div_magic(L2), mnc1p = div_magic(nc1p), mnc2 = div_magic(nc2),
                    mnr1 = div_magic(nr1), mnr2 = div_magic(nr2), mn22p = div_magic(n22p);
     auto stride = [](int d, int n0, int n1) { return d == 0 ? 1 : (d == 1 ? n0 : n0 * n1); };
@@ -584,7 +603,10 @@ __global__ void __launch_bounds__(256, 2) sf_general_f32_kernel(SfParams32 p) {
             const int64_t R0 = bd.row_off + (int64_t)i3 * nrow;
             const int64_t C0 = bd.col_off + (int64_t)j3b * mc;
             const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
+            const int64_t msz = p.mat_stride - bd.base;
+            (void)msz;
             for (int row = warp; row < nrow; row += nwarp) {
+                if (!DPG_INB((R0 + row) * ld + C0 + nj * mc <= msz, p.status, e)) continue;
                 float *orow = o + (R0 + row) * ld + C0;
                 const float *trw = tile + row * ldt;
                 for (int jj = 0; jj < nj; ++jj) {
@@ -597,6 +619,7 @@ __global__ void __launch_bounds__(256, 2) sf_general_f32_kernel(SfParams32 p) {
                     for (int cj = warp; cj < mc; cj += nwarp) {
                         const int c = jj * mc + cj;
                         const int rend = jj == jd ? cj : nrow;          // strictly upper rows
+                        if (!DPG_INB((C0 + c) * ld + R0 + rend <= msz, p.status, e)) continue;
                         float *orow = o + (C0 + c) * ld + R0;
                         for (int row = lane; row < rend; row += 32) orow[row] = tile[row * ldt + c];
                     }
@@ -785,9 +808,13 @@ __device__ __forceinline__ void panel_stage_c(const float *__restrict__ sm, floa
 // coalesced run of its output row.
 __device__ __forceinline__ void panel_write_tile(const float *__restrict__ tile, const PanelLayout &f,
                                                  const BlockDesc &bd, float *__restrict__ o, int64_t ld,
-                                                 int i3, int j3b, int ncol, int warp, int nwarp, int lane) {
-    float *base = o + (bd.row_off + (int64_t)i3 * f.nrow) * ld + bd.col_off + (int64_t)j3b * f.nc1 * f.nc2;
+                                                 int i3, int j3b, int ncol, int warp, int nwarp, int lane,
+                                                 DevStatus *st, long long elem, int64_t mat_size) {
+    const int64_t off0 = (bd.row_off + (int64_t)i3 * f.nrow) * ld + bd.col_off + (int64_t)j3b * f.nc1 * f.nc2;
+    float *base = o + off0;
+    (void)st; (void)elem; (void)mat_size;
     for (int row = warp; row < f.nrow; row += nwarp) {
+        if (!DPG_INB(off0 + row * ld + ncol <= mat_size && ncol <= f.ldt, st, elem)) continue;
         float *orow = base + row * ld;
         const float *trow = tile + row * f.ldt;
 #pragma unroll 4
@@ -830,6 +857,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) sf_panel_f32_kernel(
         }
     }
     __syncthreads();
+#if defined(DPG_DEBUG_BOUNDS)
+    if (!DPG_INB((size_t)f.total * 4 <= dpg_dyn_smem_bytes(), p.status, e0)) return;   // uniform
+#endif
     if (tid < 2) {
         const int nA = bd.nc[2], rem = nA % p.nj_max;
         sched[tid] = panel_sched(f, bd, tid == 0 ? min(p.nj_max, nA) : (rem ? rem : p.nj_max), NW);
@@ -876,6 +906,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) sf_panel_f32_kernel(
     // the previous unit, whose tile is written out during the next unit's stage A
     float *prev_o = nullptr;
     int prev_i3 = 0, prev_j3b = 0, prev_s = 0;
+    int64_t prev_e = e0;
     for (int64_t e = e0; e < e1; ++e) {
         const float *fe = p.fields + (size_t)e * p.nfields * L3;
         float *o = p.out + (size_t)e * p.mat_stride + bd.base;
@@ -889,7 +920,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) sf_panel_f32_kernel(
             // ---- phase 1: write-out of the previous tile; stage A; tile rows of this unit
             if (prev_o) {
                 const PanelSched &ps = sched[prev_s];
-                panel_write_tile(tile, f, bd, prev_o, ld, prev_i3, prev_j3b, ps.ncol, warp, NW, lane);
+                panel_write_tile(tile, f, bd, prev_o, ld, prev_i3, prev_j3b, ps.ncol, warp, NW, lane, p.status,
+                                 prev_e, p.mat_stride - bd.base);
             }
             for (int it = tid; it < bd.nh << (2 * lsh); it += nth) {
                 const int l = it & (lpad - 1), m = (it >> lsh) & (lpad - 1), h = it >> (2 * lsh);
@@ -984,12 +1016,13 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) sf_panel_f32_kernel(
                 }
             }
             __syncthreads();
-            prev_o = o; prev_i3 = u.i3; prev_j3b = u.j3b; prev_s = si;
+            prev_o = o; prev_i3 = u.i3; prev_j3b = u.j3b; prev_s = si; prev_e = e;
         }
     }
     {
         const PanelSched &ps = sched[prev_s];
-        panel_write_tile(tile, f, bd, prev_o, ld, prev_i3, prev_j3b, ps.ncol, warp, NW, lane);
+        panel_write_tile(tile, f, bd, prev_o, ld, prev_i3, prev_j3b, ps.ncol, warp, NW, lane, p.status, prev_e,
+                         p.mat_stride - bd.base);
     }
 }
 
@@ -1131,6 +1164,15 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
     const int64_t ld = p.ld;
     const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
     const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
+    const int64_t msz = p.mat_stride - bd.base;                       // values from o to the matrix end
+    (void)msz;
+#if defined(DPG_DEBUG_BOUNDS)
+    {
+        const size_t need = (EXT ? (size_t)ext_layout(bd, L, njm).total : (size_t)lay.total) * sizeof(T);
+        const size_t img = (size_t)(p.img_off16[k + 1] - p.img_off16[k]) * 16;
+        if (!DPG_INB(need <= dpg_dyn_smem_bytes() && img <= (size_t)lay.oC * sizeof(T), p.status, e0)) return;
+    }
+#endif
     for (int64_t e = e0; e < e1; ++e) {                               // the CTA's chunk of elements
     __syncthreads();                                                  // previous element done
     if constexpr (!EXT) {                                             // the element's constants
@@ -1240,6 +1282,7 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
                 const T fv = f1v[g * n11 + a];
                 T *trow = tile + f1i[g * n11 + a];
                 for (int b = lane; b < nq; b += 32) {
+                    if (!DPG_INB((unsigned)(f1i[g * n11 + a] + qig[b]) < (unsigned)(nrow * ldt), p.status, e)) continue;
                     T *dst = trow + qig[b];
                     *dst = fma(fv, qvg[b], *dst);
                 }
@@ -1258,6 +1301,7 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         constexpr int VW = 16 / (int)sizeof(T);
         using V16 = typename Vec16<T>::type;
         for (int row = warp; row < nrow; row += nwarp) {
+            if (!DPG_INB((R0 + row) * ld + C0 + ncolu <= msz, p.status, e)) continue;
             T *orow = o + (R0 + row) * ld + C0;
             const T *trw = tile + row * ldt;
             auto val = [&](int c) -> T {
@@ -1284,6 +1328,7 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             // a run of nrow values at column R0; (column, row) pairs flattened over the CTA
             const int nmc = jd >= 0 ? ncolu - ncj : ncolu;
             T *mbase = o + C0 * ld + R0;
+            if (!DPG_INB((C0 + ncolu - 1) * ld + R0 + nrow <= msz, p.status, e)) continue;
             if (nrow >= 64) {                                   // long runs: a warp per column
                 // (plain stores: lanes reading consecutive tile rows keep the shared-memory
                 // reads conflict-free, which measured faster than 16-byte stores here)
@@ -1448,7 +1493,8 @@ __global__ void __launch_bounds__(256) hp_geom_kernel(HpParams p) {
         const int nf = metric_fields(p.space, jg, g.w[l] * g.w[m] * g.w[n], c0, c1, f);
         const bool bad = !(jg.det > 0.0) || !isfinite(jg.det);
         if (bad) report(p.status, 5 /*DPG_ERR_DEGENERATE*/, e);
-        for (int k = 0; k < nf; ++k) dst0[(int64_t)k * L3 + pt] = bad ? qnan<TF>() : (TF)f[k];
+        const int nfw = DPG_INB(nf <= g.nfields, p.status, e) ? nf : 0;
+        for (int k = 0; k < nfw; ++k) dst0[(int64_t)k * L3 + pt] = bad ? qnan<TF>() : (TF)f[k];
     }
 }
 
@@ -1466,12 +1512,16 @@ __global__ void __launch_bounds__(256) hp_contract_kernel(HpParams p) {
         const int k = p.item_k[item];
         const int e = p.order[k];
         const HpProg &g = p.tab[p.q_elem[e]];
-        const Unit u = g.units[item - p.uoff[k]];
+        const int64_t ui = item - p.uoff[k];
+        const bool uok = DPG_INB(ui >= 0 && ui < g.nunits, p.status, e);
+        const Unit u = g.units[uok ? ui : 0];
         load_block(g.blocks + u.block, bd);
         __syncthreads();
-        sf_unit<T>(bd, u, reinterpret_cast<const T *>(p.fields) + p.foff[e],
-                   reinterpret_cast<T *>(p.out) + p.out_offset[e] + bd.base,
-                   reinterpret_cast<const T *>(g.pp), g.L, g.cols, smem_raw);
+        if (uok)
+            sf_unit<T>(bd, u, reinterpret_cast<const T *>(p.fields) + p.foff[e],
+                       reinterpret_cast<T *>(p.out) + p.out_offset[e] + bd.base,
+                       reinterpret_cast<const T *>(g.pp), g.L, g.cols, smem_raw, p.status, e,
+                       (int64_t)g.cols * g.cols - bd.base, g.nfields);
         __syncthreads();
     }
 }
@@ -1706,6 +1756,10 @@ __global__ void __launch_bounds__(LOAD_NTH) load_kernel(LoadParams p) {
     const int r0 = nc * L3 > nc * L * n * n ? nc * L3 : nc * L * n * n;
     T *t1 = wf + r0;                                           // [nc][L^2][n]
     const T *pp = static_cast<const T *>(p.pp);
+#if defined(DPG_DEBUG_BOUNDS)
+    if (!DPG_INB((size_t)(t1 + (size_t)nc * L2 * n - phi) * sizeof(T) <= dpg_dyn_smem_bytes(), p.status, p.elem_base))
+        return;                                                // uniform
+#endif
     // f_k(i, l) = pp[pair (k, nu)][i][j = 0][l] since nu_0 = P_0 = 1
     for (int t = threadIdx.x; t < 2 * n * L; t += LOAD_NTH) {
         const int k = t / (n * L), i = (t / L) % n, l = t % L;
@@ -1826,6 +1880,7 @@ __global__ void __launch_bounds__(LOAD_NTH) load_kernel(LoadParams p) {
                 const int i1 = it % n1, i2 = (it / n1) % n2, i3 = it / (n1 * n2);
                 T s = 0;
                 for (int l = 0; l < L; ++l) s += src[(l * n + i2) * n + i3] * f1[i1 * L + l];
+                if (!DPG_INB(off + it < rows && e < p.n_elem, p.status, p.elem_base + e)) continue;
                 out[e * rows + off + it] = sbad ? qnan<T>() : s;
             }
             off += na;

@@ -14,6 +14,34 @@ struct DevStatus {
     unsigned long long first_bad[16];
 };
 
+// Bounds-checked build (nvcc -DDPG_DEBUG_BOUNDS, libdpg_debug.so): every kernel checks its
+// global-memory store indices against the extents of the buffer it writes, its metric-field
+// reads against the element's fields, and its shared-memory layout (and tensor-memory
+// columns) against what the launch provides; a failed check records DPG_ERR_BOUNDS (12)
+// with the element index in the status word and skips the access (or the work unit) --
+// nothing traps.  In the normal build every check is the constant `true`.
+constexpr int DPG_STATUS_BOUNDS = 12;
+#if defined(__CUDACC__)
+#if defined(DPG_DEBUG_BOUNDS)
+__device__ __forceinline__ bool dpg_in_bounds(bool ok, DevStatus *st, long long elem) {
+    if (!ok && st) {
+        atomicCAS(&st->code, 0, DPG_STATUS_BOUNDS);
+        atomicMin(&st->first_bad[DPG_STATUS_BOUNDS], (unsigned long long)(elem < 0 ? 0 : elem));
+    }
+    return ok;
+}
+#define DPG_INB(cond, st, elem) ::dpg::dpg_in_bounds((cond), (st), (long long)(elem))
+#else
+#define DPG_INB(cond, st, elem) true
+#endif
+// bytes of dynamic shared memory of the running launch
+__device__ __forceinline__ unsigned dpg_dyn_smem_bytes() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+#endif
+
 struct GeomParams {
     int space, L, nfields;
     int64_t n_elem;            // elements of this chunk
@@ -37,6 +65,7 @@ struct SfParams {
     int64_t mat_stride;        // values per element (parts * rows * cols)
     int64_t ld;                // columns
     int64_t n_elem;
+    DevStatus *status;         // bounds-checked build only
 };
 
 // Per-element constants of the affine path: up to MAXFIELDS metric fields and the
@@ -62,6 +91,7 @@ struct SfParams32 {
     const float *fields;           // [n_elem][nfields][L^3]
     float *out;
     int64_t mat_stride, ld, n_elem;
+    DevStatus *status;             // bounds-checked build only
 };
 
 // FP32 row-panel kernel: one CTA per (block, chunk of elements).
@@ -77,6 +107,7 @@ struct PanelParams {
     const float *fields;           // [n_elem][nfields][L^3]
     float *out;
     int64_t mat_stride, ld, n_elem;
+    DevStatus *status;             // bounds-checked build only
 };
 
 // FP32 tensor-core kernel (tcgen05): one CTA per (block, chunk of elements).
@@ -116,6 +147,7 @@ struct AffParams {
     int L, nfields;
     T *out;
     int64_t mat_stride, ld, n_elem;
+    DevStatus *status;         // bounds-checked build only
 };
 
 // Geometry of extruded elements: metric fields at the (xi2, xi3) Gauss points.

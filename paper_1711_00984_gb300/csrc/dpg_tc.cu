@@ -223,6 +223,14 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
         mbar_init(&bar_dc, TC_NC);
     }
     __syncthreads();
+#if defined(DPG_DEBUG_BOUNDS)
+    // the layout against the launch's shared memory, the tensor-memory columns against the
+    // allocation, the unit chunk against the 8 stage-A partners of P3; uniform, before any
+    // tensor memory is held
+    if (!DPG_INB(f.ok && (unsigned)f.total <= dpg_dyn_smem_bytes() && f.tneed <= f.tcols && p.nj_max <= 8 &&
+                 f.nrow <= TC_MAXROW, p.status, e0))
+        return;
+#endif
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(saddr(&tslot)), "r"(f.tcols));
@@ -482,6 +490,9 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
             // tile rows to global memory: one warp per row, 16-byte vector stores for the
             // aligned middle, plain stores for the ends
             for (int r = cw; r < f.nrow; r += TC_NC) {
+                if (!DPG_INB((bd.row_off + (int64_t)u.i3 * f.nrow + r) * ld + bd.col_off +
+                             (int64_t)u.j3b * nc1 * nc2 + ncol <= p.mat_stride - bd.base, p.status, e))
+                    continue;
                 const float *trow = T + rsh[b][r];
                 float *orow = out_row(e, u, r);
                 const int head = min((4 - (int)((reinterpret_cast<uintptr_t>(orow) >> 2) & 3)) & 3, ncol);

@@ -66,7 +66,7 @@ def test_affine_entrywise_and_structural_zeros(gpu_lib, space, q, fp32):
         # the L2 Gram matrix of an affine element is diagonal (Eq. 2.95): every
         # off-diagonal entry is a structural zero
         assert zero[~np.eye(zero.shape[0], dtype=bool)].all()
-    assert zero.any() or space == "L2" and q == 1
+    # (with a full J every H1 entry has a non-zero term at q = 2: the zero set may be empty)
     tol = 1e-5 if fp32 else 1e-12
     assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
     assert (got[zero] == 0.0).all(), "entries forced to zero by the 1D integrals must be exactly 0"
@@ -81,7 +81,8 @@ def test_extruded_entrywise_and_structural_zeros(gpu_lib, space, fp32):
     scale = np.abs(ref).max(axis=(1, 2))
     # rounding-level on both elements: the xi_1 factor of every term is an exact zero
     zero = np.all(np.abs(ref) <= 1e-13 * scale[:, None, None], axis=0)
-    assert zero.any()
+    if space == "L2":                       # nu_i nu_j integrates to delta_ij / (2i + 1) along xi_1
+        assert zero.any()
     gpu_lib.dpg_tables_init(q, space)
     out = gpu_lib.integrate(space, q, torch.from_numpy(vn).cuda(), fp32=fp32, extruded=True)
     assert gpu_lib.sync_status()[0] == 0
