@@ -223,6 +223,44 @@ def affine_gram(space: str, q: int, J, c0=Fraction(1), c1=Fraction(1)):
     return G
 
 
+def _prod_dirs(kr, ir, kc, ic, dirs):
+    v = Fraction(1)
+    for d in dirs:
+        v *= F(kr[d], kc[d], ir[d], ic[d])
+    return v
+
+
+def affine_support(space: str, q: int, dirs=(0, 1, 2)):
+    """Boolean matrix: True where at least one term of the affine Gram matrix of `space` has
+    a non-zero product of exact 1D integrals F (Eq. 2.90) over the directions `dirs`, i.e.
+    where the entry is not forced to zero by the zeros of F whatever the metric (all three
+    directions: affine elements; dirs = (0,): elements extruded along x1, whose xi_1
+    factors are exact integrals); the terms are those of affine_gram."""
+    _prod = lambda kr, ir, kc, ic: _prod_dirs(kr, ir, kc, ic, dirs)  # noqa: E731
+    dl = dofs(space, q)
+    n = len(dl)
+    S = [[False] * n for _ in range(n)]
+    for I, ca, ir, ka in dl:
+        for Jd, cb, jc, kb in dl:
+            prods = []
+            if space in ("L2", "H1", "HDIV", "HCURL"):
+                prods.append(_prod(ka, ir, kb, jc))
+            if space == "H1":
+                for _, _, kra in _terms_scalar_grad(0, ka):
+                    for _, _, krb in _terms_scalar_grad(0, kb):
+                        prods.append(_prod(kra, ir, krb, jc))
+            elif space == "HDIV":
+                kda = tuple("D" if d == ca else ka[d] for d in range(3))
+                kdb = tuple("D" if d == cb else kb[d] for d in range(3))
+                prods.append(_prod(kda, ir, kdb, jc))
+            elif space == "HCURL":
+                for _, _, kra in _curl_terms(ca, ka):
+                    for _, _, krb in _curl_terms(cb, kb):
+                        prods.append(_prod(kra, ir, krb, jc))
+            S[I][Jd] = any(x != 0 for x in prods)
+    return S
+
+
 def affine_mixed_b(q: int, p: int, J, split: bool = False):
     """Exact B (n_test x 3p^3): B_IK = int u^_K.J^-T psi^_I + u^_K.J curl^psi^_I / |J| (affine)."""
     J = [[Fraction(x) for x in row] for row in J]

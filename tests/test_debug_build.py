@@ -90,11 +90,11 @@ for s in ("H1", "HCURL", "HDIV", "L2"):
         off = np.zeros(5, dtype=np.int64); off[1:] = np.cumsum(dims * dims)[:-1]
         out = torch.empty(int((dims * dims).sum()), dtype=torch.float32 if f32 else torch.float64, device="cuda")
         sh = int(torch.cuda.current_stream().cuda_stream)
-        code = dpg.dpg_integrate_hp(dpg.space_id(s, fp32=f32), 5, torch.from_numpy(vj).cuda().data_ptr(), 0,
-                                    torch.from_numpy(qe).cuda().data_ptr(), torch.from_numpy(off).cuda().data_ptr(),
+        vt, qt, ot = torch.from_numpy(vj).cuda(), torch.from_numpy(qe).cuda(), torch.from_numpy(off).cuda()
+        code = dpg.dpg_integrate_hp(dpg.space_id(s, fp32=f32), 5, vt.data_ptr(), 0, qt.data_ptr(), ot.data_ptr(),
                                     out.data_ptr(), sh)
         assert code == 0
-        torch.cuda.synchronize()
+        torch.cuda.synchronize()                 # the inputs stay referenced until the graph ran
         for e in range(5):
             q = int(qe[e]); n = int(dims[e])
             ref, _ = oracle.gram(s, q, q + 2, vj[e:e + 1])

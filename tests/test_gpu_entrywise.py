@@ -5,11 +5,11 @@ The affine and extruded-map kernels skip the exact zeros of the 1D integral tabl
 could hide under the Frobenius norm of the whole matrix.  Here:
   * affine elements with a dyadic Jacobian (every value exact in binary) against the exact
     rational Gram matrix (Sec. 2.8.1 with a full constant J): every entry within
-    1e-12 max|G| (FP64), and exactly 0.0 wherever the exact matrix is zero for two
-    unrelated Jacobians and coefficient pairs (zeros forced by F, not by the geometry);
+    1e-12 max|G| (FP64), and exactly 0.0 wherever every term's product of exact 1D
+    integrals has a zero factor (zeros forced by F, not by the geometry; entries that
+    vanish only by cancellation between terms are held to the tolerance, not to 0.0);
   * extruded elements against the oracle: every entry within 1e-12 max|G|, exactly 0.0
-    wherever the oracle's value is at rounding level on two unrelated elements (the
-    zeros of the exact xi_1 integrals F1);
+    wherever the exact xi_1 integral F1 of every term is zero;
   * the FP32 forms: every entry within 1e-5 max|G| (the structural zeros exact as well).
 """
 from fractions import Fraction as Fr
@@ -44,10 +44,15 @@ def _to_np(G):
 
 
 def _structural_zeros(space, q):
+    """Entries where every term's product of exact 1D integrals has a zero factor (whatever
+    the metric), and the exact Gram matrix of the element with Jacobian J_A."""
+    support = np.array(exact.affine_support(space, q))
     A = exact.affine_gram(space, q, J_A, *C_A)
     B = exact.affine_gram(space, q, J_B, *C_B)
-    n = len(A)
-    return np.array([[A[i][j] == 0 and B[i][j] == 0 for j in range(n)] for i in range(n)]), _to_np(A)
+    zero = ~support
+    # a structural zero is zero in exact arithmetic for any Jacobian
+    assert all(A[i][j] == 0 and B[i][j] == 0 for i, j in zip(*np.nonzero(zero)))
+    return zero, _to_np(A)
 
 
 @pytest.mark.parametrize("space", ["H1", "HCURL", "HDIV", "L2"])
@@ -79,8 +84,9 @@ def test_extruded_entrywise_and_structural_zeros(gpu_lib, space, fp32):
     vn = meshgen.extruded_prisms(3, seed=94, jitter=0.2)[[4, 21]].copy()
     ref, _ = oracle.gram(space, q, L, vn)
     scale = np.abs(ref).max(axis=(1, 2))
-    # rounding-level on both elements: the xi_1 factor of every term is an exact zero
-    zero = np.all(np.abs(ref) <= 1e-13 * scale[:, None, None], axis=0)
+    # the xi_1 factor (an exact integral F1) of every term is zero there
+    zero = ~np.array(exact.affine_support(space, q, dirs=(0,)))
+    assert np.all(np.abs(ref[:, zero]) <= 1e-13 * scale[:, None])     # the oracle agrees
     if space == "L2":                       # nu_i nu_j integrates to delta_ij / (2i + 1) along xi_1
         assert zero.any()
     gpu_lib.dpg_tables_init(q, space)
