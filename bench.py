@@ -621,15 +621,16 @@ def config2_record(args, dpg, pk, flush, stream, sh, dev):
     rec["roofline"] = {"kernel": "sf_general_kernel<double> (H(curl), with its geom_kernel launch)",
                        "bound": "alu", "frac": hc["roofline_frac"], "achieved_tflops": hc["tflops"],
                        "peak_tflops": pk["fp64_dfma"] / 1e12, "flops_per_launch": hc["flops"], "launch_ms": hc["ms"]}
-    aff_bytes = sum(c["fp64"]["bytes"] for c in rec["calls"] if c["map"] == "affine")
-    aff_ms = sum(c["fp64"]["ms"] for c in rec["calls"] if c["map"] == "affine")
-    rec["affine_fp64"] = {"bytes": aff_bytes, "ms": aff_ms, "gbs": aff_bytes / (aff_ms * 1e-3) / 1e9,
-                          "frac_of_hbm": aff_bytes / (aff_ms * 1e-3) / pk["hbm"]}
-    if not args.no_fp32:
-        b32 = sum(c["fp32"]["bytes"] for c in rec["calls"] if c["map"] == "affine")
-        m32 = sum(c["fp32"]["ms"] for c in rec["calls"] if c["map"] == "affine")
-        rec["affine_fp32"] = {"bytes": b32, "ms": m32, "gbs": b32 / (m32 * 1e-3) / 1e9,
-                              "frac_of_hbm": b32 / (m32 * 1e-3) / pk["hbm"]}
+    for form in (["fp64"] if args.no_fp32 else ["fp64", "fp32"]):
+        calls = [c[form] for c in rec["calls"] if c["map"] == "affine"]
+        nbytes = sum(c["bytes"] for c in calls)
+        ms = sum(c["ms"] for c in calls)
+        roof_ms = sum(c["roofline_frac"] * c["ms"] for c in calls)     # sum of max(t_alu, t_mem)
+        rec["affine_" + form] = {"bytes": nbytes, "ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9,
+                                 "roofline_ms": roof_ms, "roofline_frac": roof_ms / ms,
+                                 "hbm_only_frac": nbytes / (ms * 1e-3) / pk["hbm"],
+                                 "note": "roofline: per call the slower of its FP64 (or FP32) FMA time for the "
+                                         "algorithmic non-zero products and its output-write time, summed"}
     if not args.no_cpu:
         n = host_cores()
         cnt, t = oracle_sample(n)

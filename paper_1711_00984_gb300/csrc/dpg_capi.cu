@@ -25,9 +25,11 @@ using namespace dpg;
 namespace {
 
 constexpr size_t kWorkspaceLimit = size_t(512) << 20;   // metric fields per launch chunk
-enum { K32_MIRROR = 0, K32_PANEL = 1, K32_TC = 2 };      // FP32 general-path kernels
+enum { K32_MIRROR = 0, K32_PANEL = 1, K32_TC = 2, K32_TCC = 3 };   // FP32 general-path kernels
 int g_max_dyn_smem = 0;                                  // per launch, set at device set-up
 int g_max_dyn_smem_tc = 0;                               // the same for the tensor-core kernel
+int g_max_dyn_smem_tcc = 0;                              // and for the stage-C tensor-core kernel
+int g_smem_per_sm = 0;                                   // shared memory of an SM
 int g_tc_stall_once = 0;                                 // test hook, see dpg_test_stall_tc_once
 int g_num_sms = 152;                                     // set at device set-up
 int g_condense_method = DPG_CONDENSE_TC;                 // see dpg_condense_set_method
@@ -47,6 +49,7 @@ struct AffProg {
     unsigned char *d_img = nullptr; // constant shared-memory images of the blocks
     int *d_img_off = nullptr;       // [nblock + 1], 16-byte units
     size_t smem_values = 0;         // values of the kernel's shared memory
+    int nc4 = 1;                    // FP32 Kronecker kernel: largest ceil(nc1 / 4) of the blocks
 };
 
 struct ProgEntry {
@@ -69,6 +72,11 @@ struct ProgEntry {
     Unit *d_units32 = nullptr;
     int max_nc1_32 = 0;             // largest stage-C column extent of prog32
     int *d_block_units32 = nullptr; // [nblock + 1] unit ranges of prog32
+    // K32_TCC: constant images, block item bases, launch shape of sf_tcc_kernel
+    float *d_tcc_img = nullptr;
+    int *d_tcc_off = nullptr, *d_tcc_base = nullptr;
+    int tcc_tcols = 0, tcc_cps = 1;
+    size_t tcc_smem = 0;            // dynamic shared memory of the launch
 };
 
 using ProgKey = std::tuple<int, int, int, int, int>;   // space, q, L, p, split
@@ -129,7 +137,7 @@ int upload(const T *src, size_t n, T **dst) {
 int upload_aff_image(AffProg &ap, const HostTables &tab, bool extruded, int prec) {
     std::vector<unsigned char> img;
     std::vector<int> off;
-    if (prec) build_aff_image<float>(ap.prog, tab, extruded, img, off);
+    if (prec) build_k32_image(ap.prog, tab, extruded, img, off);
     else build_aff_image<double>(ap.prog, tab, extruded, img, off);
     int r;
     if ((r = upload(img.data(), img.size(), &ap.d_img))) return r;
@@ -167,6 +175,9 @@ int device_state(DeviceState **out) {
     g_max_dyn_smem = max_dynamic_smem(optin);
     CK(init_tc_attributes(optin));
     g_max_dyn_smem_tc = optin - tc_static_smem();
+    CK(init_tcc_attributes(optin));
+    g_max_dyn_smem_tcc = optin - tcc_static_smem();
+    CK(cudaDeviceGetAttribute(&g_smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     CK(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
     for (auto &cs : st->copy_streams) CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -200,6 +211,50 @@ int get_tables(DeviceState *ds, int q, int L, TableEntry **out) {
 // row-panel program where its shared memory fits a CTA, else the mirrored-tile program.
 // The previous device copies are freed (the caller synchronises).
 int setup_prog32(ProgEntry *pe, int space, int q, int L, int p, bool split, const HostTables &tab, int nj) {
+    // first choice: stage C on the tensor cores, stages A and B on the FMA pipe
+    {
+        Program tp = make_program(space, q, L, p, split, tab, ORDER_TCC, 1, (size_t)g_max_dyn_smem_tcc);
+        if (tp.smem_bytes <= (size_t)g_max_dyn_smem_tcc) {
+            std::vector<float> img;
+            std::vector<int> off, base(tp.nblock + 1, 0);
+            build_tcc_tables(tp, tab, img, off);
+            int tcols = 32;
+            for (int k = 0; k < tp.nblock; ++k) {
+                base[k + 1] = base[k] + tp.blocks[k].nr[2];
+                tcols = std::max(tcols, tcc_layout(tp.blocks[k], L).tcols);
+            }
+            BlockDesc *db = nullptr;
+            float *dimg = nullptr;
+            int *doff = nullptr, *dbase = nullptr;
+            int r;
+            if ((r = upload(tp.blocks, (size_t)tp.nblock, &db))) return r;
+            if ((r = upload(img.data(), img.size(), &dimg))) return r;
+            if ((r = upload(off.data(), off.size(), &doff))) return r;
+            if ((r = upload(base.data(), base.size(), &dbase))) return r;
+            cudaFree(pe->d_blocks32); cudaFree(pe->d_units32); cudaFree(pe->d_block_units32);
+            cudaFree(pe->d_ctab32); cudaFree(pe->d_ctab_off32);
+            cudaFree(pe->d_tcc_img); cudaFree(pe->d_tcc_off); cudaFree(pe->d_tcc_base);
+            pe->d_blocks32 = db; pe->d_units32 = nullptr; pe->d_block_units32 = nullptr;
+            pe->d_ctab32 = nullptr; pe->d_ctab_off32 = nullptr;
+            pe->d_tcc_img = dimg; pe->d_tcc_off = doff; pe->d_tcc_base = dbase;
+            pe->tcc_tcols = tcols;
+            // two CTAs per SM (the register budget of the kernel) when both fit the tensor
+            // memory and the shared memory; otherwise one, its shared-memory request sized so
+            // that no second CTA is placed beside it
+            const size_t st = (size_t)(tcc_static_smem() + 1024);
+            const bool two = 2 * tcols <= 512 && 2 * (tp.smem_bytes + st) <= (size_t)g_smem_per_sm;
+            pe->tcc_cps = two ? 2 : 1;
+            pe->tcc_smem = two ? tp.smem_bytes
+                               : std::min((size_t)g_max_dyn_smem_tcc,
+                                          std::max(tp.smem_bytes, (size_t)g_smem_per_sm / 2 + 1));
+            pe->kind32 = K32_TCC;
+            pe->prog32 = tp;
+            pe->max_nc1_32 = 0;
+            return DPG_OK;
+        }
+    }
+    cudaFree(pe->d_tcc_img); cudaFree(pe->d_tcc_off); cudaFree(pe->d_tcc_base);
+    pe->d_tcc_img = nullptr; pe->d_tcc_off = nullptr; pe->d_tcc_base = nullptr;
     int kind = K32_TC;
     Program np = make_program(space, q, L, p, split, tab, ORDER_TC, nj, (size_t)g_max_dyn_smem_tc);
     if (np.smem_bytes > (size_t)g_max_dyn_smem_tc) {
@@ -252,14 +307,32 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
     int r;
     if ((r = upload(pr.blocks, (size_t)pr.nblock, &pe->d_blocks))) return r;
     if ((r = upload(pr.units.data(), pr.units.size(), &pe->d_units))) return r;
+    // the FP32 Kronecker kernel: the largest chunk whose shared memory fits four CTAs per SM,
+    // else the largest that fits
+    auto k32_program = [&](bool ext) {
+        Program pk = make_program(space, q, L, p, split != 0, tab, ext ? ORDER_K32_EXT : ORDER_K32, 0, 52 * 1024);
+        if (pk.smem_bytes > 52 * 1024)
+            pk = make_program(space, q, L, p, split != 0, tab, ext ? ORDER_K32_EXT : ORDER_K32, 0,
+                              (size_t)g_max_dyn_smem);
+        return pk;
+    };
+    auto k32_nc4 = [](const Program &pk) {
+        int n = 1;
+        for (int k = 0; k < pk.nblock; ++k) n = std::max(n, (pk.blocks[k].nc[0] + 3) / 4);
+        return n;
+    };
     for (int prec = 0; prec < 2; ++prec) {
         AffProg &ap = pe->aff[prec];
-        ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL, 0, prec == 0 ? 72 * 1024 : 0);
+        ap.prog = prec == 0 ? make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL, 0, 72 * 1024)
+                            : k32_program(false);
         const Program &pa = ap.prog;
         if ((r = upload(pa.blocks, (size_t)pa.nblock, &ap.d_blocks))) return r;
         if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
         size_t m = 0;
-        for (int k = 0; k < pa.nblock; ++k) m = std::max(m, affine_smem_values(pa.blocks[k], pa.nj));
+        for (int k = 0; k < pa.nblock; ++k)
+            m = std::max(m, prec ? kron32_smem_values(pa.blocks[k], L, pa.nj, false)
+                                 : affine_smem_values(pa.blocks[k], pa.nj));
+        if (prec) ap.nc4 = k32_nc4(pa);
         if ((r = upload_aff_image(ap, tab, false, prec))) return r;
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
@@ -272,17 +345,23 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
     for (int prec = 0; prec < 2; ++prec) {
         AffProg &ap = pe->ext[prec];
         const size_t esz = prec ? sizeof(float) : sizeof(double);
-        // the largest chunk whose shared memory fits three CTAs per SM, else the largest that fits
-        size_t budget = (size_t)72 * 1024 * sizeof(double) / esz;
-        ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0, budget);
-        if (ap.prog.smem_bytes > budget)
-            ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0,
-                                   (size_t)g_max_dyn_smem * sizeof(double) / esz);
+        if (prec) {
+            ap.prog = k32_program(true);
+        } else {
+            // the largest chunk whose shared memory fits three CTAs per SM, else the largest that fits
+            size_t budget = (size_t)72 * 1024;
+            ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0, budget);
+            if (ap.prog.smem_bytes > budget)
+                ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0, (size_t)g_max_dyn_smem);
+        }
         const Program &pa = ap.prog;
         if ((r = upload(pa.blocks, (size_t)pa.nblock, &ap.d_blocks))) return r;
         if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
         size_t m = 0;
-        for (int k = 0; k < pa.nblock; ++k) m = std::max(m, extruded_smem_values(pa.blocks[k], L, pa.nj));
+        for (int k = 0; k < pa.nblock; ++k)
+            m = std::max(m, prec ? kron32_smem_values(pa.blocks[k], L, pa.nj, true)
+                                 : extruded_smem_values(pa.blocks[k], L, pa.nj));
+        if (prec) ap.nc4 = k32_nc4(pa);
         if ((r = upload_aff_image(ap, tab, true, prec))) return r;
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
@@ -349,6 +428,7 @@ void free_device_state(DeviceState &ds) {
             }
         cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
         cudaFree(kv.second->d_ctab32); cudaFree(kv.second->d_ctab_off32);
+        cudaFree(kv.second->d_tcc_img); cudaFree(kv.second->d_tcc_off); cudaFree(kv.second->d_tcc_base);
     }
     for (auto &kv : ds.hp_graphs) cudaGraphExecDestroy(kv.second);
     ds.hp_graphs.clear();
@@ -454,6 +534,26 @@ int run_general_in(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_ele
             le = launch_geom<T>(g, s);
         }
         if (le != cudaSuccess) { rc = cuda_fail(le, "geom_kernel launch", __LINE__); break; }
+        if constexpr (f32) if (pe->kind32 == K32_TCC) {
+            TccParams tp;
+            tp.blocks = pe->d_blocks32; tp.nblock = pr.nblock; tp.blk_base = pe->d_tcc_base;
+            tp.img = pe->d_tcc_img; tp.img_off = pe->d_tcc_off;
+            tp.L = L; tp.nfields = pr.nfields; tp.tcols = pe->tcc_tcols;
+            tp.pp = te->pp32;
+            tp.fields = reinterpret_cast<const float *>(ws); tp.foff = nullptr;
+            tp.out = reinterpret_cast<float *>(out + e0 * mat); tp.out_off = nullptr;
+            tp.mat_stride = mat; tp.ld = og.ld; tp.n_elem = ne;
+            tp.n_elem_dev = nullptr; tp.elist = nullptr; tp.elist_start = nullptr;
+            tp.status = ds->status; tp.smem_bytes = (int)pe->tcc_smem;
+            tp.stall_cta = g_tc_stall_once ? 0 : -1;
+            g_tc_stall_once = 0;
+            {
+                TraceRange tr("dpg contraction: general, FP32, stage C on tcgen05");
+                le = launch_tcc(tp, g_num_sms * pe->tcc_cps, pe->tcc_smem, s);
+            }
+            if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
+            continue;
+        }
         if constexpr (f32) if (pe->kind32 == K32_TC) {
             TcParams tp;
             tp.blocks = pe->d_blocks32; tp.units = pe->d_units32; tp.block_unit_begin = pe->d_block_units32;
@@ -602,7 +702,8 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne; ap.status = ds->status;
         {
             TraceRange tr("dpg contraction: affine");
-            le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
+            if constexpr (sizeof(T) == 4) le = launch_kron32(ap, aprog.smem_values * sizeof(T), aprog.nc4, false, s);
+        else le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
         }
         if (le != cudaSuccess) rc = cuda_fail(le, "sf_affine_kernel launch", __LINE__);
     }
@@ -669,7 +770,8 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne; ap.status = ds->status;
         {
             TraceRange tr("dpg contraction: extruded");
-            le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
+            if constexpr (sizeof(T) == 4) le = launch_kron32(ap, aprog.smem_values * sizeof(T), aprog.nc4, true, s);
+            else le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
         }
         if (le != cudaSuccess) { rc = cuda_fail(le, "extruded contraction launch", __LINE__); break; }
     }
@@ -742,11 +844,42 @@ int enqueue_hp(DeviceState *ds, int space, int64_t n, const double *verts, const
     p.item_k = (int *)wit; p.scan_tmp = (int64_t *)wtmp; p.fields = wfield;
     const size_t smem = ds->hp_smem[fp32 ? 1 : 0][base];
     const int ctas = g_num_sms * hp_ctas_per_sm(fp32, smem);
+    // FP32: when every initialised order has a program of the stage-C tensor-core kernel, the
+    // contraction is one launch of that kernel per order (the elements of the order from the
+    // device-side sort), else the persistent kernel over every work item
+    std::vector<std::pair<ProgEntry *, TableEntry *>> tcc(MAXQ + 1, { nullptr, nullptr });
+    bool use_tcc = fp32;
+    for (int q = 1; q <= MAXQ && use_tcc; ++q) {
+        if (!ds->h_hp[1][base][q].valid) continue;
+        auto ai = ds->active_L.find(std::make_pair(base, q));
+        if (ai == ds->active_L.end()) { use_tcc = false; break; }
+        auto pt = ds->progs.find(ProgKey{ base, q, ai->second, 0, 0 });
+        auto tt = ds->tables.find(std::make_pair(q, ai->second));
+        if (pt == ds->progs.end() || tt == ds->tables.end() || pt->second->kind32 != K32_TCC) { use_tcc = false; break; }
+        tcc[q] = { pt->second.get(), tt->second.get() };
+    }
     int rc = DPG_OK;
     cudaError_t le;
     {
         TraceRange tr("dpg hp: work generation, geometry, persistent contraction");
-        le = launch_hp(p, fp32, smem, ctas, s);
+        le = launch_hp(p, fp32, smem, ctas, s, !use_tcc);
+    }
+    for (int q = MAXQ; q >= 1 && use_tcc && le == cudaSuccess; --q) {
+        if (!tcc[q].first) continue;
+        const ProgEntry *pe = tcc[q].first;
+        const Program &pr = pe->prog32;
+        TccParams tp;
+        tp.blocks = pe->d_blocks32; tp.nblock = pr.nblock; tp.blk_base = pe->d_tcc_base;
+        tp.img = pe->d_tcc_img; tp.img_off = pe->d_tcc_off;
+        tp.L = pr.L; tp.nfields = pr.nfields; tp.tcols = pe->tcc_tcols;
+        tp.pp = tcc[q].second->pp32;
+        tp.fields = reinterpret_cast<const float *>(p.fields); tp.foff = p.foff;
+        tp.out = reinterpret_cast<float *>(out); tp.out_off = out_offset;
+        tp.mat_stride = (int64_t)pr.parts * pr.rows * pr.cols; tp.ld = pr.cols; tp.n_elem = 0;
+        tp.n_elem_dev = p.hist + q; tp.elist = p.order; tp.elist_start = p.bstart + q;
+        tp.status = ds->status; tp.smem_bytes = (int)pe->tcc_smem; tp.stall_cta = -1;
+        TraceRange tr("dpg hp: contraction of one order, FP32, stage C on tcgen05");
+        le = launch_tcc(tp, g_num_sms * pe->tcc_cps, pe->tcc_smem, s);
     }
     if (le != cudaSuccess) rc = cuda_fail(le, "hp launch sequence", __LINE__);
     for (void *w : { wfield, wtmp, wit, wf, wu, word, wsmall }) cudaFreeAsync(w, s);

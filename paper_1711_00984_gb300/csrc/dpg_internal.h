@@ -170,6 +170,42 @@ DPG_HD inline ExtLayout ext_layout(const BlockDesc &b, int L, int nj) {
     return x;
 }
 
+// Shared-memory layout (in floats, every region 16-byte aligned) of the FP32 Kronecker
+// kernel (affine and extruded maps in the FP32 form) for one block in the paper's direction
+// order and a chunk of nj stage-A partners.  Every block of the matrix is computed (no
+// mirrored tiles).  The constant image [0, oC): the exact stage-C integrals F1 dense
+// [ng][nr1][nc1p] (j1 padded to a multiple of 4 with zeros), then the exact stage-B
+// integrals F2 [nterm][(i2, j2)] (affine) or the stage-B pair products P2 [np2][(i2, j2)][m]
+// at the Gauss points (extruded).  Per unit: Q [ng][(i2, x)] with x = j2 + nc2 jj, the
+// extruded map's element fields [nfs][L][L], stage-A factors S3 [nterm][nj][L] and stage-A
+// output A [nh][L][nj], and the output tile [nrow][ldt]: tile row r = i1 + nr1 i2 holds the
+// columns c = j1 + nc1 x at r ldt + m_r + c, where m_r (0..3) is the destination row's
+// offset from 16-byte alignment, so that tile and destination float4s coincide.
+struct K32Layout {
+    int nc1p, n22, nx, nf, nrow, ncol, ldt, nfs;
+    int oF1, oF2, oP2, oC, oQ, oFx, oS3, oA, oT, total;
+};
+constexpr int K32_MAXROW = 176;    // tile rows nr1 nr2 <= 13 * 13
+DPG_HD inline K32Layout k32_layout(const BlockDesc &b, int L, int nj, bool ext) {
+    K32Layout k;
+    const int nr1 = b.nr[0], nr2 = b.nr[1], nc1 = b.nc[0], nc2 = b.nc[1];
+    k.nc1p = r4i(nc1);
+    k.n22 = nr2 * nc2; k.nx = nc2 * nj; k.nf = nr2 * k.nx;
+    k.nrow = nr1 * nr2; k.ncol = nc1 * k.nx; k.ldt = r4i(k.ncol) + 4;
+    k.nfs = ext ? distinct_fields(b) : 0;
+    k.oF1 = 0;
+    k.oF2 = k.oF1 + r4i(b.ng * nr1 * k.nc1p);
+    k.oP2 = k.oF2 + (ext ? 0 : r4i(b.nterm * k.n22));
+    k.oC = k.oP2 + (ext ? r4i(b.np2 * k.n22 * L) : 0);
+    k.oQ = k.oC;
+    k.oFx = k.oQ + r4i(b.ng * k.nf);
+    k.oS3 = k.oFx + (ext ? r4i(k.nfs * L * L) : 0);
+    k.oA = k.oS3 + (ext ? r4i(b.nterm * nj * L) : 0);
+    k.oT = k.oA + (ext ? r4i(b.nh * L * nj) : 0);
+    k.total = k.oT + k.nrow * k.ldt;
+    return k;
+}
+
 // Shared-memory layout (in floats, every region 16-byte aligned) of the FP32 row-panel
 // kernel for one block in the paper's direction order (stage C over xi_1, B over xi_2, A
 // over xi_3) and a chunk of nj stage-A partners.  Stages B and C are tensor-core
@@ -295,6 +331,72 @@ DPG_HD inline TcLayout tc_layout(const BlockDesc &b, int L, int nj) {
     f.total = (end + 127) & ~127;
     f.ok = f.n22 <= 128 && f.NB <= 256 && f.NC <= 256 && f.tneed <= TC_TMEM_COLS && f.lpad <= 16 &&
            f.nrow <= TC_MAXROW && (b.ng == 0 || (b.nh >= 1 && b.np2 >= 1));   // a block without terms: zeros
+    return f;
+}
+
+// Shared-memory and tensor-memory layout of the FP32 general kernel with stage C on the
+// tensor cores (sf_tcc_kernel) for one block in the paper's direction order.  A work item
+// is (element, block, i3) with every partner j3; its output rows (i1, i2) are computed in
+// tiles of at most 128 stage-C rows (i2, x), x = j2 + nc2 j3: whole i2 rows of x when
+// nx = nc2 nc3 <= 128 (ipt of them per tile), else chunks of 128 x of one i2.
+//   stage A (FMA)      A_h[m][j3][l] = sum_{t in h} sum_n M_t(l,m,n) P3_t(n, j3)          (Eq. 2.23)
+//   stage B (FMA)      A_C[(i2,x)][(g,l)] = sum_{h in g} sum_m P2_h(m)[i2,j2] A_h[m][j3][l] (Eq. 2.24)
+//   stage C (tcgen05)  D[(i2,x)][(i1,j1)] = sum_{g,l} A_C[(i2,x)][(g,l)] P1[(i1,j1)][(g,l)]  (Eq. 2.25)
+// Stage-C operands are K-major in the canonical no-swizzle layout (element (r, k) at byte
+// (r/8) sbo + (k/4) 128 + (r%8) 16 + (k%4) 4, sbo = 32 K), split into TF32 high and low
+// parts (three products per operand pair, FP32 accumulation); K = (g, l) with l padded to
+// lpad (a multiple of 4) and the whole K to a multiple of 8; N = (i1, j1) = i1 nc1 + j1,
+// padded to a multiple of 16.  Two accumulators of N tensor-memory columns alternate
+// between consecutive tiles.  Byte offsets from the start of dynamic shared memory; the
+// constant image [0, oC) (P1 high, P1 low, P2) is built on the host (build_tcc_tables).
+struct TccLayout {
+    int L, lpad, K, ksteps, N;
+    int nr1, nr2, nr3, nc1, nc2, nc3, nc3p;
+    int n22, n22p, nx, ipt, nxc, ntile;   // (i2,j2) pairs; x range; i2 per tile (0: x chunks); chunks per i2; tiles
+    int sbo;                               // 32 K bytes
+    int oP1, p1b, oP2, oC;                 // P1 high at oP1, low at oP1 + p1b; P2 [np2][L][n22p] floats
+    int oAC, acb;                          // A_C high at oAC, low at oAC + acb (128 rows)
+    int oA;                                // stage-A output [nh][L][nc3][lpad] floats
+    int oP3;                               // stage-A factors [nterm][L][nc3p] floats
+    int npad, oF;                          // element fields of the block's terms [nfs][L][L][npad]
+    int oW, wst;                           // per-warp staging [8][wst] floats
+    int total;                             // bytes
+    int tcols;                             // tensor-memory columns to allocate
+    int ok;
+};
+constexpr int TCC_NTH = 256;
+DPG_HD inline TccLayout tcc_layout(const BlockDesc &b, int L) {
+    TccLayout f;
+    auto r8 = [](int v) { return (v + 7) & ~7; };
+    auto r16 = [](int v) { return (v + 15) & ~15; };
+    auto a128 = [](int v) { return (v + 127) & ~127; };
+    f.L = L; f.lpad = r4i(L);
+    f.K = r8(b.ng * f.lpad); f.ksteps = f.K / 8;
+    f.nr1 = b.nr[0]; f.nr2 = b.nr[1]; f.nr3 = b.nr[2];
+    f.nc1 = b.nc[0]; f.nc2 = b.nc[1]; f.nc3 = b.nc[2]; f.nc3p = r4i(f.nc3);
+    f.N = r16(f.nr1 * f.nc1);
+    f.n22 = f.nr2 * f.nc2; f.n22p = r4i(f.n22);
+    f.nx = f.nc2 * f.nc3;
+    if (f.nx <= 128) { f.ipt = 128 / f.nx; f.nxc = 1; f.ntile = (f.nr2 + f.ipt - 1) / f.ipt; }
+    else { f.ipt = 0; f.nxc = (f.nx + 127) / 128; f.ntile = f.nr2 * f.nxc; }
+    f.sbo = 32 * f.K;
+    f.oP1 = 0; f.p1b = (f.N / 8) * f.sbo;
+    f.oP2 = f.oP1 + 2 * f.p1b;
+    f.oC = a128(f.oP2 + 4 * b.np2 * L * f.n22p);
+    f.oAC = f.oC; f.acb = 16 * f.sbo;
+    f.oA = f.oAC + 2 * f.acb;
+    f.oP3 = f.oA + 4 * b.nh * L * f.nc3 * f.lpad;
+    f.npad = L | 1;
+    f.oF = f.oP3 + 4 * b.nterm * L * f.nc3p;
+    f.oF = (f.oF + 15) & ~15;
+    f.oW = f.oF + 4 * distinct_fields(b) * L * L * f.npad;
+    f.oW = (f.oW + 15) & ~15;
+    f.wst = 32 * f.nc1 + 4;
+    f.total = a128(f.oW + 4 * 8 * f.wst);
+    f.tcols = 32;
+    while (f.tcols < 2 * f.N + 16 && f.tcols < 512) f.tcols <<= 1;
+    f.ok = (2 * f.N + 16 <= 512) && f.nc1 <= 16 && f.nc3 <= 16 && f.lpad <= 16 && b.ng >= 1 && b.nh >= 1 &&
+           b.np2 >= 1;
     return f;
 }
 

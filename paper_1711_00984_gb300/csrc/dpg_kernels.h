@@ -127,6 +127,30 @@ struct TcParams {
     int stall_cta;                 // test hook: this CTA issues no stage-B MMA (-1: none)
 };
 
+// FP32 general kernel with stage C on the tensor cores (sf_tcc_kernel): a persistent grid
+// over the work items (block, element, i3) of one program, block-major; uniform batches
+// (elist = NULL: element index = item's element) or the elements of one order of an hp
+// batch (elist[*elist_start + i], *n_elem_dev of them, per-element offsets foff / out_off).
+struct TccParams {
+    const BlockDesc *blocks;
+    int nblock;
+    const int *blk_base;           // [nblock + 1]: prefix sums of nr3 (items per element)
+    const float *img;              // constant images of the blocks (build_tcc_tables)
+    const int *img_off;            // [nblock + 1], in floats
+    int L, nfields, tcols;         // tcols: tensor-memory columns every CTA allocates
+    const float *pp;               // FP32 pair products [NPAIR][NQ1][NQ1][L]
+    const float *fields;           // [n_elem][nfields][L^3] (foff == NULL) or the base of foff
+    const int64_t *foff;
+    float *out;                    // [n_elem][mat_stride] (out_off == NULL) or the base of out_off
+    const int64_t *out_off;
+    int64_t mat_stride, ld;        // values of one element matrix (all parts), its leading dimension
+    int64_t n_elem;
+    const int *n_elem_dev, *elist, *elist_start;
+    DevStatus *status;
+    int smem_bytes;                // dynamic shared memory of the launch
+    int stall_cta;                 // test hook: this CTA commits no product (-1: none)
+};
+
 template <typename T>
 struct AffParams {
     const BlockDesc *blocks;
@@ -215,7 +239,10 @@ struct HpParams {
     void *fields;
 };
 
-cudaError_t launch_hp(const HpParams &p, bool fp32, size_t smem, int persistent_ctas, cudaStream_t s);
+// The hp sequence; contract = false stops after the geometry (the caller launches the
+// contraction itself).
+cudaError_t launch_hp(const HpParams &p, bool fp32, size_t smem, int persistent_ctas, cudaStream_t s,
+                      bool contract = true);
 int hp_ctas_per_sm(bool fp32, size_t smem);
 
 template <typename TF> cudaError_t launch_geom(const GeomParams &p, cudaStream_t s);
@@ -223,6 +250,9 @@ template <typename T> cudaError_t launch_general(const SfParams<T> &p, size_t sm
 cudaError_t launch_general_f32(const SfParams32 &p, size_t smem, int max_nc1, cudaStream_t s);
 cudaError_t launch_panel_f32(const PanelParams &p, size_t smem, cudaStream_t s);
 cudaError_t launch_tc_f32(const TcParams &p, size_t smem, cudaStream_t s);
+cudaError_t launch_tcc(const TccParams &p, int grid, size_t smem, cudaStream_t s);
+cudaError_t init_tcc_attributes(int optin_smem);
+int tcc_static_smem();
 cudaError_t init_tc_attributes(int optin_smem);
 int tc_static_smem();
 cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s);
@@ -246,6 +276,11 @@ cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s)
 // products of 128 x 256 x 8; *status (device) is set to 1 if a bounded wait ran out.
 cudaError_t launch_tc_tf32_peak(int ctas, int iters, int *status, cudaStream_t s);
 size_t affine_smem_values(const BlockDesc &b, int nj);
+// FP32 form of the affine / extruded paths (dense Kronecker products, every block computed):
+// programs of order ORDER_K32 / ORDER_K32_EXT, images of build_k32_image; nc4 = the largest
+// ceil(nc1 / 4) of the program's blocks.
+size_t kron32_smem_values(const BlockDesc &b, int L, int nj, bool ext);
+cudaError_t launch_kron32(const AffParams<float> &p, size_t smem, int nc4, bool extruded, cudaStream_t s);
 int max_dynamic_smem(int optin_smem);
 
 }  // namespace dpg

@@ -31,145 +31,12 @@
 #include <cstdint>
 
 #include "dpg_kernels.h"
+#include "dpg_tcgen05.cuh"
 
 namespace dpg {
 
 namespace {
-
-__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void report_tc(DevStatus *st, int code, long long elem) {
-    atomicCAS(&st->code, 0, code);
-    atomicMin(&st->first_bad[code], (unsigned long long)elem);
-}
-
-__device__ __forceinline__ unsigned magic(int d) { return d <= 1 ? 0u : 0xffffffffu / (unsigned)d + 1u; }
-__device__ __forceinline__ int mdiv(int x, unsigned m) { return m ? (int)__umulhi((unsigned)x, m) : x; }
-
-// Shared-memory matrix descriptor (tcgen05): start address, K-direction core-matrix
-// stride 128 bytes, 8-row-group stride sbo, fixed field 0b001 at bit 46, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, M x N.
-__device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                 :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
-}
-
-// d (+)= a b with split operands: a_lo b_hi + a_hi b_lo + a_hi b_hi
-__device__ __forceinline__ void umma3(uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl, uint32_t id,
-                                      uint32_t acc) {
-    umma(d, al, bh, id, acc);
-    umma(d, ah, bl, id, 1u);
-    umma(d, ah, bh, id, 1u);
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(saddr(bar)) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(saddr(bar)), "r"(count));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Wait for the completion of phase `parity` of bar.  The thread sleeps in try_wait (up to
-// the 20 us hint per try) instead of spinning, so waiting warps leave the issue slots to
-// the working ones.  Bounded: after about 2^31 cycles (about a second at the GB300 clock)
-// the CTA's failure flag is raised and the caller goes on; a kernel never waits without
-// limit.
-__device__ __forceinline__ void mbar_wait(uint64_t *bar, uint32_t parity, volatile int *fail) {
-    if (*fail) return;
-    long long t0 = 0;
-    for (int spin = 0;; ++spin) {
-        uint32_t ok;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-                     "selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok) : "r"(saddr(bar)), "r"(parity), "r"(20000) : "memory");
-        if (ok) return;
-        if (spin == 0) t0 = clock64();
-        else if (clock64() - t0 > (1LL << 31)) { *fail = 1; return; }
-    }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(saddr(bar)) : "memory");
-}
-
-// Barrier `id` over `nth` threads of one warp group; returns the OR of pred over them.
-__device__ __forceinline__ int group_sync_or(int id, int nth, int pred) {
-    int r;
-    asm volatile("{\n.reg .pred p, q;\nsetp.ne.b32 q, %3, 0;\nbar.red.or.pred p, %1, %2, q;\nselp.b32 %0, 1, 0, p;\n}\n"
-                 : "=r"(r) : "r"(id), "r"(nth), "r"(pred) : "memory");
-    return r;
-}
-
-// 4-byte asynchronous global -> shared copy (no register staging: the loads pipeline)
-__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(saddr(sdst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
-
-// 32 lanes x 16 consecutive columns of tensor memory; the wait is tied to the registers.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-                 :: "memory");
-}
-
-// two groups of 16 columns (taddr0, taddr1), one wait tied to all 32 registers
-__device__ __forceinline__ void tmem_ld16x2(uint32_t ta0, uint32_t ta1, uint32_t (&r)[32]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(ta0));
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(ta1));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
-                   "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :: "memory");
-}
-
-// x = hi + lo, hi = x rounded to 10 mantissa bits (the bits a TF32 operand keeps), lo exact
-__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
-    const float h = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
-    hi = h;
-    lo = x - h;
-}
-
-__device__ __forceinline__ void load_block_tc(const BlockDesc *src, BlockDesc &dst) {
-    const int *s = reinterpret_cast<const int *>(src);
-    int *d = reinterpret_cast<int *>(&dst);
-    for (int i = threadIdx.x; i < (int)(sizeof(BlockDesc) / sizeof(int)); i += blockDim.x) d[i] = s[i];
-}
+using namespace ::dpg::tc;
 
 constexpr int TC_NP = 8;           // producer warps
 constexpr int TC_NC = 8;           // consumer warps
