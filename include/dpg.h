@@ -202,7 +202,10 @@ int dpg_integrate_hp(int space, int64_t n_elem, const double *vertices, const do
  * dpg_integrate_hp; for FP64 programs that hold both diagonal blocks of the symmetric
  * matrix (their work units run from j_A = i_A up, so they are uneven) and full blocks
  * (H(curl), H(div)), a second pass picks a smaller width for the diagonal blocks alone.
- * space = DPG_H1 .. DPG_L2, optionally | DPG_FP32 (tunes the FP32 kernel).  If the environment variable DPG_AUTOTUNE_CACHE names a file, a choice stored
+ * space = DPG_H1 .. DPG_L2, optionally | DPG_FP32 (tunes the FP32 form: besides the widths
+ * of the earlier FP32 kernels it times the kernel with stage C on the tensor cores and
+ * stages A and B on the FMA pipe, reported as nj = 0; dpg_integrate_hp uses that kernel
+ * for every order that has it).  If the environment variable DPG_AUTOTUNE_CACHE names a file, a choice stored
  * there for (space, q, L, precision) is installed without timing, and new choices are
  * appended as JSON lines ({"space", "q", "L", "fp32", "nj", "ms", "nj_sym"}; nj_sym = 0:
  * the diagonal blocks use nj too).  Synchronous; allocates temporary device buffers; call it at

@@ -52,6 +52,17 @@ struct AffProg {
     int nc4 = 1;                    // FP32 Kronecker kernel: largest ceil(nc1 / 4) of the blocks
 };
 
+// Program of the FP32 general kernel with stage C on the tensor cores (sf_tcc_kernel).
+struct TccProg {
+    bool ok = false;
+    Program prog;
+    BlockDesc *d_blocks = nullptr;
+    float *d_img = nullptr;         // constant images of the blocks
+    int *d_off = nullptr, *d_base = nullptr;
+    int tcols = 0, cps = 1;         // tensor-memory columns per CTA, CTAs per SM
+    size_t smem = 0;                // dynamic shared memory of the launch
+};
+
 struct ProgEntry {
     Program prog;                   // general path: per-block contraction order
     BlockDesc *d_blocks = nullptr;
@@ -72,11 +83,8 @@ struct ProgEntry {
     Unit *d_units32 = nullptr;
     int max_nc1_32 = 0;             // largest stage-C column extent of prog32
     int *d_block_units32 = nullptr; // [nblock + 1] unit ranges of prog32
-    // K32_TCC: constant images, block item bases, launch shape of sf_tcc_kernel
-    float *d_tcc_img = nullptr;
-    int *d_tcc_off = nullptr, *d_tcc_base = nullptr;
-    int tcc_tcols = 0, tcc_cps = 1;
-    size_t tcc_smem = 0;            // dynamic shared memory of the launch
+    TccProg tcc;                    // the stage-C tensor-core program (uniform when kind32 ==
+                                    // K32_TCC; the FP32 hp contraction whenever it exists)
 };
 
 using ProgKey = std::tuple<int, int, int, int, int>;   // space, q, L, p, split
@@ -210,51 +218,51 @@ int get_tables(DeviceState *ds, int q, int L, TableEntry **out) {
 // that fits): the tensor-core program where every block fits the tcgen05 kernel, else the
 // row-panel program where its shared memory fits a CTA, else the mirrored-tile program.
 // The previous device copies are freed (the caller synchronises).
-int setup_prog32(ProgEntry *pe, int space, int q, int L, int p, bool split, const HostTables &tab, int nj) {
-    // first choice: stage C on the tensor cores, stages A and B on the FMA pipe
-    {
-        Program tp = make_program(space, q, L, p, split, tab, ORDER_TCC, 1, (size_t)g_max_dyn_smem_tcc);
-        if (tp.smem_bytes <= (size_t)g_max_dyn_smem_tcc) {
-            std::vector<float> img;
-            std::vector<int> off, base(tp.nblock + 1, 0);
-            build_tcc_tables(tp, tab, img, off);
-            int tcols = 32;
-            for (int k = 0; k < tp.nblock; ++k) {
-                base[k + 1] = base[k] + tp.blocks[k].nr[2];
-                tcols = std::max(tcols, tcc_layout(tp.blocks[k], L).tcols);
-            }
-            BlockDesc *db = nullptr;
-            float *dimg = nullptr;
-            int *doff = nullptr, *dbase = nullptr;
-            int r;
-            if ((r = upload(tp.blocks, (size_t)tp.nblock, &db))) return r;
-            if ((r = upload(img.data(), img.size(), &dimg))) return r;
-            if ((r = upload(off.data(), off.size(), &doff))) return r;
-            if ((r = upload(base.data(), base.size(), &dbase))) return r;
-            cudaFree(pe->d_blocks32); cudaFree(pe->d_units32); cudaFree(pe->d_block_units32);
-            cudaFree(pe->d_ctab32); cudaFree(pe->d_ctab_off32);
-            cudaFree(pe->d_tcc_img); cudaFree(pe->d_tcc_off); cudaFree(pe->d_tcc_base);
-            pe->d_blocks32 = db; pe->d_units32 = nullptr; pe->d_block_units32 = nullptr;
-            pe->d_ctab32 = nullptr; pe->d_ctab_off32 = nullptr;
-            pe->d_tcc_img = dimg; pe->d_tcc_off = doff; pe->d_tcc_base = dbase;
-            pe->tcc_tcols = tcols;
-            // two CTAs per SM (the register budget of the kernel) when both fit the tensor
-            // memory and the shared memory; otherwise one, its shared-memory request sized so
-            // that no second CTA is placed beside it
-            const size_t st = (size_t)(tcc_static_smem() + 1024);
-            const bool two = 2 * tcols <= 512 && 2 * (tp.smem_bytes + st) <= (size_t)g_smem_per_sm;
-            pe->tcc_cps = two ? 2 : 1;
-            pe->tcc_smem = two ? tp.smem_bytes
-                               : std::min((size_t)g_max_dyn_smem_tcc,
-                                          std::max(tp.smem_bytes, (size_t)g_smem_per_sm / 2 + 1));
-            pe->kind32 = K32_TCC;
-            pe->prog32 = tp;
-            pe->max_nc1_32 = 0;
-            return DPG_OK;
-        }
+// Build and upload the stage-C tensor-core program of pe where every block fits the kernel.
+int setup_tcc(ProgEntry *pe, int space, int q, int L, int p, bool split, const HostTables &tab) {
+    TccProg &t = pe->tcc;
+    Program tp = make_program(space, q, L, p, split, tab, ORDER_TCC, 1, (size_t)g_max_dyn_smem_tcc);
+    if (tp.smem_bytes > (size_t)g_max_dyn_smem_tcc) { t.ok = false; return DPG_OK; }
+    std::vector<float> img;
+    std::vector<int> off, base(tp.nblock + 1, 0);
+    build_tcc_tables(tp, tab, img, off);
+    int tcols = 32;
+    for (int k = 0; k < tp.nblock; ++k) {
+        base[k + 1] = base[k] + tp.blocks[k].nr[2];
+        tcols = std::max(tcols, tcc_layout(tp.blocks[k], L).tcols);
     }
-    cudaFree(pe->d_tcc_img); cudaFree(pe->d_tcc_off); cudaFree(pe->d_tcc_base);
-    pe->d_tcc_img = nullptr; pe->d_tcc_off = nullptr; pe->d_tcc_base = nullptr;
+    int r;
+    if ((r = upload(tp.blocks, (size_t)tp.nblock, &t.d_blocks))) return r;
+    if ((r = upload(img.data(), img.size(), &t.d_img))) return r;
+    if ((r = upload(off.data(), off.size(), &t.d_off))) return r;
+    if ((r = upload(base.data(), base.size(), &t.d_base))) return r;
+    t.tcols = tcols;
+    // two CTAs per SM (the register budget of the kernel) when both fit the tensor memory and
+    // the shared memory; otherwise one, its shared-memory request sized so that no second
+    // CTA is placed beside it
+    const size_t st = (size_t)(tcc_static_smem() + 1024);
+    const bool two = 2 * tcols <= 512 && 2 * (tp.smem_bytes + st) <= (size_t)g_smem_per_sm;
+    t.cps = two ? 2 : 1;
+    t.smem = two ? tp.smem_bytes
+                 : std::min((size_t)g_max_dyn_smem_tcc, std::max(tp.smem_bytes, (size_t)g_smem_per_sm / 2 + 1));
+    t.prog = tp;
+    t.ok = true;
+    return DPG_OK;
+}
+
+int setup_prog32(ProgEntry *pe, int space, int q, int L, int p, bool split, const HostTables &tab, int nj) {
+    // nj == 0: stage C on the tensor cores (stages A and B on the FMA pipe) where the
+    // program exists; nj > 0 (autotuner): the earlier FP32 kernels with stage-A chunk nj
+    if (nj == 0 && pe->tcc.ok) {
+        cudaFree(pe->d_blocks32); cudaFree(pe->d_units32); cudaFree(pe->d_block_units32);
+        cudaFree(pe->d_ctab32); cudaFree(pe->d_ctab_off32);
+        pe->d_blocks32 = nullptr; pe->d_units32 = nullptr; pe->d_block_units32 = nullptr;
+        pe->d_ctab32 = nullptr; pe->d_ctab_off32 = nullptr;
+        pe->kind32 = K32_TCC;
+        pe->prog32 = pe->tcc.prog;
+        pe->max_nc1_32 = 0;
+        return DPG_OK;
+    }
     int kind = K32_TC;
     Program np = make_program(space, q, L, p, split, tab, ORDER_TC, nj, (size_t)g_max_dyn_smem_tc);
     if (np.smem_bytes > (size_t)g_max_dyn_smem_tc) {
@@ -371,6 +379,7 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         ap.smem_values = m;
     }
     pe->flops_ext = pe->ext[0].prog.flops_extruded;
+    if ((r = setup_tcc(pe.get(), space, q, L, p, split != 0, tab))) return r;
     if ((r = setup_prog32(pe.get(), space, q, L, p, split != 0, tab, 0))) return r;
     *out = pe.get();
     ds->progs[key] = std::move(pe);
@@ -428,7 +437,8 @@ void free_device_state(DeviceState &ds) {
             }
         cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
         cudaFree(kv.second->d_ctab32); cudaFree(kv.second->d_ctab_off32);
-        cudaFree(kv.second->d_tcc_img); cudaFree(kv.second->d_tcc_off); cudaFree(kv.second->d_tcc_base);
+        cudaFree(kv.second->tcc.d_blocks); cudaFree(kv.second->tcc.d_img); cudaFree(kv.second->tcc.d_off);
+        cudaFree(kv.second->tcc.d_base);
     }
     for (auto &kv : ds.hp_graphs) cudaGraphExecDestroy(kv.second);
     ds.hp_graphs.clear();
@@ -536,20 +546,20 @@ int run_general_in(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_ele
         if (le != cudaSuccess) { rc = cuda_fail(le, "geom_kernel launch", __LINE__); break; }
         if constexpr (f32) if (pe->kind32 == K32_TCC) {
             TccParams tp;
-            tp.blocks = pe->d_blocks32; tp.nblock = pr.nblock; tp.blk_base = pe->d_tcc_base;
-            tp.img = pe->d_tcc_img; tp.img_off = pe->d_tcc_off;
-            tp.L = L; tp.nfields = pr.nfields; tp.tcols = pe->tcc_tcols;
+            tp.blocks = pe->tcc.d_blocks; tp.nblock = pr.nblock; tp.blk_base = pe->tcc.d_base;
+            tp.img = pe->tcc.d_img; tp.img_off = pe->tcc.d_off;
+            tp.L = L; tp.nfields = pr.nfields; tp.tcols = pe->tcc.tcols;
             tp.pp = te->pp32;
             tp.fields = reinterpret_cast<const float *>(ws); tp.foff = nullptr;
             tp.out = reinterpret_cast<float *>(out + e0 * mat); tp.out_off = nullptr;
             tp.mat_stride = mat; tp.ld = og.ld; tp.n_elem = ne;
             tp.n_elem_dev = nullptr; tp.elist = nullptr; tp.elist_start = nullptr;
-            tp.status = ds->status; tp.smem_bytes = (int)pe->tcc_smem;
+            tp.status = ds->status; tp.smem_bytes = (int)pe->tcc.smem;
             tp.stall_cta = g_tc_stall_once ? 0 : -1;
             g_tc_stall_once = 0;
             {
                 TraceRange tr("dpg contraction: general, FP32, stage C on tcgen05");
-                le = launch_tcc(tp, g_num_sms * pe->tcc_cps, pe->tcc_smem, s);
+                le = launch_tcc(tp, g_num_sms * pe->tcc.cps, pe->tcc.smem, s);
             }
             if (le != cudaSuccess) { rc = cuda_fail(le, "contraction kernel launch", __LINE__); break; }
             continue;
@@ -855,7 +865,7 @@ int enqueue_hp(DeviceState *ds, int space, int64_t n, const double *verts, const
         if (ai == ds->active_L.end()) { use_tcc = false; break; }
         auto pt = ds->progs.find(ProgKey{ base, q, ai->second, 0, 0 });
         auto tt = ds->tables.find(std::make_pair(q, ai->second));
-        if (pt == ds->progs.end() || tt == ds->tables.end() || pt->second->kind32 != K32_TCC) { use_tcc = false; break; }
+        if (pt == ds->progs.end() || tt == ds->tables.end() || !pt->second->tcc.ok) { use_tcc = false; break; }
         tcc[q] = { pt->second.get(), tt->second.get() };
     }
     int rc = DPG_OK;
@@ -866,20 +876,20 @@ int enqueue_hp(DeviceState *ds, int space, int64_t n, const double *verts, const
     }
     for (int q = MAXQ; q >= 1 && use_tcc && le == cudaSuccess; --q) {
         if (!tcc[q].first) continue;
-        const ProgEntry *pe = tcc[q].first;
-        const Program &pr = pe->prog32;
+        const TccProg &tg = tcc[q].first->tcc;
+        const Program &pr = tg.prog;
         TccParams tp;
-        tp.blocks = pe->d_blocks32; tp.nblock = pr.nblock; tp.blk_base = pe->d_tcc_base;
-        tp.img = pe->d_tcc_img; tp.img_off = pe->d_tcc_off;
-        tp.L = pr.L; tp.nfields = pr.nfields; tp.tcols = pe->tcc_tcols;
+        tp.blocks = tg.d_blocks; tp.nblock = pr.nblock; tp.blk_base = tg.d_base;
+        tp.img = tg.d_img; tp.img_off = tg.d_off;
+        tp.L = pr.L; tp.nfields = pr.nfields; tp.tcols = tg.tcols;
         tp.pp = tcc[q].second->pp32;
         tp.fields = reinterpret_cast<const float *>(p.fields); tp.foff = p.foff;
         tp.out = reinterpret_cast<float *>(out); tp.out_off = out_offset;
         tp.mat_stride = (int64_t)pr.parts * pr.rows * pr.cols; tp.ld = pr.cols; tp.n_elem = 0;
         tp.n_elem_dev = p.hist + q; tp.elist = p.order; tp.elist_start = p.bstart + q;
-        tp.status = ds->status; tp.smem_bytes = (int)pe->tcc_smem; tp.stall_cta = -1;
+        tp.status = ds->status; tp.smem_bytes = (int)tg.smem; tp.stall_cta = -1;
         TraceRange tr("dpg hp: contraction of one order, FP32, stage C on tcgen05");
-        le = launch_tcc(tp, g_num_sms * pe->tcc_cps, pe->tcc_smem, s);
+        le = launch_tcc(tp, g_num_sms * tg.cps, tg.smem, s);
     }
     if (le != cudaSuccess) rc = cuda_fail(le, "hp launch sequence", __LINE__);
     for (void *w : { wfield, wtmp, wit, wf, wu, word, wsmall }) cudaFreeAsync(w, s);
@@ -1283,7 +1293,7 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
     if (cache) {
         if (FILE *f = std::fopen(cache, "r")) {
             char line[256];
-            int found = 0, found_sym = 0;
+            int found = -1, found_sym = 0;
             while (std::fgets(line, sizeof(line), f)) {
                 int cs, cq, cl, cf, cn, cy = 0;
                 double cms;
@@ -1297,7 +1307,8 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
                 }
             }
             std::fclose(f);
-            if (found > 0 && install_program(pe, te, base, q, L, fp32, found, found_sym) == DPG_OK) {
+            if ((found > 0 || (fp32 && found == 0 && pe->tcc.ok)) &&
+                install_program(pe, te, base, q, L, fp32, found, found_sym) == DPG_OK) {
                 if ((r = update_hp_table(ds, base, q, pe, te))) return r;
                 if (best_nj) *best_nj = found;
                 return DPG_OK;
@@ -1327,7 +1338,8 @@ int dpg_autotune(int q, int space, void *stream, int *best_nj) {
     cudaEventCreate(&a); cudaEventCreate(&b);
     int best = orig;
     float best_ms = 1e30f;
-    for (int nj = 1; nj <= std::min(NJMAX, maxnA); ++nj) {
+    // FP32: nj = 0 is the stage-C tensor-core kernel, nj > 0 the earlier kernels
+    for (int nj = (fp32 && pe->tcc.ok) ? 0 : 1; nj <= std::min(NJMAX, maxnA); ++nj) {
         if (install_program(pe, te, base, q, L, fp32, nj) != DPG_OK) continue;
         float ts[6];
         int nt = 0;

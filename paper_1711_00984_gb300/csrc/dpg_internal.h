@@ -391,7 +391,7 @@ DPG_HD inline TccLayout tcc_layout(const BlockDesc &b, int L) {
     f.oF = (f.oF + 15) & ~15;
     f.oW = f.oF + 4 * distinct_fields(b) * L * L * f.npad;
     f.oW = (f.oW + 15) & ~15;
-    f.wst = 32 * f.nc1 + 4;
+    f.wst = 32 * 20;                       // 32 lanes x 16 columns at a stride of 20 floats
     f.total = a128(f.oW + 4 * 8 * f.wst);
     f.tcols = 32;
     while (f.tcols < 2 * f.N + 16 && f.tcols < 512) f.tcols <<= 1;

@@ -1315,12 +1315,23 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             if (lane < head) orow[lane] = val(lane);
             if (lane < ncolu - tail0) orow[tail0 + lane] = val(tail0 + lane);
             V16 *o16 = reinterpret_cast<V16 *>(orow + head);
-            for (int i = lane; i < nvec; i += 32) {
-                V16 w;
-                T *wv = reinterpret_cast<T *>(&w);
+            if (jd < 0 && !bad) {                               // plain copy (uniform branch)
+                const T *src = trw + head;
+                for (int i = lane; i < nvec; i += 32) {
+                    V16 w;
+                    T *wv = reinterpret_cast<T *>(&w);
 #pragma unroll
-                for (int x = 0; x < VW; ++x) wv[x] = val(head + VW * i + x);
-                o16[i] = w;
+                    for (int x = 0; x < VW; ++x) wv[x] = src[VW * i + x];
+                    o16[i] = w;
+                }
+            } else {
+                for (int i = lane; i < nvec; i += 32) {
+                    V16 w;
+                    T *wv = reinterpret_cast<T *>(&w);
+#pragma unroll
+                    for (int x = 0; x < VW; ++x) wv[x] = val(head + VW * i + x);
+                    o16[i] = w;
+                }
             }
         }
         if (bd.sym != 0) {
@@ -1332,10 +1343,18 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             if (nrow >= 64) {                                   // long runs: a warp per column
                 // (plain stores: lanes reading consecutive tile rows keep the shared-memory
                 // reads conflict-free, which measured faster than 16-byte stores here)
-                for (int mcix = warp; mcix < nmc; mcix += nwarp) {
-                    const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
-                    T *mrow = mbase + (int64_t)c * ld;
-                    for (int row = lane; row < nrow; row += 32) mrow[row] = bad ? nanv : tile[row * ldt + c];
+                if (!bad) {
+                    for (int mcix = warp; mcix < nmc; mcix += nwarp) {
+                        const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                        T *mrow = mbase + (int64_t)c * ld;
+                        for (int row = lane; row < nrow; row += 32) mrow[row] = tile[row * ldt + c];
+                    }
+                } else {
+                    for (int mcix = warp; mcix < nmc; mcix += nwarp) {
+                        const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                        T *mrow = mbase + (int64_t)c * ld;
+                        for (int row = lane; row < nrow; row += 32) mrow[row] = nanv;
+                    }
                 }
             } else {                                            // short runs: full warps
                 const unsigned mnrow = div_magic(nrow);

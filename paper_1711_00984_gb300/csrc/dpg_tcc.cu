@@ -41,6 +41,88 @@ __device__ __forceinline__ bool tcc_row(const TccLayout &f, int t, int rho, unsi
     return x < f.nx;
 }
 
+// Stage A (Eq. 2.23) of one item: thread = (h, l, m), the NC4 x 4 partners j3 in registers.
+template <int NC4>
+__device__ __forceinline__ void tcc_stage_a(const TccLayout &f, const BlockDesc &bd, const float *F, const float *P3,
+                                            float *A, int L, unsigned mLL, unsigned mL, int tid) {
+    const int L2 = L * L, npad = f.npad, nc3 = f.nc3, lpad = f.lpad;
+    for (int task = tid; task < bd.nh * L2; task += TCC_NTH) {
+        const int h = mdiv(task, mLL), lm = task - h * L2;
+        const int l = mdiv(lm, mL), m = lm - l * L;
+        float acc[4 * NC4];
+#pragma unroll
+        for (int j = 0; j < 4 * NC4; ++j) acc[j] = 0.0f;
+        for (int ti = 0; ti < bd.h_nterm[h]; ++ti) {
+            const int t = bd.h_terms[h][ti];
+            const float *Mt = F + (bd.term_slot[t] * L2 + l * L + m) * npad;
+            const float4 *Pt = reinterpret_cast<const float4 *>(P3 + t * L * 4 * NC4);
+            for (int n = 0; n < L; ++n) {
+                const float mv = Mt[n];
+#pragma unroll
+                for (int c4 = 0; c4 < NC4; ++c4) {
+                    const float4 q4 = Pt[n * NC4 + c4];
+                    acc[4 * c4 + 0] = fmaf(mv, q4.x, acc[4 * c4 + 0]);
+                    acc[4 * c4 + 1] = fmaf(mv, q4.y, acc[4 * c4 + 1]);
+                    acc[4 * c4 + 2] = fmaf(mv, q4.z, acc[4 * c4 + 2]);
+                    acc[4 * c4 + 3] = fmaf(mv, q4.w, acc[4 * c4 + 3]);
+                }
+            }
+        }
+        float *dst = A + ((h * L + m) * nc3) * lpad + l;
+#pragma unroll
+        for (int j = 0; j < 4 * NC4; ++j)
+            if (j < nc3) dst[j * lpad] = acc[j];
+    }
+}
+
+// Stage B (Eq. 2.24) of tile t: thread = (g, row rho), the LP4 x 4 values l in registers,
+// written split into TF32 high and low parts to the stage-C A operand.
+template <int LP4>
+__device__ __forceinline__ void tcc_stage_b(const TccLayout &f, const BlockDesc &bd, int t, unsigned mnx,
+                                            unsigned mnc2, const float *P2s, const float *A, float *ach, float *acl,
+                                            int L, int tid) {
+    constexpr int lpad = 4 * LP4;
+    const int sg = f.sbo >> 2, nc3 = f.nc3;
+    for (int task = tid; task < bd.ng * 128; task += TCC_NTH) {
+        const int g = task >> 7, rho = task & 127;
+        int i2, x;
+        if (!tcc_row(f, t, rho, mnx, i2, x)) continue;
+        const int j3 = mdiv(x, mnc2), j2 = x - j3 * f.nc2;
+        float acc[lpad];
+#pragma unroll
+        for (int j = 0; j < lpad; ++j) acc[j] = 0.0f;
+        for (int hi = 0; hi < bd.g_nh[g]; ++hi) {
+            const int h = bd.g_hs[g][hi];
+            const float *p2 = P2s + bd.h_p2[h] * L * f.n22p + i2 * f.nc2 + j2;
+            const float4 *ah = reinterpret_cast<const float4 *>(A + ((h * L) * nc3 + j3) * lpad);
+            for (int m = 0; m < L; ++m) {
+                const float pv = p2[m * f.n22p];
+                const float4 *a4 = ah + m * nc3 * LP4;
+#pragma unroll
+                for (int c4 = 0; c4 < LP4; ++c4) {
+                    const float4 av = a4[c4];
+                    acc[4 * c4 + 0] = fmaf(pv, av.x, acc[4 * c4 + 0]);
+                    acc[4 * c4 + 1] = fmaf(pv, av.y, acc[4 * c4 + 1]);
+                    acc[4 * c4 + 2] = fmaf(pv, av.z, acc[4 * c4 + 2]);
+                    acc[4 * c4 + 3] = fmaf(pv, av.w, acc[4 * c4 + 3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int c4 = 0; c4 < LP4; ++c4) {
+            const int k0 = g * lpad + 4 * c4;
+            const int off = (rho >> 3) * sg + (k0 >> 2) * 32 + (rho & 7) * 4;
+            float4 hv, lv;
+            tf32_split(acc[4 * c4 + 0], hv.x, lv.x);
+            tf32_split(acc[4 * c4 + 1], hv.y, lv.y);
+            tf32_split(acc[4 * c4 + 2], hv.z, lv.z);
+            tf32_split(acc[4 * c4 + 3], hv.w, lv.w);
+            *reinterpret_cast<float4 *>(ach + off) = hv;
+            *reinterpret_cast<float4 *>(acl + off) = lv;
+        }
+    }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(TCC_NTH, 2) sf_tcc_kernel(TccParams p) {
@@ -100,17 +182,19 @@ __global__ void __launch_bounds__(TCC_NTH, 2) sf_tcc_kernel(TccParams p) {
         for (int i1 = half; i1 < nr1; i1 += 2) {
             uint32_t r[16];
             tmem_ld16(tbase + ((uint32_t)(32 * qd) << 16) + dbuf * (uint32_t)f.N + (uint32_t)(i1 * nc1), r);
-            if (valid) {
+            {
+                float4 *w4 = reinterpret_cast<float4 *>(wb + lane * 20);   // lane stride 20: 4 wavefronts
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (j < nc1) wb[lane * nc1 + j] = __uint_as_float(r[j]);
+                for (int c4 = 0; c4 < 4; ++c4)
+                    w4[c4] = make_float4(__uint_as_float(r[4 * c4]), __uint_as_float(r[4 * c4 + 1]),
+                                         __uint_as_float(r[4 * c4 + 2]), __uint_as_float(r[4 * c4 + 3]));
             }
             __syncwarp();
             const int64_t dst = valid ? (rowi + i1) * ld + bd.col_off + (int64_t)x * nc1 : -1;
             for (int kk = lane; kk < 32 * nc1; kk += 32) {
                 const int sl = mdiv(kk, mnc1), j = kk - sl * nc1;
                 const long long d = __shfl_sync(0xffffffffu, (long long)dst, sl);
-                if (d >= 0 && DPG_INB(d + j < p.mat_stride - bd.base, p.status, e)) oe[d + j] = wb[kk];
+                if (d >= 0 && DPG_INB(d + j < p.mat_stride - bd.base, p.status, e)) oe[d + j] = wb[sl * 20 + j];
             }
             __syncwarp();
         }
@@ -194,36 +278,12 @@ __global__ void __launch_bounds__(TCC_NTH, 2) sf_tcc_kernel(TccParams p) {
         }
         __syncthreads();
 
-        // ---- stage A (Eq. 2.23): thread = (h, l, m), every j3 in registers
-        for (int task = tid; task < bd.nh * L2; task += TCC_NTH) {
-            const int h = mdiv(task, mLL), lm = task - h * L2;
-            const int l = mdiv(lm, mL), m = lm - l * L;
-            float acc[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
-            for (int ti = 0; ti < bd.h_nterm[h]; ++ti) {
-                const int t = bd.h_terms[h][ti];
-                const float *Mt = F + (bd.term_slot[t] * L2 + l * L + m) * npad;
-                const float *Pt = P3 + t * L * nc3p;
-                for (int n = 0; n < L; ++n) {
-                    const float mv = Mt[n];
-                    const float4 *p4 = reinterpret_cast<const float4 *>(Pt + n * nc3p);
-#pragma unroll
-                    for (int c4 = 0; c4 < 4; ++c4) {
-                        if (4 * c4 < nc3p) {
-                            const float4 q4 = p4[c4];
-                            acc[4 * c4 + 0] = fmaf(mv, q4.x, acc[4 * c4 + 0]);
-                            acc[4 * c4 + 1] = fmaf(mv, q4.y, acc[4 * c4 + 1]);
-                            acc[4 * c4 + 2] = fmaf(mv, q4.z, acc[4 * c4 + 2]);
-                            acc[4 * c4 + 3] = fmaf(mv, q4.w, acc[4 * c4 + 3]);
-                        }
-                    }
-                }
-            }
-            float *dst = A + ((h * L + m) * nc3) * lpad + l;
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (j < nc3) dst[j * lpad] = acc[j];
+        // ---- stage A (Eq. 2.23)
+        switch (nc3p >> 2) {
+        case 1: tcc_stage_a<1>(f, bd, F, P3, A, L, mLL, mL, tid); break;
+        case 2: tcc_stage_a<2>(f, bd, F, P3, A, L, mLL, mL, tid); break;
+        case 3: tcc_stage_a<3>(f, bd, F, P3, A, L, mLL, mL, tid); break;
+        default: tcc_stage_a<4>(f, bd, F, P3, A, L, mLL, mL, tid); break;
         }
         // padded l entries of A are read by stage B's 16-byte loads: keep them zero
         if (lpad > L)
@@ -237,52 +297,14 @@ __global__ void __launch_bounds__(TCC_NTH, 2) sf_tcc_kernel(TccParams p) {
         const float *P2s = reinterpret_cast<const float *>(smb + f.oP2);
         float *ach = reinterpret_cast<float *>(smb + f.oAC);
         float *acl = reinterpret_cast<float *>(smb + f.oAC + f.acb);
-        const int sg = f.sbo >> 2;
         for (int t = 0; t < f.ntile; ++t) {
             if (ncommit > 0) mbar_wait(&bar, (ncommit - 1) & 1, &fail);   // A_C is free again
             tc_fence_after();
-            // stage B (Eq. 2.24): thread = (g, row rho), every l in registers
-            for (int task = tid; task < bd.ng * 128; task += TCC_NTH) {
-                const int g = task >> 7, rho = task & 127;
-                int i2, x;
-                if (!tcc_row(f, t, rho, mnx, i2, x)) continue;
-                const int j3 = mdiv(x, mnc2), j2 = x - j3 * f.nc2;
-                float acc[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
-                for (int hi = 0; hi < bd.g_nh[g]; ++hi) {
-                    const int h = bd.g_hs[g][hi];
-                    const float *p2 = P2s + bd.h_p2[h] * L * f.n22p + i2 * f.nc2 + j2;
-                    const float *ah = A + ((h * L) * nc3 + j3) * lpad;
-                    for (int m = 0; m < L; ++m) {
-                        const float pv = p2[m * f.n22p];
-                        const float4 *a4 = reinterpret_cast<const float4 *>(ah + m * nc3 * lpad);
-#pragma unroll
-                        for (int c4 = 0; c4 < 4; ++c4) {
-                            if (4 * c4 < lpad) {
-                                const float4 av = a4[c4];
-                                acc[4 * c4 + 0] = fmaf(pv, av.x, acc[4 * c4 + 0]);
-                                acc[4 * c4 + 1] = fmaf(pv, av.y, acc[4 * c4 + 1]);
-                                acc[4 * c4 + 2] = fmaf(pv, av.z, acc[4 * c4 + 2]);
-                                acc[4 * c4 + 3] = fmaf(pv, av.w, acc[4 * c4 + 3]);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    if (4 * c4 < lpad) {
-                        const int k0 = g * lpad + 4 * c4;
-                        const int off = (rho >> 3) * sg + (k0 >> 2) * 32 + (rho & 7) * 4;
-                        float4 hv, lv;
-                        tf32_split(acc[4 * c4 + 0], hv.x, lv.x);
-                        tf32_split(acc[4 * c4 + 1], hv.y, lv.y);
-                        tf32_split(acc[4 * c4 + 2], hv.z, lv.z);
-                        tf32_split(acc[4 * c4 + 3], hv.w, lv.w);
-                        *reinterpret_cast<float4 *>(ach + off) = hv;
-                        *reinterpret_cast<float4 *>(acl + off) = lv;
-                    }
-                }
+            switch (lpad >> 2) {
+            case 1: tcc_stage_b<1>(f, bd, t, mnx, mnc2, P2s, A, ach, acl, L, tid); break;
+            case 2: tcc_stage_b<2>(f, bd, t, mnx, mnc2, P2s, A, ach, acl, L, tid); break;
+            case 3: tcc_stage_b<3>(f, bd, t, mnx, mnc2, P2s, A, ach, acl, L, tid); break;
+            default: tcc_stage_b<4>(f, bd, t, mnx, mnc2, P2s, A, ach, acl, L, tid); break;
             }
             fence_async_smem();
             tc_fence_before();
