@@ -145,7 +145,10 @@ int upload(const T *src, size_t n, T **dst) {
 int upload_aff_image(AffProg &ap, const HostTables &tab, bool extruded, int prec) {
     std::vector<unsigned char> img;
     std::vector<int> off;
-    if (prec) build_k32_image(ap.prog, tab, extruded, img, off);
+    // prec: 0 FP64 image, 1 FP32 image of the dense FP32 Kronecker kernel, 0x11 FP32 image of
+    // the sparse affine kernel
+    if (prec == 1) build_k32_image(ap.prog, tab, extruded, img, off);
+    else if (prec & 1) build_aff_image<float>(ap.prog, tab, extruded, img, off);
     else build_aff_image<double>(ap.prog, tab, extruded, img, off);
     int r;
     if ((r = upload(img.data(), img.size(), &ap.d_img))) return r;
@@ -329,19 +332,19 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         for (int k = 0; k < pk.nblock; ++k) n = std::max(n, (pk.blocks[k].nc[0] + 3) / 4);
         return n;
     };
+    // affine path: every block and every tile computed (rows written once each, no mirrored
+    // column runs); the algorithmic flops are those of the symmetric program
+    const double flops_aff = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL, 0, 72 * 1024).flops_affine;
+    (void)k32_program;
     for (int prec = 0; prec < 2; ++prec) {
         AffProg &ap = pe->aff[prec];
-        ap.prog = prec == 0 ? make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL, 0, 72 * 1024)
-                            : k32_program(false);
+        ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL_ALL, 0, prec == 0 ? 72 * 1024 : 0);
         const Program &pa = ap.prog;
         if ((r = upload(pa.blocks, (size_t)pa.nblock, &ap.d_blocks))) return r;
         if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
         size_t m = 0;
-        for (int k = 0; k < pa.nblock; ++k)
-            m = std::max(m, prec ? kron32_smem_values(pa.blocks[k], L, pa.nj, false)
-                                 : affine_smem_values(pa.blocks[k], pa.nj));
-        if (prec) ap.nc4 = k32_nc4(pa);
-        if ((r = upload_aff_image(ap, tab, false, prec))) return r;
+        for (int k = 0; k < pa.nblock; ++k) m = std::max(m, affine_smem_values(pa.blocks[k], pa.nj));
+        if ((r = upload_aff_image(ap, tab, false, 0x10 | prec))) return r;
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
         for (int k = 0; k < pa.nblock; ++k) ub[k + 1] += ub[k];
@@ -349,7 +352,7 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         if (m * (prec ? sizeof(float) : sizeof(double)) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
         ap.smem_values = m;
     }
-    pe->flops_aff = pe->aff[0].prog.flops_affine;
+    pe->flops_aff = flops_aff;
     for (int prec = 0; prec < 2; ++prec) {
         AffProg &ap = pe->ext[prec];
         const size_t esz = prec ? sizeof(float) : sizeof(double);
@@ -712,8 +715,7 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne; ap.status = ds->status;
         {
             TraceRange tr("dpg contraction: affine");
-            if constexpr (sizeof(T) == 4) le = launch_kron32(ap, aprog.smem_values * sizeof(T), aprog.nc4, false, s);
-        else le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
+            le = launch_affine<T>(ap, aprog.smem_values * sizeof(T), s);
         }
         if (le != cudaSuccess) rc = cuda_fail(le, "sf_affine_kernel launch", __LINE__);
     }

@@ -279,7 +279,7 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
     for (int a = 0; a < nR; ++a)
     for (int b = 0; b < nC; ++b) {
         bool symmetric = space <= S_L2 && order != ORDER_PANEL && order != ORDER_TC && order != ORDER_K32 &&
-                         order != ORDER_K32_EXT && order != ORDER_TCC;
+                         order != ORDER_K32_EXT && order != ORDER_TCC && order != ORDER_NATURAL_ALL;
         if (symmetric && b < a) continue;             // lower blocks come from mirroring
         for (int part = 0; part < pr.parts; ++part) {
             std::vector<TermSpec> ts;
@@ -371,7 +371,7 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             // ORDER_A3 keeps stage A on xi_3, ORDER_NATURAL keeps the paper's order
             static const int perms[6][3] = { { 0, 1, 2 }, { 1, 0, 2 }, { 0, 2, 1 },
                                              { 2, 0, 1 }, { 1, 2, 0 }, { 2, 1, 0 } };
-            const int nperm = (order == ORDER_NATURAL || order == ORDER_PANEL || order == ORDER_TC ||
+            const int nperm = (order == ORDER_NATURAL || order == ORDER_NATURAL_ALL || order == ORDER_PANEL || order == ORDER_TC ||
                                order == ORDER_EXTRUDED || order == ORDER_K32 || order == ORDER_K32_EXT ||
                                order == ORDER_TCC)
                                   ? 1 : (order == ORDER_A3 ? 2 : 6);
@@ -394,7 +394,8 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             const TcLayout t = tc_layout(b, L, njv);
             return t.ok ? (size_t)t.total : SIZE_MAX;
         }
-        if (order == ORDER_NATURAL) return (size_t)aff_layout_block(b, njv).total * sizeof(double);
+        if (order == ORDER_NATURAL || order == ORDER_NATURAL_ALL)
+            return (size_t)aff_layout_block(b, njv).total * sizeof(double);
         if (order == ORDER_EXTRUDED) return (size_t)ext_layout(b, L, njv).total * sizeof(double);
         if (order == ORDER_TCC) {
             const TccLayout t = tcc_layout(b, L);

@@ -47,7 +47,10 @@ HostTables make_tables(int q, int L);
 // ORDER_K32 / ORDER_K32_EXT: the paper's order and every (a, b) block built (no mirrored
 // tiles), sized for the FP32 Kronecker kernel of the affine / extruded paths (k32_layout).
 enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3, ORDER_TC = 4, ORDER_EXTRUDED = 5,
-       ORDER_K32 = 6, ORDER_K32_EXT = 7, ORDER_TCC = 8 };
+       ORDER_K32 = 6, ORDER_K32_EXT = 7, ORDER_TCC = 8, ORDER_NATURAL_ALL = 9 };
+// ORDER_NATURAL_ALL: ORDER_NATURAL with every (a, b) block built and every tile of the
+// diagonal blocks computed (no mirrored tiles): the affine kernel then writes every output
+// row itself as one contiguous run.
 // ORDER_TCC: the paper's order and every block built, for the FP32 general kernel with stage C
 // on the tensor cores (tcc_layout); a block that does not fit it makes smem_bytes SIZE_MAX.
 // force_nj > 0 fixes the stage-A chunk (autotuner); otherwise the largest chunk whose
