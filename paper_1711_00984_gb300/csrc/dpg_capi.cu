@@ -49,7 +49,6 @@ struct AffProg {
     unsigned char *d_img = nullptr; // constant shared-memory images of the blocks
     int *d_img_off = nullptr;       // [nblock + 1], 16-byte units
     size_t smem_values = 0;         // values of the kernel's shared memory
-    int nc4 = 1;                    // FP32 Kronecker kernel: largest ceil(nc1 / 4) of the blocks
 };
 
 // Program of the FP32 general kernel with stage C on the tensor cores (sf_tcc_kernel).
@@ -145,10 +144,7 @@ int upload(const T *src, size_t n, T **dst) {
 int upload_aff_image(AffProg &ap, const HostTables &tab, bool extruded, int prec) {
     std::vector<unsigned char> img;
     std::vector<int> off;
-    // prec: 0 FP64 image, 1 FP32 image of the dense FP32 Kronecker kernel, 0x11 FP32 image of
-    // the sparse affine kernel
-    if (prec == 1) build_k32_image(ap.prog, tab, extruded, img, off);
-    else if (prec & 1) build_aff_image<float>(ap.prog, tab, extruded, img, off);
+    if (prec) build_aff_image<float>(ap.prog, tab, extruded, img, off);
     else build_aff_image<double>(ap.prog, tab, extruded, img, off);
     int r;
     if ((r = upload(img.data(), img.size(), &ap.d_img))) return r;
@@ -318,33 +314,15 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
     int r;
     if ((r = upload(pr.blocks, (size_t)pr.nblock, &pe->d_blocks))) return r;
     if ((r = upload(pr.units.data(), pr.units.size(), &pe->d_units))) return r;
-    // the FP32 Kronecker kernel: the largest chunk whose shared memory fits four CTAs per SM,
-    // else the largest that fits
-    auto k32_program = [&](bool ext) {
-        Program pk = make_program(space, q, L, p, split != 0, tab, ext ? ORDER_K32_EXT : ORDER_K32, 0, 52 * 1024);
-        if (pk.smem_bytes > 52 * 1024)
-            pk = make_program(space, q, L, p, split != 0, tab, ext ? ORDER_K32_EXT : ORDER_K32, 0,
-                              (size_t)g_max_dyn_smem);
-        return pk;
-    };
-    auto k32_nc4 = [](const Program &pk) {
-        int n = 1;
-        for (int k = 0; k < pk.nblock; ++k) n = std::max(n, (pk.blocks[k].nc[0] + 3) / 4);
-        return n;
-    };
-    // affine path: every block and every tile computed (rows written once each, no mirrored
-    // column runs); the algorithmic flops are those of the symmetric program
-    const double flops_aff = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL, 0, 72 * 1024).flops_affine;
-    (void)k32_program;
     for (int prec = 0; prec < 2; ++prec) {
         AffProg &ap = pe->aff[prec];
-        ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL_ALL, 0, prec == 0 ? 72 * 1024 : 0);
+        ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_NATURAL, 0, prec == 0 ? 72 * 1024 : 0);
         const Program &pa = ap.prog;
         if ((r = upload(pa.blocks, (size_t)pa.nblock, &ap.d_blocks))) return r;
         if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
         size_t m = 0;
         for (int k = 0; k < pa.nblock; ++k) m = std::max(m, affine_smem_values(pa.blocks[k], pa.nj));
-        if ((r = upload_aff_image(ap, tab, false, 0x10 | prec))) return r;
+        if ((r = upload_aff_image(ap, tab, false, prec))) return r;
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
         for (int k = 0; k < pa.nblock; ++k) ub[k + 1] += ub[k];
@@ -352,27 +330,21 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         if (m * (prec ? sizeof(float) : sizeof(double)) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
         ap.smem_values = m;
     }
-    pe->flops_aff = flops_aff;
+    pe->flops_aff = pe->aff[0].prog.flops_affine;
     for (int prec = 0; prec < 2; ++prec) {
         AffProg &ap = pe->ext[prec];
         const size_t esz = prec ? sizeof(float) : sizeof(double);
-        if (prec) {
-            ap.prog = k32_program(true);
-        } else {
-            // the largest chunk whose shared memory fits three CTAs per SM, else the largest that fits
-            size_t budget = (size_t)72 * 1024;
-            ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0, budget);
-            if (ap.prog.smem_bytes > budget)
-                ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0, (size_t)g_max_dyn_smem);
-        }
+        // the largest chunk whose shared memory fits three CTAs per SM, else the largest that fits
+        size_t budget = (size_t)72 * 1024 * sizeof(double) / esz;
+        ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0, budget);
+        if (ap.prog.smem_bytes > budget)
+            ap.prog = make_program(space, q, L, p, split != 0, tab, ORDER_EXTRUDED, 0,
+                                   (size_t)g_max_dyn_smem * sizeof(double) / esz);
         const Program &pa = ap.prog;
         if ((r = upload(pa.blocks, (size_t)pa.nblock, &ap.d_blocks))) return r;
         if ((r = upload(pa.units.data(), pa.units.size(), &ap.d_units))) return r;
         size_t m = 0;
-        for (int k = 0; k < pa.nblock; ++k)
-            m = std::max(m, prec ? kron32_smem_values(pa.blocks[k], L, pa.nj, true)
-                                 : extruded_smem_values(pa.blocks[k], L, pa.nj));
-        if (prec) ap.nc4 = k32_nc4(pa);
+        for (int k = 0; k < pa.nblock; ++k) m = std::max(m, extruded_smem_values(pa.blocks[k], L, pa.nj));
         if ((r = upload_aff_image(ap, tab, true, prec))) return r;
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
@@ -782,8 +754,7 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         ap.mat_stride = mat; ap.ld = og.ld; ap.n_elem = ne; ap.status = ds->status;
         {
             TraceRange tr("dpg contraction: extruded");
-            if constexpr (sizeof(T) == 4) le = launch_kron32(ap, aprog.smem_values * sizeof(T), aprog.nc4, true, s);
-            else le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
+            le = launch_extruded<T>(ap, aprog.smem_values * sizeof(T), s);
         }
         if (le != cudaSuccess) { rc = cuda_fail(le, "extruded contraction launch", __LINE__); break; }
     }

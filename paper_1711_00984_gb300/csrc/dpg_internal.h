@@ -170,42 +170,6 @@ DPG_HD inline ExtLayout ext_layout(const BlockDesc &b, int L, int nj) {
     return x;
 }
 
-// Shared-memory layout (in floats, every region 16-byte aligned) of the FP32 Kronecker
-// kernel (affine and extruded maps in the FP32 form) for one block in the paper's direction
-// order and a chunk of nj stage-A partners.  Every block of the matrix is computed (no
-// mirrored tiles).  The constant image [0, oC): the exact stage-C integrals F1 dense
-// [ng][nr1][nc1p] (j1 padded to a multiple of 4 with zeros), then the exact stage-B
-// integrals F2 [nterm][(i2, j2)] (affine) or the stage-B pair products P2 [np2][(i2, j2)][m]
-// at the Gauss points (extruded).  Per unit: Q [ng][(i2, x)] with x = j2 + nc2 jj, the
-// extruded map's element fields [nfs][L][L], stage-A factors S3 [nterm][nj][L] and stage-A
-// output A [nh][L][nj], and the output tile [nrow][ldt]: tile row r = i1 + nr1 i2 holds the
-// columns c = j1 + nc1 x at r ldt + m_r + c, where m_r (0..3) is the destination row's
-// offset from 16-byte alignment, so that tile and destination float4s coincide.
-struct K32Layout {
-    int nc1p, n22, nx, nf, nrow, ncol, ldt, nfs;
-    int oF1, oF2, oP2, oC, oQ, oFx, oS3, oA, oT, total;
-};
-constexpr int K32_MAXROW = 176;    // tile rows nr1 nr2 <= 13 * 13
-DPG_HD inline K32Layout k32_layout(const BlockDesc &b, int L, int nj, bool ext) {
-    K32Layout k;
-    const int nr1 = b.nr[0], nr2 = b.nr[1], nc1 = b.nc[0], nc2 = b.nc[1];
-    k.nc1p = r4i(nc1);
-    k.n22 = nr2 * nc2; k.nx = nc2 * nj; k.nf = nr2 * k.nx;
-    k.nrow = nr1 * nr2; k.ncol = nc1 * k.nx; k.ldt = r4i(k.ncol) + 4;
-    k.nfs = ext ? distinct_fields(b) : 0;
-    k.oF1 = 0;
-    k.oF2 = k.oF1 + r4i(b.ng * nr1 * k.nc1p);
-    k.oP2 = k.oF2 + (ext ? 0 : r4i(b.nterm * k.n22));
-    k.oC = k.oP2 + (ext ? r4i(b.np2 * k.n22 * L) : 0);
-    k.oQ = k.oC;
-    k.oFx = k.oQ + r4i(b.ng * k.nf);
-    k.oS3 = k.oFx + (ext ? r4i(k.nfs * L * L) : 0);
-    k.oA = k.oS3 + (ext ? r4i(b.nterm * nj * L) : 0);
-    k.oT = k.oA + (ext ? r4i(b.nh * L * nj) : 0);
-    k.total = k.oT + k.nrow * k.ldt;
-    return k;
-}
-
 // Shared-memory layout (in floats, every region 16-byte aligned) of the FP32 row-panel
 // kernel for one block in the paper's direction order (stage C over xi_1, B over xi_2, A
 // over xi_3) and a chunk of nj stage-A partners.  Stages B and C are tensor-core

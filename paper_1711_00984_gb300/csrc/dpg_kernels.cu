@@ -1372,220 +1372,6 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
 size_t affine_smem_values(const BlockDesc &b, int nj) { return (size_t)aff_layout_block(b, nj).total; }
 
 // --------------------------------------------------------------------------------------
-// FP32 form of the affine (Sec. 2.8.1, Algorithm 10) and extruded (Algorithm 11) paths
-// --------------------------------------------------------------------------------------
-// Output-bound: on the FP32 pipe the Kronecker products cost less than writing them, so
-// stage C is computed densely (no non-zero lists, no zero-fill, no atomics) and every block
-// of the matrix is computed (no mirrored column runs): a thread takes one (i2, x = j2 +
-// nc2 jj) of the unit, keeps its ng values Q_g(i2, x) in registers and, for every i1,
-// forms the nc1 values sum_g F1_g(i1, j1) Q_g(i2, x) with the F1 row broadcast from shared
-// memory (four values per load); the values go to the tile at the destination's 16-byte
-// phase, and each tile row leaves as one run of 16-byte stores.  A CTA takes (a chunk of
-// elements, a block, a share of the block's units) like the FP64 kernel.
-template <bool EXT, int NC4>
-__global__ void __launch_bounds__(256) sf_kron32_kernel(AffParams<float> p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *sm = reinterpret_cast<float *>(smem_raw);
-    __shared__ BlockDesc bd;
-    __shared__ float cf[MAXFIELDS];
-    __shared__ int flag;
-    __shared__ float st[MAXT * NJMAX];           // s_t(jj) = sign_t c_t F3_t(i3, j3) (affine)
-    __shared__ int rsh[K32_MAXROW];              // 16-byte phase of each destination row
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int nsplit = p.nsplit;
-    const int ks = blockIdx.x % (p.nblock * nsplit);
-    const int k = ks / nsplit, split = ks - k * nsplit;
-    const int64_t e0 = (int64_t)(blockIdx.x / (p.nblock * nsplit)) * p.elems_per_cta;
-    const int64_t e1 = min(e0 + (int64_t)p.elems_per_cta, p.n_elem);
-    if (e0 >= e1) return;
-    load_block(p.blocks + k, bd);
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(p.img) + p.img_off16[k];
-        uint4 *dst = reinterpret_cast<uint4 *>(smem_raw);
-        const int n16 = p.img_off16[k + 1] - p.img_off16[k];
-        for (int i = tid; i < n16; i += nth) dst[i] = src[i];
-    }
-    __syncthreads();
-    const int nr1 = bd.nr[0], nr2 = bd.nr[1], nc1 = bd.nc[0], nc2 = bd.nc[1];
-    const int ng = bd.ng, nterm = bd.nterm, njm = p.nj_max;
-    const int n22 = nr2 * nc2, nrow = nr1 * nr2;
-    const int L = p.L, L2 = L * L;
-    const K32Layout lay = k32_layout(bd, L, njm, EXT);
-#if defined(DPG_DEBUG_BOUNDS)
-    if (!DPG_INB((size_t)lay.total * 4 <= dpg_dyn_smem_bytes() && nrow <= K32_MAXROW && lay.nc1p <= 4 * NC4 &&
-                 (p.img_off16[k + 1] - p.img_off16[k]) * 4 <= lay.oC, p.status, e0))
-        return;                                                         // uniform
-#endif
-    const float *F1 = sm + lay.oF1, *F2 = sm + lay.oF2, *P2 = sm + lay.oP2;
-    float *Q = sm + lay.oQ, *T = sm + lay.oT;
-    [[maybe_unused]] float *Fx = sm + lay.oFx, *S3 = sm + lay.oS3, *Ah = sm + lay.oA;
-    const int nc1p = lay.nc1p, ldt = lay.ldt;
-    const float *F = p.F;
-    const int64_t ld = p.ld;
-    const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
-    const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
-    const int64_t msz = p.mat_stride - bd.base;
-    (void)msz;
-    for (int64_t e = e0; e < e1; ++e) {
-        __syncthreads();                                                // previous element done
-        if constexpr (!EXT) {
-            if (tid < MAXFIELDS) cf[tid] = (float)p.consts[AFF_CONST_STRIDE * e + tid];
-            if (tid == MAXFIELDS) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
-        } else {
-            if (tid == 0) flag = p.estatus[e];
-            const float *src = p.xfields + (size_t)e * p.nfields * L2;
-            for (int it = tid; it < bd.nslot * L2; it += nth) {
-                const int sl = it / L2;
-                Fx[it] = src[(size_t)bd.slot_field[sl] * L2 + (it - sl * L2)];
-            }
-        }
-        __syncthreads();
-        float *o = p.out + (size_t)e * p.mat_stride + bd.base;
-        const bool bad = flag != 0;
-        for (int ui = ub + split; ui < ue; ui += nsplit) {
-            const Unit u = p.units[ui];
-            const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
-            const int nx = nc2 * nj, nf = nr2 * nx, ncol = nc1 * nx;
-            const unsigned mnj = div_magic(nj), mnx = div_magic(nx), mnc2 = div_magic(nc2);
-            const int64_t R0 = bd.row_off + (int64_t)i3 * nrow;
-            const int64_t C0 = bd.col_off + (int64_t)j3b * nc1 * nc2;
-            __syncthreads();                                            // previous tile written
-            for (int r = tid; r < nrow; r += nth)
-                rsh[r] = (int)((reinterpret_cast<uintptr_t>(o + (R0 + r) * ld + C0) >> 2) & 3);
-            if constexpr (!EXT) {
-                for (int it = tid; it < nterm * nj; it += nth) {
-                    const int t = fdiv(it, mnj), jj = it - t * nj;
-                    const TermDesc &td = bd.term[t];
-                    const float f3 = F[((size_t)(3 * td.kr[2] + td.kc[2]) * NQ1 + i3) * NQ1 + j3b + jj];
-                    st[it] = (td.sign > 0 ? cf[td.field] : -cf[td.field]) * f3;
-                }
-            } else {
-                for (int it = tid; it < nterm * nj * L; it += nth) {   // S3_t(jj, n), sign folded in
-                    const int r = it / L, n = it - r * L, t = fdiv(r, mnj), jj = r - t * nj;
-                    const TermDesc &td = bd.term[t];
-                    const float v = p.pp[(((size_t)(3 * td.kr[2] + td.kc[2]) * NQ1 + i3) * NQ1 + j3b + jj) * L + n];
-                    S3[it] = td.sign > 0 ? v : -v;
-                }
-            }
-            __syncthreads();
-            if constexpr (EXT) {
-                // stage A over xi3 (Eq. 2.23 on the 2D fields): A_h[m][jj]
-                for (int it = tid; it < bd.nh * L * nj; it += nth) {
-                    const int r = fdiv(it, mnj), jj = it - r * nj, h = r / L, m = r - h * L;
-                    float acc = 0.0f;
-                    for (int ti = 0; ti < bd.h_nterm[h]; ++ti) {
-                        const int t = bd.h_terms[h][ti];
-                        const float *M = Fx + bd.term_slot[t] * L2 + m * L;
-                        const float *s3 = S3 + (t * nj + jj) * L;
-                        for (int n = 0; n < L; ++n) acc = fmaf(M[n], s3[n], acc);
-                    }
-                    Ah[it] = acc;
-                }
-                __syncthreads();
-                // stage B over xi2 (Eq. 2.24): Q_g(i2, x)
-                for (int f = tid; f < ng * nf; f += nth) {
-                    const int g = f / nf, fx = f - g * nf;
-                    const int i2 = fdiv(fx, mnx), x = fx - i2 * nx, jj = fdiv(x, mnc2), j2 = x - jj * nc2;
-                    float acc = 0.0f;
-                    for (int hi = 0; hi < bd.g_nh[g]; ++hi) {
-                        const int h = bd.g_hs[g][hi];
-                        const float *p2 = P2 + (bd.h_p2[h] * n22 + i2 * nc2 + j2) * L;
-                        const float *a = Ah + h * L * nj + jj;
-                        for (int m = 0; m < L; ++m) acc = fmaf(p2[m], a[m * nj], acc);
-                    }
-                    Q[f] = acc;
-                }
-            } else {
-                // Q_g(i2, x) = sum_{t in g} s_t(jj) F2_t(i2, j2)
-                for (int f = tid; f < ng * nf; f += nth) {
-                    const int g = f / nf, fx = f - g * nf;
-                    const int i2 = fdiv(fx, mnx), x = fx - i2 * nx, jj = fdiv(x, mnc2), j2 = x - jj * nc2;
-                    float acc = 0.0f;
-                    for (int k2 = 0; k2 < bd.g_nterm[g]; ++k2) {
-                        const int t = bd.g_terms[g][k2];
-                        acc = fmaf(st[t * nj + jj], F2[t * n22 + i2 * nc2 + j2], acc);
-                    }
-                    Q[f] = acc;
-                }
-            }
-            __syncthreads();
-            // stage C (Eq. 2.25 with exact xi_1 integrals): dense Kronecker products, a
-            // thread per (i1, i2, x)
-            const unsigned mnf = div_magic(nf);
-            for (int task = tid; task < nr1 * nf; task += nth) {
-                const int i1 = fdiv(task, mnf), f = task - i1 * nf;
-                const int i2 = fdiv(f, mnx), x = f - i2 * nx;
-                float qv[MAXG];
-#pragma unroll
-                for (int g = 0; g < MAXG; ++g) qv[g] = g < ng ? Q[g * nf + f] : 0.0f;
-                {
-                    float acc[4 * NC4];
-#pragma unroll
-                    for (int j = 0; j < 4 * NC4; ++j) acc[j] = 0.0f;
-#pragma unroll
-                    for (int g = 0; g < MAXG; ++g) {
-                        if (g < ng) {
-                            const float4 *fr = reinterpret_cast<const float4 *>(F1 + (g * nr1 + i1) * nc1p);
-#pragma unroll
-                            for (int c4 = 0; c4 < NC4; ++c4) {
-                                const float4 v = fr[c4];
-                                acc[4 * c4 + 0] = fmaf(v.x, qv[g], acc[4 * c4 + 0]);
-                                acc[4 * c4 + 1] = fmaf(v.y, qv[g], acc[4 * c4 + 1]);
-                                acc[4 * c4 + 2] = fmaf(v.z, qv[g], acc[4 * c4 + 2]);
-                                acc[4 * c4 + 3] = fmaf(v.w, qv[g], acc[4 * c4 + 3]);
-                            }
-                        }
-                    }
-                    const int r = i1 + nr1 * i2;
-                    float *trow = T + r * ldt + rsh[r] + x * nc1;
-#pragma unroll
-                    for (int j = 0; j < 4 * NC4; ++j)
-                        if (j < nc1) trow[j] = acc[j];
-                }
-            }
-            __syncthreads();
-            // write-out: a warp per tile row, 16-byte stores for the aligned body
-            const float nanv = qnan<float>();
-            for (int r = warp; r < nrow; r += nwarp) {
-                if (!DPG_INB((R0 + r) * ld + C0 + ncol <= msz, p.status, e)) continue;
-                float *orow = o + (R0 + r) * ld + C0;
-                const int m = rsh[r];
-                const float *trow = T + r * ldt + m;
-                const int head = min((4 - m) & 3, ncol);
-                const int n4 = (ncol - head) >> 2, tail = head + 4 * n4;
-                if (lane < head) orow[lane] = bad ? nanv : trow[lane];
-                if (lane < ncol - tail) orow[tail + lane] = bad ? nanv : trow[tail + lane];
-                const float4 *t4 = reinterpret_cast<const float4 *>(trow + head);
-                float4 *o4 = reinterpret_cast<float4 *>(orow + head);
-                for (int c = lane; c < n4; c += 32) o4[c] = bad ? make_float4(nanv, nanv, nanv, nanv) : t4[c];
-            }
-        }
-    }
-}
-
-size_t kron32_smem_values(const BlockDesc &b, int L, int nj, bool ext) {
-    return (size_t)k32_layout(b, L, nj, ext).total;
-}
-
-template <bool EXT>
-static cudaError_t launch_kron32_t(const AffParams<float> &p, size_t smem, int nc4, cudaStream_t s) {
-    const int64_t ctas = (int64_t)p.nblock * p.nsplit * ((p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta);
-    if (ctas == 0) return cudaSuccess;
-    switch (nc4) {
-    case 1: sf_kron32_kernel<EXT, 1><<<(unsigned)ctas, 256, smem, s>>>(p); break;
-    case 2: sf_kron32_kernel<EXT, 2><<<(unsigned)ctas, 256, smem, s>>>(p); break;
-    case 3: sf_kron32_kernel<EXT, 3><<<(unsigned)ctas, 256, smem, s>>>(p); break;
-    default: sf_kron32_kernel<EXT, 4><<<(unsigned)ctas, 256, smem, s>>>(p); break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_kron32(const AffParams<float> &p, size_t smem, int nc4, bool extruded, cudaStream_t s) {
-    return extruded ? launch_kron32_t<true>(p, smem, nc4, s) : launch_kron32_t<false>(p, smem, nc4, s);
-}
-
-
-// --------------------------------------------------------------------------------------
 // hp batching: elements of mixed order q in one persistent launch
 // --------------------------------------------------------------------------------------
 // Work generation runs on the device (no host synchronisation, capturable in a CUDA
@@ -2150,14 +1936,6 @@ cudaError_t init_kernel_attributes(int optin_smem) {
         return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     };
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = one((const void *)sf_kron32_kernel<false, 1>);
-    if (e == cudaSuccess) e = one((const void *)sf_kron32_kernel<false, 2>);
-    if (e == cudaSuccess) e = one((const void *)sf_kron32_kernel<false, 3>);
-    if (e == cudaSuccess) e = one((const void *)sf_kron32_kernel<false, 4>);
-    if (e == cudaSuccess) e = one((const void *)sf_kron32_kernel<true, 1>);
-    if (e == cudaSuccess) e = one((const void *)sf_kron32_kernel<true, 2>);
-    if (e == cudaSuccess) e = one((const void *)sf_kron32_kernel<true, 3>);
-    if (e == cudaSuccess) e = one((const void *)sf_kron32_kernel<true, 4>);
     if (e == cudaSuccess) e = one((const void *)sf_general_kernel<double>);
     if (e == cudaSuccess) e = one((const void *)sf_general_kernel<float>);
     if (e == cudaSuccess) e = one((const void *)hp_contract_kernel<double>);

@@ -276,11 +276,6 @@ cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s)
 // products of 128 x 256 x 8; *status (device) is set to 1 if a bounded wait ran out.
 cudaError_t launch_tc_tf32_peak(int ctas, int iters, int *status, cudaStream_t s);
 size_t affine_smem_values(const BlockDesc &b, int nj);
-// FP32 form of the affine / extruded paths (dense Kronecker products, every block computed):
-// programs of order ORDER_K32 / ORDER_K32_EXT, images of build_k32_image; nc4 = the largest
-// ceil(nc1 / 4) of the program's blocks.
-size_t kron32_smem_values(const BlockDesc &b, int L, int nj, bool ext);
-cudaError_t launch_kron32(const AffParams<float> &p, size_t smem, int nc4, bool extruded, cudaStream_t s);
 int max_dynamic_smem(int optin_smem);
 
 }  // namespace dpg

@@ -278,8 +278,7 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
 
     for (int a = 0; a < nR; ++a)
     for (int b = 0; b < nC; ++b) {
-        bool symmetric = space <= S_L2 && order != ORDER_PANEL && order != ORDER_TC && order != ORDER_K32 &&
-                         order != ORDER_K32_EXT && order != ORDER_TCC && order != ORDER_NATURAL_ALL;
+        bool symmetric = space <= S_L2 && order != ORDER_PANEL && order != ORDER_TC && order != ORDER_TCC;
         if (symmetric && b < a) continue;             // lower blocks come from mirroring
         for (int part = 0; part < pr.parts; ++part) {
             std::vector<TermSpec> ts;
@@ -371,9 +370,8 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             // ORDER_A3 keeps stage A on xi_3, ORDER_NATURAL keeps the paper's order
             static const int perms[6][3] = { { 0, 1, 2 }, { 1, 0, 2 }, { 0, 2, 1 },
                                              { 2, 0, 1 }, { 1, 2, 0 }, { 2, 1, 0 } };
-            const int nperm = (order == ORDER_NATURAL || order == ORDER_NATURAL_ALL || order == ORDER_PANEL || order == ORDER_TC ||
-                               order == ORDER_EXTRUDED || order == ORDER_K32 || order == ORDER_K32_EXT ||
-                               order == ORDER_TCC)
+            const int nperm = (order == ORDER_NATURAL || order == ORDER_PANEL || order == ORDER_TC ||
+                               order == ORDER_EXTRUDED || order == ORDER_TCC)
                                   ? 1 : (order == ORDER_A3 ? 2 : 6);
             double best = 0.0; int bi = 0;
             for (int k = 0; k < nperm; ++k) {
@@ -394,15 +392,12 @@ Program make_program(int space, int q, int L, int p, bool split, const HostTable
             const TcLayout t = tc_layout(b, L, njv);
             return t.ok ? (size_t)t.total : SIZE_MAX;
         }
-        if (order == ORDER_NATURAL || order == ORDER_NATURAL_ALL)
-            return (size_t)aff_layout_block(b, njv).total * sizeof(double);
+        if (order == ORDER_NATURAL) return (size_t)aff_layout_block(b, njv).total * sizeof(double);
         if (order == ORDER_EXTRUDED) return (size_t)ext_layout(b, L, njv).total * sizeof(double);
         if (order == ORDER_TCC) {
             const TccLayout t = tcc_layout(b, L);
             return t.ok ? (size_t)t.total : SIZE_MAX;
         }
-        if (order == ORDER_K32 || order == ORDER_K32_EXT)
-            return (size_t)k32_layout(b, L, njv, order == ORDER_K32_EXT).total * sizeof(float);
         return smem_values(b, L, njv) * sizeof(double);
     };
     // (ORDER_PANEL: the largest chunk that fits one CTA per SM; the launch takes two
@@ -682,41 +677,6 @@ void build_aff_image(const Program &pr, const HostTables &tab, bool extruded, st
     off16[pr.nblock] = (int)(img.size() / 16);
     if (img.empty()) img.resize(16, 0);
 }
-void build_k32_image(const Program &pr, const HostTables &tab, bool extruded, std::vector<unsigned char> &img,
-                     std::vector<int> &off16) {
-    img.clear();
-    off16.assign(pr.nblock + 1, 0);
-    const int L = pr.L;
-    auto Fv = [&](int pair, int i, int j) { return (float)tab.F[((size_t)pair * NQ1 + i) * NQ1 + j]; };
-    auto ppv = [&](int pair, int i, int j, int l) {
-        return (float)tab.pp[(((size_t)pair * NQ1 + i) * NQ1 + j) * L + l];
-    };
-    for (int k = 0; k < pr.nblock; ++k) {
-        const BlockDesc &b = pr.blocks[k];
-        const K32Layout a = k32_layout(b, L, pr.nj, extruded);
-        off16[k] = (int)(img.size() / 16);
-        std::vector<float> t((size_t)a.oC, 0.0f);
-        const int n22 = b.nr[1] * b.nc[1];
-        for (int g = 0; g < b.ng; ++g)                  // F1_g(i1, j1), j1 padded with zeros
-            for (int i1 = 0; i1 < b.nr[0]; ++i1)
-                for (int j1 = 0; j1 < b.nc[0]; ++j1) t[a.oF1 + (g * b.nr[0] + i1) * a.nc1p + j1] = Fv(b.g_pair[g], i1, j1);
-        if (!extruded)                                  // F2_t(i2, j2)
-            for (int t2 = 0; t2 < b.nterm; ++t2)
-                for (int ij = 0; ij < n22; ++ij)
-                    t[a.oF2 + t2 * n22 + ij] = Fv(3 * b.term[t2].kr[1] + b.term[t2].kc[1], ij / b.nc[1], ij % b.nc[1]);
-        else                                            // P2[slot][(i2, j2)][m]
-            for (int s2 = 0; s2 < b.np2; ++s2)
-                for (int ij = 0; ij < n22; ++ij)
-                    for (int m = 0; m < L; ++m)
-                        t[a.oP2 + (s2 * n22 + ij) * L + m] = ppv(b.p2_pair[s2], ij / b.nc[1], ij % b.nc[1], m);
-        t.resize((t.size() + 3) & ~size_t(3), 0.0f);
-        const unsigned char *bytes = reinterpret_cast<const unsigned char *>(t.data());
-        img.insert(img.end(), bytes, bytes + t.size() * sizeof(float));
-    }
-    off16[pr.nblock] = (int)(img.size() / 16);
-    if (img.empty()) img.resize(16, 0);
-}
-
 template void build_aff_image<double>(const Program &, const HostTables &, bool, std::vector<unsigned char> &,
                                       std::vector<int> &);
 template void build_aff_image<float>(const Program &, const HostTables &, bool, std::vector<unsigned char> &,

@@ -44,13 +44,8 @@ HostTables make_tables(int q, int L);
 // kernel (tc_layout); a block that does not fit it makes the program's smem_bytes
 // SIZE_MAX.
 // ORDER_EXTRUDED: the paper's order, sized for the extruded-map kernel (ext_layout).
-// ORDER_K32 / ORDER_K32_EXT: the paper's order and every (a, b) block built (no mirrored
-// tiles), sized for the FP32 Kronecker kernel of the affine / extruded paths (k32_layout).
 enum { ORDER_BEST = 0, ORDER_A3 = 1, ORDER_NATURAL = 2, ORDER_PANEL = 3, ORDER_TC = 4, ORDER_EXTRUDED = 5,
-       ORDER_K32 = 6, ORDER_K32_EXT = 7, ORDER_TCC = 8, ORDER_NATURAL_ALL = 9 };
-// ORDER_NATURAL_ALL: ORDER_NATURAL with every (a, b) block built and every tile of the
-// diagonal blocks computed (no mirrored tiles): the affine kernel then writes every output
-// row itself as one contiguous run.
+       ORDER_TCC = 8 };
 // ORDER_TCC: the paper's order and every block built, for the FP32 general kernel with stage C
 // on the tensor cores (tcc_layout); a block that does not fit it makes smem_bytes SIZE_MAX.
 // force_nj > 0 fixes the stage-A chunk (autotuner); otherwise the largest chunk whose
@@ -72,11 +67,6 @@ void build_tc_tables(const Program &pr, const HostTables &tab, std::vector<float
 // [0, oC) of its layout; block k occupies bytes [16 off16[k], 16 off16[k + 1]).
 template <typename T>
 void build_aff_image(const Program &pr, const HostTables &tab, bool extruded, std::vector<unsigned char> &img,
-                     std::vector<int> &off16);
-// Constant shared-memory image of the FP32 Kronecker kernel for every block of an
-// ORDER_K32 / ORDER_K32_EXT program: the region [0, oC) of k32_layout (F1 dense, then F2 or
-// P2), in floats; block k occupies bytes [16 off16[k], 16 off16[k + 1]).
-void build_k32_image(const Program &pr, const HostTables &tab, bool extruded, std::vector<unsigned char> &img,
                      std::vector<int> &off16);
 // Constant images of the FP32 tensor-core stage-C kernel for every block of an ORDER_TCC
 // program: P1 split into TF32 high and low parts in the canonical K-major layout, then the
