@@ -55,23 +55,29 @@ UNIT = "element matrices/s"
 WORKLOAD2, Q2, L2Q = "seq_q5_8x8x8", 5, 7
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the headline's
-# dominant kernel (hp_contract_kernel<double>, H(curl)), from one ncu capture (command and
-# figures under profiles/), reported only while the source of the kernel (the text between
-# the markers below in dpg_kernels.cu) is the one the counters were taken on.
-TRAFFIC = {"bytes": None, "kernel_sha256": None, "scaled_from": None,
-           "markers": ("// general sum factorization", "// FP32 general sum factorization")}
+# dominant kernel (hp_contract_kernel<double>, the H(curl) call), from one ncu capture on the
+# first 512 elements of the headline mesh scaled to the full launch by output bytes (command
+# and figures under profiles/), reported only while the source of the kernel (the texts
+# between the marker pairs below in dpg_kernels.cu) is the one the counters were taken on.
+TRAFFIC = {"bytes": None, "kernel_sha256": None,
+           "markers": (("// general sum factorization", "// FP32 general sum factorization"),
+                       ("// hp batching: elements of mixed order q", "// FMA-rate probe"))}
+
+
+def kernel_source_hash():
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_1711_00984_gb300", "csrc", "dpg_kernels.cu")).read()
+        text = "".join(src[src.index(a):src.index(b)] for a, b in TRAFFIC["markers"])
+    except (OSError, ValueError):
+        return None
+    return hashlib.sha256(text.encode()).hexdigest()
 
 
 def dominant_traffic():
-    import hashlib
     if TRAFFIC["bytes"] is None:
         return None
-    try:
-        src = open(os.path.join(ROOT, "paper_1711_00984_gb300", "csrc", "dpg_kernels.cu")).read()
-        a, b = src.index(TRAFFIC["markers"][0]), src.index(TRAFFIC["markers"][1])
-    except (OSError, ValueError):
-        return None
-    return TRAFFIC["bytes"] if hashlib.sha256(src[a:b].encode()).hexdigest() == TRAFFIC["kernel_sha256"] else None
+    return TRAFFIC["bytes"] if kernel_source_hash() == TRAFFIC["kernel_sha256"] else None
 
 
 def parse():

@@ -312,9 +312,10 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
  *                     tensor cores -- each operand row split as 2^e sum_{u<7} d_u 2^-(8u+7)
  *                     with balanced digits |d_u| <= 128, the digit products summed exactly
  *                     in FP32 and combined in a 64-bit integer, entering the FP64 result
- *                     once per product; what is dropped lies below 2^-55 of the row maxima,
- *                     so the results agree with the FMA route to FP64 rounding of the
- *                     row-scaled sums.
+ *                     once per product; what is dropped lies below about 2^-53 of the
+ *                     product of the two rows' maxima, so the results agree with the FMA
+ *                     route normwise (relative to the row maxima), not entry by entry: an
+ *                     entry far below its row's maximum keeps fewer correct bits.
  * The factorization of the diagonal blocks and F = W^T y stay FP64 FMA in both (the panel
  * products with the inverse diagonal blocks follow the method).  Errors: DPG_ERR_ARG. */
 #define DPG_CONDENSE_FMA 0

@@ -8,10 +8,14 @@
 // rows is then 2^(e_i+e_j) sum_D 2^-(8D+14) P_D with P_D = sum_{u+v=D} d_u(i) . d_v(j),
 // and every P_D is a sum of at most 7 x 32 integer products of at most 2^14, below 2^22
 // in all: the BF16 tensor-core products accumulate it exactly in FP32.  The diagonals
-// D <= 6 (28 digit products) keep the truncation near 2^-53 of the row maxima, which is
-// FP64 rounding for these sums; they are combined exactly in a 64-bit integer and enter
-// the FP64 output once, so the FP64 pipe sees two operations per output and panel instead
-// of 32 FMAs.
+// D <= 6 (28 digit products) are combined exactly in a 64-bit integer (the D = 6 term
+// floored to 2^-5 of its unit) and enter the FP64 output once, so the FP64 pipe sees two
+// operations per output and panel instead of 32 FMAs.  Accuracy is normwise, relative to
+// the row maxima: a product of rows i and j is exact to about 2^-53 max_k|x_ik| max_k|y_jk|
+// (the dropped digit planes and the floor of D = 6, the latter a one-signed offset per
+// panel), where FP64 FMAs err by about 2^-53 sum_k |x_ik y_jk|; an entry far below its
+// row's maximum keeps fewer correct bits than under FP64 arithmetic (about 55 - log2 of
+// the ratio).
 #pragma once
 #include <cstdint>
 

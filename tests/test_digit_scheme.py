@@ -92,3 +92,20 @@ def test_condensation_model_matches_oracle():
     assert np.linalg.norm(K - Kr[0]) <= tol * np.linalg.norm(Kr[0])
     assert np.linalg.norm(F - Fr[0]) <= tol * np.linalg.norm(Fr[0])
     assert np.linalg.norm(K - Kr[0]) <= 1e-13 * np.linalg.norm(Kr[0])    # FP64 rounding, in fact
+
+
+def test_digit_products_error_is_normwise_in_the_row_maxima():
+    """The digit products are accurate relative to the rows' maxima, not entry by entry:
+    for rows whose entries span nine decades, every product a_i . b_j is within
+    2^-52 * 32 * max|a_i| max|b_j| of the exact value (Python fractions), while an entry
+    of small magnitude may keep fewer correct bits than an FP64 dot product."""
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((4, 32)) * np.geomspace(1e-6, 1e3, 32)
+    B = rng.standard_normal((5, 32)) * np.geomspace(1e3, 1e-6, 32)
+    P = product(A, B)
+    for i in range(4):
+        for j in range(5):
+            exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(A[i], B[j]))
+            bound = 2.0 ** -52 * 32 * np.abs(A[i]).max() * np.abs(B[j]).max()
+            assert abs(Fraction(float(P[i, j])) - exact) <= Fraction(bound)
