@@ -323,7 +323,6 @@ struct TccLayout {
     int oA;                                // stage-A output [nh][L][nc3][lpad] floats
     int oP3;                               // stage-A factors [nterm][L][nc3p] floats
     int npad, oF;                          // element fields of the block's terms [nfs][L][L][npad]
-    int oW, wst;                           // per-warp staging [8][wst] floats
     int total;                             // bytes
     int tcols;                             // tensor-memory columns to allocate
     int ok;
@@ -353,10 +352,7 @@ DPG_HD inline TccLayout tcc_layout(const BlockDesc &b, int L) {
     f.npad = L | 1;
     f.oF = f.oP3 + 4 * b.nterm * L * f.nc3p;
     f.oF = (f.oF + 15) & ~15;
-    f.oW = f.oF + 4 * distinct_fields(b) * L * L * f.npad;
-    f.oW = (f.oW + 15) & ~15;
-    f.wst = 32 * 20;                       // 32 lanes x 16 columns at a stride of 20 floats
-    f.total = a128(f.oW + 4 * 8 * f.wst);
+    f.total = a128(f.oF + 4 * distinct_fields(b) * L * L * f.npad);
     f.tcols = 32;
     while (f.tcols < 2 * f.N + 16 && f.tcols < 512) f.tcols <<= 1;
     f.ok = (2 * f.N + 16 <= 512) && f.nc1 <= 16 && f.nc3 <= 16 && f.lpad <= 16 && b.ng >= 1 && b.nh >= 1 &&

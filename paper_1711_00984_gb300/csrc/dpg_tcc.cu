@@ -14,8 +14,8 @@
 // (i2, x); one thread issues a tile's products and commits them to an mbarrier, and the
 // CTA computes the next tile's stage B meanwhile, then moves the previous tile's
 // accumulator (the other of two) to the output: each warp reads 32 rows of one i1 from
-// tensor memory, stages them in shared memory and writes them as runs of consecutive
-// columns of the output rows (i1, i2, i3).  Waits are bounded: a wait that runs out
+// tensor memory and every lane stores its nc1 consecutive columns of output row
+// (i1, i2, i3) (lanes hold consecutive x: a warp's stores cover contiguous runs).  Waits are bounded: a wait that runs out
 // stops the CTA, which releases its tensor memory and records DPG_ERR_TIMEOUT.
 #include <cstdint>
 
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TCC_NTH, 2) sf_tcc_kernel(TccParams p) {
     bool pend = false;
     int64_t pend_e = 0;
     int pend_i3 = 0, pend_t = 0;
-    unsigned mnx = 0, mnc2 = 0, mnc1 = 0, mLL = 0, mL = 0;
+    unsigned mnx = 0, mnc2 = 0, mLL = 0, mL = 0;
     auto adv = [](uint64_t d, uint32_t off) { return d + (uint64_t)(off >> 4); };
 
     // ---- epilogue of a finished tile: accumulator buffer dbuf -> output rows
@@ -176,27 +176,20 @@ __global__ void __launch_bounds__(TCC_NTH, 2) sf_tcc_kernel(TccParams p) {
         const int rho = 32 * qd + lane;
         int i2 = 0, x = 0;
         const bool valid = tcc_row(f, t, rho, mnx, i2, x);
-        float *wb = reinterpret_cast<float *>(smb + f.oW) + warp * f.wst;
         const int nc1 = f.nc1, nr1 = f.nr1;
         const int64_t rowi = (int64_t)bd.row_off + nr1 * i2 + (int64_t)nr1 * f.nr2 * i3;
         for (int i1 = half; i1 < nr1; i1 += 2) {
             uint32_t r[16];
             tmem_ld16(tbase + ((uint32_t)(32 * qd) << 16) + dbuf * (uint32_t)f.N + (uint32_t)(i1 * nc1), r);
-            {
-                float4 *w4 = reinterpret_cast<float4 *>(wb + lane * 20);   // lane stride 20: 4 wavefronts
+            // the lane's nc1 consecutive columns of output row (i1, i2, i3); the lanes of a
+            // warp hold consecutive x, so a warp's stores cover one contiguous run per i2
+            const int64_t d0 = (rowi + i1) * ld + bd.col_off + (int64_t)x * nc1;
+            if (valid && DPG_INB(d0 + nc1 <= p.mat_stride - bd.base, p.status, e)) {
+                float *od = oe + d0;
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4)
-                    w4[c4] = make_float4(__uint_as_float(r[4 * c4]), __uint_as_float(r[4 * c4 + 1]),
-                                         __uint_as_float(r[4 * c4 + 2]), __uint_as_float(r[4 * c4 + 3]));
+                for (int j = 0; j < 16; ++j)
+                    if (j < nc1) od[j] = __uint_as_float(r[j]);
             }
-            __syncwarp();
-            const int64_t dst = valid ? (rowi + i1) * ld + bd.col_off + (int64_t)x * nc1 : -1;
-            for (int kk = lane; kk < 32 * nc1; kk += 32) {
-                const int sl = mdiv(kk, mnc1), j = kk - sl * nc1;
-                const long long d = __shfl_sync(0xffffffffu, (long long)dst, sl);
-                if (d >= 0 && DPG_INB(d + j < p.mat_stride - bd.base, p.status, e)) oe[d + j] = wb[sl * 20 + j];
-            }
-            __syncwarp();
         }
     };
 
@@ -241,7 +234,7 @@ __global__ void __launch_bounds__(TCC_NTH, 2) sf_tcc_kernel(TccParams p) {
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int i = tid; i < (2 * f.acb) >> 4; i += TCC_NTH) ac[i] = z;
             }
-            mnx = magic(f.nx); mnc2 = magic(f.nc2); mnc1 = magic(f.nc1); mLL = magic(L2); mL = magic(L);
+            mnx = magic(f.nx); mnc2 = magic(f.nc2); mLL = magic(L2); mL = magic(L);
             cur_block = k;
             cur_e = -1;
         }
