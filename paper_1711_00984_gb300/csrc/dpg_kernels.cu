@@ -1173,14 +1173,28 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         if (!DPG_INB(need <= dpg_dyn_smem_bytes() && img <= (size_t)lay.oC * sizeof(T), p.status, e0)) return;
     }
 #endif
-    const int ldt = lay.ldt;
-    // ---- the Kronecker factor Q of unit u (qv / qi / qc), in three steps separated by CTA
-    //      barriers: the stage-A factors (EXT) or the ξ3 integrals s_t (affine); stage A over
-    //      ξ3 (EXT only); Q_g itself.  Q of the next unit is formed while the current unit's
-    //      tile is written out, so the FP64 stages overlap the stores.
-    auto prep1 = [&](const Unit &u) {
+    for (int64_t e = e0; e < e1; ++e) {                               // the CTA's chunk of elements
+    __syncthreads();                                                  // previous element done
+    if constexpr (!EXT) {                                             // the element's constants
+        if (tid < MAXFIELDS) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
+        if (tid == MAXFIELDS) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
+    } else {                                                          // its 2D metric fields
+        if (tid == 0) flag = p.estatus[e];
+        const T *src = p.xfields + (size_t)e * p.nfields * L2;
+        for (int it = tid; it < bd.nslot * L2; it += nth) {
+            const int sl = it / L2;
+            Fx[it] = src[(size_t)bd.slot_field[sl] * L2 + (it - sl * L2)];
+        }
+    }
+    __syncthreads();
+    T *o = p.out + (size_t)e * p.mat_stride + bd.base;
+    const bool bad = flag != 0;
+    for (int ui = ub + split; ui < ue; ui += nsplit) {               // this CTA's share of the units
+        const Unit u = p.units[ui];
         const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
         const unsigned mnj = div_magic(nj);
+        const int ldt = lay.ldt;
+        __syncthreads();                                                // previous unit done
         if constexpr (!EXT) {
             for (int it = tid; it < nterm * nj; it += nth) {
                 const int t = fdiv(it, mnj), jj = it - t * nj;
@@ -1198,11 +1212,15 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             }
             if (tid < MAXG) qc[tid] = n22 * nj;
         }
-    };
-    auto prep2 = [&](const Unit &u) {                                 // stage A over ξ3 (Eq. 2.23 on the 2D fields)
+        {
+            float4 *t4 = reinterpret_cast<float4 *>(tile);            // tile is 16-byte aligned
+            const int n4 = (int)((nrow * ldt * sizeof(T)) / 16);
+            for (int it = tid; it < n4; it += nth) t4[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int it = n4 * (16 / (int)sizeof(T)) + tid; it < nrow * ldt; it += nth) tile[it] = T(0);
+        }
+        __syncthreads();
         if constexpr (EXT) {
-            const int nj = u.nj;
-            const unsigned mnj = div_magic(nj);
+            // stage A over xi3 (Eq. 2.23 on the 2D fields): A_h[m][jj]
             for (int it = tid; it < bd.nh * L * nj; it += nth) {
                 const int r = fdiv(it, mnj), jj = it - r * nj, h = r / L, m = r - h * L;
                 T acc = T(0);
@@ -1214,15 +1232,8 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
                 }
                 Ah[it] = acc;
             }
-        } else {
-            (void)u;
-        }
-    };
-    auto prep3 = [&](const Unit &u) {
-        const int nj = u.nj;
-        const unsigned mnj = div_magic(nj);
-        if constexpr (EXT) {
-            // stage B over ξ2 (Eq. 2.24): Q_g[(i2,j2)][jj], dense, at its tile offset
+            __syncthreads();
+            // stage B over xi2 (Eq. 2.24): Q_g[(i2,j2)][jj], dense, at its tile offset
             for (int it = tid; it < ng * n22 * nj; it += nth) {
                 const int r = fdiv(it, mnj), jj = it - r * nj;
                 const int g = fdiv(r, mn22), ij2 = r - g * n22;
@@ -1237,44 +1248,59 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
                 qv[g * n22 * njm + ij2 * nj + jj] = acc;
                 qi[g * n22 * njm + ij2 * nj + jj] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
             }
-        } else {
-            // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2), kept as a list of its non-zeros
-            for (int it = tid; it < ng * n22 * nj; it += nth) {
-                const int r = fdiv(it, mnj), jj = it - r * nj;
-                const int g = fdiv(r, mn22), ij2 = r - g * n22;
-                T acc = T(0);
-                bool any = false;
-                const int ngt = bd.g_nterm[g];
-                for (int k2 = 0; k2 < ngt; ++k2) {
-                    const int t = bd.g_terms[g][k2];
-                    const T sv = st[t * nj + jj];
-                    if (is_zero(sv)) continue;
-                    const T f2 = F2[t * n22 + ij2];
-                    if (!is_zero(f2)) { acc = fma(sv, f2, acc); any = true; }
-                }
-                const int slot = warp_append(&qc[g], any && !is_zero(acc));
-                if (slot >= 0) {
-                    const int i2 = fdiv(ij2, mnc2), j2 = ij2 - i2 * nc2;
-                    qv[g * n22 * njm + slot] = acc;
-                    qi[g * n22 * njm + slot] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
-                }
+        }
+        // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2), kept as a list of its non-zeros
+        if constexpr (!EXT)
+        for (int it = tid; it < ng * n22 * nj; it += nth) {
+            const int r = fdiv(it, mnj), jj = it - r * nj;
+            const int g = fdiv(r, mn22), ij2 = r - g * n22;
+            T acc = T(0);
+            bool any = false;
+            const int ngt = bd.g_nterm[g];
+            for (int k2 = 0; k2 < ngt; ++k2) {
+                const int t = bd.g_terms[g][k2];
+                const T sv = st[t * nj + jj];
+                if (is_zero(sv)) continue;
+                const T f2 = F2[t * n22 + ij2];
+                if (!is_zero(f2)) { acc = fma(sv, f2, acc); any = true; }
+            }
+            const int slot = warp_append(&qc[g], any && !is_zero(acc));
+            if (slot >= 0) {
+                const int i2 = fdiv(ij2, mnc2), j2 = ij2 - i2 * nc2;
+                qv[g * n22 * njm + slot] = acc;
+                qi[g * n22 * njm + slot] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
             }
         }
-    };
-    const T nanv = qnan<T>();
-    // 16-byte vector stores of VW values where the destination is aligned, plain stores for
-    // the unaligned head and the tail of each run
-    constexpr int VW = 16 / (int)sizeof(T);
-    using V16 = typename Vec16<T>::type;
-    // tile rows [r0, r1) of unit u to their contiguous runs of the output; on the diagonal
-    // sub-tile (iA == jA of a diagonal block) the lower half is taken from the upper entries
-    auto write_rows = [&](const Unit &u, int r0, int r1, T *o, bool bad, int64_t e) {
-        const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
+        __syncthreads();
+        // scatter the non-zero products group by group (one product per entry per group):
+        // a warp per stage-C non-zero, its lanes over the Q non-zeros
+        for (int g = 0; g < ng; ++g) {
+            const int nf = f1c[g], nq = qc[g];
+            const T *qvg = qv + g * n22 * njm;
+            const int *qig = qi + g * n22 * njm;
+            for (int a = warp; a < nf; a += nwarp) {
+                const T fv = f1v[g * n11 + a];
+                T *trow = tile + f1i[g * n11 + a];
+                for (int b = lane; b < nq; b += 32) {
+                    if (!DPG_INB((unsigned)(f1i[g * n11 + a] + qig[b]) < (unsigned)(nrow * ldt), p.status, e)) continue;
+                    T *dst = trow + qig[b];
+                    *dst = fma(fv, qvg[b], *dst);
+                }
+            }
+            __syncthreads();
+        }
+        // write-out: tile rows are contiguous runs of the output; on the diagonal sub-tile
+        // (iA == jA of a diagonal block) the lower half is taken from the upper entries
         const int64_t R0 = bd.row_off + (int64_t)i3 * nrow;
         const int64_t C0 = bd.col_off + (int64_t)j3b * ncj;
         const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
+        const T nanv = qnan<T>();
         const int ncolu = ncj * nj, cb = jd * ncj;
-        for (int row = r0 + warp; row < r1; row += nwarp) {
+        // 16-byte vector stores of VW values where the destination is aligned, plain stores
+        // for the unaligned head and the tail of each run
+        constexpr int VW = 16 / (int)sizeof(T);
+        using V16 = typename Vec16<T>::type;
+        for (int row = warp; row < nrow; row += nwarp) {
             if (!DPG_INB((R0 + row) * ld + C0 + ncolu <= msz, p.status, e)) continue;
             T *orow = o + (R0 + row) * ld + C0;
             const T *trw = tile + row * ldt;
@@ -1289,7 +1315,7 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             if (lane < head) orow[lane] = val(lane);
             if (lane < ncolu - tail0) orow[tail0 + lane] = val(tail0 + lane);
             V16 *o16 = reinterpret_cast<V16 *>(orow + head);
-            if (jd < 0 && !bad) {                                       // plain copy (uniform branch)
+            if (jd < 0 && !bad) {                               // plain copy (uniform branch)
                 const T *src = trw + head;
                 for (int i = lane; i < nvec; i += 32) {
                     V16 w;
@@ -1308,107 +1334,38 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
                 }
             }
         }
-    };
-    // the mirror of the off-diagonal sub-tiles of unit u: tile column c -> output row C0 + c,
-    // a run of nrow values at column R0
-    auto write_mirror = [&](const Unit &u, T *o, bool bad, int64_t e) {
-        if (bd.sym == 0) return;
-        const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
-        const int64_t R0 = bd.row_off + (int64_t)i3 * nrow;
-        const int64_t C0 = bd.col_off + (int64_t)j3b * ncj;
-        const int jd = (bd.sym == 1 && i3 >= j3b && i3 < j3b + nj) ? i3 - j3b : -1;
-        const int ncolu = ncj * nj, cb = jd * ncj;
-        const int nmc = jd >= 0 ? ncolu - ncj : ncolu;
-        T *mbase = o + C0 * ld + R0;
-        if (!DPG_INB((C0 + ncolu - 1) * ld + R0 + nrow <= msz, p.status, e)) return;
-        if (nrow >= 64) {                                               // long runs: a warp per column
-            // (plain stores: lanes reading consecutive tile rows keep the shared-memory reads
-            // conflict-free, which measured faster than 16-byte stores here)
-            for (int mcix = warp; mcix < nmc; mcix += nwarp) {
-                const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
-                T *mrow = mbase + (int64_t)c * ld;
-                for (int row = lane; row < nrow; row += 32) mrow[row] = bad ? nanv : tile[row * ldt + c];
-            }
-        } else {                                                        // short runs: full warps
-            const unsigned mnrow = div_magic(nrow);
-            for (int it = tid; it < nmc * nrow; it += nth) {
-                const int mcix = fdiv(it, mnrow), row = it - mcix * nrow;
-                const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
-                mbase[(int64_t)c * ld + row] = bad ? nanv : tile[row * ldt + c];
-            }
-        }
-    };
-
-    for (int64_t e = e0; e < e1; ++e) {                               // the CTA's chunk of elements
-        __syncthreads();                                              // previous element done
-        if constexpr (!EXT) {                                         // the element's constants
-            if (tid < MAXFIELDS) cf[tid] = (T)p.consts[AFF_CONST_STRIDE * e + tid];
-            if (tid == MAXFIELDS) flag = (int)p.consts[AFF_CONST_STRIDE * e + AFF_CONST_STRIDE - 1];
-        } else {                                                      // its 2D metric fields
-            if (tid == 0) flag = p.estatus[e];
-            const T *src = p.xfields + (size_t)e * p.nfields * L2;
-            for (int it = tid; it < bd.nslot * L2; it += nth) {
-                const int sl = it / L2;
-                Fx[it] = src[(size_t)bd.slot_field[sl] * L2 + (it - sl * L2)];
-            }
-        }
-        __syncthreads();
-        T *o = p.out + (size_t)e * p.mat_stride + bd.base;
-        const bool bad = flag != 0;
-        int ui = ub + split;                                          // this CTA's share of the units
-        if (ui >= ue) continue;
-        Unit u = p.units[ui];
-        prep1(u);
-        __syncthreads();
-        prep2(u);
-        if constexpr (EXT) __syncthreads();
-        prep3(u);
-        for (;;) {
-            const int nj = u.nj;
-            __syncthreads();                                          // Q of u formed, tile free
-            {
-                float4 *t4 = reinterpret_cast<float4 *>(tile);        // tile is 16-byte aligned
-                const int n4 = (int)((nrow * ldt * sizeof(T)) / 16);
-                for (int it = tid; it < n4; it += nth) t4[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int it = n4 * (16 / (int)sizeof(T)) + tid; it < nrow * ldt; it += nth) tile[it] = T(0);
-            }
-            __syncthreads();
-            // scatter the non-zero products group by group (one product per entry per group):
-            // a warp per stage-C non-zero, its lanes over the Q non-zeros
-            for (int g = 0; g < ng; ++g) {
-                const int nf = f1c[g], nq = qc[g];
-                const T *qvg = qv + g * n22 * njm;
-                const int *qig = qi + g * n22 * njm;
-                for (int a = warp; a < nf; a += nwarp) {
-                    const T fv = f1v[g * n11 + a];
-                    T *trow = tile + f1i[g * n11 + a];
-                    for (int b = lane; b < nq; b += 32) {
-                        if (!DPG_INB((unsigned)(f1i[g * n11 + a] + qig[b]) < (unsigned)(nrow * ldt), p.status, e)) continue;
-                        T *dst = trow + qig[b];
-                        *dst = fma(fv, qvg[b], *dst);
+        if (bd.sym != 0) {
+            // the mirror of the off-diagonal sub-tiles: tile column c -> output row C0 + c,
+            // a run of nrow values at column R0; (column, row) pairs flattened over the CTA
+            const int nmc = jd >= 0 ? ncolu - ncj : ncolu;
+            T *mbase = o + C0 * ld + R0;
+            if (!DPG_INB((C0 + ncolu - 1) * ld + R0 + nrow <= msz, p.status, e)) continue;
+            if (nrow >= 64) {                                   // long runs: a warp per column
+                // (plain stores: lanes reading consecutive tile rows keep the shared-memory
+                // reads conflict-free, which measured faster than 16-byte stores here)
+                if (!bad) {
+                    for (int mcix = warp; mcix < nmc; mcix += nwarp) {
+                        const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                        T *mrow = mbase + (int64_t)c * ld;
+                        for (int row = lane; row < nrow; row += 32) mrow[row] = tile[row * ldt + c];
+                    }
+                } else {
+                    for (int mcix = warp; mcix < nmc; mcix += nwarp) {
+                        const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                        T *mrow = mbase + (int64_t)c * ld;
+                        for (int row = lane; row < nrow; row += 32) mrow[row] = nanv;
                     }
                 }
-                __syncthreads();
+            } else {                                            // short runs: full warps
+                const unsigned mnrow = div_magic(nrow);
+                for (int it = tid; it < nmc * nrow; it += nth) {
+                    const int mcix = fdiv(it, mnrow), row = it - mcix * nrow;
+                    const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                    mbase[(int64_t)c * ld + row] = bad ? nanv : tile[row * ldt + c];
+                }
             }
-            (void)nj;
-            // write-out of u, with Q of the next unit formed meanwhile (Q and its counts are
-            // free once the scatter has read them)
-            const int un = ui + nsplit;
-            const bool more = un < ue;
-            Unit v = u;
-            if (more) v = p.units[un];
-            if (more) prep1(v);
-            write_rows(u, 0, nrow / 2, o, bad, e);
-            __syncthreads();
-            if (more) prep2(v);
-            write_rows(u, nrow / 2, nrow, o, bad, e);
-            if constexpr (EXT) __syncthreads();
-            if (more) prep3(v);
-            write_mirror(u, o, bad, e);
-            if (!more) break;
-            ui = un;
-            u = v;
         }
+    }
     }                                                                 // element loop
 }
 
