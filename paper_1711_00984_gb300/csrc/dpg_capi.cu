@@ -236,14 +236,18 @@ int setup_tcc(ProgEntry *pe, int space, int q, int L, int p, bool split, const H
     if ((r = upload(off.data(), off.size(), &t.d_off))) return r;
     if ((r = upload(base.data(), base.size(), &t.d_base))) return r;
     t.tcols = tcols;
-    // two CTAs per SM (the register budget of the kernel) when both fit the tensor memory and
-    // the shared memory; otherwise one, its shared-memory request sized so that no second
-    // CTA is placed beside it
+    // CTAs per SM: at most three (the kernel's register budget), as many as the tensor memory
+    // (each CTA holds tcols columns for its whole life) and the shared memory allow; below
+    // three, the shared-memory request is raised so that no further CTA is placed on the SM
+    // (it would wait for tensor memory)
     const size_t st = (size_t)(tcc_static_smem() + 1024);
-    const bool two = 2 * tcols <= 512 && 2 * (tp.smem_bytes + st) <= (size_t)g_smem_per_sm;
-    t.cps = two ? 2 : 1;
-    t.smem = two ? tp.smem_bytes
-                 : std::min((size_t)g_max_dyn_smem_tcc, std::max(tp.smem_bytes, (size_t)g_smem_per_sm / 2 + 1));
+    int cps = std::min(3, 512 / tcols);
+    cps = std::min(cps, (int)((size_t)g_smem_per_sm / (tp.smem_bytes + st)));
+    cps = std::max(cps, 1);
+    size_t req = tp.smem_bytes;
+    if (cps < 3) req = std::max(req, (size_t)g_smem_per_sm / (cps + 1) - st + 16);
+    t.cps = cps;
+    t.smem = std::min(req, (size_t)g_max_dyn_smem_tcc);
     t.prog = tp;
     t.ok = true;
     return DPG_OK;

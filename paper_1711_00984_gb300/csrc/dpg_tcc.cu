@@ -125,7 +125,7 @@ __device__ __forceinline__ void tcc_stage_b(const TccLayout &f, const BlockDesc 
 
 }  // namespace
 
-__global__ void __launch_bounds__(TCC_NTH, 2) sf_tcc_kernel(TccParams p) {
+__global__ void __launch_bounds__(TCC_NTH, 3) sf_tcc_kernel(TccParams p) {
     extern __shared__ __align__(1024) unsigned char smb[];
     __shared__ BlockDesc bd;
     __shared__ TccLayout f;
