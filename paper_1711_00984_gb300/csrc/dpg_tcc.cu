@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TCC_NTH, 3) sf_tcc_kernel(TccParams p) {
     bool pend = false;
     int64_t pend_e = 0;
     int pend_i3 = 0, pend_t = 0;
-    unsigned mnx = 0, mnc2 = 0, mLL = 0, mL = 0;
+    unsigned mnx = 0, mnc2 = 0, mLL = 0, mL = 0, mnc3p = 0;
     auto adv = [](uint64_t d, uint32_t off) { return d + (uint64_t)(off >> 4); };
 
     // ---- epilogue of a finished tile: accumulator buffer dbuf -> output rows
@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(TCC_NTH, 3) sf_tcc_kernel(TccParams p) {
         while (k + 1 < p.nblock && it >= (int64_t)p.blk_base[k + 1] * ne) ++k;
         const int64_t rel = it - (int64_t)p.blk_base[k] * ne;
         const int nr3k = p.blk_base[k + 1] - p.blk_base[k];
-        const int64_t le = rel / nr3k;
+        // (32-bit division where the index allows: a 64-bit division costs far more)
+        const int64_t le = rel < 0x7fffffffLL ? (int64_t)((unsigned)rel / (unsigned)nr3k) : rel / nr3k;
         const int i3 = (int)(rel - le * nr3k);
         const int64_t e = p.elist ? (int64_t)p.elist[estart + le] : le;
 
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(TCC_NTH, 3) sf_tcc_kernel(TccParams p) {
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int i = tid; i < (2 * f.acb) >> 4; i += TCC_NTH) ac[i] = z;
             }
-            mnx = magic(f.nx); mnc2 = magic(f.nc2); mLL = magic(L2); mL = magic(L);
+            mnx = magic(f.nx); mnc2 = magic(f.nc2); mLL = magic(L2); mL = magic(L); mnc3p = magic(f.nc3p);
             cur_block = k;
             cur_e = -1;
         }
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(TCC_NTH, 3) sf_tcc_kernel(TccParams p) {
             cur_e = e;
         }
         for (int i = tid; i < bd.nterm * L * nc3p; i += TCC_NTH) {
-            const int r = i / nc3p, j3 = i - r * nc3p;
+            const int r = mdiv(i, mnc3p), j3 = i - r * nc3p;
             const int t = mdiv(r, mL), n = r - t * L;
             const TermDesc &td = bd.term[t];
             float v = 0.0f;
