@@ -75,76 +75,14 @@ __device__ __forceinline__ void tcc_stage_a(const TccLayout &f, const BlockDesc 
     }
 }
 
-// One row (rho) of the stage-C A operand from its LP4 x 4 accumulators: split into TF32 high
-// and low parts, K-major canonical layout, 16-byte stores.
-template <int LP4>
-__device__ __forceinline__ void tcc_store_row(const float (&acc)[4 * LP4], int g, int rho, int sg, float *ach,
-                                              float *acl) {
-#pragma unroll
-    for (int c4 = 0; c4 < LP4; ++c4) {
-        const int k0 = g * 4 * LP4 + 4 * c4;
-        const int off = (rho >> 3) * sg + (k0 >> 2) * 32 + (rho & 7) * 4;
-        float4 hv, lv;
-        tf32_split(acc[4 * c4 + 0], hv.x, lv.x);
-        tf32_split(acc[4 * c4 + 1], hv.y, lv.y);
-        tf32_split(acc[4 * c4 + 2], hv.z, lv.z);
-        tf32_split(acc[4 * c4 + 3], hv.w, lv.w);
-        *reinterpret_cast<float4 *>(ach + off) = hv;
-        *reinterpret_cast<float4 *>(acl + off) = lv;
-    }
-}
-
-// Stage B (Eq. 2.24) of tile t, written split into TF32 high and low parts to the stage-C A
-// operand.  Tiles of whole i2 rows and lpad <= 8: thread = (g, i2, j2, pair of j3), two rows'
-// values l in registers (the P2 value of (i2, j2) serves both); otherwise thread = (g, row).
+// Stage B (Eq. 2.24) of tile t: thread = (g, row rho), the LP4 x 4 values l in registers,
+// written split into TF32 high and low parts to the stage-C A operand.
 template <int LP4>
 __device__ __forceinline__ void tcc_stage_b(const TccLayout &f, const BlockDesc &bd, int t, unsigned mnx,
                                             unsigned mnc2, const float *P2s, const float *A, float *ach, float *acl,
                                             int L, int tid) {
     constexpr int lpad = 4 * LP4;
     const int sg = f.sbo >> 2, nc3 = f.nc3;
-    if (LP4 <= 2 && f.ipt > 0) {                         // (two rows of 12 or 16 values would spill)
-        const int i2lo = t * f.ipt, ni2 = min(f.ipt, f.nr2 - i2lo), nc2 = f.nc2;
-        const int njp = (nc3 + 1) >> 1;
-        const unsigned mjp = magic(njp), mni2 = magic(ni2);
-        const int ntask = bd.ng * ni2 * nc2 * njp;
-        for (int task = tid; task < ntask; task += TCC_NTH) {
-            const int r = mdiv(task, mjp), jp = task - r * njp;
-            const int r2 = mdiv(r, mnc2), j2 = r - r2 * nc2;
-            const int g = mdiv(r2, mni2), di2 = r2 - g * ni2;
-            const int i2 = i2lo + di2, j3a = 2 * jp;
-            const bool two = j3a + 1 < nc3;
-            float acc0[lpad], acc1[lpad];
-#pragma unroll
-            for (int j = 0; j < lpad; ++j) { acc0[j] = 0.0f; acc1[j] = 0.0f; }
-            for (int hi = 0; hi < bd.g_nh[g]; ++hi) {
-                const int h = bd.g_hs[g][hi];
-                const float *p2 = P2s + bd.h_p2[h] * L * f.n22p + i2 * nc2 + j2;
-                const float4 *ah = reinterpret_cast<const float4 *>(A + ((h * L) * nc3 + j3a) * lpad);
-                const int a1 = two ? LP4 : 0;                // the second row's j3 (or the first again)
-                for (int m = 0; m < L; ++m) {
-                    const float pv = p2[m * f.n22p];
-                    const float4 *a4 = ah + m * nc3 * LP4;
-#pragma unroll
-                    for (int c4 = 0; c4 < LP4; ++c4) {
-                        const float4 av = a4[c4], bv = a4[a1 + c4];
-                        acc0[4 * c4 + 0] = fmaf(pv, av.x, acc0[4 * c4 + 0]);
-                        acc0[4 * c4 + 1] = fmaf(pv, av.y, acc0[4 * c4 + 1]);
-                        acc0[4 * c4 + 2] = fmaf(pv, av.z, acc0[4 * c4 + 2]);
-                        acc0[4 * c4 + 3] = fmaf(pv, av.w, acc0[4 * c4 + 3]);
-                        acc1[4 * c4 + 0] = fmaf(pv, bv.x, acc1[4 * c4 + 0]);
-                        acc1[4 * c4 + 1] = fmaf(pv, bv.y, acc1[4 * c4 + 1]);
-                        acc1[4 * c4 + 2] = fmaf(pv, bv.z, acc1[4 * c4 + 2]);
-                        acc1[4 * c4 + 3] = fmaf(pv, bv.w, acc1[4 * c4 + 3]);
-                    }
-                }
-            }
-            const int rho0 = di2 * f.nx + j2 + nc2 * j3a;
-            tcc_store_row<LP4>(acc0, g, rho0, sg, ach, acl);
-            if (two) tcc_store_row<LP4>(acc1, g, rho0 + nc2, sg, ach, acl);
-        }
-        return;
-    }
     for (int task = tid; task < bd.ng * 128; task += TCC_NTH) {
         const int g = task >> 7, rho = task & 127;
         int i2, x;
@@ -170,7 +108,18 @@ __device__ __forceinline__ void tcc_stage_b(const TccLayout &f, const BlockDesc 
                 }
             }
         }
-        tcc_store_row<LP4>(acc, g, rho, sg, ach, acl);
+#pragma unroll
+        for (int c4 = 0; c4 < LP4; ++c4) {
+            const int k0 = g * lpad + 4 * c4;
+            const int off = (rho >> 3) * sg + (k0 >> 2) * 32 + (rho & 7) * 4;
+            float4 hv, lv;
+            tf32_split(acc[4 * c4 + 0], hv.x, lv.x);
+            tf32_split(acc[4 * c4 + 1], hv.y, lv.y);
+            tf32_split(acc[4 * c4 + 2], hv.z, lv.z);
+            tf32_split(acc[4 * c4 + 3], hv.w, lv.w);
+            *reinterpret_cast<float4 *>(ach + off) = hv;
+            *reinterpret_cast<float4 *>(acl + off) = lv;
+        }
     }
 }
 
