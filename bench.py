@@ -99,7 +99,7 @@ def parse():
     ap.add_argument("--elems", type=int, default=0,
                     help="elements of the --only case (default: all) or of the dpg_q6_p4_16x16x16 record")
     ap.add_argument("--fp32", action="store_true", help="FP32 form for the --only case")
-    ap.add_argument("--condense", default="tc", choices=["tc", "fma"],
+    ap.add_argument("--condense", default="tc", choices=["tc", "tcgen05", "fma"],
                     help="arithmetic of the condensation updates in the dpg_q6_p4_16x16x16 record")
     return ap.parse_args()
 

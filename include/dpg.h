@@ -318,8 +318,9 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
  *                     entry far below its row's maximum keeps fewer correct bits.
  * The factorization of the diagonal blocks and F = W^T y stay FP64 FMA in both (the panel
  * products with the inverse diagonal blocks follow the method).  Errors: DPG_ERR_ARG. */
-#define DPG_CONDENSE_FMA 0
-#define DPG_CONDENSE_TC  1
+#define DPG_CONDENSE_FMA     0
+#define DPG_CONDENSE_TC      1
+#define DPG_CONDENSE_TCGEN05 2
 int dpg_condense_set_method(int method);
 
 /* The DPG element routine of the mixed-stiffness pair in one call (Sec. 3, Eqs. 3.7-3.8):

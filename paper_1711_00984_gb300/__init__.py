@@ -324,13 +324,14 @@ def dpg_condense(n_elem: int, n: int, m: int, G: int, B: int, l: int, K: int, F:
                              stream or None)
 
 
-DPG_CONDENSE_FMA, DPG_CONDENSE_TC = 0, 1
+DPG_CONDENSE_FMA, DPG_CONDENSE_TC, DPG_CONDENSE_TCGEN05 = 0, 1, 2
 
 
 def dpg_condense_set_method(method) -> int:
-    """Arithmetic of the condensation's updates: "fma" / DPG_CONDENSE_FMA (FP64 FMA) or
-    "tc" / DPG_CONDENSE_TC (FP64 products from exact BF16 digits on the tensor cores)."""
-    m = {"fma": DPG_CONDENSE_FMA, "tc": DPG_CONDENSE_TC}.get(method, method)
+    """Arithmetic of the condensation's updates: "fma" / DPG_CONDENSE_FMA (FP64 FMA),
+    "tc" / DPG_CONDENSE_TC (FP64 products from exact BF16 digits, mma.sync) or "tcgen05" /
+    DPG_CONDENSE_TCGEN05 (the same digits on tcgen05 with tensor-memory accumulators)."""
+    m = {"fma": DPG_CONDENSE_FMA, "tc": DPG_CONDENSE_TC, "tcgen05": DPG_CONDENSE_TCGEN05}.get(method, method)
     return _check(_L().dpg_condense_set_method(int(m)), "dpg_condense_set_method")
 
 

@@ -23,7 +23,7 @@ SO = os.path.join(BUILD, "libdpg.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 SO_DEBUG = os.path.join(BUILD_DEBUG, "libdpg_debug.so")
 SOURCES = ["dpg_setup.cu", "dpg_kernels.cu", "dpg_tc.cu", "dpg_tcc.cu", "dpg_capi.cu", "dpg_noalloc.cu",
-           "dpg_condense.cu"]
+           "dpg_condense.cu", "dpg_condense5.cu"]
 HEADERS = ["dpg_internal.h", "dpg_setup.h", "dpg_kernels.h", "dpg_registry.h", "dpg_digits.cuh", "dpg_trace.h", "dpg_tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -179,6 +179,7 @@ int device_state(DeviceState **out) {
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CK(init_kernel_attributes(optin));
     CK(init_condense_attributes());
+    CK(init_condense5_attributes());
     g_max_dyn_smem = max_dynamic_smem(optin);
     CK(init_tc_attributes(optin));
     g_max_dyn_smem_tc = optin - tc_static_smem();
@@ -1138,6 +1139,37 @@ int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vert
     return DPG_OK;
 }
 
+// CTAs per SM of the condensation kernel of the current method (chunk sizes are whole waves)
+int condense_wave_per_sm() {
+    if (g_condense_method == DPG_CONDENSE_TCGEN05) return 1;
+    return condense_ctas_per_sm(g_condense_method == DPG_CONDENSE_TC);
+}
+
+// The condensation of p.n_elem elements with the current method; the tcgen05 kernel's digit
+// scratch (about 1 MB per SM at n = 882) comes from the pool, stream-ordered.
+int run_condense(DeviceState *ds, const CondParams &p, cudaStream_t s) {
+    TraceRange tr(g_condense_method == DPG_CONDENSE_TCGEN05 ? "dpg condensation (tcgen05)" : "dpg condensation");
+    if (g_condense_method != DPG_CONDENSE_TCGEN05) {
+        const cudaError_t le = launch_condense(p, g_num_sms, g_condense_method == DPG_CONDENSE_TC, s);
+        if (le != cudaSuccess) return cuda_fail(le, "condense_kernel launch", __LINE__);
+        return DPG_OK;
+    }
+    Cond5Params q;
+    q.n_elem = p.n_elem; q.elem_base = p.elem_base; q.n = p.n; q.m = p.m;
+    q.G = p.G; q.B = p.B; q.l = p.l; q.K = p.K; q.F = p.F; q.status = p.status;
+    q.scratch_per_cta = condense5_scratch_per_cta(p.n, p.m, p.l != nullptr, &q.lrows, &q.wrows);
+    const int grid = (int)std::min<int64_t>(p.n_elem, g_num_sms);
+    void *scr = nullptr;
+    CK(cudaMallocFromPoolAsync(&scr, (size_t)grid * q.scratch_per_cta, ds->pool, s));
+    q.scratch = static_cast<unsigned char *>(scr);
+    cudaError_t le = cudaMemsetAsync(scr, 0, (size_t)grid * q.scratch_per_cta, s);
+    if (le == cudaSuccess) le = launch_condense5(q, grid, s);
+    const cudaError_t fe = cudaFreeAsync(scr, s);
+    if (le != cudaSuccess) return cuda_fail(le, "condense5_kernel launch", __LINE__);
+    if (fe != cudaSuccess) return cuda_fail(fe, "cudaFreeAsync", __LINE__);
+    return DPG_OK;
+}
+
 int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, double *K, double *F,
                  void *stream) {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -1153,10 +1185,7 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
     p.n_elem = n_elem; p.elem_base = 0; p.n = n; p.m = m;
     p.G = G; p.B = B; p.l = l; p.K = K; p.F = F;
     p.status = ds->status;
-    TraceRange tr("dpg condensation");
-    const cudaError_t le = launch_condense(p, g_num_sms, g_condense_method == DPG_CONDENSE_TC, (cudaStream_t)stream);
-    if (le != cudaSuccess) return cuda_fail(le, "condense_kernel launch", __LINE__);
-    return DPG_OK;
+    return run_condense(ds, p, (cudaStream_t)stream);
 }
 
 int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *vertices,
@@ -1179,7 +1208,7 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
     // condensation kernel within about 8 GB, so that only the last chunk has a partial wave
     const size_t per_elem = ((size_t)n * n + (size_t)n * m + (with_l ? n : 0)) * sizeof(double);
     int64_t chunk = (int64_t)((size_t(8) << 30) / per_elem);
-    const int64_t wave = (int64_t)condense_ctas_per_sm(g_condense_method == DPG_CONDENSE_TC) * g_num_sms;
+    const int64_t wave = (int64_t)condense_wave_per_sm() * g_num_sms;
     if (chunk >= wave) chunk -= chunk % wave;
     if (chunk < 1) chunk = 1;
     if (chunk > n_elem) chunk = n_elem;
@@ -1214,9 +1243,7 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
         cp.G = G; cp.B = B; cp.l = l;
         cp.K = K + (size_t)e0 * m * m; cp.F = with_l ? F + (size_t)e0 * m : nullptr;
         cp.status = ds->status;
-        TraceRange tr("dpg condensation");
-        const cudaError_t le = launch_condense(cp, g_num_sms, g_condense_method == DPG_CONDENSE_TC, s);
-        if (le != cudaSuccess) rc = cuda_fail(le, "condense_kernel launch", __LINE__);
+        rc = run_condense(ds, cp, s);
     }
     const cudaError_t fe = cudaFreeAsync(ws, s);
     if (fe != cudaSuccess && rc == DPG_OK) rc = cuda_fail(fe, "cudaFreeAsync", __LINE__);
@@ -1225,7 +1252,7 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
 
 int dpg_condense_set_method(int method) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (method != DPG_CONDENSE_FMA && method != DPG_CONDENSE_TC) return DPG_ERR_ARG;
+    if (method != DPG_CONDENSE_FMA && method != DPG_CONDENSE_TC && method != DPG_CONDENSE_TCGEN05) return DPG_ERR_ARG;
     g_condense_method = method;
     return DPG_OK;
 }

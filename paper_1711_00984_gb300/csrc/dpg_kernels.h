@@ -210,6 +210,19 @@ struct CondParams {
     DevStatus *status;
 };
 
+// Static condensation with the digit products on tcgen05 (dpg_condense5.cu): as CondParams,
+// plus a per-CTA digit scratch in global memory (scratch_per_cta bytes per CTA of the grid,
+// zeroed before the first launch that uses it; lrows / wrows digit rows of L21 / W1^T).
+struct Cond5Params {
+    int64_t n_elem, elem_base;
+    int n, m;
+    double *G, *B, *l, *K, *F;
+    unsigned char *scratch;
+    size_t scratch_per_cta;
+    int lrows, wrows;
+    DevStatus *status;
+};
+
 // hp batching: per-q programs in device memory, indexed by q (entry 0 unused).
 struct HpProg {
     const BlockDesc *blocks;
@@ -269,6 +282,9 @@ template <typename T> cudaError_t launch_load(const LoadParams &p, int num_sms, 
 cudaError_t launch_condense(const CondParams &p, int num_sms, bool emu, cudaStream_t s);
 int condense_ctas_per_sm(bool emu);
 cudaError_t init_condense_attributes();
+size_t condense5_scratch_per_cta(int n, int m, bool with_l, int *lrows, int *wrows);
+cudaError_t init_condense5_attributes();
+cudaError_t launch_condense5(const Cond5Params &p, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_fma_peak(T *out, int blocks, int iters, cudaStream_t s);
 cudaError_t init_kernel_attributes(int optin_smem);
 cudaError_t launch_dmma_peak(double *out, int blocks, int iters, cudaStream_t s);

@@ -103,7 +103,7 @@ for s in ("H1", "HCURL", "HDIV", "L2"):
 G = meshgen.spd_batch(3, 70, 1e3, seed=73)
 B = rng.uniform(-1, 1, (3, 70, 20)); l = rng.uniform(-1, 1, (3, 70))
 Kr, Fr, _ = oracle.condense(G, B, l)
-for method in ("tc", "fma"):
+for method in ("tc", "fma", "tcgen05"):
     dpg.dpg_condense_set_method(method)
     K, F = dpg.condense(torch.from_numpy(G.copy()).cuda(), torch.from_numpy(B.copy()).cuda(),
                         torch.from_numpy(l.copy()).cuda())

@@ -16,10 +16,10 @@ pytestmark = pytest.mark.gpu
 EPS = np.finfo(np.float64).eps
 
 
-@pytest.fixture(params=["fma", "tc"])
+@pytest.fixture(params=["fma", "tc", "tcgen05"])
 def method(request, gpu_lib):
-    """Both arithmetics of the trailing updates (FP64 FMA; FP64 products from exact BF16
-    digits on the tensor cores) meet the same tolerance."""
+    """Every arithmetic of the trailing updates (FP64 FMA; FP64 products from exact BF16
+    digits on the tensor cores, mma.sync or tcgen05) meets the same tolerance."""
     gpu_lib.dpg_condense_set_method(request.param)
     yield request.param
     gpu_lib.dpg_condense_set_method("tc")
@@ -44,7 +44,8 @@ def check(G, K, F, Kr, Fr):
             assert np.linalg.norm(F[e] - Fr[e]) <= tol * max(np.linalg.norm(Fr[e]), 1e-300)
 
 
-@pytest.mark.parametrize("n,m", [(1, 1), (5, 3), (31, 7), (32, 64), (33, 65), (64, 1), (100, 130), (150, 24)])
+@pytest.mark.parametrize("n,m", [(1, 1), (5, 3), (31, 7), (32, 64), (33, 65), (64, 1), (65, 2), (100, 130),
+                                 (150, 24), (200, 300)])
 @pytest.mark.parametrize("with_l", [False, True])
 def test_condense_random(gpu_lib, method, n, m, with_l):
     ne = 5
@@ -185,7 +186,7 @@ def test_condense_methods_agree_and_nonfinite(gpu_lib):
     G = meshgen.spd_batch(3, 300, 1e4, seed=90)
     B = np.random.default_rng(91).standard_normal((3, 300, 40))
     out = {}
-    for meth in ("fma", "tc"):
+    for meth in ("fma", "tc", "tcgen05"):
         dpg.dpg_condense_set_method(meth)
         K, _, _, code, _ = run(dpg, G, B)
         assert code == 0
@@ -193,11 +194,14 @@ def test_condense_methods_agree_and_nonfinite(gpu_lib):
     dpg.dpg_condense_set_method("tc")
     for e in range(3):
         tol = 8 * 300 * EPS * np.linalg.cond(G[e])
-        assert np.linalg.norm(out["tc"][e] - out["fma"][e]) <= tol * np.linalg.norm(out["fma"][e])
+        for meth in ("tc", "tcgen05"):
+            assert np.linalg.norm(out[meth][e] - out["fma"][e]) <= tol * np.linalg.norm(out["fma"][e])
     G2 = G.copy()
     G2[1, 200, 40] = G2[1, 40, 200] = np.nan
+    for meth in ("tc", "tcgen05"):
+        dpg.dpg_condense_set_method(meth)
+        K, _, _, code, bad = run(dpg, G2, B)
+        assert dpg.STATUS[code] == "DPG_ERR_NOT_SPD" and bad == 1
+        assert np.isnan(K[1]).all() and np.isfinite(K[[0, 2]]).all()
     dpg.dpg_condense_set_method("tc")
-    K, _, _, code, bad = run(dpg, G2, B)
-    assert dpg.STATUS[code] == "DPG_ERR_NOT_SPD" and bad == 1
-    assert np.isnan(K[1]).all() and np.isfinite(K[[0, 2]]).all()
     assert dpg._L().dpg_condense_set_method(7) == 1
