@@ -6,8 +6,8 @@
 // One CTA per element at a time (persistent), one CTA per SM; right-looking blocked
 // Cholesky in panels of 64 columns, the load vector carried as column m of the right-hand
 // side [B | l], so that F is row m of the extended product [W | y]^T [W | y].  Per panel kb:
-//   F-phase (FP64): the 64 x 64 diagonal block is factored (a thread owns 9 entries of its
-//     lower triangle), L11 is written to G and X = L11^-1 formed by forward substitution.
+//   F-phase (FP64, shared memory): the 64 x 64 diagonal block is factored, L11 is written to
+//     G and X = L11^-1 formed by forward substitution.
 //   P-phase (panel products, digits): L21 = A21 X^T in 128-row blocks and W1^T = B1^T X^T
 //     in 128-column blocks: the rows of A21 (of B1^T) and of X are split into seven BF16
 //     digit planes, the products run on the tensor cores, the FP64 results are written back
@@ -59,8 +59,9 @@ static_assert(C5_SMEM <= 232448, "shared memory");
 constexpr int C5_LD = C5_NB + 1;
 constexpr uint32_t OFF_SD = OFF_A;                                      // double[64][65] L11
 constexpr uint32_t OFF_SX = OFF_SD + C5_NB * C5_LD * 8;                 // double[64][65] X
-constexpr uint32_t OFF_SV = OFF_SX + C5_NB * C5_LD * 8;                 // double[64] 1 / L_jj
-static_assert(OFF_SV + 64 * 8 <= C5_S * C5_APLANE, "F-phase arrays");
+constexpr uint32_t OFF_SV = OFF_SX + C5_NB * C5_LD * 8;                 // double[64] 1 / L_jj, then
+                                                                        // u16[2080] triangle order
+static_assert(OFF_SV + 64 * 8 + C5_NB * (C5_NB + 1) <= C5_S * C5_APLANE, "F-phase arrays");
 
 // Byte offset of the 16-byte chunk `chunk` (digits 8 chunk .. 8 chunk + 7) of row r within a
 // plane: K-major with the 128-byte swizzle, a row's 64 digits in one 128-byte line, its
@@ -427,77 +428,66 @@ __global__ void __launch_bounds__(C5_NTH, 1) condense5_kernel(Cond5Params p) {
             double (*sD)[C5_LD] = reinterpret_cast<double (*)[C5_LD]>(sm + OFF_SD);
             double (*sX)[C5_LD] = reinterpret_cast<double (*)[C5_LD]>(sm + OFF_SX);    // sX[j][t] = X_jt
             double *srd = reinterpret_cast<double *>(sm + OFF_SV);                      // 1 / L_jj
+            unsigned short *stab = reinterpret_cast<unsigned short *>(sm + OFF_SV + 64 * 8);
             if (worker) {
-                // The block, padded to 64 x 64 with the identity, as its lower triangle in the
-                // order column 63, 62, .., 0 (rows ascending within a column): entry idx of a
-                // thread is tid + 256 i.  Step j of the factorization updates the entries of
-                // the columns right of j, i.e. exactly the idx below T_j = (63-j)(64-j)/2, so a
-                // warp's FP64 instructions have all their lanes busy but for one warp per i.
-                constexpr int NE = (C5_NB * (C5_NB + 1) / 2 + C5_WORKERS - 1) / C5_WORKERS;    // 9
-                int er[NE], ec[NE];
-                double v[NE];
-#pragma unroll
-                for (int i = 0; i < NE; ++i) {
-                    const int idx = tid + C5_WORKERS * i;
-                    int k = 0;
-                    while ((k + 1) * (k + 2) / 2 <= idx && k < C5_NB) ++k;
-                    const bool ok = idx < C5_NB * (C5_NB + 1) / 2;
-                    ec[i] = ok ? C5_NB - 1 - k : -1;
-                    er[i] = ok ? ec[i] + idx - k * (k + 1) / 2 : -1;
-                    const int r = er[i], c = ec[i];
-                    v[i] = !ok ? 0.0 : (r < w && c < w) ? G[(size_t)(kb + r) * n + kb + c] : (r == c ? 1.0 : 0.0);
+                // The block, padded to 64 x 64 with the identity, in shared memory.  Every loop
+                // runs over exactly its active entries (dynamic bounds): a predicated FP64
+                // instruction costs the FP64 pipe as much as an active one on this part, so
+                // idle warps must not issue.  tab[idx] = (r, c) of the lower triangle in the
+                // order column 63, 62, .., 0 (rows ascending): step j updates the columns
+                // right of j, exactly the idx below T_j = (63-j)(64-j)/2.
+                for (int idx = tid; idx < C5_NB * (C5_NB + 1) / 2; idx += C5_WORKERS) {
+                    int k = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+                    if ((k + 1) * (k + 2) / 2 <= idx) ++k;
+                    if (k * (k + 1) / 2 > idx) --k;
+                    const int c = C5_NB - 1 - k, r = c + idx - k * (k + 1) / 2;
+                    stab[idx] = (unsigned short)(r | (c << 8));
                 }
-                // right-looking: at step j the pivot (final since step j - 1) gives L_jj, the
-                // column-j owners scale and publish L_rj, the columns right of j are updated
+                for (int idx = tid; idx < C5_NB * C5_NB; idx += C5_WORKERS) {
+                    const int r = idx >> 6, c = idx & 63;
+                    sD[r][c] = c > r ? 0.0 : (r < w && c < w) ? G[(size_t)(kb + r) * n + kb + c] : (r == c ? 1.0 : 0.0);
+                    sX[r][c] = r == c ? 1.0 : 0.0;
+                }
+                worker_sync();
+                // right-looking Cholesky: the pivot gives L_jj, column j is scaled, the columns
+                // right of j are updated
                 for (int j = 0; j < w; ++j) {
-#pragma unroll
-                    for (int i = 0; i < NE; ++i)
-                        if (er[i] == j && ec[i] == j) {
-                            const double d = v[i];
-                            if (!(d > 0.0) || !isfinite(d)) *sbad = 1;
-                            const double rs = rsqrt(d);
-                            srd[j] = rs;
-                            v[i] = d * rs;
-                            sD[j][j] = v[i];
-                        }
+                    if (tid == 0) {
+                        const double d = sD[j][j];
+                        if (!(d > 0.0) || !isfinite(d)) *sbad = 1;
+                        const double rs = rsqrt(d);
+                        srd[j] = rs;
+                        sD[j][j] = d * rs;
+                    }
                     worker_sync();
                     const double rj = srd[j];
-#pragma unroll
-                    for (int i = 0; i < NE; ++i)
-                        if (ec[i] == j && er[i] > j) {
-                            v[i] *= rj;
-                            sD[er[i]][j] = v[i];
-                        }
+                    for (int r = j + 1 + tid; r < C5_NB; r += C5_WORKERS) sD[r][j] *= rj;
                     worker_sync();
                     const int Tj = (C5_NB - 1 - j) * (C5_NB - j) / 2;
-#pragma unroll
-                    for (int i = 0; i < NE; ++i)
-                        if (tid + C5_WORKERS * i < Tj) v[i] = fma(-sD[er[i]][j], sD[ec[i]][j], v[i]);
-                }
-                // L11 into G (sD holds it since each column's step)
-#pragma unroll
-                for (int i = 0; i < NE; ++i) {
-                    const int r = er[i], c = ec[i];
-                    if (r >= 0 && r < w && c < w) G[(size_t)(kb + r) * n + kb + c] = v[i];
-                }
-                worker_sync();
-                // X = L11^-1, right-looking on the same entries: row t of X is final at step t
-                // (scaled by 1 / L_tt and published), then X_rc -= L_rt X_tc for c <= t < r
-#pragma unroll
-                for (int i = 0; i < NE; ++i) v[i] = (er[i] >= 0 && er[i] == ec[i]) ? 1.0 : 0.0;
-                for (int t = 0; t < w; ++t) {
-#pragma unroll
-                    for (int i = 0; i < NE; ++i)
-                        if (er[i] == t) {
-                            v[i] *= srd[t];
-                            sX[t][ec[i]] = v[i];
-                        }
+                    for (int idx = tid; idx < Tj; idx += C5_WORKERS) {
+                        const int rc = stab[idx], r = rc & 255, c = rc >> 8;
+                        sD[r][c] = fma(-sD[r][j], sD[c][j], sD[r][c]);
+                    }
                     worker_sync();
-#pragma unroll
-                    for (int i = 0; i < NE; ++i)
-                        if (ec[i] >= 0 && ec[i] <= t && er[i] > t && er[i] < w) v[i] = fma(-sD[er[i]][t], sX[t][ec[i]], v[i]);
                 }
-                worker_sync();
+                // L11 into G
+                for (int idx = tid; idx < w * w; idx += C5_WORKERS) {
+                    const int r = idx / w, c = idx - r * w;
+                    if (c <= r) G[(size_t)(kb + r) * n + kb + c] = sD[r][c];
+                }
+                // X = L11^-1 by right-looking forward substitution: row t of X is final at step t
+                // (scaled by 1 / L_tt), then X_rc -= L_rt X_tc for c <= t < r < w
+                for (int t = 0; t < w; ++t) {
+                    const double rt = srd[t];
+                    for (int c = tid; c <= t; c += C5_WORKERS) sX[t][c] *= rt;
+                    worker_sync();
+                    const int nc = t + 1, cnt = (w - 1 - t) * nc;
+                    for (int q = tid; q < cnt; q += C5_WORKERS) {
+                        const int rr = q / nc, c = q - rr * nc, r = t + 1 + rr;
+                        sX[r][c] = fma(-sD[r][t], sX[t][c], sX[r][c]);
+                    }
+                    worker_sync();
+                }
                 // digits of X (rows j, K index t) -> B buffer 0, exponents -> eB slot 0
                 const bool bad = c5_split_rows([&](int j, int t) { return (j < w && t <= j) ? sX[j][t] : 0.0; }, 1,
                                                sm + OFF_B, C5_BPLANE, eB, warp, lane);
