@@ -99,7 +99,7 @@ def parse():
     ap.add_argument("--elems", type=int, default=0,
                     help="elements of the --only case (default: all) or of the dpg_q6_p4_16x16x16 record")
     ap.add_argument("--fp32", action="store_true", help="FP32 form for the --only case")
-    ap.add_argument("--condense", default="tc", choices=["tc", "tcgen05", "fma"],
+    ap.add_argument("--condense", default="tcgen05", choices=["tcgen05", "tc", "fma"],
                     help="arithmetic of the condensation updates in the dpg_q6_p4_16x16x16 record")
     return ap.parse_args()
 
@@ -1051,6 +1051,24 @@ def run_dpg_chain(args):
         # is no longer its bound, only the yardstick of the FP64 work it stands for
         cd.update({"bound": "tensor digit products + FP64 panels",
                    "ratio_to_fp64_fma_peak": cf / (cms * 1e-3) / peak64})
+    # the other digit route (mma.sync) on the same inputs, for comparison
+    other = "tc" if args.condense == "tcgen05" else ("tcgen05" if args.condense == "tc" else None)
+    if other:
+        dpg.dpg_condense_set_method(other)
+        ts = []
+        for i in range(2):
+            refresh()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stages["condense"]()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i:
+                ts.append(a.elapsed_time(b))
+        dpg.dpg_condense_set_method(args.condense)
+        refresh()
+        cd["other_route"] = {"method": other, "ms": float(np.median(ts))}
     tot = sum(st["ms"] for st in rec["stages"].values())
     rec["element_routine_ms"] = tot
     rec["element_routines_per_s"] = ne / (tot * 1e-3)

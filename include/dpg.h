@@ -283,7 +283,9 @@ int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vert
  * columns [B | B~] as one matrix) and l the load vector.  Steps as the paper names them:
  * Cholesky factorization G = L L^T, the substitutions W = L^-1 B and y = L^-1 l, and the
  * products K = W^T W, F = W^T y.  FP64 results; the O(n^3) updates and W^T W run on the
- * tensor cores as exact digit products unless dpg_condense_set_method selects FP64 FMA.
+ * tensor cores as exact digit products unless dpg_condense_set_method selects FP64 FMA
+ * (with the default method the load vector rides along as one more column of B, so that
+ * y and F come out of the same products).
  *   n_elem   : number of elements (0 does nothing).
  *   n, m     : 1 <= n <= 8192, 1 <= m <= 8192.
  *   G        : device, double[n_elem][n][n] row-major.  Only the lower triangle is read;
@@ -297,9 +299,12 @@ int dpg_integrate_load(int space, int q_test, int64_t n_elem, const double *vert
  *   stream   : cudaStream_t.
  * An element whose G is not positive definite gets NaN in K (and F) and is reported as
  * DPG_ERR_NOT_SPD through dpg_sync_status; its G, B, l are left partially factored.  With
- * DPG_CONDENSE_TC, a value of B that is not finite is reported the same way (the FMA
- * route lets it propagate as NaN into K and F without a status).
- * No workspace is allocated (everything happens in place).
+ * the digit-product methods, a value of B or l that is not finite is reported the same way
+ * (the FMA route lets it propagate as NaN into K and F without a status).
+ * Workspace: none for DPG_CONDENSE_FMA and DPG_CONDENSE_TC (everything happens in place);
+ * DPG_CONDENSE_TCGEN05 takes a digit scratch of about 0.9 (ceil(n / 128) + ceil((m + 1) /
+ * 128)) 128 kB per SM from the library pool, stream-ordered (1.1 MB per SM at n = 882,
+ * m = 192), released before the call returns to the stream.
  * Errors: DPG_ERR_ARG, DPG_ERR_RANGE (n or m), DPG_ERR_CUDA. */
 int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, double *K, double *F,
                  void *stream);
@@ -307,17 +312,24 @@ int dpg_condense(int64_t n_elem, int n, int m, double *G, double *B, double *l, 
 /* Arithmetic of the condensation's trailing updates (the O(n^3) and O(n^2 m) part of
  * dpg_condense and dpg_condensed_system) and of K = W^T W, for every later call in the
  * process:
- *   DPG_CONDENSE_FMA: FP64 fused multiply-adds.
- *   DPG_CONDENSE_TC : (the default) the same FP64 products from exact BF16 digits on the
- *                     tensor cores -- each operand row split as 2^e sum_{u<7} d_u 2^-(8u+7)
- *                     with balanced digits |d_u| <= 128, the digit products summed exactly
- *                     in FP32 and combined in a 64-bit integer, entering the FP64 result
- *                     once per product; what is dropped lies below about 2^-53 of the
- *                     product of the two rows' maxima, so the results agree with the FMA
- *                     route normwise (relative to the row maxima), not entry by entry: an
- *                     entry far below its row's maximum keeps fewer correct bits.
- * The factorization of the diagonal blocks and F = W^T y stay FP64 FMA in both (the panel
- * products with the inverse diagonal blocks follow the method).  Errors: DPG_ERR_ARG. */
+ *   DPG_CONDENSE_FMA    : FP64 fused multiply-adds (panels of 32 columns).
+ *   DPG_CONDENSE_TC     : the same FP64 products from exact BF16 digits on the tensor cores
+ *                         (mma.sync, panels of 32) -- each operand row split as
+ *                         2^e sum_{u<7} d_u 2^-(8u+7) with balanced digits |d_u| <= 128, the
+ *                         digit products summed exactly in FP32 and combined in a 64-bit
+ *                         integer, entering the FP64 result once per product; what is dropped
+ *                         lies below about 2^-53 of the product of the two rows' maxima, so
+ *                         the results agree with the FMA route normwise (relative to the row
+ *                         maxima), not entry by entry: an entry far below its row's maximum
+ *                         keeps fewer correct bits.
+ *   DPG_CONDENSE_TCGEN05: (the default) the same digit scheme on the fifth-generation tensor
+ *                         cores (tcgen05, accumulators in tensor memory), panels of 64, the
+ *                         digits of each panel's rows split once and reused by every tile,
+ *                         the load vector carried as a column of B (F = the last row of the
+ *                         extended W^T W); one CTA per SM and a digit scratch (dpg_condense).
+ * The factorization of the diagonal blocks stays FP64 in every method (the panel products
+ * with the inverse diagonal blocks follow the method; F = W^T y is FP64 FMA in the first
+ * two).  Errors: DPG_ERR_ARG. */
 #define DPG_CONDENSE_FMA     0
 #define DPG_CONDENSE_TC      1
 #define DPG_CONDENSE_TCGEN05 2

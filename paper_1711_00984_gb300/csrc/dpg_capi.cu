@@ -32,7 +32,7 @@ int g_max_dyn_smem_tcc = 0;                              // and for the stage-C 
 int g_smem_per_sm = 0;                                   // shared memory of an SM
 int g_tc_stall_once = 0;                                 // test hook, see dpg_test_stall_tc_once
 int g_num_sms = 152;                                     // set at device set-up
-int g_condense_method = DPG_CONDENSE_TC;                 // see dpg_condense_set_method
+int g_condense_method = DPG_CONDENSE_TCGEN05;                 // see dpg_condense_set_method
 size_t g_ws_limit_test = 0;                              // see dpg_test_set_workspace_limit
 
 struct TableEntry {

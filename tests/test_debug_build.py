@@ -110,7 +110,7 @@ for method in ("tc", "fma", "tcgen05"):
     tol = 8 * 70 * 2.220446049250313e-16 * 1e3       # 8 n eps cond(G), as in the release tests
     check(("condense K", method), K, Kr, tol)
     check(("condense F", method), F, Fr, tol)
-dpg.dpg_condense_set_method("tc")
+dpg.dpg_condense_set_method("tcgen05")
 print("debug build ok")
 '''
 

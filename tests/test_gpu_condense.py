@@ -22,7 +22,7 @@ def method(request, gpu_lib):
     digits on the tensor cores, mma.sync or tcgen05) meets the same tolerance."""
     gpu_lib.dpg_condense_set_method(request.param)
     yield request.param
-    gpu_lib.dpg_condense_set_method("tc")
+    gpu_lib.dpg_condense_set_method("tcgen05")
 
 
 def run(dpg, G, B, l=None):
@@ -191,7 +191,7 @@ def test_condense_methods_agree_and_nonfinite(gpu_lib):
         K, _, _, code, _ = run(dpg, G, B)
         assert code == 0
         out[meth] = K
-    dpg.dpg_condense_set_method("tc")
+    dpg.dpg_condense_set_method("tcgen05")
     for e in range(3):
         tol = 8 * 300 * EPS * np.linalg.cond(G[e])
         for meth in ("tc", "tcgen05"):
@@ -203,5 +203,5 @@ def test_condense_methods_agree_and_nonfinite(gpu_lib):
         K, _, _, code, bad = run(dpg, G2, B)
         assert dpg.STATUS[code] == "DPG_ERR_NOT_SPD" and bad == 1
         assert np.isnan(K[1]).all() and np.isfinite(K[[0, 2]]).all()
-    dpg.dpg_condense_set_method("tc")
+    dpg.dpg_condense_set_method("tcgen05")
     assert dpg._L().dpg_condense_set_method(7) == 1
