@@ -356,13 +356,14 @@ int dpg_condensed_system(int q_test, int p_trial, int64_t n_elem, const double *
                          const double *coeffs, const double *src_coef, int64_t coef_stride, double *K,
                          double *F, void *stream);
 
-/* Test hook (not part of the method): the next launch of an FP32 tensor-core kernel of
- * the general map (DPG_FP32 through dpg_integrate) runs with its first CTA never
- * completing its tensor-core products (no stage-B product, or no commit of the stage-C
- * products), so that CTA's bounded mbarrier waits run out (after about a second), the CTA
- * releases its tensor memory and records DPG_ERR_TIMEOUT (first_bad = its first element);
- * the other CTAs and later calls are unaffected.  Exercises the kernels' failure path
- * without a GPU fault.  Returns DPG_OK. */
+/* Test hook (not part of the method): the next launch of a tcgen05 kernel -- the FP32
+ * contraction of the general map (DPG_FP32 through dpg_integrate) or the condensation
+ * (DPG_CONDENSE_TCGEN05 through dpg_condense / dpg_condensed_system) -- runs with its first
+ * CTA never completing its tensor-core products (no stage-B product, no commit of the
+ * stage-C products, or no first panel product), so that CTA's bounded mbarrier waits run out
+ * (after about a second), the CTA releases its tensor memory and records DPG_ERR_TIMEOUT
+ * (first_bad = its first element); the other CTAs and later calls are unaffected.  Exercises
+ * the kernels' failure path without a GPU fault.  Returns DPG_OK. */
 int dpg_test_stall_tc_once(void);
 
 /* Test hook (not part of the method): caps the metric-field workspace of one chunk of the

@@ -1157,6 +1157,8 @@ int run_condense(DeviceState *ds, const CondParams &p, cudaStream_t s) {
     Cond5Params q;
     q.n_elem = p.n_elem; q.elem_base = p.elem_base; q.n = p.n; q.m = p.m;
     q.G = p.G; q.B = p.B; q.l = p.l; q.K = p.K; q.F = p.F; q.status = p.status;
+    q.stall_cta = g_tc_stall_once ? 0 : -1;
+    g_tc_stall_once = 0;
     q.scratch_per_cta = condense5_scratch_per_cta(p.n, p.m, p.l != nullptr, &q.lrows, &q.wrows);
     const int grid = (int)std::min<int64_t>(p.n_elem, g_num_sms);
     void *scr = nullptr;

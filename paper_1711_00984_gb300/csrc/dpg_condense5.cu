@@ -517,9 +517,12 @@ __global__ void __launch_bounds__(C5_NTH, 1) condense5_kernel(Cond5Params p) {
                     fence_async_smem();
                 }
                 __syncthreads();
-                if (tid == C5_WORKERS) {
+                if (tid == C5_WORKERS && !*fail) {
                     tc_fence_after();
-                    c5_issue(tbase, sbase + OFF_A, C5_APLANE, sbase + OFF_B, C5_BPLANE, wn, ksteps, mma_done);
+                    // (test hook: a stalled CTA never issues its first product, so its workers'
+                    // bounded wait runs out)
+                    if (!((int)blockIdx.x == p.stall_cta && njob == 0))
+                        c5_issue(tbase, sbase + OFF_A, C5_APLANE, sbase + OFF_B, C5_BPLANE, wn, ksteps, mma_done);
                 }
                 if (worker) {
                     c5_wait(mma_done, njob & 1, fail);

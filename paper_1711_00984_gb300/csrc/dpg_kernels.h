@@ -220,6 +220,7 @@ struct Cond5Params {
     unsigned char *scratch;
     size_t scratch_per_cta;
     int lrows, wrows;
+    int stall_cta;             // test hook: this CTA issues no product for its first panel product (-1: none)
     DevStatus *status;
 };
 
