@@ -19,6 +19,11 @@ q per space; FP32-form vs FP64 speed-up at the stated error"):
                        16^3 H(curl) q = 6 Gram and mixed stiffness B (p = 4), the q = 9 H1 /
                        H(div) elements (general and affine): per call FP64 and FP32 times,
                        rooflines, FP32 error and speed-up, and a sampled oracle rate;
+  * further_workloads: the extruded map (8^3, q = 5, every space, both forms), the
+                       ultraweak acoustics element routine (16^3, q = 6, p = 4) and the DPG
+                       element routine (G, B, l and the condensation K, F) on 912 elements of
+                       the 16^3 H(curl) q = 6 / p = 4 mesh, with the condensation's other
+                       digit route beside it and K, F against the oracle on two elements;
   * roofline         : the dominant kernel of the headline step against the FP64 FMA rate
                        measured in this run; rooflines elsewhere use the measured HBM copy
                        rate (MEASURED_PEAKS.json when present, else measured here), the
@@ -547,6 +552,23 @@ def run_gpu(args):
             configs[name] = secondary_record(args, name, dpg, pk, flush, stream, sh, dev)
             torch.cuda.empty_cache()
 
+    # ---- the workloads past the Gram matrices (rank 0 of a one-GPU run): the extruded map,
+    #      the ultraweak acoustics element routine, and the DPG element routine with the
+    #      condensation on 912 elements of the 16^3 mesh (six waves of one CTA per SM)
+    more = None
+    if single and not args.no_configs:
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup = min(args.steps, 5), min(args.warmup, 2)
+        more = {}
+        for name in ("ext_q5_8x8x8", "acoustics_q6_p4_16x16x16"):
+            more[name] = secondary_full_record(sub, name, dpg, stream, sh, dev)
+            torch.cuda.empty_cache()
+        more["dpg_q6_p4_16x16x16"] = dpg_chain_record(sub, dpg, stream, sh, dev, 912)
+        torch.cuda.empty_cache()
+        code, bad = dpg.dpg_sync_status(sh)
+        if code:
+            raise RuntimeError(f"further workloads: device status {dpg.STATUS.get(code)} at element {bad}")
+
     cpu = None
     if single and not args.no_cpu:
         cnt, t = oracle_sample_hp(SPACES, host_cores())
@@ -563,7 +585,7 @@ def run_gpu(args):
                 "config": workload_config(), "output_gbs": world * out_bytes / (ms_per_step * 1e-3) / 1e9,
                 "gpu_launches": 48 * args.steps, "clocks": clk.summary(), "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "fp32_form": fp32, "hp_calls": hp_calls, "per_q": per_q,
-                "configs": configs, "autotuned_nj_fp64_fp32": tuned,
+                "configs": configs, "further_workloads": more, "autotuned_nj_fp64_fp32": tuned,
                 "per_step_ms": {"min": min(step_ms), "max": max(step_ms)},
                 "notes": {"gpu_launches": "12 library kernels per dpg_integrate_hp graph (work generation 10, "
                                           "geometry 1, persistent contraction 1) x 4 spaces per step",
@@ -770,18 +792,24 @@ SECONDARY = {
 
 def run_secondary(args):
     """Per-call FP64 and FP32 timings, rooflines and FP32 error of a secondary workload."""
-    import numpy as np
     import torch
     import paper_1711_00984_gb300 as dpg
     from paper_1711_00984_gb300 import build as dbuild
-    from paper_1711_00984_gb300 import meshgen
     dbuild.build()
     dpg.load()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
-    sh = int(stream.cuda_stream)
-    wname, q, L, calls = SECONDARY[args.workload]
+    print(json.dumps(secondary_full_record(args, args.workload, dpg, stream, int(stream.cuda_stream), dev)), flush=True)
+
+
+def secondary_full_record(args, name, dpg, stream, sh, dev):
+    """The record of a named secondary workload (its calls in both forms; the acoustics
+    workload also as its element routine)."""
+    import numpy as np
+    import torch
+    from paper_1711_00984_gb300 import meshgen
+    wname, q, L, calls = SECONDARY[name]
     w = meshgen.workload(wname)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     peak64 = dpg.dpg_measure_fma_peak(64, sh)
@@ -850,7 +878,7 @@ def run_secondary(args):
         torch.cuda.empty_cache()
     rec["measured_alu_peaks_tflops"] = {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12}
     rec["autotuned_nj_fp64_fp32"] = tuned
-    if args.workload.startswith("acoustics"):
+    if name.startswith("acoustics"):
         ne = rec["calls"][0]["elements"]
         tot64 = sum(c["fp64"]["ms"] for c in rec["calls"])
         tot32 = sum(c["fp32"]["ms"] for c in rec["calls"])
@@ -863,7 +891,7 @@ def run_secondary(args):
                                      "note": "G, B and l on the paper's CPU; here the G blocks, X and B (no load vector)"}}
         if not args.no_cpu:
             rec["element_routine"]["cpu_baseline"] = _acoustics_oracle_rate(w["verts"], q, L)
-    print(json.dumps(rec), flush=True)
+    return rec
 
 
 def _acoustics_oracle_rate(verts, q, L):
@@ -972,24 +1000,30 @@ def condense_flops(n: int, mc: int) -> float:
 
 
 def run_dpg_chain(args):
-    """The DPG element routine of the mixed-stiffness workload (Eqs. 3.7-3.8): Gram matrix G
-    of H(curl) q = 6, enriched stiffness B (vector-L2 trial p = 4), load vector l (a
-    degree-2 source), then the condensed K = B^T G^-1 B and F = B^T G^-1 l, per stage."""
-    import numpy as np
+    """The DPG element routine of the mixed-stiffness workload, as its own record."""
     import torch
-    import oracle
     import paper_1711_00984_gb300 as dpg
     from paper_1711_00984_gb300 import build as dbuild
-    from paper_1711_00984_gb300 import meshgen
     dbuild.build()
     dpg.load()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
-    sh = int(stream.cuda_stream)
+    print(json.dumps(dpg_chain_record(args, dpg, stream, int(stream.cuda_stream), dev, args.elems)), flush=True)
+
+
+def dpg_chain_record(args, dpg, stream, sh, dev, elems):
+    """The DPG element routine of the mixed-stiffness workload (Eqs. 3.7-3.8): Gram matrix G
+    of H(curl) q = 6, enriched stiffness B (vector-L2 trial p = 4), load vector l (a
+    degree-2 source), then the condensed K = B^T G^-1 B and F = B^T G^-1 l, per stage, on the
+    first `elems` elements of the 16^3 mesh (all when 0)."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1711_00984_gb300 import meshgen
     q, p, L = 6, 4, 8
     w = meshgen.workload("hcurl_q6_p4_16x16x16")
-    vn = np.ascontiguousarray(w["verts"][:args.elems] if args.elems > 0 else w["verts"])
+    vn = np.ascontiguousarray(w["verts"][:elems] if elems > 0 else w["verts"])
     v = torch.from_numpy(vn).to(dev)
     ne = v.shape[0]
     src = np.random.default_rng(6).uniform(-1.0, 1.0, 30)
@@ -1089,8 +1123,7 @@ def run_dpg_chain(args):
                        "entry_point": "dpg_condensed_system"}
     rec["measured_fp64_fma_peak_tflops"] = peak64 / 1e12
     if args.no_cpu:
-        print(json.dumps(rec), flush=True)
-        return
+        return rec
     # the oracle's chain on a bounded sample: its rate and the agreement of K and F
     idx = [0, ne - 1]
     t0 = time.perf_counter()
@@ -1104,7 +1137,7 @@ def run_dpg_chain(args):
                              "F": float(max(np.linalg.norm(Fg[i] - Fo[i]) / np.linalg.norm(Fo[i]) for i in range(2)))}
     rec["cpu_baseline"] = {"value": 2 / dt, "unit": "element routines/s", "cores": host_cores(), "kind": "oracle",
                            "sample": f"elements 0 and {ne - 1}: gram, mixed_b, load, condense"}
-    print(json.dumps(rec), flush=True)
+    return rec
 
 
 def run_case(args):
