@@ -90,6 +90,19 @@ def test_condense_config_sizes(gpu_lib, method):
     check(G, K, F, Kr, Fr)
 
 
+def test_condense_large(gpu_lib, method):
+    """n = 1400, m = 300 with the load column: 22 panels, up to 11 row blocks of the factor's
+    digits per panel, 3 blocks of W, a ragged last panel (n = 21 64 + 56)."""
+    G = meshgen.spd_batch(2, 1400, 1e3, seed=96)
+    rng = np.random.default_rng(97)
+    B = rng.standard_normal((2, 1400, 300))
+    l = rng.standard_normal((2, 1400))
+    K, F, _, code, _ = run(gpu_lib, G, B, l)
+    Kr, Fr, _ = oracle.condense(G, B, l)
+    assert code == 0
+    check(G, K, F, Kr, Fr)
+
+
 def test_condense_not_spd_and_args(gpu_lib, method):
     dpg = gpu_lib
     G = meshgen.spd_batch(4, 40, 1e2, seed=83)
