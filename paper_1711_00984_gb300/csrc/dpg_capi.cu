@@ -832,19 +832,23 @@ int enqueue_hp(DeviceState *ds, int space, int64_t n, const double *verts, const
     p.item_k = (int *)wit; p.scan_tmp = (int64_t *)wtmp; p.fields = wfield;
     const size_t smem = ds->hp_smem[fp32 ? 1 : 0][base];
     const int ctas = g_num_sms * hp_ctas_per_sm(fp32, smem);
-    // FP32: when every initialised order has a program of the stage-C tensor-core kernel, the
-    // contraction is one launch of that kernel per order (the elements of the order from the
-    // device-side sort), else the persistent kernel over every work item
+    // FP32: when every initialised order has a program of a tcgen05 kernel, the contraction is
+    // one launch per order of the kernel the order's program uses (the stage-C kernel, or the
+    // stages-B-and-C kernel where the autotuner chose it), over the elements of the order from
+    // the device-side sort; else the persistent kernel over every work item
     std::vector<std::pair<ProgEntry *, TableEntry *>> tcc(MAXQ + 1, { nullptr, nullptr });
     bool use_tcc = fp32;
+    int nvalid = 0;
     for (int q = 1; q <= MAXQ && use_tcc; ++q) {
         if (!ds->h_hp[1][base][q].valid) continue;
         auto ai = ds->active_L.find(std::make_pair(base, q));
         if (ai == ds->active_L.end()) { use_tcc = false; break; }
         auto pt = ds->progs.find(ProgKey{ base, q, ai->second, 0, 0 });
         auto tt = ds->tables.find(std::make_pair(q, ai->second));
-        if (pt == ds->progs.end() || tt == ds->tables.end() || !pt->second->tcc.ok) { use_tcc = false; break; }
+        if (pt == ds->progs.end() || tt == ds->tables.end() ||
+            !(pt->second->tcc.ok || pt->second->kind32 == K32_TC)) { use_tcc = false; break; }
         tcc[q] = { pt->second.get(), tt->second.get() };
+        ++nvalid;
     }
     int rc = DPG_OK;
     cudaError_t le;
@@ -854,7 +858,31 @@ int enqueue_hp(DeviceState *ds, int space, int64_t n, const double *verts, const
     }
     for (int q = MAXQ; q >= 1 && use_tcc && le == cudaSuccess; --q) {
         if (!tcc[q].first) continue;
-        const TccProg &tg = tcc[q].first->tcc;
+        ProgEntry *pq = tcc[q].first;
+        if (pq->kind32 == K32_TC) {
+            const Program &pr = pq->prog32;
+            TcParams tp;
+            tp.blocks = pq->d_blocks32; tp.units = pq->d_units32; tp.block_unit_begin = pq->d_block_units32;
+            tp.ctab = pq->d_ctab32; tp.ctab_off = pq->d_ctab_off32;
+            tp.nblock = pr.nblock; tp.nj_max = pr.nj;
+            // about four waves of one CTA per SM for the order's share of the elements (its
+            // count is known on the device only: the batch spread evenly over its orders)
+            const int64_t nest = std::max<int64_t>(1, n / std::max(nvalid, 1));
+            const int64_t target = (int64_t)g_num_sms * 4;
+            const int64_t epc = (nest * pr.nblock + target - 1) / target;
+            tp.elems_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(epc, 1 << 20));
+            tp.L = pr.L; tp.nfields = pr.nfields;
+            tp.pp = tcc[q].second->pp32;
+            tp.fields = reinterpret_cast<const float *>(p.fields); tp.foff = p.foff;
+            tp.out = reinterpret_cast<float *>(out); tp.out_off = out_offset;
+            tp.mat_stride = (int64_t)pr.parts * pr.rows * pr.cols; tp.ld = pr.cols; tp.n_elem = n;
+            tp.n_elem_dev = p.hist + q; tp.elist = p.order; tp.elist_start = p.bstart + q;
+            tp.status = ds->status; tp.stall_cta = -1;
+            TraceRange tr("dpg hp: contraction of one order, FP32, stages B and C on tcgen05");
+            le = launch_tc_f32(tp, pr.smem_bytes, s);
+            continue;
+        }
+        const TccProg &tg = pq->tcc;
         const Program &pr = tg.prog;
         TccParams tp;
         tp.blocks = tg.d_blocks; tp.nblock = pr.nblock; tp.blk_base = tg.d_base;

@@ -125,6 +125,11 @@ struct TcParams {
     int64_t mat_stride, ld, n_elem;
     DevStatus *status;
     int stall_cta;                 // test hook: this CTA issues no stage-B MMA (-1: none)
+    // the elements of one order of an hp batch (all NULL for a uniform batch): element i of
+    // the launch is elist[*elist_start + i], *n_elem_dev of them (n_elem: their maximum),
+    // its fields at fields + foff[e], its matrix at out + out_off[e]
+    const int *elist = nullptr, *elist_start = nullptr, *n_elem_dev = nullptr;
+    const int64_t *foff = nullptr, *out_off = nullptr;
 };
 
 // FP32 general kernel with stage C on the tensor cores (sf_tcc_kernel): a persistent grid

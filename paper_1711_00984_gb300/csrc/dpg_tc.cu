@@ -59,8 +59,16 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k = blockIdx.x % p.nblock;
     const int64_t e0 = (int64_t)(blockIdx.x / p.nblock) * p.elems_per_cta;
-    const int64_t e1 = min(e0 + (int64_t)p.elems_per_cta, p.n_elem);
+    const int64_t e1 = min(e0 + (int64_t)p.elems_per_cta, p.n_elem_dev ? (int64_t)*p.n_elem_dev : p.n_elem);
     if (e0 >= e1) return;
+    // element i of the launch -> its output matrix and its metric fields
+    const int estart = p.elist_start ? *p.elist_start : 0;
+    auto out_of = [&](int64_t i) -> float * {
+        return p.out + (p.elist ? p.out_off[p.elist[estart + i]] : i * p.mat_stride);
+    };
+    auto fields_of = [&](int64_t i) -> const float * {
+        return p.fields + (p.elist ? p.foff[p.elist[estart + i]] : i * (int64_t)p.nfields * p.L * p.L * p.L);
+    };
     load_block_tc(p.blocks + k, bd);
     __syncthreads();
     const int ub = p.block_unit_begin[k], ue = p.block_unit_begin[k + 1];
@@ -70,7 +78,7 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
         const int nr = bd.nr[0] * bd.nr[1] * bd.nr[2], nc = bd.nc[0] * bd.nc[1] * bd.nc[2];
         const int nw = TC_NTH / 32;
         for (int64_t e = e0; e < e1; ++e) {
-            float *o = p.out + (size_t)e * p.mat_stride + bd.base + (int64_t)bd.row_off * ld + bd.col_off;
+            float *o = out_of(e) + bd.base + (int64_t)bd.row_off * ld + bd.col_off;
             for (int r = warp; r < nr; r += nw)
                 for (int c = lane; c < nc; c += 32) o[r * ld + c] = 0.0f;
         }
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
             const Unit u = p.units[ui];
             const int nj = u.nj;
             if (e != fe_loaded) {                  // metric fields of the element's terms
-                const float *src = p.fields + (size_t)e * p.nfields * L3;
+                const float *src = fields_of(e);
                 for (int sl = 0; sl < f.nfs; ++sl) {
                     const float *fs = src + (size_t)bd.slot_field[sl] * L3;
                     for (int i = tid; i < L3; i += TC_NP * 32) cp_async4(F + sl * L3 + i, fs + i);
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(TC_NTH, 1) sf_tc_f32_kernel(TcParams p) {
         const unsigned mnch = magic(nch);
         // destination of tile row r of unit u (element e) and its row shift
         auto out_row = [&](int64_t e, const Unit &u, int r) -> float * {
-            return p.out + (size_t)e * p.mat_stride + bd.base + (bd.row_off + (int64_t)u.i3 * f.nrow + r) * ld +
+            return out_of(e) + bd.base + (bd.row_off + (int64_t)u.i3 * f.nrow + r) * ld +
                    bd.col_off + (int64_t)u.j3b * nc1 * nc2;
         };
         auto set_rows = [&](int64_t e, const Unit &u, int b) {

@@ -5,6 +5,8 @@ the parity tests pin to the oracle), and a sample of elements is checked against
 oracle directly.  Also: invalid orders are skipped and reported, graph replay reads the
 current contents of the input buffers, and the FP32 form stays within its target error.
 """
+import json
+
 import numpy as np
 import pytest
 import torch
@@ -108,3 +110,36 @@ def test_hp_empty_and_errors(gpu_lib, hp_case):
     assert out.numel() == 0
     assert dpg.dpg_integrate_hp(5, 1, 16, 0, 16, 16, 16, 0) == 1                     # B: not an hp space
     assert dpg.dpg_integrate_hp(1 | dpg.DPG_MAP_AFFINE, 1, 16, 0, 16, 16, 16, 0) == 1
+
+
+def test_hp_fp32_runs_the_autotuned_kernel_per_order(gpu_lib, hp_case, tmp_path, monkeypatch):
+    """FP32 hp batch where the autotuner's cached choice puts some orders on the tcgen05
+    kernel with stages B and C on the tensor cores (stage-A chunk nj > 0) and the others on
+    the stage-C kernel (nj = 0): the graph launches each order's own kernel over the elements
+    of that order, and every matrix matches the uniform path."""
+    dpg = gpu_lib
+    verts, q = hp_case
+    v = torch.from_numpy(verts).cuda()
+    qt = torch.from_numpy(q).cuda()
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("DPG_AUTOTUNE_CACHE", str(cache))
+    forced = {("HDIV", 3): 4, ("HCURL", 4): 3, ("HCURL", 2): 2}
+
+    def install(choice):
+        cache.write_text("".join(
+            json.dumps({"space": dpg.space_id(s) & 0xff, "q": qq, "L": qq + 2, "fp32": 1, "nj": nj, "ms": 0.0}) + "\n"
+            for (s, qq), nj in choice.items()))
+        for (s, qq), nj in choice.items():
+            assert dpg.dpg_autotune(qq, s, True) == nj
+    install(forced)
+    try:
+        for space in ("HDIV", "HCURL"):
+            out, off = dpg.integrate_hp(space, v, qt, fp32=True)
+            assert dpg.sync_status() == (0, -1)
+            mats = _unpack(out.double().cpu(), off.cpu(), q, space, dpg)
+            for e in range(len(q)):
+                ref = dpg.integrate(space, int(q[e]), v[e:e + 1].contiguous())[0].cpu()
+                err = float(torch.linalg.norm(mats[e] - ref) / torch.linalg.norm(ref))
+                assert err <= TOL32, (space, e, int(q[e]), err)
+    finally:
+        install({k: 0 for k in forced})              # back to the stage-C kernel
