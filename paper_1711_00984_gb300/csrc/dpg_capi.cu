@@ -49,6 +49,11 @@ struct AffProg {
     unsigned char *d_img = nullptr; // constant shared-memory images of the blocks
     int *d_img_off = nullptr;       // [nblock + 1], 16-byte units
     size_t smem_values = 0;         // values of the kernel's shared memory
+    // the matrix is diagonal whatever the element (affine only): its terms and the products
+    // D_t(r) of their diagonal exact 1D integrals, [nterm][rows]
+    bool diag = false;
+    double *d_diag = nullptr;
+    int diag_nterm = 0, diag_field[AFF_DIAG_MAXT] = {}, diag_sign[AFF_DIAG_MAXT] = {};
 };
 
 // Program of the FP32 general kernel with stage C on the tensor cores (sf_tcc_kernel).
@@ -334,6 +339,35 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         if ((r = upload(ub.data(), ub.size(), &ap.d_block_units))) return r;
         if (m * (prec ? sizeof(float) : sizeof(double)) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
         ap.smem_values = m;
+        // one square block whose every term has diagonal exact 1D integrals in each direction
+        // (the L2 Gram matrix of an affine element, by the Legendre orthogonality of
+        // Eq. 2.95): the matrix is diagonal for every element, written by a fill kernel
+        const BlockDesc &b0 = pa.blocks[0];
+        ap.diag = pa.nblock == 1 && pa.parts == 1 && b0.row_off == 0 && b0.col_off == 0 &&
+                  b0.nterm <= AFF_DIAG_MAXT && !split;
+        for (int d = 0; d < 3 && ap.diag; ++d) ap.diag = b0.nr[d] == b0.nc[d];
+        for (int t = 0; t < b0.nterm && ap.diag; ++t)
+            for (int d = 0; d < 3 && ap.diag; ++d) {
+                const TermDesc &td = b0.term[t];
+                const int pair = 3 * td.kr[d] + td.kc[d], nd = b0.nr[d];
+                for (int i = 0; i < nd && ap.diag; ++i)
+                    for (int j = 0; j < nd && ap.diag; ++j)
+                        if (i != j && tab.F[((size_t)pair * NQ1 + i) * NQ1 + j] != 0.0) ap.diag = false;
+            }
+        if (ap.diag) {
+            const int n = pa.rows, n1 = b0.nr[0], n2 = b0.nr[1];
+            std::vector<double> D((size_t)b0.nterm * n);
+            for (int t = 0; t < b0.nterm; ++t) {
+                const TermDesc &td = b0.term[t];
+                auto Fd = [&](int d, int i) { return tab.F[((size_t)(3 * td.kr[d] + td.kc[d]) * NQ1 + i) * NQ1 + i]; };
+                for (int r = 0; r < n; ++r)
+                    D[(size_t)t * n + r] = Fd(0, r % n1) * Fd(1, (r / n1) % n2) * Fd(2, r / (n1 * n2));
+                ap.diag_field[t] = td.field;
+                ap.diag_sign[t] = td.sign;
+            }
+            ap.diag_nterm = b0.nterm;
+            if ((r = upload(D.data(), D.size(), &ap.d_diag))) return r;
+        }
     }
     pe->flops_aff = pe->aff[0].prog.flops_affine;
     for (int prec = 0; prec < 2; ++prec) {
@@ -413,7 +447,7 @@ void free_device_state(DeviceState &ds) {
             for (int i = 0; i < 2; ++i) {
                 AffProg &ap = aps[i];
                 cudaFree(ap.d_blocks); cudaFree(ap.d_units); cudaFree(ap.d_block_units);
-                cudaFree(ap.d_img); cudaFree(ap.d_img_off);
+                cudaFree(ap.d_img); cudaFree(ap.d_img_off); cudaFree(ap.d_diag);
             }
         cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
         cudaFree(kv.second->d_ctab32); cudaFree(kv.second->d_ctab_off32);
@@ -679,7 +713,25 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         le = launch_affine_const(cp, s);
     }
     if (le != cudaSuccess) rc = cuda_fail(le, "affine_const_kernel launch", __LINE__);
-    for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK; e0 += per_launch) {
+    // a matrix diagonal for every element (L2, by Eq. 2.95): one store-bound kernel, its zeros
+    // written while the constants are computed
+    const int64_t span = AFF_DIAG_SPAN_BYTES / (int64_t)sizeof(T), spans = (mat + span - 1) / span;
+    const bool diag = aprog.diag && og.ld == pr.cols && mat == (int64_t)pr.rows * pr.cols &&
+                      (span - 1) / (pr.rows + 1) + 1 <= AFF_DIAG_MAXR && n_elem * spans <= INT_MAX;
+    if (diag && rc == DPG_OK) {
+        AffDiagParams<T> dp;
+        dp.n_elem = n_elem; dp.consts = (const double *)consts;
+        dp.D = aprog.d_diag; dp.nterm = aprog.diag_nterm;
+        for (int t = 0; t < AFF_DIAG_MAXT; ++t) { dp.field[t] = aprog.diag_field[t]; dp.sign[t] = aprog.diag_sign[t]; }
+        dp.out = out; dp.n = pr.rows; dp.span = span;
+        dp.spans = (int)spans; dp.status = ds->status;
+        {
+            TraceRange tr("dpg contraction: affine, diagonal matrix");
+            le = launch_affine_diag<T>(dp, s);
+        }
+        if (le != cudaSuccess) rc = cuda_fail(le, "affine_diag_kernel launch", __LINE__);
+    }
+    for (int64_t e0 = 0; e0 < n_elem && rc == DPG_OK && !diag; e0 += per_launch) {
         const int64_t ne = std::min(per_launch, n_elem - e0);
         AffParams<T> ap;
         ap.blocks = aprog.d_blocks; ap.units = aprog.d_units; ap.block_unit_begin = aprog.d_block_units;

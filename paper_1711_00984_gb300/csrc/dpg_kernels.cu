@@ -25,6 +25,32 @@ __device__ __forceinline__ void report(DevStatus *st, int code, long long elem) 
     atomicMin(&st->first_bad[code], (unsigned long long)elem);
 }
 
+// --------------------------------------------------------------------------------------
+// programmatic dependent launch: a kernel started by pdl_launch may begin while the previous
+// kernel of its stream still runs (once every CTA of that kernel has called
+// pdl_launch_dependents or exited); it calls pdl_wait, which returns when that kernel has
+// completed and its writes are visible, before it reads them.  pdl_wait is a no-op in a
+// kernel launched the ordinary way.
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename T> __device__ __forceinline__ T qnan();
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
@@ -182,6 +208,7 @@ __global__ void __launch_bounds__(256) geom_kernel(GeomParams p) {
 // the same at v and its xi1 neighbour.
 template <typename TF>
 __global__ void __launch_bounds__(256) geom2d_kernel(Geom2dParams p) {
+    pdl_launch_dependents();            // the extruded-mode contraction may start its set-up now
     const int L = p.L, L2 = L * L;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= p.n_elem * L2) return;
@@ -1038,32 +1065,48 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) sf_panel_f32_kernel(
 // Per-element constants of the affine path, one thread per element: the Jacobian from the
 // edge vectors at vertex 0 (the element must be a parallelepiped), its metric fields with
 // unit weight (the 1D integrals F carry the quadrature) and the status of the element.
-__global__ void __launch_bounds__(128) affine_const_kernel(AffConstParams p) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= p.n_elem) return;
-    const double *v = p.verts + 24 * e;
+// Returns the status code (0, DPG_ERR_DEGENERATE or DPG_ERR_NOT_AFFINE) and the number of
+// fields written to fv.
+__device__ __forceinline__ int affine_element_consts(int space, const double *v, const double *coeffs,
+                                                     int64_t e, double *fv, int *nf) {
     Jac g;
-    double scale = 0.0;
+    double x[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) x[k] = v[k];
+    // The deviations of vertices 3, 5, 6 and 7 from the parallelepiped spanned at vertex 0 by
+    // the edges to vertices 1, 2 and 4 must be within 1e-10 max |J|.  Magnitudes are compared
+    // as the bit patterns of non-negative doubles (monotone, on the integer pipe: FP64
+    // instructions are scarce); a non-finite deviation or scale fails the test.
+    constexpr unsigned long long ABS = 0x7fffffffffffffffULL, INF = 0x7ff0000000000000ULL;
+    unsigned long long smax = 0, dmax = 0;
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
-        g.J[i][0] = v[3 * 1 + i] - v[i];
-        g.J[i][1] = v[3 * 2 + i] - v[i];
-        g.J[i][2] = v[3 * 4 + i] - v[i];
-        for (int d = 0; d < 3; ++d) scale = fmax(scale, fabs(g.J[i][d]));
+        const double e1 = x[3 + i] - x[i], e2 = x[6 + i] - x[i], e4 = x[12 + i] - x[i];
+        g.J[i][0] = e1; g.J[i][1] = e2; g.J[i][2] = e4;
+        smax = max(smax, max(__double_as_longlong(e1) & ABS, max(__double_as_longlong(e2) & ABS,
+                                                                  __double_as_longlong(e4) & ABS)));
+        const double d3 = (x[9 + i] - x[i]) - e1 - e2, d5 = (x[15 + i] - x[i]) - e1 - e4;
+        const double d6 = (x[18 + i] - x[i]) - e2 - e4, d7 = (x[21 + i] - x[i]) - e1 - e2 - e4;
+        dmax = max(dmax, max(max(__double_as_longlong(d3) & ABS, __double_as_longlong(d5) & ABS),
+                             max(__double_as_longlong(d6) & ABS, __double_as_longlong(d7) & ABS)));
     }
-    int f = 0;
-    for (int c = 0; c < 8; ++c) {
-        const double s1 = c & 1, s2 = (c >> 1) & 1, s3 = (c >> 2) & 1;
-        for (int i = 0; i < 3; ++i) {
-            const double pred = v[i] + g.J[i][0] * s1 + g.J[i][1] * s2 + g.J[i][2] * s3;
-            if (!(fabs(v[3 * c + i] - pred) <= 1e-10 * scale)) f = 6; /*DPG_ERR_NOT_AFFINE*/
-        }
-    }
+    const unsigned long long tol = (unsigned long long)__double_as_longlong(1e-10 * __longlong_as_double(smax)) & ABS;
+    int f = (tol < INF && dmax <= tol) ? 0 : 6; /*DPG_ERR_NOT_AFFINE*/
     finish_jac(g);
     if (f == 0 && (!(g.det > 0.0) || !isfinite(g.det))) f = 5; /*DPG_ERR_DEGENERATE*/
-    const double c0 = p.coeffs ? p.coeffs[2 * e] : 1.0;
-    const double c1 = p.coeffs ? p.coeffs[2 * e + 1] : 1.0;
+    const double c0 = coeffs ? coeffs[2 * e] : 1.0;
+    const double c1 = coeffs ? coeffs[2 * e + 1] : 1.0;
+    *nf = metric_fields(space, g, 1.0, c0, c1, fv);
+    return f;
+}
+
+__global__ void __launch_bounds__(128) affine_const_kernel(AffConstParams p) {
+    pdl_launch_dependents();            // the consumer may start its set-up now
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.n_elem) return;
     double fv[MAXFIELDS];
-    const int nf = metric_fields(p.space, g, 1.0, c0, c1, fv);
+    int nf = 0;
+    const int f = affine_element_consts(p.space, p.verts + 24 * e, p.coeffs, e, fv, &nf);
     double *dst = p.consts + AFF_CONST_STRIDE * e;
     for (int k = 0; k < nf; ++k) dst[k] = fv[k];
     dst[AFF_CONST_STRIDE - 1] = (double)f;
@@ -1173,6 +1216,7 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         if (!DPG_INB(need <= dpg_dyn_smem_bytes() && img <= (size_t)lay.oC * sizeof(T), p.status, e0)) return;
     }
 #endif
+    pdl_wait();                         // the constants / 2D fields of the kernel before
     for (int64_t e = e0; e < e1; ++e) {                               // the CTA's chunk of elements
     __syncthreads();                                                  // previous element done
     if constexpr (!EXT) {                                             // the element's constants
@@ -1671,7 +1715,9 @@ cudaError_t launch_panel_f32(const PanelParams &p, size_t smem, cudaStream_t s) 
 
 cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s) {
     if (p.n_elem == 0) return cudaSuccess;
-    affine_const_kernel<<<(unsigned)((p.n_elem + 127) / 128), 128, 0, s>>>(p);
+    // one warp per CTA: a thread's few hundred FP64 operations would queue on the FP64 pipe
+    // (2 per clock per SM) of the few SMs that blocks of 128 threads occupy
+    affine_const_kernel<<<(unsigned)((p.n_elem + 31) / 32), 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -1679,18 +1725,79 @@ template <typename T>
 cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s) {
     const int64_t ctas = (int64_t)p.nblock * p.nsplit * ((p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta);
     if (ctas == 0) return cudaSuccess;
-    sf_affine_kernel<T, false><<<(unsigned)ctas, 256, smem, s>>>(p);
-    return cudaGetLastError();
+    return pdl_launch(sf_affine_kernel<T, false>, (unsigned)ctas, 256, smem, s, p);
 }
 template cudaError_t launch_affine<double>(const AffParams<double> &, size_t, cudaStream_t);
 template cudaError_t launch_affine<float>(const AffParams<float> &, size_t, cudaStream_t);
+
+// Store-bound: a CTA per span of one element's matrix, launched after affine_const_kernel
+// as its programmatic dependent: the span's zeros (16-byte stores where aligned) are written
+// while the constants are computed; after pdl_wait the diagonal entries of the span (a failed
+// element: NaN over the span, by the threads that wrote its zeros).
+template <typename T>
+__global__ void __launch_bounds__(256) affine_diag_kernel(AffDiagParams<T> p) {
+    __shared__ double dsh[AFF_DIAG_MAXT * AFF_DIAG_MAXR];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int64_t e = blockIdx.x / p.spans;
+    const int sp = (int)(blockIdx.x - e * p.spans);
+    const int n = p.n;
+    const int64_t nn = (int64_t)n * n;
+    const int64_t s0 = sp * p.span, s1 = min(s0 + p.span, nn);
+    const int64_t r0 = (s0 + n) / (n + 1), r1 = (s1 + n) / (n + 1);  // diagonal r (n + 1) in [s0, s1)
+    const int nd = (int)(r1 - r0), nterm = p.nterm;
+#if defined(DPG_DEBUG_BOUNDS)
+    if (!DPG_INB(nd <= AFF_DIAG_MAXR && nterm <= AFF_DIAG_MAXT && s0 < s1, p.status, e)) return;
+#endif
+    for (int i = tid; i < nterm * nd; i += nth) {
+        const int t = i / nd, j = i - t * nd;
+        dsh[i] = p.D[(size_t)t * n + r0 + j];
+    }
+    T *seg = p.out + e * nn + s0;
+    const int len = (int)(s1 - s0);
+    constexpr int VW = 16 / (int)sizeof(T);
+    using V16 = typename Vec16<T>::type;
+    const int head = min((int)((VW - (int)((reinterpret_cast<uintptr_t>(seg) / sizeof(T)) % VW)) % VW), len);
+    const int nvec = (len - head) / VW, tail0 = head + VW * nvec;
+    auto fill = [&](T v) {
+        if (tid < head) seg[tid] = v;
+        if (tid < len - tail0) seg[tail0 + tid] = v;
+        V16 w;
+        T *wv = reinterpret_cast<T *>(&w);
+#pragma unroll
+        for (int x = 0; x < VW; ++x) wv[x] = v;
+        V16 *s16 = reinterpret_cast<V16 *>(seg + head);
+        for (int i = tid; i < nvec; i += nth) s16[i] = w;
+    };
+    fill(T(0));
+    pdl_wait();                         // the element constants
+    const double *cf = p.consts + AFF_CONST_STRIDE * e;
+    const bool bad = cf[AFF_CONST_STRIDE - 1] != 0.0;
+    __syncthreads();                    // table and zeros before the diagonal
+    if (bad) {
+        fill(qnan<T>());
+    } else {
+        for (int j = tid; j < nd; j += nth) {
+            double acc = 0.0;
+            for (int t = 0; t < nterm; ++t)
+                acc += (p.sign[t] > 0 ? cf[p.field[t]] : -cf[p.field[t]]) * dsh[t * nd + j];
+            p.out[e * nn + (r0 + j) * (n + 1)] = (T)acc;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_affine_diag(const AffDiagParams<T> &p, cudaStream_t s) {
+    if (p.n_elem == 0) return cudaSuccess;
+    return pdl_launch(affine_diag_kernel<T>, (unsigned)(p.n_elem * p.spans), 256, 0, s, p);
+}
+template cudaError_t launch_affine_diag<double>(const AffDiagParams<double> &, cudaStream_t);
+template cudaError_t launch_affine_diag<float>(const AffDiagParams<float> &, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_extruded(const AffParams<T> &p, size_t smem, cudaStream_t s) {
     const int64_t ctas = (int64_t)p.nblock * p.nsplit * ((p.n_elem + p.elems_per_cta - 1) / p.elems_per_cta);
     if (ctas == 0) return cudaSuccess;
-    sf_affine_kernel<T, true><<<(unsigned)ctas, 256, smem, s>>>(p);
-    return cudaGetLastError();
+    return pdl_launch(sf_affine_kernel<T, true>, (unsigned)ctas, 256, smem, s, p);
 }
 template cudaError_t launch_extruded<double>(const AffParams<double> &, size_t, cudaStream_t);
 template cudaError_t launch_extruded<float>(const AffParams<float> &, size_t, cudaStream_t);

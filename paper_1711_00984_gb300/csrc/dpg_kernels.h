@@ -179,6 +179,25 @@ struct AffParams {
     DevStatus *status;         // bounds-checked build only
 };
 
+// Affine elements whose matrix is diagonal for every element (one square block, every term
+// with diagonal exact 1D integrals): zeros, and on the diagonal
+// G_rr = sum_t sign_t c_t D_t(r), D_t(r) = F_t1(i1, i1) F_t2(i2, i2) F_t3(i3, i3),
+// r = i1 + nr1 (i2 + nr2 i3).  A CTA writes a span of one element.
+constexpr int AFF_DIAG_MAXT = 4;            // terms
+constexpr int AFF_DIAG_SPAN_BYTES = 65536;  // output bytes per CTA
+constexpr int AFF_DIAG_MAXR = 192;          // diagonal entries per CTA (shared-memory table)
+template <typename T>
+struct AffDiagParams {
+    int64_t n_elem;
+    const double *consts;                   // [n_elem][AFF_CONST_STRIDE] from affine_const_kernel
+    const double *D;                        // [nterm][n]
+    int nterm, field[AFF_DIAG_MAXT], sign[AFF_DIAG_MAXT];
+    T *out;                                 // [n_elem][n][n]
+    int n, spans;                           // CTAs per element
+    int64_t span;                           // values per CTA
+    DevStatus *status;
+};
+
 // Geometry of extruded elements: metric fields at the (xi2, xi3) Gauss points.
 struct Geom2dParams {
     int space, L, nfields;
@@ -276,6 +295,7 @@ cudaError_t init_tc_attributes(int optin_smem);
 int tc_static_smem();
 cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s);
 template <typename T> cudaError_t launch_affine(const AffParams<T> &p, size_t smem, cudaStream_t s);
+template <typename T> cudaError_t launch_affine_diag(const AffDiagParams<T> &p, cudaStream_t s);
 template <typename T> cudaError_t launch_extruded(const AffParams<T> &p, size_t smem, cudaStream_t s);
 template <typename TF> cudaError_t launch_geom2d(const Geom2dParams &p, cudaStream_t s);
 // Vector-valued Gram matrices (DPG_VEC3): the scalar Gram matrix of each element sits in the

@@ -197,10 +197,12 @@ def test_degenerate_element_reported(gpu_lib):
     assert gpu_lib.sync_status() == (0, -1)                               # cleared
 
 
-def test_non_affine_element_on_affine_path(gpu_lib):
+@pytest.mark.parametrize("space,fp32", [("H1", False), ("L2", False), ("L2", True)])
+def test_non_affine_element_on_affine_path(gpu_lib, space, fp32):
+    # L2: the diagonal-matrix kernel of the affine path (Eq. 2.95), its NaN rows included
     v = meshgen.affine_parallelepipeds(2, seed=4)
     v[2] = meshgen.jittered_grid(2, seed=4, jitter=0.2)[2]
-    got, code, bad = run(gpu_lib, "H1", 2, v, affine=True)
+    got, code, bad = run(gpu_lib, space, 2, v, affine=True, fp32=fp32)
     assert code == 6 and bad == 2
     assert np.all(np.isnan(got[2])) and np.all(np.isfinite(np.delete(got, 2, axis=0)))
 
