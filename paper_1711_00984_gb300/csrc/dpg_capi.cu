@@ -49,6 +49,8 @@ struct AffProg {
     unsigned char *d_img = nullptr; // constant shared-memory images of the blocks
     int *d_img_off = nullptr;       // [nblock + 1], 16-byte units
     size_t smem_values = 0;         // values of the kernel's shared memory
+    unsigned *d_qlist = nullptr;    // structural stage-B lists of the units (affine only)
+    int *d_qoff = nullptr;          // [nunits + 1]
     // the matrix is diagonal whatever the element (affine only): its terms and the products
     // D_t(r) of their diagonal exact 1D integrals, [nterm][rows]
     bool diag = false;
@@ -333,6 +335,13 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         size_t m = 0;
         for (int k = 0; k < pa.nblock; ++k) m = std::max(m, affine_smem_values(pa.blocks[k], pa.nj));
         if ((r = upload_aff_image(ap, tab, false, prec))) return r;
+        {
+            std::vector<unsigned> ql;
+            std::vector<int> qo;
+            if (!build_aff_qlists(pa, tab, ql, qo)) return DPG_ERR_RANGE;
+            if ((r = upload(ql.data(), ql.size(), &ap.d_qlist))) return r;
+            if ((r = upload(qo.data(), qo.size(), &ap.d_qoff))) return r;
+        }
         std::vector<int> ub(pa.nblock + 1, 0);
         for (const Unit &u : pa.units) ub[u.block + 1]++;
         for (int k = 0; k < pa.nblock; ++k) ub[k + 1] += ub[k];
@@ -448,6 +457,7 @@ void free_device_state(DeviceState &ds) {
                 AffProg &ap = aps[i];
                 cudaFree(ap.d_blocks); cudaFree(ap.d_units); cudaFree(ap.d_block_units);
                 cudaFree(ap.d_img); cudaFree(ap.d_img_off); cudaFree(ap.d_diag);
+                cudaFree(ap.d_qlist); cudaFree(ap.d_qoff);
             }
         cudaFree(kv.second->d_blocks32); cudaFree(kv.second->d_units32); cudaFree(kv.second->d_block_units32);
         cudaFree(kv.second->d_ctab32); cudaFree(kv.second->d_ctab_off32);
@@ -736,7 +746,7 @@ int run_affine(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem, c
         AffParams<T> ap;
         ap.blocks = aprog.d_blocks; ap.units = aprog.d_units; ap.block_unit_begin = aprog.d_block_units;
         ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit; ap.elems_per_cta = epc;
-        ap.img = aprog.d_img; ap.img_off16 = aprog.d_img_off;
+        ap.img = aprog.d_img; ap.img_off16 = aprog.d_img_off; ap.qlist = aprog.d_qlist; ap.qoff = aprog.d_qoff;
         ap.xfields = nullptr; ap.estatus = nullptr; ap.pp = nullptr; ap.L = pr.L; ap.nfields = pr.nfields;
         if constexpr (sizeof(T) == 8) ap.F = te->F64; else ap.F = te->F32;
         ap.consts = (const double *)consts + AFF_CONST_STRIDE * e0;
@@ -802,7 +812,7 @@ int run_extruded(DeviceState *ds, ProgEntry *pe, TableEntry *te, int64_t n_elem,
         AffParams<T> ap;
         ap.blocks = aprog.d_blocks; ap.units = aprog.d_units; ap.block_unit_begin = aprog.d_block_units;
         ap.nblock = pr.nblock; ap.nj_max = pr.nj; ap.nsplit = nsplit; ap.elems_per_cta = epc;
-        ap.img = aprog.d_img; ap.img_off16 = aprog.d_img_off;
+        ap.img = aprog.d_img; ap.img_off16 = aprog.d_img_off; ap.qlist = nullptr; ap.qoff = nullptr;
         if constexpr (sizeof(T) == 8) { ap.F = te->F64; ap.pp = te->pp64; } else { ap.F = te->F32; ap.pp = te->pp32; }
         ap.consts = nullptr;
         ap.xfields = fields; ap.estatus = est;

@@ -1127,20 +1127,6 @@ __device__ __forceinline__ bool is_zero(float x) {
     return (b << 1) == 0u;
 }
 
-// Slot of this lane's item in a list compacted by a whole warp: one shared atomic per warp
-// and list (the lanes of a warp may append to different lists g); -1 when keep is false.
-__device__ __forceinline__ int warp_append(int *count, bool keep) {
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned all = __activemask();
-    const unsigned peers = __match_any_sync(all, reinterpret_cast<uintptr_t>(count));
-    const unsigned want = __ballot_sync(all, keep) & peers;
-    int base = 0;
-    const int leader = want ? __ffs(want) - 1 : -1;
-    if ((int)lane == leader) base = atomicAdd(count, __popc(want));
-    base = __shfl_sync(peers, base, leader < 0 ? (__ffs(peers) - 1) : leader);
-    return keep ? base + __popc(want & ((1u << lane) - 1u)) : -1;
-}
-
 // EXT = false: affine elements (Sec. 2.8.1, Algorithm 10), Q_g from exact 1D integrals and
 // the element's constant metric.  EXT = true: extruded elements (Algorithm 11), Q_g = the
 // stage-B result of a 2D sum factorization over (xi2, xi3): A_h[m][jj] = sum_{t in h} sum_n
@@ -1238,6 +1224,14 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
         const int i3 = u.i3, j3b = u.j3b, nj = u.nj;
         const unsigned mnj = div_magic(nj);
         const int ldt = lay.ldt;
+        // the unit's structural stage-B list (affine), its first entries loaded ahead
+        int q0 = 0, q1 = 0;
+        unsigned code_next = 0u;
+        if constexpr (!EXT) {
+            q0 = p.qoff[ui];
+            q1 = p.qoff[ui + 1];
+            if (q0 + tid - lane < q1) code_next = p.qlist[q0 + tid];
+        }
         __syncthreads();                                                // previous unit done
         if constexpr (!EXT) {
             for (int it = tid; it < nterm * nj; it += nth) {
@@ -1293,26 +1287,42 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
                 qi[g * n22 * njm + ij2 * nj + jj] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
             }
         }
-        // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2), kept as a list of its non-zeros
+        // Q_g(i2, j2, jj) = sum_{t in g} s_t(jj) F2_t(i2, j2), kept as a list of its non-zeros.
+        // The unit's structural list of each group (entries and the terms whose two factors
+        // are non-zero, padded to whole warps) drives the products; a warp appends the entries
+        // that are non-zero for this element (a zero metric constant cancels some) to its
+        // group's list with a ballot and one shared atomic.
         if constexpr (!EXT)
-        for (int it = tid; it < ng * n22 * nj; it += nth) {
-            const int r = fdiv(it, mnj), jj = it - r * nj;
-            const int g = fdiv(r, mn22), ij2 = r - g * n22;
-            T acc = T(0);
-            bool any = false;
-            const int ngt = bd.g_nterm[g];
-            for (int k2 = 0; k2 < ngt; ++k2) {
-                const int t = bd.g_terms[g][k2];
-                const T sv = st[t * nj + jj];
-                if (is_zero(sv)) continue;
-                const T f2 = F2[t * n22 + ij2];
-                if (!is_zero(f2)) { acc = fma(sv, f2, acc); any = true; }
-            }
-            const int slot = warp_append(&qc[g], any && !is_zero(acc));
-            if (slot >= 0) {
-                const int i2 = fdiv(ij2, mnc2), j2 = ij2 - i2 * nc2;
-                qv[g * n22 * njm + slot] = acc;
-                qi[g * n22 * njm + slot] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
+        for (int it0 = q0 + tid - lane; it0 < q1; it0 += nth) {          // whole warps
+            unsigned code = code_next;
+            if (it0 + nth < q1) code_next = p.qlist[it0 + nth + lane];
+#if defined(DPG_DEBUG_BOUNDS)
+            // an entry outside the tile is reported and taken as empty (every lane reaches
+            // the ballot)
+            if (!DPG_INB((int)(code & 0xff) < n22 && (int)((code >> 8) & 0xf) < nj && (int)(code >> 24) < ng,
+                         p.status, e))
+                code = (int)(code >> 24) < ng ? (code & 0xff000000u) : 0u;
+#endif
+            {   // one group per warp (lists padded to whole warps, the padding with its group)
+                const int ij2 = code & 0xff, jj = (code >> 8) & 0xf, g = (int)(code >> 24);
+                T *qvg = qv + g * n22 * njm;
+                int *qig = qi + g * n22 * njm;
+                T acc = T(0);
+                for (unsigned m = (code >> 12) & 0xfffu; m; m &= m - 1) {
+                    const int t = bd.g_terms[g][__ffs(m) - 1];
+                    acc = fma(st[t * nj + jj], F2[t * n22 + ij2], acc);
+                }
+                const bool keep = !is_zero(acc);
+                const unsigned want = __ballot_sync(0xffffffffu, keep);
+                int base = 0;
+                if (lane == 0 && want) base = atomicAdd(&qc[g], __popc(want));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (keep) {
+                    const int slot = base + __popc(want & ((1u << lane) - 1u));
+                    const int i2 = fdiv(ij2, mnc2), j2 = ij2 - i2 * nc2;
+                    qvg[slot] = acc;
+                    qig[slot] = nr1 * i2 * ldt + nc1 * (j2 + nc2 * jj);
+                }
             }
         }
         __syncthreads();
@@ -1384,7 +1394,35 @@ __global__ void __launch_bounds__(256) sf_affine_kernel(AffParams<T> p) {
             const int nmc = jd >= 0 ? ncolu - ncj : ncolu;
             T *mbase = o + C0 * ld + R0;
             if (!DPG_INB((C0 + ncolu - 1) * ld + R0 + nrow <= msz, p.status, e)) continue;
-            if (nrow >= 64) {                                   // long runs: a warp per column
+            if (nrow < 64 && ((ld * (int64_t)sizeof(T)) & 15) == 0) {
+                // short runs in rows of 16-byte multiples: every run has the alignment of the
+                // first, so a run is a head of up to VW - 1 values, 16-byte stores of VW
+                // consecutive tile rows (lanes along the run) and a tail
+                const int h = min((int)((VW - (int)((reinterpret_cast<uintptr_t>(mbase) / sizeof(T)) % VW)) % VW), nrow);
+                const int nv = (nrow - h) / VW, t0 = h + VW * nv, nsc = nrow - t0 + h;
+                if (nv > 0) {
+                    const unsigned mnv = div_magic(nv);
+                    for (int it = tid; it < nmc * nv; it += nth) {
+                        const int mcix = fdiv(it, mnv), v = it - mcix * nv;
+                        const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                        const T *src = tile + (h + VW * v) * ldt + c;
+                        V16 w;
+                        T *wv = reinterpret_cast<T *>(&w);
+#pragma unroll
+                        for (int x = 0; x < VW; ++x) wv[x] = bad ? nanv : src[x * ldt];
+                        reinterpret_cast<V16 *>(mbase + (int64_t)c * ld + h)[v] = w;
+                    }
+                }
+                if (nsc > 0) {
+                    const unsigned mns = div_magic(nsc);
+                    for (int it = tid; it < nmc * nsc; it += nth) {
+                        const int mcix = fdiv(it, mns), k = it - mcix * nsc;
+                        const int row = k < h ? k : t0 + (k - h);
+                        const int c = (jd >= 0 && mcix >= cb) ? mcix + ncj : mcix;
+                        mbase[(int64_t)c * ld + row] = bad ? nanv : tile[row * ldt + c];
+                    }
+                }
+            } else if (nrow >= 64) {                                   // long runs: a warp per column
                 // (plain stores: lanes reading consecutive tile rows keep the shared-memory
                 // reads conflict-free, which measured faster than 16-byte stores here)
                 if (!bad) {

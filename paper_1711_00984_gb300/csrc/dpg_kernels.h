@@ -167,6 +167,8 @@ struct AffParams {
     const T *F;                // exact 1D integrals [NPAIR][NQ1][NQ1]
     const void *img;           // constant shared-memory images of the blocks (build_aff_image)
     const int *img_off16;      // [nblock + 1], in 16-byte units
+    const unsigned *qlist;     // structural stage-B lists of the units (affine; build_aff_qlists)
+    const int *qoff;           // [nunits + 1] list starts (affine)
     const double *consts;      // [n_elem][AFF_CONST_STRIDE] from affine_const_kernel (affine)
     // extruded maps: 2D metric fields [n_elem][nfields][L][L] (xi2, xi3) from geom2d_kernel,
     // per-element status, pair products at the Gauss points [NPAIR][NQ1][NQ1][L]

@@ -679,6 +679,37 @@ void build_aff_image(const Program &pr, const HostTables &tab, bool extruded, st
 }
 template void build_aff_image<double>(const Program &, const HostTables &, bool, std::vector<unsigned char> &,
                                       std::vector<int> &);
+
+bool build_aff_qlists(const Program &pr, const HostTables &tab, std::vector<unsigned> &ql, std::vector<int> &qo) {
+    ql.clear();
+    qo.assign(pr.units.size() + 1, 0);
+    auto nz = [&](int pair, int i, int j) { return tab.F[((size_t)pair * NQ1 + i) * NQ1 + j] != 0.0; };
+    for (size_t ui = 0; ui < pr.units.size(); ++ui) {
+        const Unit &u = pr.units[ui];
+        const BlockDesc &b = pr.blocks[u.block];
+        const int nc2 = b.nc[1], n22 = b.nr[1] * b.nc[1];
+        if (n22 > 255 || u.nj > 15 || b.ng > 15) return false;
+        qo[ui] = (int)ql.size();
+        for (int g = 0; g < b.ng; ++g) {
+            if (b.g_nterm[g] > 12) return false;
+            for (int ij2 = 0; ij2 < n22; ++ij2)
+                for (int jj = 0; jj < u.nj; ++jj) {
+                    unsigned m = 0;
+                    for (int k2 = 0; k2 < b.g_nterm[g]; ++k2) {
+                        const TermDesc &td = b.term[b.g_terms[g][k2]];
+                        if (nz(3 * td.kr[1] + td.kc[1], ij2 / nc2, ij2 % nc2) &&
+                            nz(3 * td.kr[2] + td.kc[2], u.i3, u.j3b + jj))
+                            m |= 1u << k2;
+                    }
+                    if (m) ql.push_back((unsigned)ij2 | (unsigned)jj << 8 | m << 12 | (unsigned)g << 24);
+                }
+            while (ql.size() % 32) ql.push_back((unsigned)g << 24);   // empty entries: whole warps
+        }
+    }
+    qo[pr.units.size()] = (int)ql.size();
+    if (ql.empty()) ql.push_back(0u);
+    return true;
+}
 template void build_aff_image<float>(const Program &, const HostTables &, bool, std::vector<unsigned char> &,
                                      std::vector<int> &);
 

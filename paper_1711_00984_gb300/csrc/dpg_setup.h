@@ -68,6 +68,14 @@ void build_tc_tables(const Program &pr, const HostTables &tab, std::vector<float
 template <typename T>
 void build_aff_image(const Program &pr, const HostTables &tab, bool extruded, std::vector<unsigned char> &img,
                      std::vector<int> &off16);
+// Structurally non-zero entries of the affine stage-B products Q_g(i2, j2, jj) of every unit
+// (Algorithm 10 with a constant metric): entry (ij2 = i2 nc2 + j2, jj) of group g with the
+// mask of the group's terms whose exact integrals F2_t(i2, j2) and F3_t(i3, j3b + jj) are
+// both non-zero (bit k2: term g_terms[g][k2]), coded ij2 | jj << 8 | mask << 12 | g << 24.
+// Per unit the groups' lists in group order, each in (ij2, jj) order and padded with empty
+// entries (mask 0) to a multiple of 32; the list of unit u is [qo[u], qo[u + 1]).  False if a
+// block does not fit the code.
+bool build_aff_qlists(const Program &pr, const HostTables &tab, std::vector<unsigned> &ql, std::vector<int> &qo);
 // Constant images of the FP32 tensor-core stage-C kernel for every block of an ORDER_TCC
 // program: P1 split into TF32 high and low parts in the canonical K-major layout, then the
 // stage-B factors P2 (the region [0, oC) of tcc_layout), in floats; off[k] is the first
