@@ -75,7 +75,12 @@ extern "C" {
  * matrix against the FP64 form.  General-path FP32 Gram matrices are computed block by
  * block without mirroring, so they are symmetric to rounding, not bit for bit. */
 #define DPG_FP32        0x100  /* FP32 form (above) */
-#define DPG_MAP_AFFINE  0x200  /* elements are parallelepipeds: O(p^6) path, Sec. 2.8.1 */
+/* DPG_MAP_AFFINE: the elements are parallelepipeds (constant Jacobian, Sec. 2.8.1): the
+ * O(p^6) path of Algorithm 10 with the exact 1D integrals F of Eq. 2.90.  An element whose
+ * vertices 3, 5, 6 or 7 deviate from the parallelepiped spanned at vertex 0 by the edges to
+ * vertices 1, 2 and 4 by more than 1e-10 times the largest |J_ab| (or by a non-finite amount)
+ * is reported as DPG_ERR_NOT_AFFINE and NaN-filled. */
+#define DPG_MAP_AFFINE  0x200
 #define DPG_B_SPLIT     0x400  /* B only: write [2][rows][cols] = (mass part, curl part) */
 /* DPG_MAP_EXTRUDED: the elements are extrusions along x1 of a bilinear quadrilateral in
  * (x2, x3), the second map of Eq. 2.89: x1 = x1(v0) + lambda1 xi1 with lambda1 the same on
