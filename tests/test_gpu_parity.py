@@ -161,6 +161,33 @@ def test_q9_sampled(gpu_lib, space):
         assert code == 0 and rel_errs(got, ref).max() <= TOL64
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+def test_affine_l2_diagonal_q9_unaligned_output(gpu_lib, fp32):
+    """The L2 Gram matrix of an affine element is diagonal (Legendre orthogonality, Eq. 2.95)
+    and is written by a fill kernel: at q = 9 (729 rows) one element covers many of its CTAs,
+    and an output starting one value past a 16-byte boundary takes its unaligned head and
+    tail.  Off-diagonal entries are exact zeros; nothing is written before the output."""
+    q, L = 9, 11
+    gpu_lib.dpg_tables_init_L(q, L, "L2")
+    v = meshgen.affine_parallelepipeds(2, seed=81)[:2]
+    rng = np.random.default_rng(81)
+    c = np.stack([rng.uniform(0.5, 2, 2), rng.uniform(0.5, 2, 2)], axis=1)
+    n = gpu_lib.dpg_matrix_rows("L2", q)
+    dt = torch.float32 if fp32 else torch.float64
+    buf = torch.full((2 * n * n + 1,), float("nan"), dtype=dt, device="cuda")
+    out = buf[1:].view(2, n, n)
+    gpu_lib.integrate("L2", q, torch.from_numpy(v).cuda(), torch.from_numpy(c).cuda(), fp32=fp32, affine=True,
+                      out=out)
+    code, _ = gpu_lib.sync_status()
+    assert code == 0
+    assert torch.isnan(buf[0]).item()
+    got = out.double().cpu().numpy()
+    for e in range(2):
+        assert np.count_nonzero(got[e] - np.diag(np.diagonal(got[e]))) == 0
+    ref, _ = oracle.gram("L2", q, L, v, c)
+    assert rel_errs(got, ref).max() <= (TOL32 if fp32 else TOL64)
+
+
 # ---------------------------------------------------------------- edges and device faults
 
 def test_every_entry_written(gpu_lib):
