@@ -1753,7 +1753,7 @@ cudaError_t launch_panel_f32(const PanelParams &p, size_t smem, cudaStream_t s) 
 
 cudaError_t launch_affine_const(const AffConstParams &p, cudaStream_t s) {
     if (p.n_elem == 0) return cudaSuccess;
-    // one warp per CTA: a thread's few hundred FP64 operations would queue on the FP64 pipe
+    // one warp per CTA: a thread's hundred-odd FP64 operations would queue on the FP64 pipe
     // (2 per clock per SM) of the few SMs that blocks of 128 threads occupy
     affine_const_kernel<<<(unsigned)((p.n_elem + 31) / 32), 32, 0, s>>>(p);
     return cudaGetLastError();
