@@ -1,0 +1,72 @@
+// Host-only check of the structural stage-B lists of the affine path (build_aff_qlists)
+// against the affine flop count that make_program computes by its own loops (Sec. 2.8.1):
+// the stage-B products are the set bits of the entries' term masks, the stage-C products
+// are, per entry, the non-zero exact integrals F1_g(i1, j1) of its group, and twice their
+// sum must be flops_affine.  Also checks the list format: per unit a run of whole 32-entry
+// chunks, one group per chunk, indices inside the block.  Prints one JSON line per
+// (space, q, p, form); exit status 1 on the first failed check.
+#include "dpg_setup.h"
+
+#include <cstdio>
+#include <vector>
+
+using namespace dpg;
+
+static int fail(const char *what, int space, int q, int p, int prec) {
+    std::printf("{\"fail\": \"%s\", \"space\": %d, \"q\": %d, \"p\": %d, \"prec\": %d}\n", what, space, q, p, prec);
+    return 1;
+}
+
+int main() {
+    const int spaces[] = { S_H1, S_HCURL, S_HDIV, S_L2, S_B };
+    for (int space : spaces)
+        for (int q = 1; q <= 7; ++q) {
+            const int L = q + 2;
+            const HostTables tab = make_tables(q, L);
+            auto Fnz = [&](int pair, int i, int j) { return tab.F[((size_t)pair * NQ1 + i) * NQ1 + j] != 0.0; };
+            for (int p = (space == S_B ? 1 : 0); p <= (space == S_B ? q : 0); ++p)
+                for (int prec = 0; prec < 2; ++prec) {
+                    // the affine programs of both forms, as the library builds them
+                    const Program pa = make_program(space, q, L, p, false, tab, ORDER_NATURAL, 0,
+                                                    prec == 0 ? 72 * 1024 : 0);
+                    std::vector<unsigned> ql;
+                    std::vector<int> qo;
+                    if (!build_aff_qlists(pa, tab, ql, qo)) return fail("builder refused", space, q, p, prec);
+                    if (qo.size() != pa.units.size() + 1) return fail("offset count", space, q, p, prec);
+                    double nB = 0.0, nC = 0.0;
+                    long entries = 0;
+                    for (size_t u = 0; u < pa.units.size(); ++u) {
+                        const Unit &un = pa.units[u];
+                        const BlockDesc &b = pa.blocks[un.block];
+                        if (b.dir[0] != 0 || b.dir[1] != 1 || b.dir[2] != 2) return fail("order", space, q, p, prec);
+                        const int n22 = b.nr[1] * b.nc[1];
+                        if (qo[u + 1] < qo[u] || (qo[u + 1] - qo[u]) % 32 != 0 || qo[u] % 32 != 0)
+                            return fail("padding", space, q, p, prec);
+                        for (int c0 = qo[u]; c0 < qo[u + 1]; c0 += 32) {
+                            const int g = (int)(ql[c0] >> 24);
+                            if (g >= b.ng) return fail("group", space, q, p, prec);
+                            int nzF1 = 0;
+                            for (int i1 = 0; i1 < b.nr[0]; ++i1)
+                                for (int j1 = 0; j1 < b.nc[0]; ++j1) nzF1 += Fnz(b.g_pair[g], i1, j1);
+                            for (int k = c0; k < c0 + 32; ++k) {
+                                const unsigned code = ql[k];
+                                const int ij2 = code & 0xff, jj = (code >> 8) & 0xf;
+                                const unsigned m = (code >> 12) & 0xfffu;
+                                if ((int)(code >> 24) != g) return fail("mixed chunk", space, q, p, prec);
+                                if (m == 0) continue;                           // padding
+                                if (ij2 >= n22 || jj >= un.nj || (m >> b.g_nterm[g]) != 0)
+                                    return fail("index", space, q, p, prec);
+                                nB += __builtin_popcount(m);
+                                nC += nzF1;
+                                ++entries;
+                            }
+                        }
+                    }
+                    if (2.0 * (nB + nC) != pa.flops_affine) return fail("flop count", space, q, p, prec);
+                    std::printf("{\"space\": %d, \"q\": %d, \"p\": %d, \"prec\": %d, \"units\": %zu, \"entries\": %ld, "
+                                "\"stage_b\": %.0f, \"stage_c\": %.0f}\n",
+                                space, q, p, prec, pa.units.size(), entries, nB, nC);
+                }
+        }
+    return 0;
+}
