@@ -348,31 +348,15 @@ int get_program(DeviceState *ds, int space, int q, int L, int p, int split, cons
         if ((r = upload(ub.data(), ub.size(), &ap.d_block_units))) return r;
         if (m * (prec ? sizeof(float) : sizeof(double)) > (size_t)g_max_dyn_smem) return DPG_ERR_RANGE;
         ap.smem_values = m;
-        // one square block whose every term has diagonal exact 1D integrals in each direction
-        // (the L2 Gram matrix of an affine element, by the Legendre orthogonality of
-        // Eq. 2.95): the matrix is diagonal for every element, written by a fill kernel
-        const BlockDesc &b0 = pa.blocks[0];
-        ap.diag = pa.nblock == 1 && pa.parts == 1 && b0.row_off == 0 && b0.col_off == 0 &&
-                  b0.nterm <= AFF_DIAG_MAXT && !split;
-        for (int d = 0; d < 3 && ap.diag; ++d) ap.diag = b0.nr[d] == b0.nc[d];
-        for (int t = 0; t < b0.nterm && ap.diag; ++t)
-            for (int d = 0; d < 3 && ap.diag; ++d) {
-                const TermDesc &td = b0.term[t];
-                const int pair = 3 * td.kr[d] + td.kc[d], nd = b0.nr[d];
-                for (int i = 0; i < nd && ap.diag; ++i)
-                    for (int j = 0; j < nd && ap.diag; ++j)
-                        if (i != j && tab.F[((size_t)pair * NQ1 + i) * NQ1 + j] != 0.0) ap.diag = false;
-            }
+        // a matrix diagonal for every element (the L2 Gram matrix, Eq. 2.95) is written by a
+        // fill kernel from the products of the diagonal 1D integrals
+        std::vector<double> D;
+        ap.diag = affine_diagonal(pa, tab, AFF_DIAG_MAXT, D);
         if (ap.diag) {
-            const int n = pa.rows, n1 = b0.nr[0], n2 = b0.nr[1];
-            std::vector<double> D((size_t)b0.nterm * n);
+            const BlockDesc &b0 = pa.blocks[0];
             for (int t = 0; t < b0.nterm; ++t) {
-                const TermDesc &td = b0.term[t];
-                auto Fd = [&](int d, int i) { return tab.F[((size_t)(3 * td.kr[d] + td.kc[d]) * NQ1 + i) * NQ1 + i]; };
-                for (int r = 0; r < n; ++r)
-                    D[(size_t)t * n + r] = Fd(0, r % n1) * Fd(1, (r / n1) % n2) * Fd(2, r / (n1 * n2));
-                ap.diag_field[t] = td.field;
-                ap.diag_sign[t] = td.sign;
+                ap.diag_field[t] = b0.term[t].field;
+                ap.diag_sign[t] = b0.term[t].sign;
             }
             ap.diag_nterm = b0.nterm;
             if ((r = upload(D.data(), D.size(), &ap.d_diag))) return r;

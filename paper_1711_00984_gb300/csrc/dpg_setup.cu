@@ -680,6 +680,32 @@ void build_aff_image(const Program &pr, const HostTables &tab, bool extruded, st
 template void build_aff_image<double>(const Program &, const HostTables &, bool, std::vector<unsigned char> &,
                                       std::vector<int> &);
 
+bool affine_diagonal(const Program &pa, const HostTables &tab, int max_terms, std::vector<double> &D) {
+    D.clear();
+    const BlockDesc &b0 = pa.blocks[0];
+    bool diag = pa.nblock == 1 && pa.parts == 1 && b0.row_off == 0 && b0.col_off == 0 &&
+                b0.nterm <= max_terms && !pa.split;
+    for (int d = 0; d < 3 && diag; ++d) diag = b0.nr[d] == b0.nc[d];
+    for (int t = 0; t < b0.nterm && diag; ++t)
+        for (int d = 0; d < 3 && diag; ++d) {
+            const TermDesc &td = b0.term[t];
+            const int pair = 3 * td.kr[d] + td.kc[d], nd = b0.nr[d];
+            for (int i = 0; i < nd && diag; ++i)
+                for (int j = 0; j < nd && diag; ++j)
+                    if (i != j && tab.F[((size_t)pair * NQ1 + i) * NQ1 + j] != 0.0) diag = false;
+        }
+    if (!diag) return false;
+    const int n = pa.rows, n1 = b0.nr[0], n2 = b0.nr[1];
+    D.assign((size_t)b0.nterm * n, 0.0);
+    for (int t = 0; t < b0.nterm; ++t) {
+        const TermDesc &td = b0.term[t];
+        auto Fd = [&](int d, int i) { return tab.F[((size_t)(3 * td.kr[d] + td.kc[d]) * NQ1 + i) * NQ1 + i]; };
+        for (int r = 0; r < n; ++r)
+            D[(size_t)t * n + r] = Fd(0, r % n1) * Fd(1, (r / n1) % n2) * Fd(2, r / (n1 * n2));
+    }
+    return true;
+}
+
 bool build_aff_qlists(const Program &pr, const HostTables &tab, std::vector<unsigned> &ql, std::vector<int> &qo) {
     ql.clear();
     qo.assign(pr.units.size() + 1, 0);

@@ -76,6 +76,13 @@ void build_aff_image(const Program &pr, const HostTables &tab, bool extruded, st
 // entries (mask 0) to a multiple of 32; the list of unit u is [qo[u], qo[u + 1]).  False if a
 // block does not fit the code.
 bool build_aff_qlists(const Program &pr, const HostTables &tab, std::vector<unsigned> &ql, std::vector<int> &qo);
+// Whether the matrix of an affine program is diagonal for every element: one square block at
+// the origin, at most max_terms terms, each with diagonal exact 1D integrals in every
+// direction (the L2 Gram matrix, by the Legendre orthogonality of Eq. 2.95).  If so, D holds
+// per term t the products D[t][r] = F_t1(i1, i1) F_t2(i2, i2) F_t3(i3, i3) of its diagonal
+// integrals at r = i1 + nr1 (i2 + nr2 i3), and the element's matrix is
+// diag(sum_t sign_t c_t D[t][r]).
+bool affine_diagonal(const Program &pa, const HostTables &tab, int max_terms, std::vector<double> &D);
 // Constant images of the FP32 tensor-core stage-C kernel for every block of an ORDER_TCC
 // program: P1 split into TF32 high and low parts in the canonical K-major layout, then the
 // stage-B factors P2 (the region [0, oC) of tcc_layout), in floats; off[k] is the first

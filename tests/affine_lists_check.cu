@@ -3,10 +3,14 @@
 // the stage-B products are the set bits of the entries' term masks, the stage-C products
 // are, per entry, the non-zero exact integrals F1_g(i1, j1) of its group, and twice their
 // sum must be flops_affine.  Also checks the list format: per unit a run of whole 32-entry
-// chunks, one group per chunk, indices inside the block.  Prints one JSON line per
-// (space, q, p, form); exit status 1 on the first failed check.
+// chunks, one group per chunk, indices inside the block.  Then the diagonal-matrix test of
+// the affine programs (affine_diagonal, any number of terms): it must hold for L2 and for no
+// other space, and the L2 table must be the product of the Legendre norms of Eq. 2.95,
+// D(r) = 1 / ((2 i1 + 1)(2 i2 + 1)(2 i3 + 1)).  Prints one JSON line per (space, q, p,
+// form); exit status 1 on the first failed check.
 #include "dpg_setup.h"
 
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -63,9 +67,24 @@ int main() {
                         }
                     }
                     if (2.0 * (nB + nC) != pa.flops_affine) return fail("flop count", space, q, p, prec);
+                    std::vector<double> D;
+                    const bool diag = affine_diagonal(pa, tab, MAXT, D);
+                    if (diag != (space == S_L2)) return fail("diagonal test", space, q, p, prec);
+                    double derr = 0.0;
+                    if (diag) {
+                        const BlockDesc &b0 = pa.blocks[0];
+                        if (b0.nterm != 1 || (int)D.size() != pa.rows || pa.rows != q * q * q)
+                            return fail("diagonal table size", space, q, p, prec);
+                        for (int r = 0; r < pa.rows; ++r) {
+                            const int i1 = r % q, i2 = (r / q) % q, i3 = r / (q * q);
+                            const double ref = 1.0 / ((2.0 * i1 + 1) * (2.0 * i2 + 1) * (2.0 * i3 + 1));
+                            derr = std::fmax(derr, std::fabs(D[r] - ref) / ref);
+                        }
+                        if (!(derr <= 1e-13)) return fail("Legendre norms", space, q, p, prec);
+                    }
                     std::printf("{\"space\": %d, \"q\": %d, \"p\": %d, \"prec\": %d, \"units\": %zu, \"entries\": %ld, "
-                                "\"stage_b\": %.0f, \"stage_c\": %.0f}\n",
-                                space, q, p, prec, pa.units.size(), entries, nB, nC);
+                                "\"stage_b\": %.0f, \"stage_c\": %.0f, \"diagonal\": %d, \"legendre_err\": %.3g}\n",
+                                space, q, p, prec, pa.units.size(), entries, nB, nC, (int)diag, derr);
                 }
         }
     return 0;
