@@ -22,13 +22,14 @@ static int fail(const char *what, int space, int q, int p, int prec) {
 }
 
 int main() {
-    const int spaces[] = { S_H1, S_HCURL, S_HDIV, S_L2, S_B };
+    const int spaces[] = { S_H1, S_HCURL, S_HDIV, S_L2, S_B, S_AX, S_AB };
     for (int space : spaces)
         for (int q = 1; q <= 7; ++q) {
             const int L = q + 2;
             const HostTables tab = make_tables(q, L);
             auto Fnz = [&](int pair, int i, int j) { return tab.F[((size_t)pair * NQ1 + i) * NQ1 + j] != 0.0; };
-            for (int p = (space == S_B ? 1 : 0); p <= (space == S_B ? q : 0); ++p)
+            const bool mixed = space == S_B || space == S_AB;           // trial order p = 1..q
+            for (int p = (mixed ? 1 : 0); p <= (mixed ? q : 0); ++p)
                 for (int prec = 0; prec < 2; ++prec) {
                     // the affine programs of both forms, as the library builds them
                     const Program pa = make_program(space, q, L, p, false, tab, ORDER_NATURAL, 0,

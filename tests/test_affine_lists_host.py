@@ -5,7 +5,8 @@ Q_g(i2, j2, jj) of a work unit, with the mask of its contributing terms) are bui
 host.  `affine_lists_check.cu` links the library's set-up object and recounts, from the
 lists, the stage-B and stage-C products of every unit; their sum must equal the affine flop
 count that the term program computes by its own loops over (i3, j3) pairs (Sec. 2.8.1), for
-every space, q = 1..7 and both forms.  It also checks the list format the kernel relies on
+every space (the four Gram spaces, B, and the acoustics cross block and B of Eqs. 3.16-3.18),
+q = 1..7 and both forms.  It also checks the list format the kernel relies on
 (whole 32-entry chunks of one group, indices inside the block), and that the affine matrix is
 detected as diagonal for L2 alone, with the table of the fill kernel equal to the Legendre
 norms of Eq. 2.95.
@@ -29,7 +30,8 @@ def test_affine_structural_lists_match_flop_count(tmp_path):
     lines = [json.loads(s) for s in r.stdout.splitlines() if s.startswith("{")]
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
     assert not [x for x in lines if "fail" in x]
-    # H1, H(curl), H(div), L2 at q = 1..7 and B at p = 1..q, each in both forms
-    assert len(lines) == 2 * (4 * 7 + sum(range(1, 8)))
+    # H1, H(curl), H(div), L2 and the acoustics cross block at q = 1..7, B and the acoustic B
+    # at p = 1..q, each in both forms
+    assert len(lines) == 2 * (5 * 7 + 2 * sum(range(1, 8)))
     assert all(x["entries"] > 0 and x["stage_b"] >= x["entries"] for x in lines)
     assert [x["space"] for x in lines if x["diagonal"]] == [4] * 14       # L2, q = 1..7, both forms
